@@ -1,0 +1,279 @@
+"""Seeded synthetic PairHMM workloads.
+
+This module only draws inputs: reads, haplotypes, Phred qualities and the pair index,
+in the library's batch layout.  It holds none of the forward algorithm's arithmetic and
+is shared by the tests, the benchmark and the oracle legs, so that both sides of every
+parity check see the same bytes.
+
+Batch layout (a dict of numpy arrays):
+    read_bases  uint8   ASCII A/C/G/T/N, all reads concatenated
+    read_off    uint64  n_reads + 1 offsets into read_bases
+    base_q, ins_q, del_q, gcp_q   uint8 numeric Phred 0..93, laid out like read_bases
+    hap_bases   uint8   ASCII A/C/G/T/N, all haplotypes concatenated
+    hap_off     uint64  n_haps + 1 offsets
+    pair_read, pair_hap uint32 one (read, haplotype) index per pair
+
+The shapes follow the workloads the paper evaluates on (GIAB short- and long-read sets,
+Table "GIAB Dataset Description"; the 10s set; equal-length synthetic pairs of
+32..131072 bp, Section 4.1) -- none of those datasets is used or reproduced; only their
+length and error structure is imitated.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+ACGT = np.frombuffer(b"ACGT", dtype=np.uint8)
+
+
+def _rng(seed: int, stream: int) -> np.random.Generator:
+    return np.random.Generator(np.random.PCG64(np.random.SeedSequence([seed, stream])))
+
+
+def _random_bases(rng, n: int) -> np.ndarray:
+    return ACGT[rng.integers(0, 4, size=n)]
+
+
+def _substitute(rng, seq: np.ndarray, rate: float) -> np.ndarray:
+    """Replace each base with probability ``rate`` by one of the other three."""
+    out = seq.copy()
+    m = rng.random(len(seq)) < rate
+    if m.any():
+        codes = np.searchsorted(ACGT, out[m])  # N never occurs in templates
+        shift = rng.integers(1, 4, size=int(m.sum()))
+        out[m] = ACGT[(codes + shift) % 4]
+    return out
+
+
+def _mutate(rng, template: np.ndarray, start: int, length: int, sub_rate: float,
+            indel_rate: float) -> np.ndarray:
+    """Read of exactly ``length`` bases copied from ``template[start:]`` with
+    substitutions and 1-3 bp insertions/deletions (50:50).  Runs past the template end
+    are filled with random bases."""
+    if indel_rate <= 0.0:
+        seg = template[start:start + length]
+        if len(seg) < length:
+            seg = np.concatenate([seg, _random_bases(rng, length - len(seg))])
+        return _substitute(rng, seg, sub_rate)
+    pieces = []
+    have = 0
+    pos = start
+    n_t = len(template)
+    # Events are drawn per template base with a geometric gap.
+    while have < length:
+        gap = int(rng.geometric(indel_rate)) if indel_rate < 1.0 else 1
+        take = min(gap - 1, length - have, max(n_t - pos, 0))
+        if take > 0:
+            pieces.append(template[pos:pos + take])
+            have += take
+            pos += take
+        if have >= length:
+            break
+        if pos >= n_t:
+            pieces.append(_random_bases(rng, length - have))
+            have = length
+            break
+        ln = int(rng.integers(1, 4))
+        if rng.random() < 0.5:  # insertion into the read
+            ins = _random_bases(rng, min(ln, length - have))
+            pieces.append(ins)
+            have += len(ins)
+        else:  # deletion from the read
+            pos += ln
+    read = np.concatenate(pieces)[:length] if pieces else np.zeros(0, np.uint8)
+    return _substitute(rng, read, sub_rate)
+
+
+def _pack(reads, quals, haps, pair_read, pair_hap) -> dict:
+    """Concatenate per-read / per-haplotype arrays into the batch layout."""
+    rl = np.array([len(r) for r in reads], dtype=np.uint64)
+    hl = np.array([len(h) for h in haps], dtype=np.uint64)
+    b = {
+        "read_bases": np.concatenate(reads).astype(np.uint8) if reads else np.zeros(0, np.uint8),
+        "read_off": np.concatenate([[0], np.cumsum(rl)]).astype(np.uint64),
+        "hap_bases": np.concatenate(haps).astype(np.uint8) if haps else np.zeros(0, np.uint8),
+        "hap_off": np.concatenate([[0], np.cumsum(hl)]).astype(np.uint64),
+        "pair_read": np.asarray(pair_read, dtype=np.uint32),
+        "pair_hap": np.asarray(pair_hap, dtype=np.uint32),
+    }
+    for i, name in enumerate(("base_q", "ins_q", "del_q", "gcp_q")):
+        b[name] = (np.concatenate([q[i] for q in quals]).astype(np.uint8) if quals
+                   else np.zeros(0, np.uint8))
+    return b
+
+
+def cells(b: dict) -> int:
+    """Sum over pairs of read length x haplotype length (the cell-update count)."""
+    rl = np.diff(b["read_off"].astype(np.int64))
+    hl = np.diff(b["hap_off"].astype(np.int64))
+    return int(np.sum(rl[b["pair_read"]] * hl[b["pair_hap"]]))
+
+
+def pair_lengths(b: dict):
+    rl = np.diff(b["read_off"].astype(np.int64))
+    hl = np.diff(b["hap_off"].astype(np.int64))
+    return rl[b["pair_read"]], hl[b["pair_hap"]]
+
+
+# ----------------------------------------------------------------------------------------
+# Workloads
+# ----------------------------------------------------------------------------------------
+
+def plain_pairs(n_pairs: int = 64, seed: int = 0, k_range=(200, 400), l_range=(100, 150),
+                sub_rate=0.01, indel_rate=0.001, q_range=(10, 40), gap_q=45, gcp_q=10) -> dict:
+    """Short-read parity set: one haplotype per pair, uniform ACGT of length U{k_range};
+    the read (length U{l_range}) starts at a random haplotype offset, with substitutions
+    and 1-3 bp indels; base quals U{q_range}, ins/del quals ``gap_q``, gcp ``gcp_q``."""
+    rng = _rng(seed, 1)
+    reads, quals, haps = [], [], []
+    for _ in range(n_pairs):
+        k = int(rng.integers(k_range[0], k_range[1] + 1))
+        l = int(rng.integers(l_range[0], l_range[1] + 1))
+        hap = _random_bases(rng, k)
+        off = int(rng.integers(0, max(k - l, 0) + 1))
+        read = _mutate(rng, hap, off, l, sub_rate, indel_rate)
+        bq = rng.integers(q_range[0], q_range[1] + 1, size=l).astype(np.uint8)
+        q_i = np.full(l, gap_q, np.uint8)
+        quals.append((bq, q_i, q_i.copy(), np.full(l, gcp_q, np.uint8)))
+        reads.append(read)
+        haps.append(hap)
+    idx = np.arange(n_pairs)
+    return _pack(reads, quals, haps, idx, idx)
+
+
+def short_read_regions(n_regions: int = 2000, reads_per_region: int = 50, seed: int = 0,
+                       max_haps: int = 8, read_len: int = 150, ref_range=(250, 600),
+                       max_pairs: int | None = None) -> dict:
+    """Active-region short-read batch: per region a random reference window of length
+    U{ref_range}; H ~ U{1..max_haps} haplotypes = reference + SNPs (1e-3 per base) and
+    1 bp indels (1e-4 per base); ``reads_per_region`` reads of ``read_len`` bp, each from
+    a random haplotype at a random offset, with a per-read substitution rate
+    U[0.5%, 2%] and then 1% of bases set to N.  Base quals: 85% U{30..41}, 15% U{2..29};
+    ins/del quals U{40..45} per base; gcp 10.  Pairs = every read x every haplotype of
+    its region (about 4.5 pairs per read).  ``max_pairs`` truncates in region order."""
+    rng = _rng(seed, 2)
+    reads, quals, haps = [], [], []
+    pr, ph = [], []
+    n_pairs = 0
+    for _ in range(n_regions):
+        rlen = int(rng.integers(ref_range[0], ref_range[1] + 1))
+        ref = _random_bases(rng, rlen)
+        h_count = int(rng.integers(1, max_haps + 1))
+        h0 = len(haps)
+        for _h in range(h_count):
+            hap = _substitute(rng, ref, 1e-3)
+            ev = np.flatnonzero(rng.random(rlen) < 1e-4)
+            for p in ev[::-1]:
+                if rng.random() < 0.5:
+                    hap = np.concatenate([hap[:p], _random_bases(rng, 1), hap[p:]])
+                elif len(hap) > 1:
+                    hap = np.concatenate([hap[:p], hap[p + 1:]])
+            haps.append(hap)
+        r0 = len(reads)
+        src = rng.integers(0, h_count, size=reads_per_region)
+        err = rng.uniform(0.005, 0.02, size=reads_per_region)
+        for r in range(reads_per_region):
+            hap = haps[h0 + int(src[r])]
+            off = int(rng.integers(0, max(len(hap) - read_len, 0) + 1))
+            read = _mutate(rng, hap, off, read_len, float(err[r]), 0.0)
+            nm = rng.random(read_len) < 0.01
+            read[nm] = ord("N")
+            hi = rng.random(read_len) < 0.85
+            bq = np.where(hi, rng.integers(30, 42, size=read_len),
+                          rng.integers(2, 30, size=read_len)).astype(np.uint8)
+            iq = rng.integers(40, 46, size=read_len).astype(np.uint8)
+            dq = rng.integers(40, 46, size=read_len).astype(np.uint8)
+            quals.append((bq, iq, dq, np.full(read_len, 10, np.uint8)))
+            reads.append(read)
+        for r in range(reads_per_region):
+            for h in range(h_count):
+                pr.append(r0 + r)
+                ph.append(h0 + h)
+        n_pairs += reads_per_region * h_count
+        if max_pairs is not None and n_pairs >= max_pairs:
+            break
+    if max_pairs is not None:
+        pr, ph = pr[:max_pairs], ph[:max_pairs]
+    return _pack(reads, quals, haps, pr, ph)
+
+
+def long_pairs(n_pairs: int = 64, seed: int = 0, k_range=(1000, 100000), read_frac=(0.9, 1.0),
+               sub_rate=0.05, indel_rate=0.03, q_range=(5, 30), gap_q=45, gcp_q=10) -> dict:
+    """Long-read pairs: haplotype length log-uniform in ``k_range``; the read is
+    90-100% of the haplotype length, copied from a random offset with substitutions and
+    1-3 bp indels; base quals U{q_range}, ins/del quals ``gap_q``, gcp ``gcp_q``."""
+    rng = _rng(seed, 3)
+    reads, quals, haps = [], [], []
+    for _ in range(n_pairs):
+        k = int(round(np.exp(rng.uniform(np.log(k_range[0]), np.log(k_range[1])))))
+        l = max(1, int(round(k * rng.uniform(read_frac[0], read_frac[1]))))
+        hap = _random_bases(rng, k)
+        off = int(rng.integers(0, k - l + 1))
+        read = _mutate(rng, hap, off, l, sub_rate, indel_rate)
+        bq = rng.integers(q_range[0], q_range[1] + 1, size=l).astype(np.uint8)
+        q_i = np.full(l, gap_q, np.uint8)
+        quals.append((bq, q_i, q_i.copy(), np.full(l, gcp_q, np.uint8)))
+        reads.append(read)
+        haps.append(hap)
+    idx = np.arange(n_pairs)
+    return _pack(reads, quals, haps, idx, idx)
+
+
+def uneven_pairs(n_pairs: int = 1_000_000, seed: int = 0, len_range=(50, 20000)) -> dict:
+    """Uneven-length batch: read and haplotype lengths each log-uniform in
+    ``len_range``, drawn independently and swapped so that haplotype >= read; the read
+    is copied from a random haplotype offset with the short-read error and quality model
+    (substitutions U[0.5%, 2%], 1% N, quals 85% U{30..41} / 15% U{2..29}, ins/del
+    U{40..45}, gcp 10)."""
+    rng = _rng(seed, 4)
+    lo, hi = np.log(len_range[0]), np.log(len_range[1])
+    a = np.rint(np.exp(rng.uniform(lo, hi, size=n_pairs))).astype(np.int64)
+    c = np.rint(np.exp(rng.uniform(lo, hi, size=n_pairs))).astype(np.int64)
+    ls, ks = np.minimum(a, c), np.maximum(a, c)
+    reads, quals, haps = [], [], []
+    for p in range(n_pairs):
+        l, k = int(ls[p]), int(ks[p])
+        hap = _random_bases(rng, k)
+        off = int(rng.integers(0, k - l + 1))
+        read = _substitute(rng, hap[off:off + l], float(rng.uniform(0.005, 0.02)))
+        read[rng.random(l) < 0.01] = ord("N")
+        hi_q = rng.random(l) < 0.85
+        bq = np.where(hi_q, rng.integers(30, 42, size=l), rng.integers(2, 30, size=l)).astype(np.uint8)
+        quals.append((bq, rng.integers(40, 46, size=l).astype(np.uint8),
+                      rng.integers(40, 46, size=l).astype(np.uint8), np.full(l, 10, np.uint8)))
+        reads.append(read)
+        haps.append(hap)
+    idx = np.arange(n_pairs)
+    return _pack(reads, quals, haps, idx, idx)
+
+
+def equal_length(n_pairs: int, length: int, seed: int = 0) -> dict:
+    """Equal-length synthetic pairs (read length = haplotype length), the shape of the
+    paper's scalability sweep (Section 4.3): random haplotype, read = haplotype with 1%
+    substitutions; quals U{10..40}, ins/del 45, gcp 10."""
+    return plain_pairs(n_pairs, seed=seed + 1000 * length, k_range=(length, length),
+                       l_range=(length, length), sub_rate=0.01, indel_rate=0.0)
+
+
+def subset(b: dict, pairs) -> dict:
+    """Batch restricted to the given pair indices (reads/haplotypes are shared)."""
+    out = dict(b)
+    pairs = np.asarray(pairs, dtype=np.int64)
+    out["pair_read"] = np.ascontiguousarray(b["pair_read"][pairs])
+    out["pair_hap"] = np.ascontiguousarray(b["pair_hap"][pairs])
+    return out
+
+
+def from_strings(pairs) -> dict:
+    """Batch from explicit (read, hap, base_q, ins_q, del_q, gcp_q) tuples; qualities may
+    be scalars or sequences.  Used for hand-made edge cases."""
+    reads, quals, haps = [], [], []
+    for (r, h, bq, iq, dq, gq) in pairs:
+        r = np.frombuffer(r.encode() if isinstance(r, str) else bytes(r), np.uint8).copy()
+        h = np.frombuffer(h.encode() if isinstance(h, str) else bytes(h), np.uint8).copy()
+        l = len(r)
+        q = tuple(np.broadcast_to(np.asarray(x, dtype=np.uint8), (l,)).copy() for x in (bq, iq, dq, gq))
+        reads.append(r)
+        haps.append(h)
+        quals.append(q)
+    idx = np.arange(len(pairs))
+    return _pack(reads, quals, haps, idx, idx)
