@@ -1,0 +1,187 @@
+/*
+ * phmm.h -- C ABI of the GB300 (sm_103a) row-wise PairHMM forward library.
+ *
+ * The library scores every (read, haplotype) pair of a batch as log10 P(read | hap)
+ * with the PairHMM forward algorithm over the Match / Insertion / Deletion matrices
+ * (paper, Section 2, Eq. 1-4), evaluated row by row as the paper's Section 3.1
+ * reformulation proposes: each row's M and I cells come from the previous row in
+ * parallel, and the in-row deletion dependency D[i][j] = T_MD_i M[i][j-1] + T_DD_i D[i][j-1]
+ * (Eq. 2, unrolled in Eq. 5-6) is evaluated as a first-order linear-recurrence scan
+ * (Section 3.4, Algorithm 1).  Every step runs in this library's CUDA kernels; the
+ * ABI exposes plain pointers and sizes only.
+ *
+ * Conventions for every entry point:
+ *   - Return value: PHMM_OK (0), PHMM_PENDING (1) or a negative phmm_status.  Errors are
+ *     returned, never thrown across the ABI.  phmm_strerror() names them.
+ *   - A context is bound to one CUDA device and one stream.  Calls on one context are
+ *     serialised by an internal mutex (thread-safe per context).
+ *
+ * Input model (paper Section 2): a read of length l with four per-base quality strings
+ * (base quality Q_i, insertion ins_i, deletion del_i, gap continuation gcp_i) and a
+ * haplotype of length k.  Qualities are numeric Phred 0..93 (the paper's "Q - 33" is
+ * the ASCII offset; subtract 33 before calling).  q(x) = 10^(-x/10):
+ *   P(r_i|h_j) = 1 - q(Q_i) on a match, q(Q_i)/3 on a mismatch (Eq. 3); an 'N' on
+ *   either side counts as a match;  T_MI_i = q(ins_i), T_MD_i = q(del_i),
+ *   T_MM_i = 1 - T_MI_i - T_MD_i, T_II_i = T_DD_i = q(gcp_i), T_IM_i = T_DM_i = 1 - q(gcp_i)
+ *   (Section 2 fixes 0.1 / 0.9, i.e. gcp = 10).
+ * Output: log10 L with L = sum_j M[l][j] + I[l][j] / C (Eq. 4), where C = D[0][j] * k is
+ * the initial scale of Eq. 1 (so L keeps the 1/k start prior).
+ */
+#ifndef PHMM_H
+#define PHMM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PHMM_ABI_VERSION 1
+
+/* Opaque context: device arenas, stream, captured graphs, pending tickets. */
+typedef struct phmm_ctx phmm_ctx;
+
+typedef enum {
+    PHMM_OK = 0,          /* done */
+    PHMM_PENDING = 1,     /* phmm_poll: submitted work not finished yet */
+    PHMM_EINVAL = -1,     /* bad argument, base other than ACGTN, quality > 93, empty
+                             read or haplotype, non-monotone offsets, pair index out
+                             of range */
+    PHMM_ENOMEM = -2,     /* the batch's device footprint exceeds the memory budget */
+    PHMM_EBUSY = -3,      /* max_inflight tickets already pending */
+    PHMM_ECUDA = -4,      /* a CUDA runtime call failed (context unusable) */
+    PHMM_ETIMEOUT = -5,   /* phmm_poll timed out, or a device-side bounded wait gave up */
+    PHMM_ECANCELED = -6,  /* work cancelled by phmm_destroy */
+    PHMM_ENOTFOUND = -7   /* unknown or already retired ticket */
+} phmm_status;
+
+typedef enum {
+    PHMM_PREC_FP32_RESCUE = 0, /* FP32 bulk with power-of-two rescaling; pairs flagged
+                                  by the underflow test are recomputed in FP64 (default) */
+    PHMM_PREC_FP64 = 1,        /* every pair in FP64 (same batched engine) */
+    PHMM_PREC_FP32_ONLY = 2    /* FP32 without the FP64 rescue pass (diagnostics) */
+} phmm_precision;
+
+/* phmm_config.flags */
+#define PHMM_F_NO_GRAPH 0x1u        /* launch kernels directly instead of replaying a
+                                       captured CUDA graph */
+#define PHMM_F_LAUNCH_PER_PAIR 0x2u /* with PHMM_PREC_FP64: one kernel launch per pair
+                                       (the plain FP64 comparator) */
+#define PHMM_F_FORCE_RESCUE 0x4u    /* flag every pair for the FP64 rescue pass (tests) */
+
+typedef struct {
+    int device;               /* CUDA device ordinal */
+    int precision;            /* phmm_precision */
+    size_t mem_budget_bytes;  /* admission budget for one batch's device footprint;
+                                 0 = 90% of the device's free memory at create time */
+    unsigned max_inflight;    /* tickets that may be pending at once; 0 = 4 */
+    unsigned flags;           /* PHMM_F_* */
+    void *stream;             /* cudaStream_t to run on; NULL = a stream owned by the
+                                 context.  The caller keeps a passed stream alive until
+                                 phmm_destroy. */
+    int cols_per_lane;        /* haplotype columns per thread (the paper's N): 0 = chosen
+                                 by the built-in tuner, else 16, 24 or 32 */
+} phmm_config;
+
+/*
+ * One batch.  Reads and haplotypes are concatenated; offsets have n+1 entries and must
+ * be non-decreasing with lengths >= 1.  Bases are ASCII A/C/G/T/N (either case).  The
+ * four quality arrays have the layout of read_bases.  A pair is (pair_read[p],
+ * pair_hap[p]).  All pointers are host pointers unless inputs_on_device (then every
+ * input array is a device pointer of the context's device) or outputs_on_device.
+ */
+typedef struct {
+    uint32_t n_reads;
+    const uint8_t *read_bases;
+    const uint64_t *read_off;
+    const uint8_t *base_q;
+    const uint8_t *ins_q;
+    const uint8_t *del_q;
+    const uint8_t *gcp_q;
+    uint32_t n_haps;
+    const uint8_t *hap_bases;
+    const uint64_t *hap_off;
+    uint32_t n_pairs;
+    const uint32_t *pair_read;
+    const uint32_t *pair_hap;
+    double *out_log10;        /* n_pairs results, caller-owned */
+    uint8_t *out_flags;       /* optional (may be NULL): per pair PHMM_PAIR_* bits */
+    int inputs_on_device;
+    int outputs_on_device;
+} phmm_batch;
+
+/* out_flags bits */
+#define PHMM_PAIR_RESCUED 0x1u  /* recomputed in FP64 by the rescue pass */
+#define PHMM_PAIR_RESCALED 0x2u /* power-of-two rescaling was applied */
+#define PHMM_PAIR_FP64 0x4u     /* final value computed in FP64 */
+/* why the FP32 pass selected a pair for the FP64 rescue (kept when it was rescued) */
+#define PHMM_PAIR_DANGER 0x8u     /* a checkpoint row maximum fell below the danger level */
+#define PHMM_PAIR_NONFINITE 0x10u /* an inf / nan appeared */
+#define PHMM_PAIR_SMALL_SUM 0x20u /* the FP32 last-row sum failed the underflow test */
+#define PHMM_PAIR_DEGENERATE 0x40u /* gcp Phred 0 (T_DD = 1): factored FP32 form unusable */
+#define PHMM_PAIR_ERROR 0x80u   /* invalid input or device error for this pair */
+
+/* Per-ticket statistics (device times from CUDA events on the context's stream). */
+typedef struct {
+    uint64_t cells;           /* sum over pairs of l * k */
+    uint32_t n_pairs;
+    uint32_t n_rescued;       /* pairs recomputed in FP64 by the rescue pass */
+    uint32_t n_long;          /* pairs that spanned more than one warp */
+    uint32_t cols_per_lane;   /* N used */
+    float ms_total;           /* device time from first to last kernel of the ticket */
+    float ms_forward;         /* the main FP32 (or FP64) forward kernel(s) */
+    float ms_rescue;          /* FP64 rescue pass (0 if nothing was rescued) */
+    float ms_h2d;             /* host-to-device copies (host inputs only) */
+    uint32_t kernel_launches; /* kernels launched for the ticket */
+    uint32_t status_bits;     /* device status word (0 = clean) */
+} phmm_stats;
+
+/* Create a context on cfg->device.  *out receives the handle.  PHMM_EINVAL on a bad
+ * config, PHMM_ECUDA if the device cannot be used. */
+int phmm_create(const phmm_config *cfg, phmm_ctx **out);
+
+/* Validate a batch, copy host inputs to device arenas (before returning, so the caller
+ * may reuse host input buffers immediately), and enqueue the forward computation on the
+ * context's stream.  *ticket identifies it for phmm_poll.  Device inputs and all
+ * outputs must stay valid until phmm_poll returns a terminal status for the ticket.
+ * PHMM_EINVAL / PHMM_ENOMEM (batch larger than the budget) / PHMM_EBUSY / PHMM_ECUDA. */
+int phmm_submit_batch(phmm_ctx *ctx, const phmm_batch *batch, uint64_t *ticket);
+
+/* Wait up to timeout_ms (0 = just test, < 0 = forever) for a ticket.  PHMM_OK when its
+ * outputs are written, PHMM_PENDING if not finished, PHMM_EINVAL if a base or quality of
+ * the batch was invalid (those pairs carry PHMM_PAIR_ERROR and NaN), PHMM_ETIMEOUT if a
+ * device-side wait gave up.  A terminal status retires the ticket. */
+int phmm_poll(phmm_ctx *ctx, uint64_t ticket, int timeout_ms);
+
+/* Statistics of a finished (not yet retired, or the most recently retired) ticket. */
+int phmm_get_stats(phmm_ctx *ctx, uint64_t ticket, phmm_stats *out);
+
+/* Cancel pending work (waits for the stream), free every device and host resource. */
+void phmm_destroy(phmm_ctx *ctx);
+
+/* Static description of a status code. */
+const char *phmm_strerror(int status);
+
+/* ABI version of the loaded library (PHMM_ABI_VERSION at build time). */
+int phmm_abi_version(void);
+
+/* Number of SMs and the FP32 cell-update roofline of the context's device:
+ * 2 * 128 FP32 lanes * SMs * max SM clock / 12 FLOP per cell (Eq. 2 as written:
+ * 6 multiplies and 6 adds per cell).  Writes cells per second into *cups. */
+int phmm_device_info(phmm_ctx *ctx, int *sms, double *max_clock_mhz, double *cups);
+
+/*
+ * Test entry: the lane-level linear-recurrence scan of Section 3.4 (Algorithm 1) on its
+ * own, as the forward kernels run it: one warp, each lane owns 32 consecutive elements,
+ * a sequential pass inside the lane, then a warp shuffle scan of the lane aggregates
+ * with multiplier a^32.  For n values y[0..n) (device pointer, FP32, 1 <= n <= 1024)
+ * writes z[t] = sum_{s <= t} a^(t-s) y[s] (device pointer).  Runs synchronously.
+ */
+int phmm_scan_test(phmm_ctx *ctx, const float *y, float *z, int n, float a);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PHMM_H */

@@ -1,0 +1,536 @@
+// Row-wise PairHMM forward engine (device side).
+//
+// What one lane does (paper Section 3.4, mapped to sm_103a): a pair's haplotype columns
+// are split across the G lanes of a team (a sub-warp, or a whole warp per segment of a
+// multi-warp pair); lane t owns N consecutive columns and keeps their M and I values of
+// the previous row in registers.  Per read row i:
+//
+//  1. M and I of row i from row i-1 (Eq. 2 / Eq. 7), left to right over the lane's N
+//     columns.  The deletion term D[i-1][j-1] is carried along the lane as
+//     D-hat = D / T_MD (so one FMA advances it: D-hat[j] = M[j-1] + g D-hat[j-1]), and the
+//     FP32 form is factored so each cell costs 7 FMA-pipe operations:
+//        S  = fma(T_MD_{i-1}, Dhat[i-1][j-1], I[i-1][j-1])          I' + D'
+//        u  = fma(T_MM_i / (1-g_i), M[i-1][j-1], S)
+//        M  = P(r_i|h_j) (1-g_i) * u                                  (Eq. 2, M)
+//        I  = fma(T_MI_i, M[i-1][j], g_i * I[i-1][j])                (Eq. 2, I)
+//        Dhat[i-1][j] = fma(g_{i-1}, Dhat[i-1][j-1], M[i-1][j-1])    (carry of row i-1)
+//        y  = fma(g_i, y, M[i][j])                                    (local D-hat of row i)
+//     The FP64 instantiation keeps the unfactored product (one more multiply) so that
+//     g = 1 stays exact.
+//  2. The deletion recurrence of row i across lanes is a first-order linear recurrence
+//     D-hat[j+N] = g^N D-hat[j] + y_lane: an exclusive Kogge-Stone scan over the team with
+//     the operator (a, b) o (a', b') = (a a', a' b + b') and a = g^N (Algorithm 1, but
+//     the exclusive value comes straight out of the scan: no subtraction, no division).
+//     Powers are applied as two factors so products that are representable stay so.
+//  3. Between warps of one pair, the last lane publishes its last column's M, I, D-hat
+//     and exponent for row i into the next warp's shared-memory ring (tagged 64-bit
+//     words, no fences), the next warp folds that carry in.  Warps run skewed by about
+//     one row, so the hand-off latency is paid once per segment, not once per row.
+//  4. Every R rows the segment's largest |M|, |I| is checked; values are multiplied by
+//     an exact power of two when it leaves [2^lo, 2^hi] (the paper is silent on
+//     rescaling; the initial scale 2^120 / k alone cannot hold long reads).  A row max
+//     below the danger level flags the pair for the FP64 rescue pass.
+//  5. After row l: S = sum over the team's columns of M + I (Eq. 4) in FP64.
+#pragma once
+
+#include <climits>
+#include <cstdint>
+
+#include "phmm_internal.h"
+
+namespace phmm {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+template <typename T>
+struct Num;
+
+template <>
+struct Num<float> {
+    using Rec = Rec32;
+    static constexpr int kLog2C = 120;      // C = 2^120 (FP32 initial scale of D)
+    static constexpr int kHi = 100;         // rescale when the row max >= 2^kHi ...
+    static constexpr int kLo = 40;          // ... or < 2^kLo
+    static constexpr int kTarget = 96;      // new row max in [2^95, 2^96)
+    static constexpr int kDanger = -100;    // below: flag for the FP64 rescue pass
+    static constexpr int kDropBudget = 140; // kLo - kDanger
+    static constexpr int kGrowBudget = 26;  // (127 - 1) - kHi
+    static constexpr int kMinExp = -126, kMaxExp = 127;
+    static constexpr bool kFactored = true;
+    static constexpr int kWords = 4;        // mailbox words per row: M, I, D-hat, E
+    __device__ static __forceinline__ float pow2(int e) {
+        return __uint_as_float((uint32_t)(e + 127) << 23);
+    }
+    // frexp-style exponent: m in [2^(e-1), 2^e) for normal m > 0; INT_MIN for 0 and
+    // subnormals; INT_MAX for inf / nan.
+    __device__ static __forceinline__ int expo(float m) {
+        const uint32_t b = __float_as_uint(m) & 0x7fffffffu;
+        const int f = (int)(b >> 23);
+        if (f == 0) return INT_MIN;
+        if (f == 255) return INT_MAX;
+        return f - 126;
+    }
+};
+
+template <>
+struct Num<double> {
+    using Rec = Rec64;
+    static constexpr int kLog2C = 1020;     // C = 2^1020 (Eq. 1)
+    static constexpr int kHi = 900;
+    static constexpr int kLo = 300;
+    static constexpr int kTarget = 800;
+    static constexpr int kDanger = -950;
+    static constexpr int kDropBudget = 1250;
+    static constexpr int kGrowBudget = 120;
+    static constexpr int kMinExp = -1022, kMaxExp = 1023;
+    static constexpr bool kFactored = false;
+    static constexpr int kWords = 8;        // M, I, D-hat as two 32-bit halves each, E
+    __device__ static __forceinline__ double pow2(int e) {
+        return __longlong_as_double((long long)((uint64_t)(e + 1023) << 52));
+    }
+    __device__ static __forceinline__ int expo(double m) {
+        const uint64_t b = (uint64_t)__double_as_longlong(m) & 0x7fffffffffffffffull;
+        const int f = (int)(b >> 52);
+        if (f == 0) return INT_MIN;
+        if (f == 2047) return INT_MAX;
+        return f - 1022;
+    }
+};
+
+// x * 2^s for any s (two exact steps when 2^s alone is not representable).
+template <typename T>
+__device__ __forceinline__ T scale2(T x, int s) {
+    using NT = Num<T>;
+    if (s >= NT::kMinExp && s <= NT::kMaxExp) return x * NT::pow2(s);
+    if (s < 2 * NT::kMinExp) return T(0);
+    const int s1 = s / 2;
+    return (x * NT::pow2(s1)) * NT::pow2(s - s1);
+}
+
+__device__ __forceinline__ Rec32 load_rec(const Rec32* p) {
+    const float4 a = __ldg(reinterpret_cast<const float4*>(p));
+    const float4 b = __ldg(reinterpret_cast<const float4*>(p) + 1);
+    Rec32 r;
+    r.pm = a.x; r.px = a.y; r.a = a.z; r.b = a.w;
+    r.mi = b.x; r.g = b.y; r.gm = b.z; r.meta = __float_as_uint(b.w);
+    return r;
+}
+__device__ __forceinline__ Rec64 load_rec(const Rec64* p) {
+    const double2* q = reinterpret_cast<const double2*>(p);
+    const double2 a = __ldg(q), b = __ldg(q + 1), c = __ldg(q + 2), d = __ldg(q + 3);
+    Rec64 r;
+    r.pm = a.x; r.px = a.y; r.a = b.x; r.b = b.y; r.mi = c.x; r.g = c.y; r.gm = d.x;
+    r.meta = (uint64_t)__double_as_longlong(d.y);
+    return r;
+}
+
+// Powers of g for the lane's scan (see PowRow): a pointer to the table row of the
+// current gcp; the factors are read through L1 when used (uniform addresses), which
+// keeps them out of the register file.
+template <typename T>
+struct Pow {
+    const PowRow<T>* row;
+    int gcp;
+    __device__ __forceinline__ void load(const PowRow<T>* __restrict__ tab, int gq) {
+        row = tab + gq;
+        gcp = gq;
+    }
+    __device__ __forceinline__ T sp1(int s) const { return __ldg(&row->sp1[s]); }
+    __device__ __forceinline__ T sp2(int s) const { return __ldg(&row->sp2[s]); }
+    __device__ __forceinline__ T lp1(int t) const { return __ldg(&row->lp1[t]); }
+    __device__ __forceinline__ T lp2(int t) const { return __ldg(&row->lp2[t]); }
+    __device__ __forceinline__ T last1() const { return __ldg(&row->last1); }
+    __device__ __forceinline__ T last2() const { return __ldg(&row->last2); }
+};
+
+// Inclusive segmented scan z_t = sum_{s<=t} a^(t-s) x_s over the team (lt = lane in
+// team); a^(2^s) = sp1[s] * sp2[s].  nsteps is warp-uniform.
+template <typename T>
+__device__ __forceinline__ T team_scan(T x, int lt, const Pow<T>& pw, int nsteps) {
+#pragma unroll
+    for (int s = 0; s < 5; ++s) {
+        if (s < nsteps) {
+            const int off = 1 << s;
+            const T up = __shfl_up_sync(kFull, x, off);
+            const T t = up * pw.sp1(s);
+            if (lt >= off) x = fma(t, pw.sp2(s), x);
+        }
+    }
+    return x;
+}
+
+template <typename V>
+__device__ __forceinline__ V team_sum(V x, int lt, int last_lane, int nsteps) {
+#pragma unroll
+    for (int s = 0; s < 5; ++s) {
+        if (s < nsteps) {
+            const int off = 1 << s;
+            const V up = __shfl_up_sync(kFull, x, off);
+            if (lt >= off) x += up;
+        }
+    }
+    return __shfl_sync(kFull, x, last_lane);
+}
+
+template <typename V>
+__device__ __forceinline__ V team_max(V x, int lt, int last_lane, int nsteps) {
+#pragma unroll
+    for (int s = 0; s < 5; ++s) {
+        if (s < nsteps) {
+            const int off = 1 << s;
+            const V up = __shfl_up_sync(kFull, x, off);
+            if (lt >= off) x = fmax(x, up);
+        }
+    }
+    return __shfl_sync(kFull, x, last_lane);
+}
+
+__device__ __forceinline__ uint32_t team_or(uint32_t x, int lt, int last_lane, int nsteps) {
+#pragma unroll
+    for (int s = 0; s < 5; ++s) {
+        if (s < nsteps) {
+            const int off = 1 << s;
+            const uint32_t up = __shfl_up_sync(kFull, x, off);
+            if (lt >= off) x |= up;
+        }
+    }
+    return __shfl_sync(kFull, x, last_lane);
+}
+
+// Base code of an ASCII haplotype / read byte: A=0 C=1 G=2 T=3 N=4, -1 otherwise.
+__device__ __forceinline__ int base_code(uint32_t c) {
+    c |= 0x20u;  // lower case
+    switch (c) {
+    case 'a': return 0;
+    case 'c': return 1;
+    case 'g': return 2;
+    case 't': return 3;
+    case 'n': return 4;
+    default: return -1;
+    }
+}
+
+// ------------------------------------------------------------------------------------
+// Shared-memory mailbox between consecutive warp segments of one pair.
+// Word = (payload32 << 32) | row tag; a row is complete when every word carries its tag.
+// ------------------------------------------------------------------------------------
+constexpr long long kSpinLimit = 1ll << 22;  // polls (with backoff) before giving up
+
+struct SmemLink {
+    unsigned long long* in_ring;   // my inbound ring  [kRing][words]
+    unsigned long long* out_ring;  // next segment's ring
+    volatile int* my_cons;         // rows I have consumed (written by me)
+    volatile int* next_cons;       // rows the next segment consumed (read by me)
+    bool has_left, has_right;
+};
+
+__device__ __forceinline__ void st_vol(unsigned long long* p, unsigned long long v) {
+    *reinterpret_cast<volatile unsigned long long*>(p) = v;
+}
+__device__ __forceinline__ unsigned long long ld_vol(const unsigned long long* p) {
+    return *reinterpret_cast<const volatile unsigned long long*>(p);
+}
+__device__ __forceinline__ unsigned long long tagw(uint32_t payload, int row) {
+    return ((unsigned long long)payload << 32) | (uint32_t)row;
+}
+
+template <typename T>
+__device__ __forceinline__ void pack_vals(T m, T i, T d, int e, uint32_t* w);
+template <>
+__device__ __forceinline__ void pack_vals<float>(float m, float i, float d, int e, uint32_t* w) {
+    w[0] = __float_as_uint(m); w[1] = __float_as_uint(i); w[2] = __float_as_uint(d);
+    w[3] = (uint32_t)e;
+}
+template <>
+__device__ __forceinline__ void pack_vals<double>(double m, double i, double d, int e, uint32_t* w) {
+    const unsigned long long a = (unsigned long long)__double_as_longlong(m);
+    const unsigned long long b = (unsigned long long)__double_as_longlong(i);
+    const unsigned long long c = (unsigned long long)__double_as_longlong(d);
+    w[0] = (uint32_t)a; w[1] = (uint32_t)(a >> 32); w[2] = (uint32_t)b; w[3] = (uint32_t)(b >> 32);
+    w[4] = (uint32_t)c; w[5] = (uint32_t)(c >> 32); w[6] = (uint32_t)e; w[7] = 0;
+}
+template <typename T>
+__device__ __forceinline__ void unpack_vals(const uint32_t* w, T& m, T& i, T& d, int& e);
+template <>
+__device__ __forceinline__ void unpack_vals<float>(const uint32_t* w, float& m, float& i, float& d, int& e) {
+    m = __uint_as_float(w[0]); i = __uint_as_float(w[1]); d = __uint_as_float(w[2]); e = (int)w[3];
+}
+template <>
+__device__ __forceinline__ void unpack_vals<double>(const uint32_t* w, double& m, double& i, double& d, int& e) {
+    m = __longlong_as_double((long long)(((unsigned long long)w[1] << 32) | w[0]));
+    i = __longlong_as_double((long long)(((unsigned long long)w[3] << 32) | w[2]));
+    d = __longlong_as_double((long long)(((unsigned long long)w[5] << 32) | w[4]));
+    e = (int)w[6];
+}
+
+// Producer side (called by the segment's last lane): wait for ring space, then publish.
+template <typename T>
+__device__ bool link_send(const SmemLink& L, int row, T m, T i, T d, int e) {
+    constexpr int W = Num<T>::kWords;
+    bool ok = true;
+    long long spins = 0;
+    while (*L.next_cons < row - kRing) {
+        if (++spins > kSpinLimit) { ok = false; break; }
+        __nanosleep(64);
+    }
+    uint32_t w[W];
+    pack_vals<T>(m, i, d, e, w);
+    unsigned long long* slot = L.out_ring + (row % kRing) * W;
+#pragma unroll
+    for (int q = 0; q < W; ++q) st_vol(slot + q, tagw(w[q], row));
+    return ok;
+}
+
+// Consumer side (called by the segment's first lane): wait for the row, read it.
+template <typename T>
+__device__ bool link_recv(const SmemLink& L, int row, T& m, T& i, T& d, int& e) {
+    constexpr int W = Num<T>::kWords;
+    const unsigned long long* slot = L.in_ring + (row % kRing) * W;
+    uint32_t w[W];
+    bool ok = true;
+    long long spins = 0;
+    for (;;) {
+        bool all = true;
+#pragma unroll
+        for (int q = 0; q < W; ++q) {
+            const unsigned long long v = ld_vol(slot + q);
+            w[q] = (uint32_t)(v >> 32);
+            all &= ((uint32_t)v == (uint32_t)row);
+        }
+        if (all) break;
+        if (++spins > kSpinLimit) { ok = false; break; }
+        __nanosleep(32);
+    }
+    unpack_vals<T>(w, m, i, d, e);
+    *L.my_cons = row;
+    return ok;
+}
+
+// Checkpoint interval R from the batch's worst per-row drop and growth (bits * 64),
+// so that between checkpoints no value can overflow and the row max cannot fall from
+// 2^lo to below the danger level.
+template <typename T>
+__device__ __forceinline__ int checkpoint_interval(const uint32_t* dropgrow) {
+    using NT = Num<T>;
+    const uint32_t d = max(dropgrow[0], 1u), g = max(dropgrow[1], 1u);
+    int r1 = (int)((uint64_t)NT::kDropBudget * 64u / d);
+    int r2 = (int)((uint64_t)NT::kGrowBudget * 64u / g);
+    int r = min(r1, r2);
+    return max(1, min(r, 64));
+}
+
+struct SegOut {
+    double S;
+    int E;
+    uint32_t flags;
+};
+
+// ------------------------------------------------------------------------------------
+// One team / segment: rows 1..lmax over the lane's N columns.  Returns the team's
+// final (S, E, flags) in every lane of the team (valid when the team's l <= lmax).
+//   rec      the read's records (row i at rec[i-1]), l rows; lmax >= l is the warp's
+//            row count (rows beyond l recompute row l harmlessly)
+//   hap, k   the haplotype (ASCII) and its length; col0 = the lane's first column - 1
+//   lt       lane in team; tlast = absolute lane of the team's last lane; nsteps = scan
+//            steps (warp-uniform)
+//   R        checkpoint interval
+// ------------------------------------------------------------------------------------
+template <typename T, int N, bool LINKED>
+__device__ SegOut seg_run(const typename Num<T>::Rec* __restrict__ rec, int l, int lmax,
+                          const uint8_t* __restrict__ hap, int k, int col0, int lt, int tlast,
+                          int nsteps, const PowRow<T>* __restrict__ pow_tab, int R,
+                          const SmemLink& link, uint32_t* __restrict__ status) {
+    using NT = Num<T>;
+    using Rec = typename NT::Rec;
+    static_assert(N <= 32, "match masks hold 32 columns");
+
+    // Match masks of the lane's columns (Eq. 3; an N matches every base).
+    uint32_t bmA = 0, bmC = 0, bmG = 0, bmT = 0;
+    uint32_t flags = 0;
+    const int nvalid = max(0, min(k - col0, N));
+#pragma unroll
+    for (int c = 0; c < N; ++c) {
+        if (c < nvalid) {
+            const int code = base_code(hap[col0 + c]);
+            const uint32_t bit = 1u << c;
+            if (code < 0) flags |= PF_BAD;
+            if (code == 0 || code == 4) bmA |= bit;
+            if (code == 1 || code == 4) bmC |= bit;
+            if (code == 2 || code == 4) bmG |= bit;
+            if (code == 3 || code == 4) bmT |= bit;
+        }
+    }
+
+    T M[N], I[N];
+    int E = 0;
+    T ml = T(0), sl = T(0), dt = T(0), gprev = T(0);
+    Pow<T> pw;
+    pw.row = pow_tab;
+    pw.gcp = -1;
+    SegOut out;
+    out.S = 0.0;
+    out.E = 0;
+    out.flags = 0;
+    const bool active = l > 0;
+    const T cinit = active && k > 0 ? (T)(ldexp(1.0, NT::kLog2C) / (double)k) : T(0);
+
+    Rec cur = load_rec(rec);
+    for (int i = 1; i <= lmax; ++i) {
+        Rec nxt = cur;
+        if (i < lmax) nxt = load_rec(rec + min(i, max(l, 1) - 1));
+        const uint32_t meta = (uint32_t)cur.meta;
+        const int gq = (int)((meta >> META_GCP_SHIFT) & 0xffu);
+        if (gq != pw.gcp) pw.load(pow_tab, min(gq, kMaxPhred));
+        if (i <= l) {
+            if (meta & META_BAD) flags |= PF_BAD;
+            if (NT::kFactored && (meta & META_DEGEN)) flags |= PF_DEGEN;
+        }
+        const int code = (int)(meta & META_CODE_MASK);
+        const uint32_t mask = code == 0 ? bmA : code == 1 ? bmC : code == 2 ? bmG
+                            : code == 3 ? bmT : 0xffffffffu;
+        const T pim = cur.pm, pix = cur.px, rg = cur.g;
+        T y = T(0), yprev = T(0);
+        if (i == 1) {
+            // Row 1 (Eq. 1-2): M = P (1 - g_1) C / k, I = 0.
+            const T c1 = NT::kFactored ? cinit : cinit * cur.gm;
+#pragma unroll
+            for (int c = 0; c < N; ++c) {
+                const T p = ((mask >> c) & 1u) ? pim : pix;
+                M[c] = p * c1;
+                I[c] = T(0);
+                if (c == N - 1) yprev = y;
+                y = fma(rg, y, M[c]);
+            }
+        } else {
+            const T ra = cur.a, rb = cur.b, rmi = cur.mi, rgm = cur.gm;
+#pragma unroll
+            for (int c = 0; c < N; ++c) {
+                const T S = fma(rb, dt, sl);
+                T u;
+                if (NT::kFactored) u = fma(ra, ml, S);
+                else u = fma(ra, ml, rgm * S);
+                const T p = ((mask >> c) & 1u) ? pim : pix;
+                const T mn = p * u;
+                const T in = fma(rmi, M[c], rg * I[c]);
+                dt = fma(gprev, dt, ml);
+                ml = M[c];
+                sl = I[c];
+                M[c] = mn;
+                I[c] = in;
+                if (c == N - 1) yprev = y;
+                y = fma(rg, y, mn);
+            }
+        }
+
+        // Deletion scan of row i across the team: W = D-hat at the lane's first column.
+        const T Z = team_scan<T>(y, lt, pw, nsteps);
+        T Wd = __shfl_up_sync(kFull, Z, 1);
+        if (lt == 0) Wd = T(0);
+
+        // Carry from the previous warp segment (multi-warp pairs).
+        T lM = T(0), lI = T(0), lD = T(0);
+        int Eleft = INT_MIN;
+        if (LINKED && link.has_left) {
+            int e_in = 0;
+            if ((threadIdx.x & 31) == 0) {
+                if (!link_recv<T>(link, i, lM, lI, lD, e_in)) {
+                    flags |= PF_TIMEOUT;
+                    atomicOr(status, ST_TIMEOUT);
+                }
+            }
+            lM = __shfl_sync(kFull, lM, 0);
+            lI = __shfl_sync(kFull, lI, 0);
+            lD = __shfl_sync(kFull, lD, 0);
+            Eleft = __shfl_sync(kFull, e_in, 0);
+        }
+
+        // Checkpoint: power-of-two rescaling of the segment (uniform across the warp).
+        int Enew = E;
+        if (i == 1 || (i - 1) % R == 0) {
+            T m = T(0);
+#pragma unroll
+            for (int c = 0; c < N; ++c) m = fmax(m, fmax(fabs(M[c]), fabs(I[c])));
+            m = team_max<T>(m, lt, tlast, nsteps);
+            const int e = NT::expo(m);
+            int desired = E;
+            if (e == INT_MAX) {
+                if (i <= l) flags |= PF_NONFINITE;
+            } else if (e != INT_MIN && (e > NT::kHi || e <= NT::kLo)) {
+                desired = E + (e - NT::kTarget);
+            }
+            Enew = desired;
+            bool forced = false;
+            if (LINKED && link.has_left && Eleft > Enew) {
+                Enew = Eleft;
+                forced = true;
+            }
+            // A segment whose largest value is zero or subnormal holds no mass of its
+            // own (it sits beside the alignment band); an empty row as a whole is caught
+            // by the underflow test on the final sum.
+            if (!forced && e != INT_MIN && e <= NT::kDanger && i <= l) flags |= PF_DANGER;
+        }
+        if (Enew != E) {
+            const int s = E - Enew;
+#pragma unroll
+            for (int c = 0; c < N; ++c) {
+                M[c] = scale2(M[c], s);
+                I[c] = scale2(I[c], s);
+            }
+            Wd = scale2(Wd, s);
+            yprev = scale2(yprev, s);
+            if (i <= l) flags |= PF_RESCALED;
+            E = Enew;
+        }
+        if (LINKED && link.has_left) {
+            // Left values into this segment's scale (E >= Eleft always holds here).
+            const int d = Eleft - E;
+            lM = scale2(lM, d);
+            lI = scale2(lI, d);
+            lD = scale2(lD, d);
+            const T Wseg = fma(rg, lD, lM);  // D-hat at the segment's first column
+            Wd = fma(Wseg * pw.lp1(lt), pw.lp2(lt), Wd);
+        }
+        // D-hat at the lane's last column (needed by the next lane's first cell).
+        const T Dlast = fma(Wd * pw.last1(), pw.last2(), yprev);
+
+        if (LINKED && link.has_right && (threadIdx.x & 31) == 31) {
+            if (!link_send<T>(link, i, M[N - 1], I[N - 1], Dlast, E)) {
+                flags |= PF_TIMEOUT;
+                atomicOr(status, ST_TIMEOUT);
+            }
+        }
+
+        // Eq. 4 when a team of this warp finishes (warp-uniform participation).
+        if (__any_sync(kFull, i == l)) {
+            double s = 0.0;
+#pragma unroll
+            for (int c = 0; c < N; ++c)
+                if (c < nvalid) s += (double)M[c] + (double)I[c];
+            s = team_sum<double>(s, lt, tlast, nsteps);
+            const uint32_t f = team_or(flags, lt, tlast, nsteps);
+            if (i == l) {
+                out.S = s;
+                out.E = E;
+                out.flags = f;
+            }
+        }
+
+        // Inputs of the next row's first column.
+        T nm = __shfl_up_sync(kFull, M[N - 1], 1);
+        T ni = __shfl_up_sync(kFull, I[N - 1], 1);
+        T nd = __shfl_up_sync(kFull, Dlast, 1);
+        if (lt == 0) {
+            nm = lM;
+            ni = lI;
+            nd = lD;
+        }
+        ml = nm;
+        sl = ni;
+        dt = nd;
+        gprev = rg;
+        cur = nxt;
+    }
+    return out;
+}
+
+}  // namespace phmm

@@ -1,0 +1,402 @@
+// Kernels of the row-wise PairHMM library: coefficient prep, the persistent forward
+// kernel, the log10 reduction / rescue selection, the FP64 rescue pass, the FP64
+// launch-per-pair comparator and the scan test.  Instantiated for float in
+// kernels_f32.cu and for double in kernels_f64.cu.
+#pragma once
+
+#include <cmath>
+#include <cstdint>
+
+#include "engine.cuh"
+#include "phmm_internal.h"
+
+namespace phmm {
+
+// ------------------------------------------------------------------------------------
+// Double-float helpers for the FP32 prep (Phred tables: see PhredTables).
+// ------------------------------------------------------------------------------------
+struct df {
+    float hi, lo;
+};
+__device__ __forceinline__ df quick_two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ df two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+__device__ __forceinline__ df df_mul(df a, df b) {
+    const float p = __fmul_rn(a.hi, b.hi);
+    float e = fmaf(a.hi, b.hi, -p);
+    e = fmaf(a.hi, b.lo, e);
+    e = fmaf(a.lo, b.hi, e);
+    return quick_two_sum(p, e);
+}
+__device__ __forceinline__ df df_sub(df a, df b) {
+    const df s = two_sum(a.hi, -b.hi);
+    return quick_two_sum(s.hi, __fadd_rn(s.lo, __fsub_rn(a.lo, b.lo)));
+}
+__device__ __forceinline__ df to_df(double v) {
+    const float hi = (float)v;
+    return {hi, (float)(v - (double)hi)};
+}
+
+// SplitMix64 output function (Steele, Lea, Flood 2014) as a counter-based mixer.
+__device__ __forceinline__ uint64_t mix64(uint64_t z) {
+    z += 0x9e3779b97f4a7c15ull;
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+    return z ^ (z >> 31);
+}
+
+// Unbiased stochastic rounding of hi + lo to float: rounding errors of per-row
+// coefficients then average out over long reads instead of adding up.
+__device__ __forceinline__ float sround(df v, uint32_t u24) {
+    if (v.lo == 0.0f || !isfinite(v.hi)) return v.hi;
+    const float nb = nextafterf(v.hi, v.lo > 0.0f ? INFINITY : -INFINITY);
+    const float gap = fabsf(__fsub_rn(nb, v.hi));
+    const float u = (float)u24 * 0x1p-24f;
+    return (__fmul_rn(u, gap) < fabsf(v.lo)) ? nb : v.hi;
+}
+
+__device__ __forceinline__ int read_code(uint32_t c) { return base_code(c); }
+
+// Per-base record inputs with validation.  Returns META_BAD-tagged meta on bad input.
+struct BaseQ {
+    int code, Q, ins, del, gcp, delp;
+    bool bad;
+};
+__device__ __forceinline__ BaseQ base_inputs(const BatchHeader* __restrict__ H, uint64_t b) {
+    BaseQ r;
+    r.code = read_code(H->read_bases[b]);
+    r.Q = H->base_q[b];
+    r.ins = H->ins_q[b];
+    r.del = H->del_q[b];
+    r.gcp = H->gcp_q[b];
+    r.delp = b > 0 ? H->del_q[b - 1] : 0;
+    r.bad = r.code < 0 || r.Q > kMaxPhred || r.ins > kMaxPhred || r.del > kMaxPhred ||
+            r.gcp > kMaxPhred;
+    r.code = r.code < 0 ? 4 : r.code;
+    r.Q = min(r.Q, kMaxPhred);
+    r.ins = min(r.ins, kMaxPhred);
+    r.del = min(r.del, kMaxPhred);
+    r.gcp = min(r.gcp, kMaxPhred);
+    r.delp = min(r.delp, kMaxPhred);
+    return r;
+}
+
+__device__ __forceinline__ Rec32 make_rec32(const BaseQ& x, const float2* tq, const float2* tom,
+                                            const float2* tq3, const float2* tinv, uint32_t seed,
+                                            uint64_t b) {
+    const df q_i = {tq[x.ins].x, tq[x.ins].y};
+    const df q_d = {tq[x.del].x, tq[x.del].y};
+    const df om_g = {tom[x.gcp].x, tom[x.gcp].y};
+    const df om_Q = {tom[x.Q].x, tom[x.Q].y};
+    const df q3_Q = {tq3[x.Q].x, tq3[x.Q].y};
+    const df inv_g = {tinv[x.gcp].x, tinv[x.gcp].y};
+    const df one = {1.0f, 0.0f};
+    const df tmm = df_sub(df_sub(one, q_i), q_d);  // T_MM = 1 - T_MI - T_MD
+    const uint64_t h = mix64(((uint64_t)seed << 40) ^ (b * 4u));
+    Rec32 r;
+    r.pm = sround(df_mul(om_Q, om_g), (uint32_t)(h & 0xffffffu));          // (1-e)(1-g)
+    r.px = sround(df_mul(q3_Q, om_g), (uint32_t)((h >> 24) & 0xffffffu));  // e/3 (1-g)
+    r.a = sround(df_mul(tmm, inv_g), (uint32_t)((h >> 40) & 0xffffffu));   // T_MM/(1-g)
+    r.b = tq[x.delp].x;                                                      // T_MD of the previous row
+    r.mi = q_i.hi;
+    r.g = tq[x.gcp].x;
+    r.gm = om_g.hi;
+    uint32_t meta = (uint32_t)x.code | ((uint32_t)x.gcp << META_GCP_SHIFT);
+    if (x.bad) meta |= META_BAD;
+    if (!(om_g.hi >= 0x1p-20f) || !isfinite(r.a)) meta |= META_DEGEN;
+    r.meta = meta;
+    return r;
+}
+
+__device__ __forceinline__ Rec64 make_rec64(const BaseQ& x, const PhredTables& T) {
+    Rec64 r;
+    r.pm = T.om[x.Q];
+    r.px = T.q3[x.Q];
+    r.a = 1.0 - T.q[x.ins] - T.q[x.del];
+    r.b = T.q[x.delp];
+    r.mi = T.q[x.ins];
+    r.g = T.q[x.gcp];
+    r.gm = T.om[x.gcp];
+    uint64_t meta = (uint64_t)x.code | ((uint64_t)x.gcp << META_GCP_SHIFT);
+    if (x.bad) meta |= META_BAD;
+    r.meta = meta;
+    return r;
+}
+
+// Worst per-row drop and growth of the row max in bits (see checkpoint_interval):
+// the max can fall by at most min(T_MI, g) per row and grow by at most
+// max(|T_MM| + (1-g) + T_MD, T_MI + g).
+__device__ __forceinline__ void drop_grow(const BaseQ& x, const PhredTables& T, uint32_t& d,
+                                          uint32_t& g) {
+    const float qi = (float)T.q[x.ins], qd = (float)T.q[x.del], qg = (float)T.q[x.gcp];
+    const float drop = -log2f(fminf(qi, qg));
+    const float tmm = fabsf(1.0f - qi - qd);
+    const float grow = log2f(fmaxf(tmm + (1.0f - qg) + qd, qi + qg));
+    d = (uint32_t)ceilf(fmaxf(drop, 0.0f) * 64.0f) + 1u;
+    g = (uint32_t)ceilf(fmaxf(grow, 0.0f) * 64.0f) + 1u;
+}
+
+__device__ __forceinline__ void block_max2(uint32_t d, uint32_t g, uint32_t* out) {
+    __shared__ uint32_t sd[32], sg[32];
+    d = __reduce_max_sync(kFull, d);
+    g = __reduce_max_sync(kFull, g);
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) { sd[w] = d; sg[w] = g; }
+    __syncthreads();
+    if (w == 0) {
+        const int nw = (blockDim.x + 31) >> 5;
+        d = lane < nw ? sd[lane] : 0u;
+        g = lane < nw ? sg[lane] : 0u;
+        d = __reduce_max_sync(kFull, d);
+        g = __reduce_max_sync(kFull, g);
+        if (lane == 0) {
+            atomicMax(out, d);
+            atomicMax(out + 1, g);
+        }
+    }
+}
+
+__device__ __forceinline__ void load_tables(const PhredTables* __restrict__ G, PhredTables& S) {
+    for (int i = threadIdx.x; i < kPhredTab; i += blockDim.x) {
+        S.q[i] = G->q[i];
+        S.om[i] = G->om[i];
+        S.q3[i] = G->q3[i];
+        S.inv[i] = G->inv[i];
+    }
+}
+
+// Pair descriptors (grid-stride): desc[p] = offsets and lengths of pair p.
+__device__ __forceinline__ void build_desc(const BatchHeader* __restrict__ H) {
+    const uint32_t n = H->n_pairs;
+    for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
+        const uint32_t r = H->pair_read[p], h = H->pair_hap[p];
+        PairDesc d;
+        d.roff = H->read_off[r];
+        d.hoff = H->hap_off[h];
+        d.l = (uint32_t)(H->read_off[r + 1] - d.roff);
+        d.k = (uint32_t)(H->hap_off[h + 1] - d.hoff);
+        H->desc[p] = d;
+    }
+}
+
+// ------------------------------------------------------------------------------------
+// Forward kernel pieces
+// ------------------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ const typename Num<T>::Rec* recs_of(const BatchHeader* H);
+template <>
+__device__ __forceinline__ const Rec32* recs_of<float>(const BatchHeader* H) { return H->rec32; }
+template <>
+__device__ __forceinline__ const Rec64* recs_of<double>(const BatchHeader* H) { return H->rec64; }
+
+template <typename T>
+struct CtaShared {
+    unsigned long long ring[kCtaWarps * kRing * Num<T>::kWords];
+    int cons[kCtaWarps + 1];
+    SegOut out[kCtaWarps];
+    uint32_t item;
+};
+
+template <typename T>
+__device__ __forceinline__ void cta_clear(CtaShared<T>& sh) {
+    constexpr int n = kCtaWarps * kRing * Num<T>::kWords;
+    for (int q = threadIdx.x; q < n; q += blockDim.x) sh.ring[q] = 0ull;
+    if (threadIdx.x <= kCtaWarps) sh.cons[threadIdx.x] = 0;
+}
+
+// Warps w0 .. w0+W-1 of the CTA run pair `pair`, one column segment of 32 N each.
+template <typename T, int N>
+__device__ __forceinline__ void cta_pair_run(const BatchHeader* __restrict__ H,
+                                             const PowRow<T>* __restrict__ pow, uint32_t pair,
+                                             int w0, int W, CtaShared<T>& sh, int R) {
+    constexpr int KW = Num<T>::kWords;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int s = warp - w0;
+    if (s < 0 || s >= W) return;
+    const PairDesc d = H->desc[pair];
+    SmemLink L;
+    L.in_ring = sh.ring + warp * kRing * KW;
+    L.out_ring = sh.ring + min(warp + 1, kCtaWarps - 1) * kRing * KW;
+    L.my_cons = sh.cons + warp;
+    L.next_cons = sh.cons + warp + 1;
+    L.has_left = s > 0;
+    L.has_right = s < W - 1;
+    const int col0 = (s * 32 + lane) * N;
+    const SegOut o = seg_run<T, N, true>(recs_of<T>(H) + d.roff, (int)d.l, (int)d.l,
+                                         H->hap_bases + d.hoff, (int)d.k, col0, lane, 31, 5,
+                                         pow, R, L, H->status);
+    if (lane == 0) sh.out[warp] = o;
+}
+
+// Combine the W segment partials of one pair: L * C = sum_s S_s 2^(E_s).
+template <typename T>
+__device__ __forceinline__ Partial cta_combine(const CtaShared<T>& sh, int w0, int W) {
+    int Eref = INT_MIN;
+    uint32_t f = 0;
+    for (int w = w0; w < w0 + W; ++w) {
+        f |= sh.out[w].flags;
+        if (sh.out[w].S != 0.0) Eref = max(Eref, sh.out[w].E);
+    }
+    double S = 0.0;
+    if (Eref == INT_MIN) Eref = sh.out[w0].E;
+    else
+        for (int w = w0; w < w0 + W; ++w)
+            if (sh.out[w].S != 0.0) S += ldexp(sh.out[w].S, sh.out[w].E - Eref);
+    Partial p;
+    p.S = S;
+    p.E = Eref;
+    p.flags = f | PF_DONE;
+    p.n_extra = 0;
+    p.extra_base = 0;
+    return p;
+}
+
+template <typename T>
+__device__ const typename Num<T>::Rec* dummy_rec();
+
+// One warp item: packed teams of short pairs.
+template <typename T, int N>
+__device__ __forceinline__ void warp_item_run(const BatchHeader* __restrict__ H,
+                                              const PowRow<T>* __restrict__ pow, uint32_t wi,
+                                              int R) {
+    using Rec = typename Num<T>::Rec;
+    const int lane = threadIdx.x & 31;
+    const WarpItem it = H->witems[wi];
+    int tbase = lane, tsize = 1, maxG = 1;
+    uint32_t pair = 0xffffffffu;
+    for (uint32_t t = 0; t < it.n_teams; ++t) {
+        const Team tm = H->teams[it.first_team + t];
+        maxG = max(maxG, (int)tm.size);
+        if (lane >= tm.base && lane < tm.base + tm.size) {
+            tbase = tm.base;
+            tsize = tm.size;
+            pair = tm.pair;
+        }
+    }
+    int nsteps = 0;
+    while ((1 << nsteps) < maxG) ++nsteps;
+    const int lt = lane - tbase, tlast = tbase + tsize - 1;
+    int l = 0, k = 0;
+    const Rec* rec = dummy_rec<T>();
+    const uint8_t* hap = H->hap_bases;
+    if (pair != 0xffffffffu) {
+        const PairDesc d = H->desc[pair];
+        l = (int)d.l;
+        k = (int)d.k;
+        rec = recs_of<T>(H) + d.roff;
+        hap = H->hap_bases + d.hoff;
+    }
+    const int lmax = (int)__reduce_max_sync(kFull, (unsigned)l);
+    SmemLink L{};
+    const SegOut o = seg_run<T, N, false>(rec, l, lmax, hap, k, lt * N, lt, tlast, nsteps, pow,
+                                          R, L, H->status);
+    if (pair != 0xffffffffu && lt == 0) {
+        Partial p;
+        p.S = o.S;
+        p.E = o.E;
+        p.flags = o.flags | PF_DONE;
+        p.n_extra = 0;
+        p.extra_base = 0;
+        H->parts[pair] = p;
+    }
+}
+
+// Persistent forward kernel: CTA items (multi-warp pairs, longest first), then warp
+// items (packed short pairs, longest first), both taken from atomic counters.
+template <typename T, int N>
+__global__ void __launch_bounds__(kCtaThreads, 1)
+k_forward(const BatchHeader* __restrict__ H, const PowRow<T>* __restrict__ pow) {
+    __shared__ CtaShared<T> sh;
+    const int R = checkpoint_interval<T>(H->dropgrow);
+    const uint32_t n_c = H->n_citems, n_w = H->n_witems;
+    for (;;) {
+        if (threadIdx.x == 0) sh.item = atomicAdd(&H->counters[0], 1u);
+        cta_clear<T>(sh);
+        __syncthreads();
+        const uint32_t it = sh.item;
+        if (it >= n_c) break;
+        const CtaItem ci = H->citems[it];
+        const int warp = threadIdx.x >> 5;
+        for (uint32_t q = 0; q < ci.n; ++q) {
+            const CtaPair cp = H->cpairs[ci.first + q];
+            if (warp >= cp.w0 && warp < cp.w0 + cp.W)
+                cta_pair_run<T, N>(H, pow, cp.pair, cp.w0, cp.W, sh, R);
+        }
+        __syncthreads();
+        if ((threadIdx.x & 31) == 0) {
+            for (uint32_t q = 0; q < ci.n; ++q) {
+                const CtaPair cp = H->cpairs[ci.first + q];
+                if (warp == cp.w0) H->parts[cp.pair] = cta_combine<T>(sh, cp.w0, cp.W);
+            }
+        }
+        __syncthreads();
+    }
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+        uint32_t wi = 0;
+        if (lane == 0) wi = atomicAdd(&H->counters[1], 1u);
+        wi = __shfl_sync(kFull, wi, 0);
+        if (wi >= n_w) break;
+        warp_item_run<T, N>(H, pow, wi, R);
+    }
+}
+
+// log10 L per pair (Eq. 4 with C divided out) and selection for the FP64 rescue pass.
+// mode: 0 FP32 + rescue, 1 FP64, 2 FP32 only.
+template <typename T>
+__global__ void k_finalize(const BatchHeader* __restrict__ H) {
+    using NT = Num<T>;
+    const uint32_t n = H->n_pairs;
+    const uint32_t mode = H->mode;
+    for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
+        const Partial q = H->parts[p];
+        const PairDesc d = H->desc[p];
+        uint32_t f = q.flags;
+        double v;
+        uint8_t of = 0;
+        bool rescue = false;
+        if (!(f & PF_DONE)) {
+            v = NAN;
+            of |= 0x80u;
+            atomicOr(H->status, ST_TOO_LONG);
+        } else if (f & PF_BAD) {
+            v = NAN;
+            of |= 0x80u;
+            atomicOr(H->status, ST_BAD_INPUT);
+        } else {
+            if (q.S > 0.0 && isfinite(q.S))
+                v = log10(q.S) + (double)(q.E - NT::kLog2C) * 0.30102999566398119521;
+            else
+                v = q.S == 0.0 ? -INFINITY : NAN;
+            if (f & PF_RESCALED) of |= 0x2u;
+            if (mode == 1) of |= 0x4u;
+            if (f & PF_TIMEOUT) of |= 0x80u;
+            if (mode == 0) {
+                // Underflow test (the FP32 sum in stored units against 1e4 * 3 l k FLT_MIN)
+                // plus the kernel's own danger / non-finite / degenerate flags.
+                const double tau = 3.0e4 * (double)d.l * (double)d.k * 1.1754943508222875e-38;
+                if (f & PF_DANGER) of |= 0x8u;
+                if ((f & PF_NONFINITE) || !isfinite(q.S)) of |= 0x10u;
+                if (!(q.S > tau)) of |= 0x20u;
+                if (f & PF_DEGEN) of |= 0x40u;
+                rescue = H->force_rescue || (of & 0x78u) || !isfinite(v);
+            } else if (!isfinite(q.S)) {
+                atomicOr(H->status, ST_NONFINITE);
+            }
+        }
+        H->out[p] = v;
+        H->out_flags[p] = of;
+        if (rescue) {
+            const uint32_t idx = atomicAdd(&H->counters[2], 1u);
+            H->rescue_list[idx] = p;
+        }
+    }
+}
+
+}  // namespace phmm

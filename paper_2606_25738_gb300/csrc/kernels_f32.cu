@@ -1,0 +1,118 @@
+// FP32 instantiation: coefficient prep (double-float + stochastic rounding), the
+// persistent FP32 forward kernel for N = 16 / 24 / 32 columns per lane, finalize, and
+// the scan test.
+#include "kernels.cuh"
+#include "launch.h"
+
+namespace phmm {
+
+__device__ Rec32 g_dummy32;
+
+template <>
+__device__ const Rec32* dummy_rec<float>() { return &g_dummy32; }
+
+__global__ void k_reset(const BatchHeader* __restrict__ H) {
+    if (threadIdx.x < 4) H->counters[threadIdx.x] = 0u;
+    if (threadIdx.x == 0) {
+        H->status[0] = 0u;
+        H->dropgrow[0] = 0u;
+        H->dropgrow[1] = 0u;
+    }
+}
+
+// One record per read base, plus pair descriptors and the batch's drop / grow maxima.
+__global__ void __launch_bounds__(256) k_prep32(const BatchHeader* __restrict__ H,
+                                                const PhredTables* __restrict__ TG) {
+    __shared__ float2 tq[kPhredTab], tom[kPhredTab], tq3[kPhredTab], tinv[kPhredTab];
+    for (int i = threadIdx.x; i < kPhredTab; i += blockDim.x) {
+        const df a = to_df(TG->q[i]), b = to_df(TG->om[i]), c = to_df(TG->q3[i]),
+                 d = to_df(TG->inv[i]);
+        tq[i] = make_float2(a.hi, a.lo);
+        tom[i] = make_float2(b.hi, b.lo);
+        tq3[i] = make_float2(c.hi, c.lo);
+        tinv[i] = make_float2(d.hi, d.lo);
+    }
+    __syncthreads();
+    uint32_t dmax = 0, gmax = 0;
+    const uint64_t n = H->n_read_bases;
+    const uint32_t seed = H->seed;
+    for (uint64_t b = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; b < n;
+         b += (uint64_t)gridDim.x * blockDim.x) {
+        const BaseQ x = base_inputs(H, b);
+        const Rec32 r = make_rec32(x, tq, tom, tq3, tinv, seed, b);
+        float4* dst = reinterpret_cast<float4*>(H->rec32 + b);
+        dst[0] = make_float4(r.pm, r.px, r.a, r.b);
+        dst[1] = make_float4(r.mi, r.g, r.gm, __uint_as_float(r.meta));
+        if (x.bad) atomicOr(H->status, ST_BAD_INPUT);
+        const float qi = tq[x.ins].x, qd = tq[x.del].x, qg = tq[x.gcp].x;
+        const float drop = -log2f(fminf(qi, qg));
+        const float grow = log2f(fmaxf(fabsf(1.0f - qi - qd) + (1.0f - qg) + qd, qi + qg));
+        dmax = max(dmax, (uint32_t)ceilf(fmaxf(drop, 0.0f) * 64.0f) + 1u);
+        gmax = max(gmax, (uint32_t)ceilf(fmaxf(grow, 0.0f) * 64.0f) + 1u);
+    }
+    block_max2(dmax, gmax, H->dropgrow);
+    build_desc(H);
+}
+
+template __global__ void k_forward<float, 16>(const BatchHeader*, const PowRow<float>*);
+template __global__ void k_forward<float, 24>(const BatchHeader*, const PowRow<float>*);
+template __global__ void k_forward<float, 32>(const BatchHeader*, const PowRow<float>*);
+template __global__ void k_finalize<float>(const BatchHeader*);
+
+// Scan test: one warp, lane t owns y[32t .. 32t+31]; `row` is in global memory.
+__global__ void k_scan_test(const float* __restrict__ y, float* __restrict__ z, int n,
+                            const PowRow<float>* __restrict__ row) {
+    const int lane = threadIdx.x & 31;
+    Pow<float> pw;
+    pw.row = row;
+    pw.gcp = 0;
+    const float a = row->pad1;  // the multiplier itself
+    float loc[32];
+    float v = 0.0f;
+#pragma unroll
+    for (int c = 0; c < 32; ++c) {
+        const int e = lane * 32 + c;
+        v = fmaf(a, v, e < n ? y[e] : 0.0f);
+        loc[c] = v;
+    }
+    const float Z = team_scan<float>(v, lane, pw, 5);
+    float W = __shfl_up_sync(kFull, Z, 1);
+    if (lane == 0) W = 0.0f;
+#pragma unroll
+    for (int c = 0; c < 32; ++c) {
+        W *= a;
+        const int e = lane * 32 + c;
+        if (e < n) z[e] = loc[c] + W;
+    }
+}
+
+void launch_reset(const BatchHeader* H, cudaStream_t s) { k_reset<<<1, 32, 0, s>>>(H); }
+
+void launch_prep32(const BatchHeader* H, const PhredTables* T, int grid, cudaStream_t s) {
+    k_prep32<<<grid, 256, 0, s>>>(H, T);
+}
+
+void launch_forward32(int N, const BatchHeader* H, const void* pow, int grid, cudaStream_t s) {
+    const PowRow<float>* p = static_cast<const PowRow<float>*>(pow);
+    if (N == 16) k_forward<float, 16><<<grid, kCtaThreads, 0, s>>>(H, p);
+    else if (N == 24) k_forward<float, 24><<<grid, kCtaThreads, 0, s>>>(H, p);
+    else k_forward<float, 32><<<grid, kCtaThreads, 0, s>>>(H, p);
+}
+
+int occupancy_forward32(int N) {
+    int b = 0;
+    if (N == 16) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_forward<float, 16>, kCtaThreads, 0);
+    else if (N == 24) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_forward<float, 24>, kCtaThreads, 0);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_forward<float, 32>, kCtaThreads, 0);
+    return b > 0 ? b : 1;
+}
+
+void launch_finalize32(const BatchHeader* H, int grid, cudaStream_t s) {
+    k_finalize<float><<<grid, 256, 0, s>>>(H);
+}
+
+void launch_scan_test(const float* y, float* z, int n, const void* pow_row, cudaStream_t s) {
+    k_scan_test<<<1, 32, 0, s>>>(y, z, n, static_cast<const PowRow<float>*>(pow_row));
+}
+
+}  // namespace phmm

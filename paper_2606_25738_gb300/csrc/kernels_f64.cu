@@ -1,0 +1,136 @@
+// FP64 instantiation: prep of FP64 records (all reads, or only the reads of pairs
+// selected for rescue), the FP64 forward kernel, the rescue pass, the one-launch-per-
+// pair comparator kernel and finalize.
+#include "kernels.cuh"
+#include "launch.h"
+
+namespace phmm {
+
+__device__ Rec64 g_dummy64;
+
+template <>
+__device__ const Rec64* dummy_rec<double>() { return &g_dummy64; }
+
+__global__ void __launch_bounds__(256) k_prep64_all(const BatchHeader* __restrict__ H,
+                                                    const PhredTables* __restrict__ TG) {
+    __shared__ PhredTables T;
+    load_tables(TG, T);
+    __syncthreads();
+    uint32_t dmax = 0, gmax = 0;
+    const uint64_t n = H->n_read_bases;
+    for (uint64_t b = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; b < n;
+         b += (uint64_t)gridDim.x * blockDim.x) {
+        const BaseQ x = base_inputs(H, b);
+        H->rec64[b] = make_rec64(x, T);
+        if (x.bad) atomicOr(H->status, ST_BAD_INPUT);
+        uint32_t d, g;
+        drop_grow(x, T, d, g);
+        dmax = max(dmax, d);
+        gmax = max(gmax, g);
+    }
+    block_max2(dmax, gmax, H->dropgrow);
+    build_desc(H);
+}
+
+// Records of the reads of the pairs selected for rescue (one block per pair).
+__global__ void __launch_bounds__(256) k_prep64_list(const BatchHeader* __restrict__ H,
+                                                     const PhredTables* __restrict__ TG) {
+    __shared__ PhredTables T;
+    load_tables(TG, T);
+    __syncthreads();
+    const uint32_t n = H->counters[2];
+    for (uint32_t r = blockIdx.x; r < n; r += gridDim.x) {
+        const PairDesc d = H->desc[H->rescue_list[r]];
+        for (uint32_t i = threadIdx.x; i < d.l; i += blockDim.x) {
+            const uint64_t b = d.roff + i;
+            H->rec64[b] = make_rec64(base_inputs(H, b), T);
+        }
+    }
+}
+
+template __global__ void k_forward<double, kN64>(const BatchHeader*, const PowRow<double>*);
+template __global__ void k_finalize<double>(const BatchHeader*);
+
+__device__ __forceinline__ double log10_of(const Partial& q) {
+    if (q.S > 0.0 && isfinite(q.S))
+        return log10(q.S) + (double)(q.E - Num<double>::kLog2C) * 0.30102999566398119521;
+    return q.S == 0.0 ? -INFINITY : NAN;
+}
+
+// FP64 rescue pass: one CTA per selected pair, persistent over the rescue list.
+__global__ void __launch_bounds__(kCtaThreads, 1)
+k_rescue(const BatchHeader* __restrict__ H, const PowRow<double>* __restrict__ pow) {
+    __shared__ CtaShared<double> sh;
+    const int R = checkpoint_interval<double>(H->dropgrow);
+    const uint32_t n = H->counters[2];
+    for (;;) {
+        if (threadIdx.x == 0) sh.item = atomicAdd(&H->counters[3], 1u);
+        cta_clear<double>(sh);
+        __syncthreads();
+        const uint32_t r = sh.item;
+        if (r >= n) break;
+        const uint32_t p = H->rescue_list[r];
+        const PairDesc d = H->desc[p];
+        const int W = (int)((d.k + 32u * kN64 - 1u) / (32u * kN64));
+        if (W <= kCtaWarps) cta_pair_run<double, kN64>(H, pow, p, 0, W, sh, R);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            uint8_t of = (uint8_t)((H->out_flags[p] & 0x78u) | 0x1u | 0x4u);
+            double v;
+            if (W > kCtaWarps) {
+                v = NAN;
+                of |= 0x80u;
+                atomicOr(H->status, ST_TOO_LONG);
+            } else {
+                const Partial q = cta_combine<double>(sh, 0, W);
+                v = log10_of(q);
+                if (q.flags & PF_RESCALED) of |= 0x2u;
+                if (q.flags & (PF_TIMEOUT | PF_BAD)) of |= 0x80u;
+                if (!isfinite(q.S)) atomicOr(H->status, ST_NONFINITE);
+            }
+            H->out[p] = v;
+            H->out_flags[p] = of;
+        }
+        __syncthreads();
+    }
+}
+
+// Plain FP64 comparator: one launch (one CTA) per pair.
+__global__ void __launch_bounds__(kCtaThreads, 1)
+k_single(const BatchHeader* __restrict__ H, const PowRow<double>* __restrict__ pow, uint32_t pair) {
+    __shared__ CtaShared<double> sh;
+    const int R = checkpoint_interval<double>(H->dropgrow);
+    cta_clear<double>(sh);
+    __syncthreads();
+    const PairDesc d = H->desc[pair];
+    const int W = (int)((d.k + 32u * kN64 - 1u) / (32u * kN64));
+    if (W <= kCtaWarps) cta_pair_run<double, kN64>(H, pow, pair, 0, W, sh, R);
+    __syncthreads();
+    if (threadIdx.x == 0 && W <= kCtaWarps) H->parts[pair] = cta_combine<double>(sh, 0, W);
+}
+
+void launch_prep64_all(const BatchHeader* H, const PhredTables* T, int grid, cudaStream_t s) {
+    k_prep64_all<<<grid, 256, 0, s>>>(H, T);
+}
+void launch_prep64_list(const BatchHeader* H, const PhredTables* T, int grid, cudaStream_t s) {
+    k_prep64_list<<<grid, 256, 0, s>>>(H, T);
+}
+void launch_forward64(const BatchHeader* H, const void* pow, int grid, cudaStream_t s) {
+    k_forward<double, kN64><<<grid, kCtaThreads, 0, s>>>(H, static_cast<const PowRow<double>*>(pow));
+}
+void launch_finalize64(const BatchHeader* H, int grid, cudaStream_t s) {
+    k_finalize<double><<<grid, 256, 0, s>>>(H);
+}
+void launch_rescue64(const BatchHeader* H, const void* pow, int grid, cudaStream_t s) {
+    k_rescue<<<grid, kCtaThreads, 0, s>>>(H, static_cast<const PowRow<double>*>(pow));
+}
+void launch_single64(const BatchHeader* H, const void* pow, uint32_t pair, cudaStream_t s) {
+    k_single<<<1, kCtaThreads, 0, s>>>(H, static_cast<const PowRow<double>*>(pow), pair);
+}
+int occupancy_forward64() {
+    int b = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_forward<double, kN64>, kCtaThreads, 0);
+    return b > 0 ? b : 1;
+}
+
+}  // namespace phmm

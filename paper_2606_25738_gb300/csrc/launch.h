@@ -1,0 +1,32 @@
+// Host-side launchers of the kernels (defined in kernels_f32.cu / kernels_f64.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "phmm_internal.h"
+
+namespace phmm {
+
+struct PhredTables;
+
+// FP32 unit
+void launch_reset(const BatchHeader* H, cudaStream_t s);
+void launch_prep32(const BatchHeader* H, const PhredTables* T, int grid, cudaStream_t s);
+void launch_forward32(int N, const BatchHeader* H, const void* pow, int grid, cudaStream_t s);
+void launch_finalize32(const BatchHeader* H, int grid, cudaStream_t s);
+int occupancy_forward32(int N);  // resident CTAs per SM
+// pow_row: a device pointer to one PowRow<float>
+void launch_scan_test(const float* y, float* z, int n, const void* pow_row, cudaStream_t s);
+
+// FP64 unit
+void launch_prep64_all(const BatchHeader* H, const PhredTables* T, int grid, cudaStream_t s);
+void launch_prep64_list(const BatchHeader* H, const PhredTables* T, int grid, cudaStream_t s);
+void launch_forward64(const BatchHeader* H, const void* pow, int grid, cudaStream_t s);
+void launch_finalize64(const BatchHeader* H, int grid, cudaStream_t s);
+void launch_rescue64(const BatchHeader* H, const void* pow, int grid, cudaStream_t s);
+void launch_single64(const BatchHeader* H, const void* pow, uint32_t pair, cudaStream_t s);
+int occupancy_forward64();
+
+constexpr int kN64 = 8;   // columns per lane of the FP64 kernels
+
+}  // namespace phmm

@@ -1,0 +1,165 @@
+// Internal data structures shared by the host runtime and the CUDA kernels of the
+// row-wise PairHMM library.  Nothing here is part of the public C ABI (include/phmm.h).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace phmm {
+
+// ----------------------------------------------------------------------------------
+// Per read-row coefficient records, written by the prep kernels, one per read base,
+// in the layout of the concatenated reads (record of row i of read r sits at
+// read_off[r] + i - 1).
+//
+// FP32 record (factored form of Eq. 2 for row i, see engine.cuh):
+//   pm = (1 - e_i)(1 - g_i), px = (e_i / 3)(1 - g_i)        match / mismatch factor
+//   a  = T_MM_i / (1 - g_i)                                  M -> M over I/D weight
+//   b  = T_MD_{i-1}                                          D-hat -> D of row i-1
+//   mi = T_MI_i, g = T_II_i = T_DD_i, gm = 1 - g_i
+// FP64 record (unfactored, robust for g = 1):
+//   pm = 1 - e_i, px = e_i / 3, a = T_MM_i, b = T_MD_{i-1}, mi, g, gm as above.
+// meta: bits 0..2 read base code (A=0 C=1 G=2 T=3 N=4), bits 8..15 gcp Phred
+// (row of the power table), META_DEGEN, META_BAD.
+// ----------------------------------------------------------------------------------
+struct alignas(16) Rec32 {
+    float pm, px, a, b, mi, g, gm;
+    uint32_t meta;
+};
+struct alignas(16) Rec64 {
+    double pm, px, a, b, mi, g, gm;
+    uint64_t meta;
+};
+
+constexpr uint32_t META_CODE_MASK = 0x7u;
+constexpr int META_GCP_SHIFT = 8;
+constexpr uint32_t META_DEGEN = 1u << 16;  // 1 - g_i too small for the factored form
+constexpr uint32_t META_BAD = 1u << 17;    // invalid base or quality > 93
+
+constexpr int kMaxPhred = 93;
+constexpr int kPhredTab = 96;  // table rows (>= kMaxPhred + 1)
+
+// Per-pair descriptor (built on the device from the pair index and the offsets).
+struct PairDesc {
+    uint64_t roff;  // offset of the read's first base / record
+    uint64_t hoff;  // offset of the haplotype's first base
+    uint32_t l;     // read length (rows)
+    uint32_t k;     // haplotype length (columns)
+};
+
+// Partial result of one segment (a team or one warp of a multi-warp pair):
+// L * C = S * 2^E summed over its columns of the last row (Eq. 4).
+struct alignas(16) Partial {
+    double S;
+    int32_t E;
+    uint32_t flags;      // PF_* below
+    uint32_t n_extra;    // segment 0 of a multi-warp pair: number of further partials
+    uint32_t extra_base; // ... and where they start in the partial array
+};
+
+// Partial / pair flags (device side)
+constexpr uint32_t PF_DONE = 1u << 0;       // written
+constexpr uint32_t PF_DANGER = 1u << 1;     // a checkpoint row max fell below the danger level
+constexpr uint32_t PF_NONFINITE = 1u << 2;  // inf / nan met
+constexpr uint32_t PF_DEGEN = 1u << 3;      // factored FP32 form not applicable
+constexpr uint32_t PF_BAD = 1u << 4;        // invalid input
+constexpr uint32_t PF_RESCALED = 1u << 5;   // a power-of-two rescale happened
+constexpr uint32_t PF_TIMEOUT = 1u << 6;    // a bounded wait gave up
+constexpr uint32_t PF_TOO_LONG = 1u << 7;   // pair exceeds what this kernel can hold
+
+// Device status word bits
+constexpr uint32_t ST_BAD_INPUT = 1u << 0;
+constexpr uint32_t ST_TIMEOUT = 1u << 1;
+constexpr uint32_t ST_TOO_LONG = 1u << 2;
+constexpr uint32_t ST_NONFINITE = 1u << 3;
+
+// ----------------------------------------------------------------------------------
+// Work plan (host-built).
+//   Short pairs (k <= 32 N): a team of G = ceil(k / N) lanes; teams are packed into
+//   warps (sum of G <= 32).  A warp item lists its teams.
+//   Long pairs (k > 32 N): W = ceil(k / (32 N)) warps of one CTA (W <= kCtaWarps),
+//   one warp per column segment, carries passed through shared memory.  A CTA item
+//   lists pairs with their warp ranges.
+// ----------------------------------------------------------------------------------
+constexpr int kCtaWarps = 16;
+constexpr int kCtaThreads = kCtaWarps * 32;
+constexpr int kRing = 8;  // rows buffered between two warp segments
+
+struct Team {
+    uint32_t pair;
+    uint8_t base;   // first lane
+    uint8_t size;   // lanes (G)
+    uint16_t pad;
+};
+struct WarpItem {
+    uint32_t first_team;
+    uint32_t n_teams;
+};
+struct CtaPair {
+    uint32_t pair;
+    uint8_t w0;     // first warp
+    uint8_t W;      // warps
+    uint16_t pad;
+    uint32_t extra_base;  // partial slots of segments 1..W-1
+};
+struct CtaItem {
+    uint32_t first;
+    uint32_t n;
+};
+
+// Power table row for one gcp Phred value g = q(gcp) and one N (columns per lane):
+// every power p is stored as two factors p1 * p2 = p so that a product v * p1 * p2 stays
+// representable whenever v * p is (see engine.cuh, scan).
+template <typename T>
+struct PowRow {
+    T sp1[5], sp2[5];   // g^(N * 2^s), s = 0..4: Kogge-Stone steps
+    T lp1[32], lp2[32]; // g^(N * t), t = 0..31: segment carry into lane t
+    T last1, last2;     // g^(N - 1): from a lane's first column to its last
+    T pad1, pad2;
+};
+
+// Phred tables staged in shared memory by the prep kernels.  Each value is a pair
+// (hi, lo) with hi + lo the FP64 value (host-computed), so FP32 prep can form the
+// record coefficients in double-float arithmetic and round them stochastically.
+//   q[x] = 10^(-x/10)      om[x] = 1 - q[x]      q3[x] = q[x] / 3      inv[x] = 1 / om[x]
+// ------------------------------------------------------------------------------------
+struct PhredTables {
+    double q[kPhredTab], om[kPhredTab], q3[kPhredTab], inv[kPhredTab];
+};
+
+// Everything a batch's kernels read, in one device-resident header (so a captured CUDA
+// graph stays valid while arrays move).
+struct BatchHeader {
+    // inputs (device pointers)
+    const uint8_t *read_bases, *base_q, *ins_q, *del_q, *gcp_q, *hap_bases;
+    const uint64_t *read_off, *hap_off;
+    const uint32_t *pair_read, *pair_hap;
+    uint64_t n_read_bases;
+    uint32_t n_reads, n_haps, n_pairs;
+    // derived
+    PairDesc *desc;
+    Rec32 *rec32;
+    Rec64 *rec64;
+    // plan
+    const WarpItem *witems;
+    const Team *teams;
+    const CtaItem *citems;
+    const CtaPair *cpairs;
+    uint32_t n_witems, n_citems;
+    uint32_t n_partials;
+    uint32_t force_rescue;   // 1: every pair goes to the FP64 rescue pass
+    Partial *parts;
+    // outputs
+    double *out;             // n_pairs log10 L
+    uint8_t *out_flags;      // n_pairs PHMM_PAIR_* bits
+    uint32_t *rescue_list;   // pairs needing the FP64 pass
+    // scratch counters (zeroed per launch by k_reset)
+    uint32_t *counters;      // [0] CTA items [1] warp items [2] rescue count [3] rescue items
+    uint32_t *status;        // ST_* bits
+    uint32_t *dropgrow;      // [0] max drop bits * 64, [1] max grow bits * 64 (prep)
+    uint32_t seed;
+    uint32_t mode;           // 0 FP32+rescue, 1 FP64, 2 FP32 only
+};
+
+}  // namespace phmm

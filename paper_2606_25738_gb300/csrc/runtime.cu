@@ -1,0 +1,834 @@
+// Host runtime of the row-wise PairHMM library: the C ABI of include/phmm.h, contexts,
+// per-ticket device arenas, the work planner (length buckets and team packing), the
+// built-in tuner for N, CUDA-graph capture and replay, and ticket polling.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <limits>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+#include "launch.h"
+#include "phmm.h"
+#include "phmm_internal.h"
+
+using namespace phmm;
+
+namespace {
+
+// ------------------------------------------------------------------------------------
+// Buffers
+// ------------------------------------------------------------------------------------
+struct DevBuf {
+    void* p = nullptr;
+    size_t cap = 0;
+};
+struct HostBuf {
+    void* p = nullptr;
+    size_t cap = 0;
+};
+
+cudaError_t ensure(DevBuf& b, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    if (bytes <= b.cap) return cudaSuccess;
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.cap = 0;
+    const size_t nb = std::max(bytes, (size_t)4096);
+    cudaError_t e = cudaMalloc(&b.p, nb);
+    if (e != cudaSuccess) {
+        b.p = nullptr;
+        return e;
+    }
+    b.cap = nb;
+    return cudaSuccess;
+}
+cudaError_t ensure(HostBuf& b, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    if (bytes <= b.cap) return cudaSuccess;
+    if (b.p) cudaFreeHost(b.p);
+    b.p = nullptr;
+    b.cap = 0;
+    cudaError_t e = cudaMallocHost(&b.p, bytes);
+    if (e != cudaSuccess) {
+        b.p = nullptr;
+        return e;
+    }
+    b.cap = bytes;
+    return cudaSuccess;
+}
+void release(DevBuf& b) {
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.cap = 0;
+}
+void release(HostBuf& b) {
+    if (b.p) cudaFreeHost(b.p);
+    b.p = nullptr;
+    b.cap = 0;
+}
+
+// ------------------------------------------------------------------------------------
+// Work plan
+// ------------------------------------------------------------------------------------
+struct Plan {
+    std::vector<Team> teams;
+    std::vector<WarpItem> witems;
+    std::vector<CtaPair> cpairs;
+    std::vector<CtaItem> citems;
+    uint32_t n_long = 0, n_too_long = 0;
+    double cost = 0.0;  // tuner cost model (lane-cell slots + per-row overheads)
+    int N = 0;
+};
+
+// Cost model constants (issue slots): per lane and cell of a row, and per lane and row
+// (scan, shuffles, record loads, checkpoint share).
+constexpr double kCellCost = 8.0;
+constexpr double kRowCost = 70.0;
+
+// Short pairs: teams of G = ceil(k/N) lanes, packed best-fit into 32-lane warps within
+// runs of similar read length (rows of a warp are the max over its teams).  Long pairs:
+// W = ceil(k / 32N) warps of one CTA, packed best-fit into 16-warp CTAs.
+void make_plan(const uint32_t* l, const uint32_t* k, uint32_t n, int N, Plan& P) {
+    P = Plan();
+    P.N = N;
+    const uint32_t short_max = 32u * (uint32_t)N;
+    std::vector<uint32_t> sh, lo;
+    sh.reserve(n);
+    for (uint32_t p = 0; p < n; ++p) {
+        if (k[p] <= short_max) sh.push_back(p);
+        else if ((k[p] + short_max - 1) / short_max <= (uint32_t)kCtaWarps) lo.push_back(p);
+        else P.n_too_long++;
+    }
+    auto G_of = [&](uint32_t p) { return (k[p] + (uint32_t)N - 1) / (uint32_t)N; };
+    std::stable_sort(sh.begin(), sh.end(), [&](uint32_t a, uint32_t b) {
+        if (l[a] != l[b]) return l[a] > l[b];
+        return G_of(a) > G_of(b);
+    });
+    // runs of similar l
+    size_t i = 0;
+    struct Bin {
+        uint32_t first_team, n_teams, rem, lmax;
+    };
+    std::vector<Bin> bins;
+    std::vector<std::vector<uint32_t>> open(33);
+    std::vector<std::vector<Team>> bin_teams;
+    while (i < sh.size()) {
+        const uint32_t l0 = l[sh[i]];
+        size_t j = i;
+        while (j < sh.size() && (double)l[sh[j]] >= 0.94 * (double)l0) ++j;
+        std::vector<uint32_t> run(sh.begin() + i, sh.begin() + j);
+        std::stable_sort(run.begin(), run.end(), [&](uint32_t a, uint32_t b) { return G_of(a) > G_of(b); });
+        bins.clear();
+        bin_teams.clear();
+        for (auto& o : open) o.clear();
+        for (uint32_t p : run) {
+            const uint32_t G = G_of(p);
+            int r = -1;
+            for (uint32_t c = G; c <= 32; ++c)
+                if (!open[c].empty()) {
+                    r = (int)c;
+                    break;
+                }
+            uint32_t b;
+            if (r < 0) {
+                b = (uint32_t)bins.size();
+                bins.push_back({0, 0, 32, 0});
+                bin_teams.emplace_back();
+            } else {
+                b = open[r].back();
+                open[r].pop_back();
+            }
+            Team t;
+            t.pair = p;
+            t.base = (uint8_t)(32 - bins[b].rem);
+            t.size = (uint8_t)G;
+            t.pad = 0;
+            bin_teams[b].push_back(t);
+            bins[b].rem -= G;
+            bins[b].lmax = std::max(bins[b].lmax, l[p]);
+            if (bins[b].rem > 0) open[bins[b].rem].push_back(b);
+        }
+        for (size_t b = 0; b < bins.size(); ++b) {
+            WarpItem w;
+            w.first_team = (uint32_t)P.teams.size();
+            w.n_teams = (uint32_t)bin_teams[b].size();
+            for (const Team& t : bin_teams[b]) P.teams.push_back(t);
+            P.witems.push_back(w);
+            P.cost += (double)bins[b].lmax * 32.0 * (N * kCellCost + kRowCost);
+        }
+        i = j;
+    }
+    // long pairs
+    P.n_long = (uint32_t)lo.size();
+    auto W_of = [&](uint32_t p) { return (k[p] + short_max - 1) / short_max; };
+    std::stable_sort(lo.begin(), lo.end(), [&](uint32_t a, uint32_t b) {
+        const double ca = (double)l[a] * W_of(a), cb = (double)l[b] * W_of(b);
+        return ca > cb;
+    });
+    struct CBin {
+        std::vector<CtaPair> pairs;
+        uint32_t rem, lmax;
+    };
+    std::vector<CBin> cb;
+    std::vector<std::vector<uint32_t>> copen(kCtaWarps + 1);
+    size_t a = 0;
+    while (a < lo.size()) {
+        const uint32_t l0 = l[lo[a]];
+        size_t b2 = a;
+        while (b2 < lo.size() && (double)l[lo[b2]] >= 0.9 * (double)l0) ++b2;
+        cb.clear();
+        for (auto& o : copen) o.clear();
+        for (size_t q = a; q < b2; ++q) {
+            const uint32_t p = lo[q], W = W_of(p);
+            int r = -1;
+            for (uint32_t c = W; c <= (uint32_t)kCtaWarps; ++c)
+                if (!copen[c].empty()) {
+                    r = (int)c;
+                    break;
+                }
+            uint32_t bi;
+            if (r < 0) {
+                bi = (uint32_t)cb.size();
+                cb.push_back({{}, (uint32_t)kCtaWarps, 0});
+            } else {
+                bi = copen[r].back();
+                copen[r].pop_back();
+            }
+            CtaPair cp;
+            cp.pair = p;
+            cp.w0 = (uint8_t)(kCtaWarps - cb[bi].rem);
+            cp.W = (uint8_t)W;
+            cp.pad = 0;
+            cp.extra_base = 0;
+            cb[bi].pairs.push_back(cp);
+            cb[bi].rem -= W;
+            cb[bi].lmax = std::max(cb[bi].lmax, l[p]);
+            if (cb[bi].rem > 0) copen[cb[bi].rem].push_back(bi);
+        }
+        for (auto& c : cb) {
+            CtaItem it;
+            it.first = (uint32_t)P.cpairs.size();
+            it.n = (uint32_t)c.pairs.size();
+            for (auto& cp : c.pairs) P.cpairs.push_back(cp);
+            P.citems.push_back(it);
+            P.cost += (double)c.lmax * kCtaWarps * 32.0 * (N * kCellCost + kRowCost);
+        }
+        a = b2;
+    }
+}
+
+// ------------------------------------------------------------------------------------
+// Host-side tables
+// ------------------------------------------------------------------------------------
+void build_phred_tables(PhredTables& T) {
+    for (int x = 0; x < kPhredTab; ++x) {
+        const int q = std::min(x, kMaxPhred);
+        const double v = std::pow(10.0, -(double)q / 10.0);
+        T.q[x] = v;
+        T.om[x] = 1.0 - v;
+        T.q3[x] = v / 3.0;
+        T.inv[x] = 1.0 / (1.0 - v);  // inf for x = 0 (g = 1): flagged as degenerate
+    }
+}
+
+// Split power g^m (g = q(gcp)) into two factors whose product is g^m, each normal when
+// g^m >= min_normal^2 (see PowRow).
+template <typename T>
+void split_pow(int gcp, double m, T& p1, T& p2) {
+    const double lg = -(double)gcp / 10.0 * m;  // log10 of g^m
+    const double min_lg = std::log10((double)std::numeric_limits<T>::min());
+    if (lg >= min_lg) {
+        p1 = (T)std::pow(10.0, lg);
+        p2 = (T)1;
+    } else {
+        const double h = std::pow(10.0, lg / 2.0);
+        p1 = (T)h;
+        p2 = (T)h;
+    }
+}
+
+template <typename T>
+void build_pow_table(int N, std::vector<PowRow<T>>& out) {
+    out.assign(kPhredTab, PowRow<T>());
+    for (int x = 0; x < kPhredTab; ++x) {
+        const int gq = std::min(x, kMaxPhred);
+        PowRow<T>& r = out[x];
+        for (int s = 0; s < 5; ++s) split_pow<T>(gq, (double)N * (double)(1 << s), r.sp1[s], r.sp2[s]);
+        for (int t = 0; t < 32; ++t) split_pow<T>(gq, (double)N * t, r.lp1[t], r.lp2[t]);
+        split_pow<T>(gq, (double)(N - 1), r.last1, r.last2);
+        r.pad1 = (T)std::pow(10.0, -(double)gq / 10.0);
+        r.pad2 = (T)0;
+    }
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------------------
+// Context
+// ------------------------------------------------------------------------------------
+struct Slot {
+    DevBuf in_bases, in_bq, in_iq, in_dq, in_gq, in_hap, in_roff, in_hoff, in_pr, in_ph;
+    DevBuf desc, rec32, rec64, teams, witems, cpairs, citems, parts, out, oflags, rescue;
+    DevBuf small;  // counters[4], status[1], dropgrow[2]
+    DevBuf hdr;
+    HostBuf h_out, h_oflags, h_small, h_roff, h_hoff, h_pr, h_ph;
+    BatchHeader hh;
+    cudaEvent_t ev_copy = nullptr, ev_start = nullptr, ev_fwd0 = nullptr, ev_fwd1 = nullptr,
+                ev_res0 = nullptr, ev_res1 = nullptr, ev_end = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    int g_key = -1;
+    uint64_t ticket = 0;
+    int state = 0;  // 0 free, 1 pending
+    double* user_out = nullptr;
+    uint8_t* user_flags = nullptr;
+    bool out_on_dev = false;
+    uint32_t n_pairs = 0;
+    phmm_stats st{};
+    bool has_stats = false;
+    int host_status = PHMM_OK;
+};
+
+struct phmm_ctx {
+    int dev = 0;
+    phmm_config cfg{};
+    cudaStream_t stream = nullptr, copy_stream = nullptr;
+    bool own_stream = false;
+    std::mutex mu;
+    std::vector<Slot> slots;
+    uint64_t next_ticket = 0;
+    int sms = 0;
+    double max_mhz = 0.0;
+    size_t budget = 0;
+    DevBuf tables;                          // PhredTables
+    DevBuf scan_row;                        // scan test: one PowRow<float> (global memory)
+    DevBuf pow32[3];                        // N = 16, 24, 32
+    DevBuf pow64;
+    int occ32[3] = {1, 1, 1}, occ64 = 1;
+    bool dead = false;
+    uint32_t seed = 0x5eed1234u;
+    uint64_t last_retired = 0;
+    phmm_stats last_stats{};
+};
+
+namespace {
+
+const int kNs[3] = {16, 24, 32};
+int n_index(int N) { return N == 16 ? 0 : N == 24 ? 1 : 2; }
+
+#define CK(x)                                   \
+    do {                                        \
+        cudaError_t e_ = (x);                   \
+        if (e_ != cudaSuccess) {                \
+            ctx->dead = true;                   \
+            return PHMM_ECUDA;                  \
+        }                                       \
+    } while (0)
+
+int launch_sequence(phmm_ctx* ctx, Slot& S, int N, bool record_events) {
+    cudaStream_t s = ctx->stream;
+    const BatchHeader* H = static_cast<const BatchHeader*>(S.hdr.p);
+    const PhredTables* T = static_cast<const PhredTables*>(ctx->tables.p);
+    const int prec = ctx->cfg.precision;
+    const int grid_pre = ctx->sms * 4;
+    auto rec = [&](cudaEvent_t ev) {
+        if (record_events) return cudaEventRecordWithFlags(ev, s, cudaEventRecordExternal);
+        return cudaEventRecord(ev, s);
+    };
+    launch_reset(H, s);
+    if (prec == PHMM_PREC_FP64) {
+        launch_prep64_all(H, T, grid_pre, s);
+        CK(rec(S.ev_fwd0));
+        launch_forward64(H, ctx->pow64.p, ctx->sms * ctx->occ64, s);
+        CK(rec(S.ev_fwd1));
+        launch_finalize64(H, grid_pre, s);
+        CK(rec(S.ev_res0));
+        CK(rec(S.ev_res1));
+    } else {
+        launch_prep32(H, T, grid_pre, s);
+        CK(rec(S.ev_fwd0));
+        launch_forward32(N, H, ctx->pow32[n_index(N)].p, ctx->sms * ctx->occ32[n_index(N)], s);
+        CK(rec(S.ev_fwd1));
+        launch_finalize32(H, grid_pre, s);
+        CK(rec(S.ev_res0));
+        if (prec == PHMM_PREC_FP32_RESCUE) {
+            launch_prep64_list(H, T, ctx->sms * 2, s);
+            launch_rescue64(H, ctx->pow64.p, ctx->sms * ctx->occ64, s);
+        }
+        CK(rec(S.ev_res1));
+    }
+    CK(cudaGetLastError());
+    return PHMM_OK;
+}
+
+int kernels_per_launch(int prec) {
+    return prec == PHMM_PREC_FP64 ? 4 : prec == PHMM_PREC_FP32_RESCUE ? 6 : 4;
+}
+
+uint64_t u64(const void* p) { return (uint64_t)(uintptr_t)p; }
+
+}  // namespace
+
+extern "C" {
+
+int phmm_abi_version(void) { return PHMM_ABI_VERSION; }
+
+const char* phmm_strerror(int s) {
+    switch (s) {
+    case PHMM_OK: return "ok";
+    case PHMM_PENDING: return "pending";
+    case PHMM_EINVAL: return "invalid argument or input";
+    case PHMM_ENOMEM: return "batch exceeds the device memory budget";
+    case PHMM_EBUSY: return "too many batches in flight";
+    case PHMM_ECUDA: return "CUDA error";
+    case PHMM_ETIMEOUT: return "timed out";
+    case PHMM_ECANCELED: return "cancelled";
+    case PHMM_ENOTFOUND: return "unknown ticket";
+    default: return "unknown status";
+    }
+}
+
+int phmm_create(const phmm_config* cfg, phmm_ctx** out) {
+    if (!cfg || !out) return PHMM_EINVAL;
+    *out = nullptr;
+    if (cfg->precision < 0 || cfg->precision > 2) return PHMM_EINVAL;
+    if (cfg->cols_per_lane != 0 && cfg->cols_per_lane != 16 && cfg->cols_per_lane != 24 &&
+        cfg->cols_per_lane != 32)
+        return PHMM_EINVAL;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || cfg->device < 0 || cfg->device >= ndev)
+        return PHMM_ECUDA;
+    phmm_ctx* ctx = new phmm_ctx();
+    ctx->dev = cfg->device;
+    ctx->cfg = *cfg;
+    if (ctx->cfg.max_inflight == 0) ctx->cfg.max_inflight = 4;
+    if (ctx->cfg.max_inflight > 64) ctx->cfg.max_inflight = 64;
+    auto fail = [&](int code) {
+        phmm_destroy(ctx);
+        return code;
+    };
+    if (cudaSetDevice(ctx->dev) != cudaSuccess) return fail(PHMM_ECUDA);
+    cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount, ctx->dev);
+    int khz = 0;
+    cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, ctx->dev);
+    ctx->max_mhz = khz / 1000.0;
+    if (cfg->stream) {
+        ctx->stream = static_cast<cudaStream_t>(cfg->stream);
+    } else {
+        if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess)
+            return fail(PHMM_ECUDA);
+        ctx->own_stream = true;
+    }
+    if (cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking) != cudaSuccess)
+        return fail(PHMM_ECUDA);
+    size_t fr = 0, tot = 0;
+    cudaMemGetInfo(&fr, &tot);
+    ctx->budget = cfg->mem_budget_bytes ? cfg->mem_budget_bytes : (size_t)(0.9 * (double)fr);
+    // tables
+    PhredTables T;
+    build_phred_tables(T);
+    if (ensure(ctx->tables, sizeof(T)) != cudaSuccess) return fail(PHMM_ECUDA);
+    cudaMemcpy(ctx->tables.p, &T, sizeof(T), cudaMemcpyHostToDevice);
+    for (int q = 0; q < 3; ++q) {
+        std::vector<PowRow<float>> v;
+        build_pow_table<float>(kNs[q], v);
+        if (ensure(ctx->pow32[q], v.size() * sizeof(v[0])) != cudaSuccess) return fail(PHMM_ECUDA);
+        cudaMemcpy(ctx->pow32[q].p, v.data(), v.size() * sizeof(v[0]), cudaMemcpyHostToDevice);
+        ctx->occ32[q] = occupancy_forward32(kNs[q]);
+    }
+    {
+        std::vector<PowRow<double>> v;
+        build_pow_table<double>(kN64, v);
+        if (ensure(ctx->pow64, v.size() * sizeof(v[0])) != cudaSuccess) return fail(PHMM_ECUDA);
+        cudaMemcpy(ctx->pow64.p, v.data(), v.size() * sizeof(v[0]), cudaMemcpyHostToDevice);
+        ctx->occ64 = occupancy_forward64();
+    }
+    ctx->slots.resize(ctx->cfg.max_inflight);
+    for (auto& S : ctx->slots) {
+        cudaEvent_t* evs[] = {&S.ev_copy, &S.ev_start, &S.ev_fwd0, &S.ev_fwd1, &S.ev_res0, &S.ev_res1, &S.ev_end};
+        for (auto* e : evs)
+            if (cudaEventCreate(e) != cudaSuccess) return fail(PHMM_ECUDA);
+        if (ensure(S.small, 64) != cudaSuccess || ensure(S.h_small, 64) != cudaSuccess ||
+            ensure(S.hdr, sizeof(BatchHeader)) != cudaSuccess)
+            return fail(PHMM_ECUDA);
+    }
+    if (cudaGetLastError() != cudaSuccess) return fail(PHMM_ECUDA);
+    *out = ctx;
+    return PHMM_OK;
+}
+
+void phmm_destroy(phmm_ctx* ctx) {
+    if (!ctx) return;
+    cudaSetDevice(ctx->dev);
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    if (ctx->copy_stream) cudaStreamSynchronize(ctx->copy_stream);
+    for (auto& S : ctx->slots) {
+        DevBuf* d[] = {&S.in_bases, &S.in_bq, &S.in_iq, &S.in_dq, &S.in_gq, &S.in_hap, &S.in_roff,
+                       &S.in_hoff, &S.in_pr, &S.in_ph, &S.desc, &S.rec32, &S.rec64, &S.teams,
+                       &S.witems, &S.cpairs, &S.citems, &S.parts, &S.out, &S.oflags, &S.rescue,
+                       &S.small, &S.hdr};
+        for (auto* b : d) release(*b);
+        HostBuf* h[] = {&S.h_out, &S.h_oflags, &S.h_small, &S.h_roff, &S.h_hoff, &S.h_pr, &S.h_ph};
+        for (auto* b : h) release(*b);
+        cudaEvent_t evs[] = {S.ev_copy, S.ev_start, S.ev_fwd0, S.ev_fwd1, S.ev_res0, S.ev_res1, S.ev_end};
+        for (auto e : evs)
+            if (e) cudaEventDestroy(e);
+        if (S.gexec) cudaGraphExecDestroy(S.gexec);
+    }
+    release(ctx->tables);
+    release(ctx->scan_row);
+    for (auto& b : ctx->pow32) release(b);
+    release(ctx->pow64);
+    if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
+    if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+    delete ctx;
+}
+
+int phmm_device_info(phmm_ctx* ctx, int* sms, double* max_clock_mhz, double* cups) {
+    if (!ctx) return PHMM_EINVAL;
+    if (sms) *sms = ctx->sms;
+    if (max_clock_mhz) *max_clock_mhz = ctx->max_mhz;
+    if (cups) *cups = 2.0 * 128.0 * ctx->sms * ctx->max_mhz * 1e6 / 12.0;
+    return PHMM_OK;
+}
+
+int phmm_submit_batch(phmm_ctx* ctx, const phmm_batch* b, uint64_t* ticket) {
+    if (!ctx || !b || !ticket) return PHMM_EINVAL;
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    if (ctx->dead) return PHMM_ECUDA;
+    if (cudaSetDevice(ctx->dev) != cudaSuccess) return PHMM_ECUDA;
+    if (b->n_pairs > 0 && (!b->read_bases || !b->read_off || !b->base_q || !b->ins_q || !b->del_q ||
+                           !b->gcp_q || !b->hap_bases || !b->hap_off || !b->pair_read ||
+                           !b->pair_hap || !b->out_log10))
+        return PHMM_EINVAL;
+    if (b->n_pairs > 0 && (b->n_reads == 0 || b->n_haps == 0)) return PHMM_EINVAL;
+    // a free slot
+    Slot* S = nullptr;
+    for (auto& s : ctx->slots)
+        if (s.state == 0) {
+            S = &s;
+            break;
+        }
+    if (!S) return PHMM_EBUSY;
+    const bool dev_in = b->inputs_on_device != 0;
+    const uint32_t nr = b->n_reads, nh = b->n_haps, np = b->n_pairs;
+    // host views of offsets and the pair index
+    const uint64_t *roff = b->read_off, *hoff = b->hap_off;
+    const uint32_t *pr = b->pair_read, *ph = b->pair_hap;
+    if (dev_in && np > 0) {
+        CK(ensure(S->h_roff, (nr + 1) * 8ull));
+        CK(ensure(S->h_hoff, (nh + 1) * 8ull));
+        CK(ensure(S->h_pr, np * 4ull));
+        CK(ensure(S->h_ph, np * 4ull));
+        CK(cudaMemcpyAsync(S->h_roff.p, b->read_off, (nr + 1) * 8ull, cudaMemcpyDeviceToHost, ctx->copy_stream));
+        CK(cudaMemcpyAsync(S->h_hoff.p, b->hap_off, (nh + 1) * 8ull, cudaMemcpyDeviceToHost, ctx->copy_stream));
+        CK(cudaMemcpyAsync(S->h_pr.p, b->pair_read, np * 4ull, cudaMemcpyDeviceToHost, ctx->copy_stream));
+        CK(cudaMemcpyAsync(S->h_ph.p, b->pair_hap, np * 4ull, cudaMemcpyDeviceToHost, ctx->copy_stream));
+        CK(cudaStreamSynchronize(ctx->copy_stream));
+        roff = static_cast<const uint64_t*>(S->h_roff.p);
+        hoff = static_cast<const uint64_t*>(S->h_hoff.p);
+        pr = static_cast<const uint32_t*>(S->h_pr.p);
+        ph = static_cast<const uint32_t*>(S->h_ph.p);
+    }
+    // validation: offsets non-decreasing with lengths >= 1, indices in range
+    std::vector<uint32_t> L(np), K(np);
+    uint64_t cells = 0;
+    if (np > 0) {
+        if (roff[0] != 0 || hoff[0] != 0) return PHMM_EINVAL;
+        for (uint32_t r = 0; r < nr; ++r)
+            if (roff[r + 1] <= roff[r] || roff[r + 1] - roff[r] > 0xffffffull) return PHMM_EINVAL;
+        for (uint32_t h = 0; h < nh; ++h)
+            if (hoff[h + 1] <= hoff[h] || hoff[h + 1] - hoff[h] > 0xffffffull) return PHMM_EINVAL;
+        for (uint32_t p = 0; p < np; ++p) {
+            if (pr[p] >= nr || ph[p] >= nh) return PHMM_EINVAL;
+            L[p] = (uint32_t)(roff[pr[p] + 1] - roff[pr[p]]);
+            K[p] = (uint32_t)(hoff[ph[p] + 1] - hoff[ph[p]]);
+            cells += (uint64_t)L[p] * K[p];
+        }
+    }
+    const uint64_t nbases = np > 0 ? roff[nr] : 0, nhb = np > 0 ? hoff[nh] : 0;
+    // plan (FP32: N from the config or the cost model; FP64: kN64)
+    Plan P;
+    int N = kN64;
+    if (ctx->cfg.precision == PHMM_PREC_FP64) {
+        make_plan(L.data(), K.data(), np, kN64, P);
+        N = kN64;
+    } else if (ctx->cfg.cols_per_lane) {
+        N = ctx->cfg.cols_per_lane;
+        make_plan(L.data(), K.data(), np, N, P);
+    } else {
+        Plan best;
+        bool have = false;
+        for (int q = 0; q < 3; ++q) {
+            Plan c;
+            make_plan(L.data(), K.data(), np, kNs[q], c);
+            const double pen = (double)c.n_too_long * 1e18;
+            if (!have || c.cost + pen < best.cost + (double)best.n_too_long * 1e18) {
+                best = std::move(c);
+                have = true;
+            }
+        }
+        P = std::move(best);
+        N = P.N;
+    }
+    // footprint and admission
+    const bool need64 = ctx->cfg.precision != PHMM_PREC_FP32_ONLY;
+    const uint64_t foot = (dev_in ? 0 : nbases * 5 + nhb + (nr + 1) * 8ull + (nh + 1) * 8ull + np * 8ull) +
+                          np * (sizeof(PairDesc) + sizeof(Partial) + 8 + 1 + 4) +
+                          (ctx->cfg.precision == PHMM_PREC_FP64 ? 0 : nbases * sizeof(Rec32)) +
+                          (need64 ? nbases * sizeof(Rec64) : 0) +
+                          P.teams.size() * sizeof(Team) + P.witems.size() * sizeof(WarpItem) +
+                          P.cpairs.size() * sizeof(CtaPair) + P.citems.size() * sizeof(CtaItem);
+    if (foot > ctx->budget) return PHMM_ENOMEM;
+    // device arenas
+    BatchHeader& hh = S->hh;
+    memset(&hh, 0, sizeof(hh));
+    if (dev_in) {
+        hh.read_bases = b->read_bases; hh.base_q = b->base_q; hh.ins_q = b->ins_q;
+        hh.del_q = b->del_q; hh.gcp_q = b->gcp_q; hh.hap_bases = b->hap_bases;
+        hh.read_off = b->read_off; hh.hap_off = b->hap_off;
+        hh.pair_read = b->pair_read; hh.pair_hap = b->pair_hap;
+    } else if (np > 0) {
+        CK(ensure(S->in_bases, nbases)); CK(ensure(S->in_bq, nbases)); CK(ensure(S->in_iq, nbases));
+        CK(ensure(S->in_dq, nbases)); CK(ensure(S->in_gq, nbases)); CK(ensure(S->in_hap, nhb));
+        CK(ensure(S->in_roff, (nr + 1) * 8ull)); CK(ensure(S->in_hoff, (nh + 1) * 8ull));
+        CK(ensure(S->in_pr, np * 4ull)); CK(ensure(S->in_ph, np * 4ull));
+        cudaStream_t cs = ctx->copy_stream;
+        CK(cudaMemcpyAsync(S->in_bases.p, b->read_bases, nbases, cudaMemcpyHostToDevice, cs));
+        CK(cudaMemcpyAsync(S->in_bq.p, b->base_q, nbases, cudaMemcpyHostToDevice, cs));
+        CK(cudaMemcpyAsync(S->in_iq.p, b->ins_q, nbases, cudaMemcpyHostToDevice, cs));
+        CK(cudaMemcpyAsync(S->in_dq.p, b->del_q, nbases, cudaMemcpyHostToDevice, cs));
+        CK(cudaMemcpyAsync(S->in_gq.p, b->gcp_q, nbases, cudaMemcpyHostToDevice, cs));
+        CK(cudaMemcpyAsync(S->in_hap.p, b->hap_bases, nhb, cudaMemcpyHostToDevice, cs));
+        CK(cudaMemcpyAsync(S->in_roff.p, b->read_off, (nr + 1) * 8ull, cudaMemcpyHostToDevice, cs));
+        CK(cudaMemcpyAsync(S->in_hoff.p, b->hap_off, (nh + 1) * 8ull, cudaMemcpyHostToDevice, cs));
+        CK(cudaMemcpyAsync(S->in_pr.p, b->pair_read, np * 4ull, cudaMemcpyHostToDevice, cs));
+        CK(cudaMemcpyAsync(S->in_ph.p, b->pair_hap, np * 4ull, cudaMemcpyHostToDevice, cs));
+        hh.read_bases = (const uint8_t*)S->in_bases.p; hh.base_q = (const uint8_t*)S->in_bq.p;
+        hh.ins_q = (const uint8_t*)S->in_iq.p; hh.del_q = (const uint8_t*)S->in_dq.p;
+        hh.gcp_q = (const uint8_t*)S->in_gq.p; hh.hap_bases = (const uint8_t*)S->in_hap.p;
+        hh.read_off = (const uint64_t*)S->in_roff.p; hh.hap_off = (const uint64_t*)S->in_hoff.p;
+        hh.pair_read = (const uint32_t*)S->in_pr.p; hh.pair_hap = (const uint32_t*)S->in_ph.p;
+    }
+    CK(ensure(S->desc, np * sizeof(PairDesc)));
+    if (ctx->cfg.precision != PHMM_PREC_FP64) CK(ensure(S->rec32, nbases * sizeof(Rec32)));
+    if (need64) CK(ensure(S->rec64, nbases * sizeof(Rec64)));
+    CK(ensure(S->teams, P.teams.size() * sizeof(Team)));
+    CK(ensure(S->witems, P.witems.size() * sizeof(WarpItem)));
+    CK(ensure(S->cpairs, P.cpairs.size() * sizeof(CtaPair)));
+    CK(ensure(S->citems, P.citems.size() * sizeof(CtaItem)));
+    CK(ensure(S->parts, np * sizeof(Partial)));
+    CK(ensure(S->out, np * 8ull));
+    CK(ensure(S->oflags, np * 1ull));
+    CK(ensure(S->rescue, np * 4ull));
+    CK(ensure(S->h_out, np * 8ull));
+    CK(ensure(S->h_oflags, np * 1ull));
+    cudaStream_t cs = ctx->copy_stream;
+    if (!P.teams.empty()) CK(cudaMemcpyAsync(S->teams.p, P.teams.data(), P.teams.size() * sizeof(Team), cudaMemcpyHostToDevice, cs));
+    if (!P.witems.empty()) CK(cudaMemcpyAsync(S->witems.p, P.witems.data(), P.witems.size() * sizeof(WarpItem), cudaMemcpyHostToDevice, cs));
+    if (!P.cpairs.empty()) CK(cudaMemcpyAsync(S->cpairs.p, P.cpairs.data(), P.cpairs.size() * sizeof(CtaPair), cudaMemcpyHostToDevice, cs));
+    if (!P.citems.empty()) CK(cudaMemcpyAsync(S->citems.p, P.citems.data(), P.citems.size() * sizeof(CtaItem), cudaMemcpyHostToDevice, cs));
+    CK(cudaMemsetAsync(S->parts.p, 0, np * sizeof(Partial), cs));
+    hh.n_read_bases = nbases;
+    hh.n_reads = nr;
+    hh.n_haps = nh;
+    hh.n_pairs = np;
+    hh.desc = (PairDesc*)S->desc.p;
+    hh.rec32 = (Rec32*)S->rec32.p;
+    hh.rec64 = (Rec64*)S->rec64.p;
+    hh.witems = (const WarpItem*)S->witems.p;
+    hh.teams = (const Team*)S->teams.p;
+    hh.citems = (const CtaItem*)S->citems.p;
+    hh.cpairs = (const CtaPair*)S->cpairs.p;
+    hh.n_witems = (uint32_t)P.witems.size();
+    hh.n_citems = (uint32_t)P.citems.size();
+    hh.n_partials = np;
+    hh.force_rescue = (ctx->cfg.flags & PHMM_F_FORCE_RESCUE) ? 1u : 0u;
+    hh.parts = (Partial*)S->parts.p;
+    hh.out = (double*)S->out.p;
+    hh.out_flags = (uint8_t*)S->oflags.p;
+    hh.rescue_list = (uint32_t*)S->rescue.p;
+    hh.counters = (uint32_t*)S->small.p;
+    hh.status = (uint32_t*)S->small.p + 4;
+    hh.dropgrow = (uint32_t*)S->small.p + 5;
+    hh.seed = ctx->seed;
+    hh.mode = (uint32_t)ctx->cfg.precision;
+    CK(cudaMemcpyAsync(S->hdr.p, &hh, sizeof(hh), cudaMemcpyHostToDevice, cs));
+    CK(cudaEventRecord(S->ev_copy, cs));
+    // host inputs may be released when submit returns
+    CK(cudaEventSynchronize(S->ev_copy));
+    cudaStream_t s = ctx->stream;
+    CK(cudaStreamWaitEvent(s, S->ev_copy, 0));
+    CK(cudaEventRecord(S->ev_start, s));
+    uint32_t launches = 0;
+    if (np > 0) {
+        const bool per_pair = ctx->cfg.precision == PHMM_PREC_FP64 && (ctx->cfg.flags & PHMM_F_LAUNCH_PER_PAIR);
+        const bool use_graph = !(ctx->cfg.flags & PHMM_F_NO_GRAPH) && !per_pair;
+        if (per_pair) {
+            const BatchHeader* H = static_cast<const BatchHeader*>(S->hdr.p);
+            launch_reset(H, s);
+            launch_prep64_all(H, static_cast<const PhredTables*>(ctx->tables.p), ctx->sms * 4, s);
+            CK(cudaEventRecord(S->ev_fwd0, s));
+            for (uint32_t p = 0; p < np; ++p) launch_single64(H, ctx->pow64.p, p, s);
+            CK(cudaEventRecord(S->ev_fwd1, s));
+            launch_finalize64(H, ctx->sms * 4, s);
+            CK(cudaEventRecord(S->ev_res0, s));
+            CK(cudaEventRecord(S->ev_res1, s));
+            CK(cudaGetLastError());
+            launches = np + 3;
+        } else if (use_graph) {
+            const int key = ctx->cfg.precision * 100 + N;
+            if (!S->gexec || S->g_key != key) {
+                if (S->gexec) cudaGraphExecDestroy(S->gexec);
+                S->gexec = nullptr;
+                cudaGraph_t g = nullptr;
+                CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+                const int rc = launch_sequence(ctx, *S, N, true);
+                cudaError_t e2 = cudaStreamEndCapture(s, &g);
+                if (rc != PHMM_OK || e2 != cudaSuccess) {
+                    if (g) cudaGraphDestroy(g);
+                    ctx->dead = true;
+                    return PHMM_ECUDA;
+                }
+                cudaError_t e3 = cudaGraphInstantiate(&S->gexec, g, 0);
+                cudaGraphDestroy(g);
+                CK(e3);
+                S->g_key = key;
+            }
+            CK(cudaGraphLaunch(S->gexec, s));
+            launches = (uint32_t)kernels_per_launch(ctx->cfg.precision);
+        } else {
+            const int rc = launch_sequence(ctx, *S, N, false);
+            if (rc != PHMM_OK) return rc;
+            launches = (uint32_t)kernels_per_launch(ctx->cfg.precision);
+        }
+        // outputs
+        if (b->outputs_on_device) {
+            CK(cudaMemcpyAsync(b->out_log10, S->out.p, np * 8ull, cudaMemcpyDeviceToDevice, s));
+            if (b->out_flags) CK(cudaMemcpyAsync(b->out_flags, S->oflags.p, np, cudaMemcpyDeviceToDevice, s));
+        } else {
+            CK(cudaMemcpyAsync(S->h_out.p, S->out.p, np * 8ull, cudaMemcpyDeviceToHost, s));
+            CK(cudaMemcpyAsync(S->h_oflags.p, S->oflags.p, np, cudaMemcpyDeviceToHost, s));
+        }
+        CK(cudaMemcpyAsync(S->h_small.p, S->small.p, 32, cudaMemcpyDeviceToHost, s));
+    } else {
+        memset(S->h_small.p, 0, 32);
+        CK(cudaEventRecord(S->ev_fwd0, s));
+        CK(cudaEventRecord(S->ev_fwd1, s));
+        CK(cudaEventRecord(S->ev_res0, s));
+        CK(cudaEventRecord(S->ev_res1, s));
+    }
+    CK(cudaEventRecord(S->ev_end, s));
+    S->ticket = ++ctx->next_ticket;
+    S->state = 1;
+    S->user_out = b->out_log10;
+    S->user_flags = b->out_flags;
+    S->out_on_dev = b->outputs_on_device != 0;
+    S->n_pairs = np;
+    S->has_stats = false;
+    memset(&S->st, 0, sizeof(S->st));
+    S->st.cells = cells;
+    S->st.n_pairs = np;
+    S->st.n_long = P.n_long;
+    S->st.cols_per_lane = (uint32_t)N;
+    S->st.kernel_launches = launches;
+    S->host_status = P.n_too_long ? PHMM_EINVAL : PHMM_OK;
+    *ticket = S->ticket;
+    return PHMM_OK;
+}
+
+int phmm_poll(phmm_ctx* ctx, uint64_t ticket, int timeout_ms) {
+    if (!ctx) return PHMM_EINVAL;
+    Slot* S = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(ctx->mu);
+        for (auto& s : ctx->slots)
+            if (s.state == 1 && s.ticket == ticket) S = &s;
+        if (!S) return PHMM_ENOTFOUND;
+    }
+    cudaSetDevice(ctx->dev);
+    const auto t0 = std::chrono::steady_clock::now();
+    for (;;) {
+        const cudaError_t q = cudaEventQuery(S->ev_end);
+        if (q == cudaSuccess) break;
+        if (q != cudaErrorNotReady) {
+            ctx->dead = true;
+            return PHMM_ECUDA;
+        }
+        if (timeout_ms == 0) return PHMM_PENDING;
+        if (timeout_ms > 0) {
+            const double el = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+            if (el >= timeout_ms) return PHMM_PENDING;
+        }
+        std::this_thread::sleep_for(std::chrono::microseconds(50));
+    }
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    if (!S->out_on_dev && S->n_pairs > 0) {
+        memcpy(S->user_out, S->h_out.p, S->n_pairs * 8ull);
+        if (S->user_flags) memcpy(S->user_flags, S->h_oflags.p, S->n_pairs);
+    }
+    const uint32_t* sm = static_cast<const uint32_t*>(S->h_small.p);
+    S->st.n_rescued = sm[2];
+    S->st.status_bits = sm[4];
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, S->ev_start, S->ev_end);
+    S->st.ms_total = ms;
+    ms = 0.f;
+    cudaEventElapsedTime(&ms, S->ev_fwd0, S->ev_fwd1);
+    S->st.ms_forward = ms;
+    ms = 0.f;
+    cudaEventElapsedTime(&ms, S->ev_res0, S->ev_res1);
+    S->st.ms_rescue = ms;
+    ctx->last_stats = S->st;
+    ctx->last_retired = S->ticket;
+    S->state = 0;
+    int rc = S->host_status;
+    if (sm[4] & ST_TIMEOUT) rc = PHMM_ETIMEOUT;
+    else if (sm[4] & (ST_BAD_INPUT | ST_TOO_LONG)) rc = PHMM_EINVAL;
+    return rc;
+}
+
+int phmm_get_stats(phmm_ctx* ctx, uint64_t ticket, phmm_stats* out) {
+    if (!ctx || !out) return PHMM_EINVAL;
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    if (ticket == ctx->last_retired) {
+        *out = ctx->last_stats;
+        return PHMM_OK;
+    }
+    for (auto& s : ctx->slots)
+        if (s.state == 1 && s.ticket == ticket) {
+            *out = s.st;
+            return PHMM_PENDING;
+        }
+    return PHMM_ENOTFOUND;
+}
+
+int phmm_scan_test(phmm_ctx* ctx, const float* y, float* z, int n, float a) {
+    if (!ctx || !y || !z || n < 1 || n > 1024 || !(a >= 0.0f) || !(a <= 1.0f)) return PHMM_EINVAL;
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    cudaSetDevice(ctx->dev);
+    PowRow<float> row{};
+    const double la = a > 0.0f ? std::log10((double)a) : -1e9;
+    for (int s = 0; s < 5; ++s) {
+        const double m = 32.0 * (1 << s);
+        const double lg = la * m;
+        if (lg >= std::log10((double)std::numeric_limits<float>::min())) {
+            row.sp1[s] = (float)std::pow(10.0, lg);
+            row.sp2[s] = 1.0f;
+        } else {
+            row.sp1[s] = row.sp2[s] = (float)std::pow(10.0, lg / 2.0);
+        }
+    }
+    row.pad1 = a;
+    CK(ensure(ctx->scan_row, sizeof(row)));
+    CK(cudaMemcpyAsync(ctx->scan_row.p, &row, sizeof(row), cudaMemcpyHostToDevice, ctx->stream));
+    launch_scan_test(y, z, n, ctx->scan_row.p, ctx->stream);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(ctx->stream));
+    return PHMM_OK;
+}
+
+}  // extern "C"

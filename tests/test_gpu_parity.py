@@ -1,0 +1,202 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle, element by element.
+
+Tolerances (absolute, in log10 L): 1e-3 for the FP32 path, 1e-9 for FP64 (the FP64 mode
+and every pair the rescue pass recomputed).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2606_25738_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL32 = 1e-3
+TOL64 = 1e-9
+
+
+@pytest.fixture(scope="module")
+def phmm():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2606_25738_gb300 import phmm as P
+    return P
+
+
+def _check(out, flags, ref, tol32=TOL32, tol64=TOL64):
+    out = np.asarray(out)
+    ref = np.asarray(ref)
+    fin = np.isfinite(ref)
+    assert np.array_equal(np.isfinite(out), fin), (out[~fin], ref[~fin])
+    assert np.array_equal(out[~fin], ref[~fin]) or np.all(np.isnan(out[~fin]) == np.isnan(ref[~fin]))
+    d = np.abs(out[fin] - ref[fin])
+    tol = np.where((flags[fin] & 0x5) != 0, tol64, tol32)
+    bad = np.flatnonzero(d > tol)
+    assert bad.size == 0, "max |dlog10| %g at %s (flags %s)" % (d.max(), bad[:8], flags[fin][bad[:8]])
+    return float(d.max()) if d.size else 0.0
+
+
+def test_plain_64_pairs_fp32(phmm):
+    """64 short pairs (200-400 bp haplotypes, 100-150 bp reads): FP32 + rescue vs oracle."""
+    b = W.plain_pairs(64, seed=0)
+    with phmm.Context(precision="fp32") as ctx:
+        out, flags, rc, st = ctx.run(b)
+    assert rc == 0
+    _check(out, flags, oracle.batch(b))
+    assert st["kernel_launches"] >= 4
+
+
+def test_plain_64_pairs_fp64(phmm):
+    b = W.plain_pairs(64, seed=0)
+    with phmm.Context(precision="fp64") as ctx:
+        out, flags, rc, st = ctx.run(b)
+    assert np.all(flags & phmm.PAIR_FP64)
+    ref = oracle.batch(b)
+    assert np.max(np.abs(out - ref)) <= TOL64
+
+
+def test_force_rescue_fp64_pass(phmm):
+    """Every pair through the FP64 rescue pass: results within 1e-9 and flagged."""
+    b = W.plain_pairs(32, seed=5)
+    with phmm.Context(precision="fp32", flags=phmm.F_FORCE_RESCUE) as ctx:
+        out, flags, rc, st = ctx.run(b)
+    assert st["n_rescued"] == 32
+    assert np.all(flags & phmm.PAIR_RESCUED)
+    assert np.max(np.abs(out - oracle.batch(b))) <= TOL64
+
+
+@pytest.mark.parametrize("N", [16, 24, 32])
+def test_columns_per_lane(phmm, N):
+    """Every compiled N gives oracle-equal results, including multi-warp pairs."""
+    b = W.plain_pairs(40, seed=11, k_range=(1, 40 * N), l_range=(1, 300), indel_rate=0.01)
+    with phmm.Context(precision="fp32", cols_per_lane=N) as ctx:
+        out, flags, rc, st = ctx.run(b)
+    assert st["cols_per_lane"] == N
+    _check(out, flags, oracle.batch(b))
+
+
+@pytest.mark.parametrize("N", [16, 24, 32])
+def test_fp32_path_without_rescue(phmm, N):
+    """The FP32 engine alone (no FP64 rescue pass): short teams and multi-warp pairs up
+    to 16 warps stay within 1e-3 and none of them is flagged for rescue."""
+    b = W.plain_pairs(48, seed=12, k_range=(1, 16 * 32 * N), l_range=(1, 400), indel_rate=0.01)
+    with phmm.Context(precision="fp32_only", cols_per_lane=N) as ctx:
+        out, flags, rc, st = ctx.run(b)
+    assert st["n_long"] > 0
+    assert np.all((flags & 0x78) == 0), flags[(flags & 0x78) != 0]
+    ref = oracle.batch(b)
+    assert np.max(np.abs(out - ref)) <= TOL32
+
+
+def _edge_batch(N=32):
+    rng = np.random.default_rng(3)
+    rs = lambda n: "".join(rng.choice(list("ACGT"), size=n))
+    hap = rs(300)
+    pairs = [
+        ("A", "A", 30, 45, 45, 10),                  # l = k = 1
+        ("C", "ACGTA", 30, 45, 45, 10),              # l = 1
+        (rs(10), rs(3), 30, 45, 45, 10),             # l > k
+        (rs(40), "G", 20, 45, 45, 10),               # k = 1
+        ("N" * 50, hap[:120], 30, 45, 45, 10),       # all-N read
+        (hap[10:90], hap, 0, 45, 45, 10),            # Phred 0 base quality
+        (hap[10:90], hap, 93, 45, 45, 10),           # Phred 93
+        (hap[5:60], hap, 30, 93, 93, 10),            # near-zero gap opens
+        (hap[5:60], hap, 30, 10, 10, 10),            # frequent gaps
+        (hap[:100] + hap[150:250], hap, 30, 45, 45, 10),   # 50 bp deletion
+        (hap[:60] + rs(40) + hap[60:150], hap, 30, 45, 45, 10),  # 40 bp insertion
+        (hap[:N], hap[:N], 30, 45, 45, 10),          # k = N
+        (hap[:N + 1], hap[:N + 1], 30, 45, 45, 10),  # k = N + 1
+        (rs(120), rs(32 * N), 30, 45, 45, 10),       # k = 32 N (one full warp)
+        (rs(120), rs(32 * N + 1), 30, 45, 45, 10),   # k = 32 N + 1 (two warps)
+        (rs(150), rs(3 * 32 * N - 1), 30, 45, 45, 10),
+        (rs(30), rs(600), 30, 45, 45, 10),
+        (hap[:200], hap, np.arange(200) % 41, np.arange(200) % 30 + 15, 40, 10),  # per-row quals
+        (hap[:150], hap, 25, 40, 40, np.arange(150) % 20 + 5),  # per-row gap continuation
+        (hap[:150].lower(), hap.lower(), 30, 45, 45, 10),  # lower case
+    ]
+    return W.from_strings(pairs)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_edge_cases(phmm, prec):
+    b = _edge_batch()
+    with phmm.Context(precision=prec, cols_per_lane=32 if prec == "fp32" else 0) as ctx:
+        out, flags, rc, st = ctx.run(b)
+    ref = oracle.batch(b)
+    if prec == "fp64":
+        fin = np.isfinite(ref)
+        assert np.array_equal(np.isfinite(out), fin)
+        assert np.max(np.abs(out[fin] - ref[fin])) <= TOL64
+    else:
+        _check(out, flags, ref)
+
+
+def test_long_deletion_50bp(phmm):
+    """A read whose best alignment needs a 50 bp deletion: the carry crosses lanes and
+    warps through the scan and must not be dropped."""
+    rng = np.random.default_rng(9)
+    hap = "".join(rng.choice(list("ACGT"), size=2000))
+    read = hap[100:700] + hap[750:1350]
+    b = W.from_strings([(read, hap, 30, 45, 45, 10)])
+    for N in (16, 32):
+        with phmm.Context(precision="fp32", cols_per_lane=N) as ctx:
+            out, flags, rc, st = ctx.run(b)
+        _check(out, flags, oracle.batch(b))
+
+
+def test_scan_unit(phmm):
+    import torch
+    rng = np.random.default_rng(1)
+    with phmm.Context() as ctx:
+        for n, a in ((1, 0.1), (31, 0.5), (33, 0.1), (1024, 0.1), (1000, 0.9), (517, 1.0)):
+            y = rng.uniform(0.5, 2.0, n).astype(np.float32)
+            z = ctx.scan_test(torch.from_numpy(y).cuda(), a).cpu().numpy()
+            ref = np.zeros(n)
+            acc = 0.0
+            for t in range(n):
+                acc = a * acc + float(y[t])
+                ref[t] = acc
+            assert np.allclose(z, ref, rtol=1e-5, atol=0), (n, a)
+
+
+def test_device_inputs_outputs(phmm):
+    import torch
+    b = W.plain_pairs(24, seed=2)
+    d = phmm.to_device(b)
+    out = torch.empty(24, dtype=torch.float64, device="cuda")
+    fl = torch.zeros(24, dtype=torch.uint8, device="cuda")
+    with phmm.Context() as ctx:
+        t = ctx.submit(d, out, fl)
+        assert ctx.poll(t, -1) == 0
+    _check(out.cpu().numpy(), fl.cpu().numpy(), oracle.batch(b))
+
+
+def test_graph_replay_equals_eager(phmm):
+    b = W.plain_pairs(48, seed=4, k_range=(100, 1500))
+    with phmm.Context() as c1:
+        a1, f1, _, _ = c1.run(b)
+        a2, f2, _, _ = c1.run(b)  # graph replay
+    with phmm.Context(flags=phmm.F_NO_GRAPH) as c2:
+        a3, f3, _, _ = c2.run(b)
+    assert np.array_equal(a1, a2) and np.array_equal(a1, a3)
+    assert np.array_equal(f1, f3)
+
+
+def test_invalid_input_reported(phmm):
+    b = W.from_strings([("ACGT", "ACGT", 30, 45, 45, 10), ("AXGT", "ACGT", 30, 45, 45, 10),
+                        ("ACGT", "ACGT", 94, 45, 45, 10), ("ACG", "AC?T", 30, 45, 45, 10)])
+    with phmm.Context() as ctx:
+        out, flags, rc, st = ctx.run(b, check=False)
+    assert rc == phmm.PHMM_EINVAL
+    assert math.isfinite(out[0]) and np.all(np.isnan(out[1:]))
+    assert np.all(flags[1:] & phmm.PAIR_ERROR)
+
+
+def test_launch_per_pair_fp64(phmm):
+    b = W.plain_pairs(8, seed=6)
+    with phmm.Context(precision="fp64", flags=phmm.F_LAUNCH_PER_PAIR) as ctx:
+        out, flags, rc, st = ctx.run(b)
+    assert st["kernel_launches"] == 8 + 3
+    assert np.max(np.abs(out - oracle.batch(b))) <= TOL64
