@@ -80,8 +80,13 @@ typedef struct {
     void *stream;             /* cudaStream_t to run on; NULL = a stream owned by the
                                  context.  The caller keeps a passed stream alive until
                                  phmm_destroy. */
-    int cols_per_lane;        /* haplotype columns per thread (the paper's N): 0 = chosen
-                                 by the built-in tuner, else 16, 24 or 32 */
+    int cols_per_lane;        /* haplotype columns per thread (the paper's N) for FP32 short
+                                 pairs: 12 or 16 fixes the packed-team width, 24 or 32 the
+                                 scalar-team width, 0 = chosen by the built-in tuner.
+                                 Multi-warp pairs use 32 (FP32); FP64 kernels use 8. */
+    int kernel_variant;       /* FP32 short pairs: 0 or 1 = pairs of the same read share
+                                 packed teams (two haplotypes per thread in float2 halves),
+                                 the rest run in scalar teams; 2 = scalar teams only */
 } phmm_config;
 
 /*
@@ -135,6 +140,7 @@ typedef struct {
     float ms_h2d;             /* host-to-device copies (host inputs only) */
     uint32_t kernel_launches; /* kernels launched for the ticket */
     uint32_t status_bits;     /* device status word (0 = clean) */
+    float ms_host;            /* host time of phmm_submit_batch's planning and enqueue */
 } phmm_stats;
 
 /* Create a context on cfg->device.  *out receives the handle.  PHMM_EINVAL on a bad

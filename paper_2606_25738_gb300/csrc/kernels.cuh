@@ -6,6 +6,7 @@
 
 #include <cmath>
 #include <cstdint>
+#include <type_traits>
 
 #include "engine.cuh"
 #include "phmm_internal.h"
@@ -15,17 +16,9 @@ namespace phmm {
 // ------------------------------------------------------------------------------------
 // Double-float helpers for the FP32 prep (Phred tables: see PhredTables).
 // ------------------------------------------------------------------------------------
-struct df {
-    float hi, lo;
-};
 __device__ __forceinline__ df quick_two_sum(float a, float b) {
     const float s = __fadd_rn(a, b);
     return {s, __fsub_rn(b, __fsub_rn(s, a))};
-}
-__device__ __forceinline__ df two_sum(float a, float b) {
-    const float s = __fadd_rn(a, b);
-    const float bb = __fsub_rn(s, a);
-    return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
 }
 __device__ __forceinline__ df df_mul(df a, df b) {
     const float p = __fmul_rn(a.hi, b.hi);
@@ -260,7 +253,9 @@ __device__ __forceinline__ Partial cta_combine(const CtaShared<T>& sh, int w0, i
 template <typename T>
 __device__ const typename Num<T>::Rec* dummy_rec();
 
-// One warp item: packed teams of short pairs.
+// One warp item.  FP64: scalar teams of seg_run.  FP32 (k_forward_short): kind 0 = lean
+// scalar teams (width NS), kind 1 = packed teams of two haplotypes of the same read
+// (width NP).
 template <typename T, int N>
 __device__ __forceinline__ void warp_item_run(const BatchHeader* __restrict__ H,
                                               const PowRow<T>* __restrict__ pow, uint32_t wi,
@@ -269,7 +264,7 @@ __device__ __forceinline__ void warp_item_run(const BatchHeader* __restrict__ H,
     const int lane = threadIdx.x & 31;
     const WarpItem it = H->witems[wi];
     int tbase = lane, tsize = 1, maxG = 1;
-    uint32_t pair = 0xffffffffu;
+    uint32_t pair = kNoPair;
     for (uint32_t t = 0; t < it.n_teams; ++t) {
         const Team tm = H->teams[it.first_team + t];
         maxG = max(maxG, (int)tm.size);
@@ -285,7 +280,7 @@ __device__ __forceinline__ void warp_item_run(const BatchHeader* __restrict__ H,
     int l = 0, k = 0;
     const Rec* rec = dummy_rec<T>();
     const uint8_t* hap = H->hap_bases;
-    if (pair != 0xffffffffu) {
+    if (pair != kNoPair) {
         const PairDesc d = H->desc[pair];
         l = (int)d.l;
         k = (int)d.k;
@@ -294,9 +289,9 @@ __device__ __forceinline__ void warp_item_run(const BatchHeader* __restrict__ H,
     }
     const int lmax = (int)__reduce_max_sync(kFull, (unsigned)l);
     SmemLink L{};
-    const SegOut o = seg_run<T, N, false>(rec, l, lmax, hap, k, lt * N, lt, tlast, nsteps, pow,
-                                          R, L, H->status);
-    if (pair != 0xffffffffu && lt == 0) {
+    const SegOut o = seg_run<T, N, false>(rec, l, lmax, hap, k, lt * N, lt, tlast, nsteps, pow, R,
+                                          L, H->status);
+    if (pair != kNoPair && lt == 0) {
         Partial p;
         p.S = o.S;
         p.E = o.E;
@@ -307,14 +302,26 @@ __device__ __forceinline__ void warp_item_run(const BatchHeader* __restrict__ H,
     }
 }
 
-// Persistent forward kernel: CTA items (multi-warp pairs, longest first), then warp
-// items (packed short pairs, longest first), both taken from atomic counters.
-template <typename T, int N>
+__device__ __forceinline__ void write_part(const BatchHeader* __restrict__ H, uint32_t pair,
+                                           const SegOut& o) {
+    Partial p;
+    p.S = o.S;
+    p.E = o.E;
+    p.flags = o.flags | PF_DONE;
+    p.n_extra = 0;
+    p.extra_base = 0;
+    H->parts[pair] = p;
+}
+
+// Persistent forward kernel for multi-warp pairs: CTA items (longest first) taken from
+// an atomic counter; with WARP_ITEMS it then also takes warp items (the FP64 engine, which
+// has no packed short kernel).
+template <typename T, int N, bool WARP_ITEMS>
 __global__ void __launch_bounds__(kCtaThreads, 1)
 k_forward(const BatchHeader* __restrict__ H, const PowRow<T>* __restrict__ pow) {
     __shared__ CtaShared<T> sh;
     const int R = checkpoint_interval<T>(H->dropgrow);
-    const uint32_t n_c = H->n_citems, n_w = H->n_witems;
+    const uint32_t n_c = H->n_citems;
     for (;;) {
         if (threadIdx.x == 0) sh.item = atomicAdd(&H->counters[0], 1u);
         cta_clear<T>(sh);
@@ -337,13 +344,117 @@ k_forward(const BatchHeader* __restrict__ H, const PowRow<T>* __restrict__ pow) 
         }
         __syncthreads();
     }
+    if constexpr (WARP_ITEMS) {
+        const uint32_t n_w = H->n_witems;
+        const int lane = threadIdx.x & 31;
+        for (;;) {
+            uint32_t wi = 0;
+            if (lane == 0) wi = atomicAdd(&H->counters[1], 1u);
+            wi = __shfl_sync(kFull, wi, 0);
+            if (wi >= n_w) break;
+            warp_item_run<T, N>(H, pow, wi, R);
+        }
+    }
+}
+
+// Team lookup of a warp item: this lane's team (first lane, size, pairs) and the scan
+// steps of the widest team.
+struct TeamOf {
+    int lt, tlast, nsteps;
+    uint32_t pair, pair2;
+};
+__device__ __forceinline__ TeamOf team_of(const Team* __restrict__ teams, const WarpItem& it) {
+    const int lane = threadIdx.x & 31;
+    int tbase = lane, tsize = 1, maxG = 1;
+    uint32_t pair = kNoPair, pair2 = kNoPair;
+    for (uint32_t t = 0; t < it.n_teams; ++t) {
+        const Team tm = teams[it.first_team + t];
+        maxG = max(maxG, (int)tm.size);
+        if (lane >= tm.base && lane < tm.base + tm.size) {
+            tbase = tm.base;
+            tsize = tm.size;
+            pair = tm.pair;
+            pair2 = tm.pair2;
+        }
+    }
+    int nsteps = 0;
+    while ((1 << nsteps) < maxG) ++nsteps;
+    return {lane - tbase, tbase + tsize - 1, nsteps, pair, pair2};
+}
+
+// Persistent kernels for short pairs in FP32 (warp items taken from atomic counters).
+// Small CTAs: residency is set by registers, not by a CTA-wide shape.
+constexpr int kShortThreads = 128;
+
+// Lean scalar teams, N columns per lane (item list witems / counters[1]).
+template <int N>
+__global__ void __launch_bounds__(kShortThreads, 4)
+k_short_scalar(const BatchHeader* __restrict__ H, const PowRow<float>* __restrict__ pow) {
+    Rec32* const s_ring = nullptr;  // records are prefetched through registers
+    const int R = checkpoint_interval<float>(H->dropgrow);
+    const uint32_t n_w = H->n_witems;
     const int lane = threadIdx.x & 31;
     for (;;) {
         uint32_t wi = 0;
         if (lane == 0) wi = atomicAdd(&H->counters[1], 1u);
         wi = __shfl_sync(kFull, wi, 0);
         if (wi >= n_w) break;
-        warp_item_run<T, N>(H, pow, wi, R);
+        const TeamOf t = team_of(H->teams, H->witems[wi]);
+        int l = 0, k = 0;
+        const Rec32* rec = dummy_rec<float>();
+        const uint8_t* hap = H->hap_bases;
+        if (t.pair != kNoPair) {
+            const PairDesc d = H->desc[t.pair];
+            l = (int)d.l;
+            k = (int)d.k;
+            rec = H->rec32 + d.roff;
+            hap = H->hap_bases + d.hoff;
+        }
+        const int lmax = (int)__reduce_max_sync(kFull, (unsigned)l);
+        const SegOut o = team_run_lean<N>(rec, l, lmax, hap, k, t.lt * N, t.lt, t.tlast, t.nsteps, pow, R,
+                                          s_ring);
+        if (t.pair != kNoPair && t.lt == 0) write_part(H, t.pair, o);
+    }
+}
+
+// Packed teams of two haplotypes of the same read, N columns per lane (item list
+// witems2 / counters[4]).
+template <int N, int MINB>
+__global__ void __launch_bounds__(kShortThreads, MINB)
+k_short_packed(const BatchHeader* __restrict__ H, const PowRow<float>* __restrict__ pow) {
+    Rec32* const s_ring = nullptr;  // records are prefetched through registers
+    const int R = checkpoint_interval<float>(H->dropgrow);
+    const uint32_t n_w = H->n_witems2;
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+        uint32_t wi = 0;
+        if (lane == 0) wi = atomicAdd(&H->counters[4], 1u);
+        wi = __shfl_sync(kFull, wi, 0);
+        if (wi >= n_w) break;
+        const TeamOf t = team_of(H->teams, H->witems2[wi]);
+        int l = 0, k = 0, k2 = 0;
+        const Rec32* rec = dummy_rec<float>();
+        const uint8_t* hap = H->hap_bases;
+        const uint8_t* hap2 = H->hap_bases;
+        if (t.pair != kNoPair) {
+            const PairDesc d = H->desc[t.pair];
+            l = (int)d.l;
+            k = (int)d.k;
+            rec = H->rec32 + d.roff;
+            hap = H->hap_bases + d.hoff;
+        }
+        if (t.pair2 != kNoPair) {
+            const PairDesc d = H->desc[t.pair2];
+            k2 = (int)d.k;
+            hap2 = H->hap_bases + d.hoff;
+        }
+        const int lmax = (int)__reduce_max_sync(kFull, (unsigned)l);
+        const PairOut2 o = team_run_sr2<N>(rec, l, lmax, hap, k, hap2, k2, t.lt * N, t.lt, t.tlast,
+                                           t.nsteps, pow, R, s_ring);
+        if (t.lt == 0) {
+            if (t.pair != kNoPair) write_part(H, t.pair, o.a);
+            if (t.pair2 != kNoPair) write_part(H, t.pair2, o.b);
+        }
     }
 }
 

@@ -12,7 +12,7 @@ template <>
 __device__ const Rec32* dummy_rec<float>() { return &g_dummy32; }
 
 __global__ void k_reset(const BatchHeader* __restrict__ H) {
-    if (threadIdx.x < 4) H->counters[threadIdx.x] = 0u;
+    if (threadIdx.x < 8) H->counters[threadIdx.x] = 0u;
     if (threadIdx.x == 0) {
         H->status[0] = 0u;
         H->dropgrow[0] = 0u;
@@ -54,10 +54,11 @@ __global__ void __launch_bounds__(256) k_prep32(const BatchHeader* __restrict__ 
     build_desc(H);
 }
 
-template __global__ void k_forward<float, 16>(const BatchHeader*, const PowRow<float>*);
-template __global__ void k_forward<float, 24>(const BatchHeader*, const PowRow<float>*);
-template __global__ void k_forward<float, 32>(const BatchHeader*, const PowRow<float>*);
-template __global__ void k_finalize<float>(const BatchHeader*);
+template __global__ void k_forward<float, kNLong32, false>(const BatchHeader*, const PowRow<float>*);
+template __global__ void k_short_scalar<24>(const BatchHeader*, const PowRow<float>*);
+template __global__ void k_short_scalar<32>(const BatchHeader*, const PowRow<float>*);
+template __global__ void k_short_packed<12, 4>(const BatchHeader*, const PowRow<float>*);
+template __global__ void k_short_packed<16, 3>(const BatchHeader*, const PowRow<float>*);
 
 // Scan test: one warp, lane t owns y[32t .. 32t+31]; `row` is in global memory.
 __global__ void k_scan_test(const float* __restrict__ y, float* __restrict__ z, int n,
@@ -92,18 +93,47 @@ void launch_prep32(const BatchHeader* H, const PhredTables* T, int grid, cudaStr
     k_prep32<<<grid, 256, 0, s>>>(H, T);
 }
 
-void launch_forward32(int N, const BatchHeader* H, const void* pow, int grid, cudaStream_t s) {
-    const PowRow<float>* p = static_cast<const PowRow<float>*>(pow);
-    if (N == 16) k_forward<float, 16><<<grid, kCtaThreads, 0, s>>>(H, p);
-    else if (N == 24) k_forward<float, 24><<<grid, kCtaThreads, 0, s>>>(H, p);
-    else k_forward<float, 32><<<grid, kCtaThreads, 0, s>>>(H, p);
+void launch_forward32_long(const BatchHeader* H, const void* pow, int grid, cudaStream_t s) {
+    k_forward<float, kNLong32, false><<<grid, kCtaThreads, 0, s>>>(H, static_cast<const PowRow<float>*>(pow));
 }
 
-int occupancy_forward32(int N) {
+void launch_short_scalar(int N, const BatchHeader* H, const void* pow, int grid, cudaStream_t s) {
+    const PowRow<float>* p = static_cast<const PowRow<float>*>(pow);
+    if (N == 24) k_short_scalar<24><<<grid, kShortThreads, 0, s>>>(H, p);
+    else k_short_scalar<32><<<grid, kShortThreads, 0, s>>>(H, p);
+}
+
+void launch_short_packed(int N, const BatchHeader* H, const void* pow, int grid, cudaStream_t s) {
+    const PowRow<float>* p = static_cast<const PowRow<float>*>(pow);
+    if (N == 12) k_short_packed<12, 4><<<grid, kShortThreads, 0, s>>>(H, p);
+    else k_short_packed<16, 3><<<grid, kShortThreads, 0, s>>>(H, p);
+}
+
+static void prefer_smem(const void* f) {
+    cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+}
+
+int occupancy_short_scalar(int N) {
+    prefer_smem((const void*)k_short_scalar<24>);
+    prefer_smem((const void*)k_short_scalar<32>);
     int b = 0;
-    if (N == 16) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_forward<float, 16>, kCtaThreads, 0);
-    else if (N == 24) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_forward<float, 24>, kCtaThreads, 0);
-    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_forward<float, 32>, kCtaThreads, 0);
+    if (N == 24) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_short_scalar<24>, kShortThreads, 0);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_short_scalar<32>, kShortThreads, 0);
+    return b > 0 ? b : 1;
+}
+
+int occupancy_short_packed(int N) {
+    prefer_smem((const void*)k_short_packed<12, 4>);
+    prefer_smem((const void*)k_short_packed<16, 3>);
+    int b = 0;
+    if (N == 12) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_short_packed<12, 4>, kShortThreads, 0);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_short_packed<16, 3>, kShortThreads, 0);
+    return b > 0 ? b : 1;
+}
+
+int occupancy_forward32_long() {
+    int b = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_forward<float, kNLong32, false>, kCtaThreads, 0);
     return b > 0 ? b : 1;
 }
 

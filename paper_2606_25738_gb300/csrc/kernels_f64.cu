@@ -48,7 +48,7 @@ __global__ void __launch_bounds__(256) k_prep64_list(const BatchHeader* __restri
     }
 }
 
-template __global__ void k_forward<double, kN64>(const BatchHeader*, const PowRow<double>*);
+template __global__ void k_forward<double, kN64, true>(const BatchHeader*, const PowRow<double>*);
 template __global__ void k_finalize<double>(const BatchHeader*);
 
 __device__ __forceinline__ double log10_of(const Partial& q) {
@@ -116,7 +116,7 @@ void launch_prep64_list(const BatchHeader* H, const PhredTables* T, int grid, cu
     k_prep64_list<<<grid, 256, 0, s>>>(H, T);
 }
 void launch_forward64(const BatchHeader* H, const void* pow, int grid, cudaStream_t s) {
-    k_forward<double, kN64><<<grid, kCtaThreads, 0, s>>>(H, static_cast<const PowRow<double>*>(pow));
+    k_forward<double, kN64, true><<<grid, kCtaThreads, 0, s>>>(H, static_cast<const PowRow<double>*>(pow));
 }
 void launch_finalize64(const BatchHeader* H, int grid, cudaStream_t s) {
     k_finalize<double><<<grid, 256, 0, s>>>(H);
@@ -129,7 +129,7 @@ void launch_single64(const BatchHeader* H, const void* pow, uint32_t pair, cudaS
 }
 int occupancy_forward64() {
     int b = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_forward<double, kN64>, kCtaThreads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_forward<double, kN64, true>, kCtaThreads, 0);
     return b > 0 ? b : 1;
 }
 

@@ -12,9 +12,13 @@ struct PhredTables;
 // FP32 unit
 void launch_reset(const BatchHeader* H, cudaStream_t s);
 void launch_prep32(const BatchHeader* H, const PhredTables* T, int grid, cudaStream_t s);
-void launch_forward32(int N, const BatchHeader* H, const void* pow, int grid, cudaStream_t s);
+void launch_forward32_long(const BatchHeader* H, const void* pow, int grid, cudaStream_t s);
+void launch_short_scalar(int N, const BatchHeader* H, const void* pow, int grid, cudaStream_t s);
+void launch_short_packed(int N, const BatchHeader* H, const void* pow, int grid, cudaStream_t s);
 void launch_finalize32(const BatchHeader* H, int grid, cudaStream_t s);
-int occupancy_forward32(int N);  // resident CTAs per SM
+int occupancy_forward32_long();          // resident CTAs per SM
+int occupancy_short_scalar(int N);
+int occupancy_short_packed(int N);
 // pow_row: a device pointer to one PowRow<float>
 void launch_scan_test(const float* y, float* z, int n, const void* pow_row, cudaStream_t s);
 
@@ -27,6 +31,9 @@ void launch_rescue64(const BatchHeader* H, const void* pow, int grid, cudaStream
 void launch_single64(const BatchHeader* H, const void* pow, uint32_t pair, cudaStream_t s);
 int occupancy_forward64();
 
-constexpr int kN64 = 8;   // columns per lane of the FP64 kernels
+constexpr int kN64 = 8;       // columns per lane of the FP64 kernels
+constexpr int kNLong32 = 32;  // columns per lane of FP32 multi-warp pairs
+constexpr int kPackedNs[2] = {12, 16};  // FP32 packed same-read team widths
+constexpr int kScalarNs[2] = {24, 32};  // FP32 scalar team widths  // columns per lane of the FP64 kernels
 
 }  // namespace phmm

@@ -86,8 +86,13 @@ constexpr int kCtaWarps = 16;
 constexpr int kCtaThreads = kCtaWarps * 32;
 constexpr int kRing = 8;  // rows buffered between two warp segments
 
+constexpr uint32_t kNoPair = 0xffffffffu;
+
+// A team: G lanes of one warp running one pair, or (FP32) two pairs packed into the x / y
+// halves of float2 registers (pair2 = kNoPair when there is no second pair).
 struct Team {
     uint32_t pair;
+    uint32_t pair2;
     uint8_t base;   // first lane
     uint8_t size;   // lanes (G)
     uint16_t pad;
@@ -142,11 +147,12 @@ struct BatchHeader {
     Rec32 *rec32;
     Rec64 *rec64;
     // plan
-    const WarpItem *witems;
+    const WarpItem *witems;   // FP32: scalar teams; FP64: all teams
+    const WarpItem *witems2;  // FP32: packed same-read teams
     const Team *teams;
     const CtaItem *citems;
     const CtaPair *cpairs;
-    uint32_t n_witems, n_citems;
+    uint32_t n_witems, n_citems, n_witems2;
     uint32_t n_partials;
     uint32_t force_rescue;   // 1: every pair goes to the FP64 rescue pass
     Partial *parts;
@@ -155,7 +161,8 @@ struct BatchHeader {
     uint8_t *out_flags;      // n_pairs PHMM_PAIR_* bits
     uint32_t *rescue_list;   // pairs needing the FP64 pass
     // scratch counters (zeroed per launch by k_reset)
-    uint32_t *counters;      // [0] CTA items [1] warp items [2] rescue count [3] rescue items
+    uint32_t *counters;      // 8 words: [0] CTA items [1] warp items [2] rescue count
+                             // [3] rescue items [4] packed warp items
     uint32_t *status;        // ST_* bits
     uint32_t *dropgrow;      // [0] max drop bits * 64, [1] max grow bits * 64 (prep)
     uint32_t seed;

@@ -5,6 +5,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <limits>
 #include <mutex>
@@ -76,12 +77,15 @@ void release(HostBuf& b) {
 // ------------------------------------------------------------------------------------
 struct Plan {
     std::vector<Team> teams;
-    std::vector<WarpItem> witems;
+    std::vector<WarpItem> witems;   // scalar teams (FP64: all teams)
+    std::vector<WarpItem> witems2;  // FP32 packed same-read teams
     std::vector<CtaPair> cpairs;
     std::vector<CtaItem> citems;
     uint32_t n_long = 0, n_too_long = 0;
     double cost = 0.0;  // tuner cost model (lane-cell slots + per-row overheads)
-    int N = 0;
+    int N = 0;        // scalar team width (FP64: the only width)
+    int NP = 0;       // packed team width (0: no packed teams)
+    bool packed = false;
 };
 
 // Cost model constants (issue slots): per lane and cell of a row, and per lane and row
@@ -89,44 +93,40 @@ struct Plan {
 constexpr double kCellCost = 8.0;
 constexpr double kRowCost = 70.0;
 
-// Short pairs: teams of G = ceil(k/N) lanes, packed best-fit into 32-lane warps within
-// runs of similar read length (rows of a warp are the max over its teams).  Long pairs:
-// W = ceil(k / 32N) warps of one CTA, packed best-fit into 16-warp CTAs.
-void make_plan(const uint32_t* l, const uint32_t* k, uint32_t n, int N, Plan& P) {
-    P = Plan();
-    P.N = N;
-    const uint32_t short_max = 32u * (uint32_t)N;
-    std::vector<uint32_t> sh, lo;
-    sh.reserve(n);
-    for (uint32_t p = 0; p < n; ++p) {
-        if (k[p] <= short_max) sh.push_back(p);
-        else if ((k[p] + short_max - 1) / short_max <= (uint32_t)kCtaWarps) lo.push_back(p);
-        else P.n_too_long++;
-    }
-    auto G_of = [&](uint32_t p) { return (k[p] + (uint32_t)N - 1) / (uint32_t)N; };
-    std::stable_sort(sh.begin(), sh.end(), [&](uint32_t a, uint32_t b) {
-        if (l[a] != l[b]) return l[a] > l[b];
-        return G_of(a) > G_of(b);
+// Bin-pack teams (G lanes each) into 32-lane warp items within runs of similar row
+// count; a warp item runs the max row count of its teams.  Appends to `teams` / `items`.
+static void pack_teams(std::vector<Team>& run_teams, std::vector<uint32_t>& run_l,
+                       std::vector<Team>& teams, std::vector<WarpItem>& items, double cell_w,
+                       double& cost) {
+    // order by l descending, then G descending
+    std::vector<uint32_t> ord(run_teams.size());
+    for (size_t q = 0; q < ord.size(); ++q) ord[q] = (uint32_t)q;
+    std::stable_sort(ord.begin(), ord.end(), [&](uint32_t a, uint32_t b) {
+        if (run_l[a] != run_l[b]) return run_l[a] > run_l[b];
+        return run_teams[a].size > run_teams[b].size;
     });
-    // runs of similar l
-    size_t i = 0;
     struct Bin {
-        uint32_t first_team, n_teams, rem, lmax;
+        uint32_t rem, lmax;
+        int32_t head, tail;
     };
     std::vector<Bin> bins;
+    std::vector<Team> bt;
+    std::vector<int32_t> nxt;
     std::vector<std::vector<uint32_t>> open(33);
-    std::vector<std::vector<Team>> bin_teams;
-    while (i < sh.size()) {
-        const uint32_t l0 = l[sh[i]];
+    size_t i = 0;
+    while (i < ord.size()) {
+        const uint32_t l0 = run_l[ord[i]];
         size_t j = i;
-        while (j < sh.size() && (double)l[sh[j]] >= 0.94 * (double)l0) ++j;
-        std::vector<uint32_t> run(sh.begin() + i, sh.begin() + j);
-        std::stable_sort(run.begin(), run.end(), [&](uint32_t a, uint32_t b) { return G_of(a) > G_of(b); });
+        while (j < ord.size() && (double)run_l[ord[j]] >= 0.94 * (double)l0) ++j;
+        std::stable_sort(ord.begin() + i, ord.begin() + j,
+                         [&](uint32_t a, uint32_t b) { return run_teams[a].size > run_teams[b].size; });
         bins.clear();
-        bin_teams.clear();
+        bt.clear();
+        nxt.clear();
         for (auto& o : open) o.clear();
-        for (uint32_t p : run) {
-            const uint32_t G = G_of(p);
+        for (size_t q = i; q < j; ++q) {
+            Team t = run_teams[ord[q]];
+            const uint32_t G = t.size;
             int r = -1;
             for (uint32_t c = G; c <= 32; ++c)
                 if (!open[c].empty()) {
@@ -136,35 +136,101 @@ void make_plan(const uint32_t* l, const uint32_t* k, uint32_t n, int N, Plan& P)
             uint32_t b;
             if (r < 0) {
                 b = (uint32_t)bins.size();
-                bins.push_back({0, 0, 32, 0});
-                bin_teams.emplace_back();
+                bins.push_back({32, 0, -1, -1});
             } else {
                 b = open[r].back();
                 open[r].pop_back();
             }
-            Team t;
-            t.pair = p;
             t.base = (uint8_t)(32 - bins[b].rem);
-            t.size = (uint8_t)G;
-            t.pad = 0;
-            bin_teams[b].push_back(t);
+            bt.push_back(t);
+            nxt.push_back(-1);
+            const int32_t id = (int32_t)bt.size() - 1;
+            if (bins[b].tail < 0) bins[b].head = id;
+            else nxt[bins[b].tail] = id;
+            bins[b].tail = id;
             bins[b].rem -= G;
-            bins[b].lmax = std::max(bins[b].lmax, l[p]);
+            bins[b].lmax = std::max(bins[b].lmax, run_l[ord[q]]);
             if (bins[b].rem > 0) open[bins[b].rem].push_back(b);
         }
-        for (size_t b = 0; b < bins.size(); ++b) {
+        for (auto& bn : bins) {
             WarpItem w;
-            w.first_team = (uint32_t)P.teams.size();
-            w.n_teams = (uint32_t)bin_teams[b].size();
-            for (const Team& t : bin_teams[b]) P.teams.push_back(t);
-            P.witems.push_back(w);
-            P.cost += (double)bins[b].lmax * 32.0 * (N * kCellCost + kRowCost);
+            w.first_team = (uint32_t)teams.size();
+            w.n_teams = 0;
+            for (int32_t id = bn.head; id >= 0; id = nxt[id]) {
+                teams.push_back(bt[id]);
+                w.n_teams++;
+            }
+            items.push_back(w);
+            cost += (double)bn.lmax * 32.0 * (cell_w * kCellCost + kRowCost);
         }
         i = j;
     }
+}
+
+// Work plan.  Short pairs: a scalar team of G = ceil(k / Ns) lanes (k <= 32 Ns); with
+// NP > 0 (FP32), two pairs of the same read with k <= 32 NP share a packed team of
+// ceil(max k / NP) lanes (x / y halves).  Long pairs: W = ceil(k / (32 Nl)) warps of one
+// CTA, packed best-fit into 16-warp CTAs.  Items are ordered longest first.
+void make_plan(const uint32_t* l, const uint32_t* k, const uint32_t* pr, uint32_t n, int Ns, int NP,
+               int Nl, Plan& P) {
+    P = Plan();
+    P.N = Ns;
+    P.NP = NP;
+    P.packed = NP > 0;
+    const uint32_t short_max = 32u * (uint32_t)Ns, packed_max = 32u * (uint32_t)NP;
+    const uint32_t seg = 32u * (uint32_t)Nl;
+    std::vector<uint32_t> lo;
+    std::vector<Team> st, pt;  // scalar / packed teams
+    std::vector<uint32_t> sl, pl;
+    auto mk = [](uint32_t a, uint32_t b, uint32_t G) {
+        Team t;
+        t.pair = a;
+        t.pair2 = b;
+        t.base = 0;
+        t.size = (uint8_t)G;
+        t.pad = 0;
+        return t;
+    };
+    std::vector<uint32_t> pk;  // packed-eligible pairs, grouped by read below
+    for (uint32_t p = 0; p < n; ++p) {
+        if (NP > 0 && k[p] <= packed_max) pk.push_back(p);
+        else if (k[p] <= short_max) {
+            st.push_back(mk(p, kNoPair, (k[p] + Ns - 1) / Ns));
+            sl.push_back(l[p]);
+        } else if ((k[p] + seg - 1) / seg <= (uint32_t)kCtaWarps) lo.push_back(p);
+        else P.n_too_long++;
+    }
+    if (!pk.empty()) {
+        std::stable_sort(pk.begin(), pk.end(), [&](uint32_t a, uint32_t b) {
+            if (pr[a] != pr[b]) return pr[a] < pr[b];
+            return k[a] > k[b];
+        });
+        size_t q = 0;
+        while (q < pk.size()) {
+            size_t e = q;
+            while (e < pk.size() && pr[pk[e]] == pr[pk[q]]) ++e;
+            for (; q + 1 < e; q += 2) {
+                const uint32_t a = pk[q], b = pk[q + 1];
+                pt.push_back(mk(a, b, (std::max(k[a], k[b]) + NP - 1) / NP));
+                pl.push_back(l[a]);
+            }
+            if (q < e) {  // odd one out: a scalar team
+                const uint32_t a = pk[q];
+                if (k[a] <= short_max) {
+                    st.push_back(mk(a, kNoPair, (k[a] + Ns - 1) / Ns));
+                    sl.push_back(l[a]);
+                } else {
+                    lo.push_back(a);
+                }
+                ++q;
+            }
+        }
+    }
+    pack_teams(st, sl, P.teams, P.witems, (double)Ns, P.cost);
+    pack_teams(pt, pl, P.teams, P.witems2, 2.0 * NP * 1.2, P.cost);
     // long pairs
     P.n_long = (uint32_t)lo.size();
-    auto W_of = [&](uint32_t p) { return (k[p] + short_max - 1) / short_max; };
+    auto W_of = [&](uint32_t p) { return (k[p] + seg - 1) / seg; };
     std::stable_sort(lo.begin(), lo.end(), [&](uint32_t a, uint32_t b) {
         const double ca = (double)l[a] * W_of(a), cb = (double)l[b] * W_of(b);
         return ca > cb;
@@ -215,7 +281,7 @@ void make_plan(const uint32_t* l, const uint32_t* k, uint32_t n, int N, Plan& P)
             it.n = (uint32_t)c.pairs.size();
             for (auto& cp : c.pairs) P.cpairs.push_back(cp);
             P.citems.push_back(it);
-            P.cost += (double)c.lmax * kCtaWarps * 32.0 * (N * kCellCost + kRowCost);
+            P.cost += (double)c.lmax * kCtaWarps * 32.0 * (Nl * kCellCost * 1.6 + kRowCost);
         }
         a = b2;
     }
@@ -272,7 +338,7 @@ void build_pow_table(int N, std::vector<PowRow<T>>& out) {
 // ------------------------------------------------------------------------------------
 struct Slot {
     DevBuf in_bases, in_bq, in_iq, in_dq, in_gq, in_hap, in_roff, in_hoff, in_pr, in_ph;
-    DevBuf desc, rec32, rec64, teams, witems, cpairs, citems, parts, out, oflags, rescue;
+    DevBuf desc, rec32, rec64, teams, witems, witems2, cpairs, citems, parts, out, oflags, rescue;
     DevBuf small;  // counters[4], status[1], dropgrow[2]
     DevBuf hdr;
     HostBuf h_out, h_oflags, h_small, h_roff, h_hoff, h_pr, h_ph;
@@ -289,6 +355,10 @@ struct Slot {
     uint32_t n_pairs = 0;
     phmm_stats st{};
     bool has_stats = false;
+    Plan plan;
+    bool plan_valid = false;
+    uint64_t plan_hash = 0;
+    uint32_t plan_np = 0;
     int host_status = PHMM_OK;
 };
 
@@ -305,9 +375,12 @@ struct phmm_ctx {
     size_t budget = 0;
     DevBuf tables;                          // PhredTables
     DevBuf scan_row;                        // scan test: one PowRow<float> (global memory)
-    DevBuf pow32[3];                        // N = 16, 24, 32
+    DevBuf pow32[5];                        // N = 12, 16, 20, 24 (packed short), 32 (long)
     DevBuf pow64;
-    int occ32[3] = {1, 1, 1}, occ64 = 1;
+    int occ_packed[2] = {1, 1}, occ_scalar[2] = {1, 1}, occ_long = 1, occ64 = 1;
+    cudaStream_t stream2 = nullptr;         // graph branch: multi-warp pairs
+    cudaStream_t stream3 = nullptr;         // graph branch: packed short teams
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_join3 = nullptr;
     bool dead = false;
     uint32_t seed = 0x5eed1234u;
     uint64_t last_retired = 0;
@@ -316,8 +389,10 @@ struct phmm_ctx {
 
 namespace {
 
-const int kNs[3] = {16, 24, 32};
-int n_index(int N) { return N == 16 ? 0 : N == 24 ? 1 : 2; }
+const int kPowN[5] = {12, 16, 20, 24, 32};
+int pow_index(int N) { return N == 12 ? 0 : N == 16 ? 1 : N == 20 ? 2 : N == 24 ? 3 : 4; }
+
+
 
 #define CK(x)                                   \
     do {                                        \
@@ -328,7 +403,7 @@ int n_index(int N) { return N == 16 ? 0 : N == 24 ? 1 : 2; }
         }                                       \
     } while (0)
 
-int launch_sequence(phmm_ctx* ctx, Slot& S, int N, bool record_events) {
+int launch_sequence(phmm_ctx* ctx, Slot& S, int N, int NP, bool record_events) {
     cudaStream_t s = ctx->stream;
     const BatchHeader* H = static_cast<const BatchHeader*>(S.hdr.p);
     const PhredTables* T = static_cast<const PhredTables*>(ctx->tables.p);
@@ -350,7 +425,17 @@ int launch_sequence(phmm_ctx* ctx, Slot& S, int N, bool record_events) {
     } else {
         launch_prep32(H, T, grid_pre, s);
         CK(rec(S.ev_fwd0));
-        launch_forward32(N, H, ctx->pow32[n_index(N)].p, ctx->sms * ctx->occ32[n_index(N)], s);
+        // fork: multi-warp pairs and packed teams on two more branches, scalar teams here
+        CK(cudaEventRecord(ctx->ev_fork, s));
+        CK(cudaStreamWaitEvent(ctx->stream2, ctx->ev_fork, 0));
+        CK(cudaStreamWaitEvent(ctx->stream3, ctx->ev_fork, 0));
+        launch_forward32_long(H, ctx->pow32[pow_index(kNLong32)].p, ctx->sms * ctx->occ_long, ctx->stream2);
+        CK(cudaEventRecord(ctx->ev_join, ctx->stream2));
+        if (NP > 0) launch_short_packed(NP, H, ctx->pow32[pow_index(NP)].p, ctx->sms * ctx->occ_packed[NP == 12 ? 0 : 1], ctx->stream3);
+        CK(cudaEventRecord(ctx->ev_join3, ctx->stream3));
+        launch_short_scalar(N, H, ctx->pow32[pow_index(N)].p, ctx->sms * ctx->occ_scalar[N == 24 ? 0 : 1], s);
+        CK(cudaStreamWaitEvent(s, ctx->ev_join, 0));
+        CK(cudaStreamWaitEvent(s, ctx->ev_join3, 0));
         CK(rec(S.ev_fwd1));
         launch_finalize32(H, grid_pre, s);
         CK(rec(S.ev_res0));
@@ -364,8 +449,9 @@ int launch_sequence(phmm_ctx* ctx, Slot& S, int N, bool record_events) {
     return PHMM_OK;
 }
 
-int kernels_per_launch(int prec) {
-    return prec == PHMM_PREC_FP64 ? 4 : prec == PHMM_PREC_FP32_RESCUE ? 6 : 4;
+int kernels_per_launch(int prec, int NP) {
+    const int packed = NP > 0 ? 1 : 0;
+    return prec == PHMM_PREC_FP64 ? 4 : prec == PHMM_PREC_FP32_RESCUE ? 7 + packed : 5 + packed;
 }
 
 uint64_t u64(const void* p) { return (uint64_t)(uintptr_t)p; }
@@ -395,9 +481,13 @@ int phmm_create(const phmm_config* cfg, phmm_ctx** out) {
     if (!cfg || !out) return PHMM_EINVAL;
     *out = nullptr;
     if (cfg->precision < 0 || cfg->precision > 2) return PHMM_EINVAL;
-    if (cfg->cols_per_lane != 0 && cfg->cols_per_lane != 16 && cfg->cols_per_lane != 24 &&
-        cfg->cols_per_lane != 32)
-        return PHMM_EINVAL;
+    if (cfg->kernel_variant < 0 || cfg->kernel_variant > 2) return PHMM_EINVAL;
+    {
+        const int n = cfg->cols_per_lane;
+        const bool okp = n == 12 || n == 16;  // packed widths
+        const bool oks = n == 24 || n == 32;  // scalar widths
+        if (n != 0 && !(cfg->kernel_variant == 2 ? oks : (okp || oks))) return PHMM_EINVAL;
+    }
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || cfg->device < 0 || cfg->device >= ndev)
         return PHMM_ECUDA;
@@ -432,13 +522,25 @@ int phmm_create(const phmm_config* cfg, phmm_ctx** out) {
     build_phred_tables(T);
     if (ensure(ctx->tables, sizeof(T)) != cudaSuccess) return fail(PHMM_ECUDA);
     cudaMemcpy(ctx->tables.p, &T, sizeof(T), cudaMemcpyHostToDevice);
-    for (int q = 0; q < 3; ++q) {
+    for (int q = 0; q < 5; ++q) {
         std::vector<PowRow<float>> v;
-        build_pow_table<float>(kNs[q], v);
+        build_pow_table<float>(kPowN[q], v);
         if (ensure(ctx->pow32[q], v.size() * sizeof(v[0])) != cudaSuccess) return fail(PHMM_ECUDA);
         cudaMemcpy(ctx->pow32[q].p, v.data(), v.size() * sizeof(v[0]), cudaMemcpyHostToDevice);
-        ctx->occ32[q] = occupancy_forward32(kNs[q]);
     }
+    for (int q = 0; q < 2; ++q) ctx->occ_packed[q] = occupancy_short_packed(kPackedNs[q]);
+    for (int q = 0; q < 2; ++q) ctx->occ_scalar[q] = occupancy_short_scalar(kScalarNs[q]);
+    ctx->occ_long = occupancy_forward32_long();
+    if (getenv("PHMM_DEBUG"))
+        fprintf(stderr, "phmm: sms %d occupancy packed12 %d packed16 %d scalar24 %d scalar32 %d long %d fp64 %d\n",
+                ctx->sms, ctx->occ_packed[0], ctx->occ_packed[1], ctx->occ_scalar[0], ctx->occ_scalar[1],
+                ctx->occ_long, ctx->occ64);
+    if (cudaStreamCreateWithFlags(&ctx->stream2, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&ctx->stream3, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->ev_join3, cudaEventDisableTiming) != cudaSuccess)
+        return fail(PHMM_ECUDA);
     {
         std::vector<PowRow<double>> v;
         build_pow_table<double>(kN64, v);
@@ -468,7 +570,7 @@ void phmm_destroy(phmm_ctx* ctx) {
     for (auto& S : ctx->slots) {
         DevBuf* d[] = {&S.in_bases, &S.in_bq, &S.in_iq, &S.in_dq, &S.in_gq, &S.in_hap, &S.in_roff,
                        &S.in_hoff, &S.in_pr, &S.in_ph, &S.desc, &S.rec32, &S.rec64, &S.teams,
-                       &S.witems, &S.cpairs, &S.citems, &S.parts, &S.out, &S.oflags, &S.rescue,
+                       &S.witems, &S.witems2, &S.cpairs, &S.citems, &S.parts, &S.out, &S.oflags, &S.rescue,
                        &S.small, &S.hdr};
         for (auto* b : d) release(*b);
         HostBuf* h[] = {&S.h_out, &S.h_oflags, &S.h_small, &S.h_roff, &S.h_hoff, &S.h_pr, &S.h_ph};
@@ -480,6 +582,13 @@ void phmm_destroy(phmm_ctx* ctx) {
     }
     release(ctx->tables);
     release(ctx->scan_row);
+    if (ctx->stream2) cudaStreamSynchronize(ctx->stream2);
+    if (ctx->stream3) cudaStreamSynchronize(ctx->stream3);
+    if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+    if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
+    if (ctx->ev_join3) cudaEventDestroy(ctx->ev_join3);
+    if (ctx->stream2) cudaStreamDestroy(ctx->stream2);
+    if (ctx->stream3) cudaStreamDestroy(ctx->stream3);
     for (auto& b : ctx->pow32) release(b);
     release(ctx->pow64);
     if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
@@ -550,37 +659,55 @@ int phmm_submit_batch(phmm_ctx* ctx, const phmm_batch* b, uint64_t* ticket) {
         }
     }
     const uint64_t nbases = np > 0 ? roff[nr] : 0, nhb = np > 0 ? hoff[nh] : 0;
-    // plan (FP32: N from the config or the cost model; FP64: kN64)
-    Plan P;
-    int N = kN64;
-    if (ctx->cfg.precision == PHMM_PREC_FP64) {
-        make_plan(L.data(), K.data(), np, kN64, P);
-        N = kN64;
-    } else if (ctx->cfg.cols_per_lane) {
-        N = ctx->cfg.cols_per_lane;
-        make_plan(L.data(), K.data(), np, N, P);
-    } else {
-        Plan best;
-        bool have = false;
-        for (int q = 0; q < 3; ++q) {
-            Plan c;
-            make_plan(L.data(), K.data(), np, kNs[q], c);
-            const double pen = (double)c.n_too_long * 1e18;
-            if (!have || c.cost + pen < best.cost + (double)best.n_too_long * 1e18) {
-                best = std::move(c);
-                have = true;
-            }
-        }
-        P = std::move(best);
-        N = P.N;
+    // plan (FP32: packed short width from the config or the cost model; FP64: kN64).
+    // A batch with the same pair lengths as this slot's previous one reuses its plan.
+    const auto th0 = std::chrono::steady_clock::now();
+    uint64_t hsh = 1469598103934665603ull ^ ((uint64_t)ctx->cfg.precision << 32) ^ (uint64_t)ctx->cfg.cols_per_lane ^ ((uint64_t)ctx->cfg.kernel_variant << 40);
+    for (uint32_t p = 0; p < np; ++p) {
+        hsh = (hsh ^ ((uint64_t)L[p] << 24 ^ K[p])) * 1099511628211ull;
     }
+    hsh ^= np;
+    Plan& P = S->plan;
+    int N = kN64;
+    const bool reuse = S->plan_valid && S->plan_hash == hsh && S->plan_np == np;
+    if (!reuse) {
+        if (ctx->cfg.precision == PHMM_PREC_FP64) {
+            make_plan(L.data(), K.data(), pr, np, kN64, 0, kN64, P);
+        } else {
+            // kernel_variant 2: scalar teams only; otherwise pairs of the same read share
+            // packed teams.  cols_per_lane fixes the packed width (12, 16) or the scalar
+            // width (24, 32); anything left open is chosen by the cost model.
+            const int v = ctx->cfg.kernel_variant, n = ctx->cfg.cols_per_lane;
+            std::vector<std::pair<int, int>> cand;  // (Ns, NP)
+            for (int ns : {32, 24})
+                for (int npk : {16, 12, 0}) {
+                    if ((v == 2) != (npk == 0)) continue;
+                    if ((n == 24 || n == 32) && ns != n) continue;
+                    if ((n == 12 || n == 16) && npk != n) continue;
+                    cand.push_back({ns, npk});
+                }
+            Plan best;
+            bool have = false;
+            for (auto& cd : cand) {
+                Plan c;
+                make_plan(L.data(), K.data(), pr, np, cd.first, cd.second, kNLong32, c);
+                const double cost = c.cost + (double)c.n_too_long * 1e18;
+                if (!have || cost < best.cost + (double)best.n_too_long * 1e18) {
+                    best = std::move(c);
+                    have = true;
+                }
+            }
+            P = std::move(best);
+        }
+    }
+    N = P.N;
     // footprint and admission
     const bool need64 = ctx->cfg.precision != PHMM_PREC_FP32_ONLY;
     const uint64_t foot = (dev_in ? 0 : nbases * 5 + nhb + (nr + 1) * 8ull + (nh + 1) * 8ull + np * 8ull) +
                           np * (sizeof(PairDesc) + sizeof(Partial) + 8 + 1 + 4) +
                           (ctx->cfg.precision == PHMM_PREC_FP64 ? 0 : nbases * sizeof(Rec32)) +
                           (need64 ? nbases * sizeof(Rec64) : 0) +
-                          P.teams.size() * sizeof(Team) + P.witems.size() * sizeof(WarpItem) +
+                          P.teams.size() * sizeof(Team) + (P.witems.size() + P.witems2.size()) * sizeof(WarpItem) +
                           P.cpairs.size() * sizeof(CtaPair) + P.citems.size() * sizeof(CtaItem);
     if (foot > ctx->budget) return PHMM_ENOMEM;
     // device arenas
@@ -616,10 +743,13 @@ int phmm_submit_batch(phmm_ctx* ctx, const phmm_batch* b, uint64_t* ticket) {
     CK(ensure(S->desc, np * sizeof(PairDesc)));
     if (ctx->cfg.precision != PHMM_PREC_FP64) CK(ensure(S->rec32, nbases * sizeof(Rec32)));
     if (need64) CK(ensure(S->rec64, nbases * sizeof(Rec64)));
-    CK(ensure(S->teams, P.teams.size() * sizeof(Team)));
-    CK(ensure(S->witems, P.witems.size() * sizeof(WarpItem)));
-    CK(ensure(S->cpairs, P.cpairs.size() * sizeof(CtaPair)));
-    CK(ensure(S->citems, P.citems.size() * sizeof(CtaItem)));
+    if (!reuse) CK(ensure(S->teams, P.teams.size() * sizeof(Team)));
+    if (!reuse) {
+        CK(ensure(S->witems, P.witems.size() * sizeof(WarpItem)));
+        CK(ensure(S->witems2, P.witems2.size() * sizeof(WarpItem)));
+        CK(ensure(S->cpairs, P.cpairs.size() * sizeof(CtaPair)));
+        CK(ensure(S->citems, P.citems.size() * sizeof(CtaItem)));
+    }
     CK(ensure(S->parts, np * sizeof(Partial)));
     CK(ensure(S->out, np * 8ull));
     CK(ensure(S->oflags, np * 1ull));
@@ -627,10 +757,13 @@ int phmm_submit_batch(phmm_ctx* ctx, const phmm_batch* b, uint64_t* ticket) {
     CK(ensure(S->h_out, np * 8ull));
     CK(ensure(S->h_oflags, np * 1ull));
     cudaStream_t cs = ctx->copy_stream;
-    if (!P.teams.empty()) CK(cudaMemcpyAsync(S->teams.p, P.teams.data(), P.teams.size() * sizeof(Team), cudaMemcpyHostToDevice, cs));
-    if (!P.witems.empty()) CK(cudaMemcpyAsync(S->witems.p, P.witems.data(), P.witems.size() * sizeof(WarpItem), cudaMemcpyHostToDevice, cs));
-    if (!P.cpairs.empty()) CK(cudaMemcpyAsync(S->cpairs.p, P.cpairs.data(), P.cpairs.size() * sizeof(CtaPair), cudaMemcpyHostToDevice, cs));
-    if (!P.citems.empty()) CK(cudaMemcpyAsync(S->citems.p, P.citems.data(), P.citems.size() * sizeof(CtaItem), cudaMemcpyHostToDevice, cs));
+    if (!reuse) {
+        if (!P.teams.empty()) CK(cudaMemcpyAsync(S->teams.p, P.teams.data(), P.teams.size() * sizeof(Team), cudaMemcpyHostToDevice, cs));
+        if (!P.witems.empty()) CK(cudaMemcpyAsync(S->witems.p, P.witems.data(), P.witems.size() * sizeof(WarpItem), cudaMemcpyHostToDevice, cs));
+        if (!P.witems2.empty()) CK(cudaMemcpyAsync(S->witems2.p, P.witems2.data(), P.witems2.size() * sizeof(WarpItem), cudaMemcpyHostToDevice, cs));
+        if (!P.cpairs.empty()) CK(cudaMemcpyAsync(S->cpairs.p, P.cpairs.data(), P.cpairs.size() * sizeof(CtaPair), cudaMemcpyHostToDevice, cs));
+        if (!P.citems.empty()) CK(cudaMemcpyAsync(S->citems.p, P.citems.data(), P.citems.size() * sizeof(CtaItem), cudaMemcpyHostToDevice, cs));
+    }
     CK(cudaMemsetAsync(S->parts.p, 0, np * sizeof(Partial), cs));
     hh.n_read_bases = nbases;
     hh.n_reads = nr;
@@ -640,6 +773,8 @@ int phmm_submit_batch(phmm_ctx* ctx, const phmm_batch* b, uint64_t* ticket) {
     hh.rec32 = (Rec32*)S->rec32.p;
     hh.rec64 = (Rec64*)S->rec64.p;
     hh.witems = (const WarpItem*)S->witems.p;
+    hh.witems2 = (const WarpItem*)S->witems2.p;
+    hh.n_witems2 = (uint32_t)P.witems2.size();
     hh.teams = (const Team*)S->teams.p;
     hh.citems = (const CtaItem*)S->citems.p;
     hh.cpairs = (const CtaPair*)S->cpairs.p;
@@ -651,9 +786,9 @@ int phmm_submit_batch(phmm_ctx* ctx, const phmm_batch* b, uint64_t* ticket) {
     hh.out = (double*)S->out.p;
     hh.out_flags = (uint8_t*)S->oflags.p;
     hh.rescue_list = (uint32_t*)S->rescue.p;
-    hh.counters = (uint32_t*)S->small.p;
-    hh.status = (uint32_t*)S->small.p + 4;
-    hh.dropgrow = (uint32_t*)S->small.p + 5;
+    hh.counters = (uint32_t*)S->small.p;          // words 0..7
+    hh.status = (uint32_t*)S->small.p + 8;        // word 8
+    hh.dropgrow = (uint32_t*)S->small.p + 9;      // words 9, 10
     hh.seed = ctx->seed;
     hh.mode = (uint32_t)ctx->cfg.precision;
     CK(cudaMemcpyAsync(S->hdr.p, &hh, sizeof(hh), cudaMemcpyHostToDevice, cs));
@@ -680,13 +815,13 @@ int phmm_submit_batch(phmm_ctx* ctx, const phmm_batch* b, uint64_t* ticket) {
             CK(cudaGetLastError());
             launches = np + 3;
         } else if (use_graph) {
-            const int key = ctx->cfg.precision * 100 + N;
+            const int key = ctx->cfg.precision * 10000 + N * 100 + P.NP;
             if (!S->gexec || S->g_key != key) {
                 if (S->gexec) cudaGraphExecDestroy(S->gexec);
                 S->gexec = nullptr;
                 cudaGraph_t g = nullptr;
                 CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-                const int rc = launch_sequence(ctx, *S, N, true);
+                const int rc = launch_sequence(ctx, *S, N, P.NP, true);
                 cudaError_t e2 = cudaStreamEndCapture(s, &g);
                 if (rc != PHMM_OK || e2 != cudaSuccess) {
                     if (g) cudaGraphDestroy(g);
@@ -699,11 +834,11 @@ int phmm_submit_batch(phmm_ctx* ctx, const phmm_batch* b, uint64_t* ticket) {
                 S->g_key = key;
             }
             CK(cudaGraphLaunch(S->gexec, s));
-            launches = (uint32_t)kernels_per_launch(ctx->cfg.precision);
+            launches = (uint32_t)kernels_per_launch(ctx->cfg.precision, P.NP);
         } else {
-            const int rc = launch_sequence(ctx, *S, N, false);
+            const int rc = launch_sequence(ctx, *S, N, P.NP, false);
             if (rc != PHMM_OK) return rc;
-            launches = (uint32_t)kernels_per_launch(ctx->cfg.precision);
+            launches = (uint32_t)kernels_per_launch(ctx->cfg.precision, P.NP);
         }
         // outputs
         if (b->outputs_on_device) {
@@ -713,9 +848,9 @@ int phmm_submit_batch(phmm_ctx* ctx, const phmm_batch* b, uint64_t* ticket) {
             CK(cudaMemcpyAsync(S->h_out.p, S->out.p, np * 8ull, cudaMemcpyDeviceToHost, s));
             CK(cudaMemcpyAsync(S->h_oflags.p, S->oflags.p, np, cudaMemcpyDeviceToHost, s));
         }
-        CK(cudaMemcpyAsync(S->h_small.p, S->small.p, 32, cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(S->h_small.p, S->small.p, 64, cudaMemcpyDeviceToHost, s));
     } else {
-        memset(S->h_small.p, 0, 32);
+        memset(S->h_small.p, 0, 64);
         CK(cudaEventRecord(S->ev_fwd0, s));
         CK(cudaEventRecord(S->ev_fwd1, s));
         CK(cudaEventRecord(S->ev_res0, s));
@@ -733,9 +868,13 @@ int phmm_submit_batch(phmm_ctx* ctx, const phmm_batch* b, uint64_t* ticket) {
     S->st.cells = cells;
     S->st.n_pairs = np;
     S->st.n_long = P.n_long;
-    S->st.cols_per_lane = (uint32_t)N;
+    S->st.cols_per_lane = (uint32_t)(P.NP > 0 ? P.NP : N);
     S->st.kernel_launches = launches;
     S->host_status = P.n_too_long ? PHMM_EINVAL : PHMM_OK;
+    S->plan_valid = true;
+    S->plan_hash = hsh;
+    S->plan_np = np;
+    S->st.ms_host = (float)std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - th0).count();
     *ticket = S->ticket;
     return PHMM_OK;
 }
@@ -772,7 +911,7 @@ int phmm_poll(phmm_ctx* ctx, uint64_t ticket, int timeout_ms) {
     }
     const uint32_t* sm = static_cast<const uint32_t*>(S->h_small.p);
     S->st.n_rescued = sm[2];
-    S->st.status_bits = sm[4];
+    S->st.status_bits = sm[8];
     float ms = 0.f;
     cudaEventElapsedTime(&ms, S->ev_start, S->ev_end);
     S->st.ms_total = ms;
@@ -786,8 +925,8 @@ int phmm_poll(phmm_ctx* ctx, uint64_t ticket, int timeout_ms) {
     ctx->last_retired = S->ticket;
     S->state = 0;
     int rc = S->host_status;
-    if (sm[4] & ST_TIMEOUT) rc = PHMM_ETIMEOUT;
-    else if (sm[4] & (ST_BAD_INPUT | ST_TOO_LONG)) rc = PHMM_EINVAL;
+    if (sm[8] & ST_TIMEOUT) rc = PHMM_ETIMEOUT;
+    else if (sm[8] & (ST_BAD_INPUT | ST_TOO_LONG)) rc = PHMM_EINVAL;
     return rc;
 }
 

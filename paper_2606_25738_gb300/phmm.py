@@ -39,7 +39,7 @@ class Config(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int), ("precision", ctypes.c_int),
                 ("mem_budget_bytes", ctypes.c_size_t), ("max_inflight", ctypes.c_uint),
                 ("flags", ctypes.c_uint), ("stream", ctypes.c_void_p),
-                ("cols_per_lane", ctypes.c_int)]
+                ("cols_per_lane", ctypes.c_int), ("kernel_variant", ctypes.c_int)]
 
 
 class Batch(ctypes.Structure):
@@ -59,7 +59,7 @@ class Stats(ctypes.Structure):
                 ("cols_per_lane", ctypes.c_uint32), ("ms_total", ctypes.c_float),
                 ("ms_forward", ctypes.c_float), ("ms_rescue", ctypes.c_float),
                 ("ms_h2d", ctypes.c_float), ("kernel_launches", ctypes.c_uint32),
-                ("status_bits", ctypes.c_uint32)]
+                ("status_bits", ctypes.c_uint32), ("ms_host", ctypes.c_float)]
 
     def as_dict(self) -> dict:
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -120,9 +120,11 @@ class Context:
     """One library context (device, stream, arenas, captured graphs)."""
 
     def __init__(self, device: int = 0, precision: str = "fp32", flags: int = 0, stream=None,
-                 cols_per_lane: int = 0, mem_budget: int = 0, max_inflight: int = 2):
+                 cols_per_lane: int = 0, mem_budget: int = 0, max_inflight: int = 2,
+                 variant: str = "auto"):
         cfg = Config(device, PREC[precision], mem_budget, max_inflight, flags,
-                     ctypes.c_void_p(stream) if stream else None, cols_per_lane)
+                     ctypes.c_void_p(stream) if stream else None, cols_per_lane,
+                     {"auto": 0, "packed": 1, "scalar": 2}[variant])
         h = ctypes.c_void_p()
         rc = _lib.phmm_create(ctypes.byref(cfg), ctypes.byref(h))
         if rc != PHMM_OK:

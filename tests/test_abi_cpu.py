@@ -57,9 +57,13 @@ def test_create_rejects_bad_config(lib):
     import ctypes
     so = lib.library()
     h = ctypes.c_void_p()
-    cfg = lib.Config(0, 7, 0, 0, 0, None, 0)  # bad precision
+    cfg = lib.Config(0, 7, 0, 0, 0, None, 0, 0)  # bad precision
     assert so.phmm_create(ctypes.byref(cfg), ctypes.byref(h)) == lib.PHMM_EINVAL
-    cfg = lib.Config(0, 0, 0, 0, 0, None, 20)  # bad columns per lane
+    cfg = lib.Config(0, 0, 0, 0, 0, None, 13, 0)  # bad columns per lane
+    assert so.phmm_create(ctypes.byref(cfg), ctypes.byref(h)) == lib.PHMM_EINVAL
+    cfg = lib.Config(0, 0, 0, 0, 0, None, 12, 2)  # 12 is a packed width only
+    assert so.phmm_create(ctypes.byref(cfg), ctypes.byref(h)) == lib.PHMM_EINVAL
+    cfg = lib.Config(0, 0, 0, 0, 0, None, 0, 5)  # bad variant
     assert so.phmm_create(ctypes.byref(cfg), ctypes.byref(h)) == lib.PHMM_EINVAL
     assert so.phmm_create(None, ctypes.byref(h)) == lib.PHMM_EINVAL
 

@@ -67,22 +67,37 @@ def test_force_rescue_fp64_pass(phmm):
     assert np.max(np.abs(out - oracle.batch(b))) <= TOL64
 
 
-@pytest.mark.parametrize("N", [16, 24, 32])
-def test_columns_per_lane(phmm, N):
-    """Every compiled N gives oracle-equal results, including multi-warp pairs."""
-    b = W.plain_pairs(40, seed=11, k_range=(1, 40 * N), l_range=(1, 300), indel_rate=0.01)
-    with phmm.Context(precision="fp32", cols_per_lane=N) as ctx:
+VARIANTS = [("packed", 12), ("packed", 16), ("scalar", 24), ("scalar", 32)]
+
+
+@pytest.mark.parametrize("variant,N", [("packed", 12), ("packed", 16)])
+def test_packed_same_read_teams(phmm, variant, N):
+    """Active-region batches: haplotypes of the same read packed two per thread."""
+    b = W.short_read_regions(n_regions=30, seed=8)
+    with phmm.Context(precision="fp32_only", cols_per_lane=N, variant=variant) as ctx:
         out, flags, rc, st = ctx.run(b)
     assert st["cols_per_lane"] == N
+    ref = oracle.batch(b)
+    assert np.max(np.abs(out - ref)) <= TOL32
+    assert np.all((flags & 0x78) == 0)
+
+
+@pytest.mark.parametrize("variant,N", VARIANTS)
+def test_columns_per_lane(phmm, variant, N):
+    """Every compiled short-team kernel (packed: two pairs per lane; scalar) gives
+    oracle-equal results, together with multi-warp pairs beyond 32 N columns."""
+    b = W.plain_pairs(40, seed=11, k_range=(1, 40 * N), l_range=(1, 300), indel_rate=0.01)
+    with phmm.Context(precision="fp32", cols_per_lane=N, variant=variant) as ctx:
+        out, flags, rc, st = ctx.run(b)
     _check(out, flags, oracle.batch(b))
 
 
-@pytest.mark.parametrize("N", [16, 24, 32])
-def test_fp32_path_without_rescue(phmm, N):
-    """The FP32 engine alone (no FP64 rescue pass): short teams and multi-warp pairs up
-    to 16 warps stay within 1e-3 and none of them is flagged for rescue."""
-    b = W.plain_pairs(48, seed=12, k_range=(1, 16 * 32 * N), l_range=(1, 400), indel_rate=0.01)
-    with phmm.Context(precision="fp32_only", cols_per_lane=N) as ctx:
+@pytest.mark.parametrize("variant,N", VARIANTS)
+def test_fp32_path_without_rescue(phmm, variant, N):
+    """The FP32 engine alone (no FP64 rescue pass): packed short teams and multi-warp
+    pairs up to 16 warps x 1024 columns stay within 1e-3 and none is flagged for rescue."""
+    b = W.plain_pairs(48, seed=12, k_range=(1, 16384), l_range=(1, 400), indel_rate=0.01)
+    with phmm.Context(precision="fp32_only", cols_per_lane=N, variant=variant) as ctx:
         out, flags, rc, st = ctx.run(b)
     assert st["n_long"] > 0
     assert np.all((flags & 0x78) == 0), flags[(flags & 0x78) != 0]
@@ -90,7 +105,7 @@ def test_fp32_path_without_rescue(phmm, N):
     assert np.max(np.abs(out - ref)) <= TOL32
 
 
-def _edge_batch(N=32):
+def _edge_batch(N=16):
     rng = np.random.default_rng(3)
     rs = lambda n: "".join(rng.choice(list("ACGT"), size=n))
     hap = rs(300)
@@ -108,9 +123,10 @@ def _edge_batch(N=32):
         (hap[:60] + rs(40) + hap[60:150], hap, 30, 45, 45, 10),  # 40 bp insertion
         (hap[:N], hap[:N], 30, 45, 45, 10),          # k = N
         (hap[:N + 1], hap[:N + 1], 30, 45, 45, 10),  # k = N + 1
-        (rs(120), rs(32 * N), 30, 45, 45, 10),       # k = 32 N (one full warp)
-        (rs(120), rs(32 * N + 1), 30, 45, 45, 10),   # k = 32 N + 1 (two warps)
-        (rs(150), rs(3 * 32 * N - 1), 30, 45, 45, 10),
+        (rs(120), rs(32 * N), 30, 45, 45, 10),       # k = 32 N (one full packed team)
+        (rs(120), rs(32 * N + 1), 30, 45, 45, 10),   # k = 32 N + 1 (multi-warp path)
+        (rs(150), rs(3 * 1024 - 1), 30, 45, 45, 10), # three 1024-column warp segments
+        (rs(150), rs(3 * 1024 + 1), 30, 45, 45, 10),
         (rs(30), rs(600), 30, 45, 45, 10),
         (hap[:200], hap, np.arange(200) % 41, np.arange(200) % 30 + 15, 40, 10),  # per-row quals
         (hap[:150], hap, 25, 40, 40, np.arange(150) % 20 + 5),  # per-row gap continuation
@@ -119,10 +135,11 @@ def _edge_batch(N=32):
     return W.from_strings(pairs)
 
 
-@pytest.mark.parametrize("prec", ["fp32", "fp64"])
-def test_edge_cases(phmm, prec):
+@pytest.mark.parametrize("prec,variant", [("fp32", "packed"), ("fp32", "scalar"), ("fp64", "auto")])
+def test_edge_cases(phmm, prec, variant):
     b = _edge_batch()
-    with phmm.Context(precision=prec, cols_per_lane=32 if prec == "fp32" else 0) as ctx:
+    n = {"packed": 16, "scalar": 24}.get(variant, 0) if prec == "fp32" else 0
+    with phmm.Context(precision=prec, cols_per_lane=n, variant=variant) as ctx:
         out, flags, rc, st = ctx.run(b)
     ref = oracle.batch(b)
     if prec == "fp64":
@@ -140,8 +157,8 @@ def test_long_deletion_50bp(phmm):
     hap = "".join(rng.choice(list("ACGT"), size=2000))
     read = hap[100:700] + hap[750:1350]
     b = W.from_strings([(read, hap, 30, 45, 45, 10)])
-    for N in (16, 32):
-        with phmm.Context(precision="fp32", cols_per_lane=N) as ctx:
+    for N, v in ((12, "packed"), (16, "packed"), (24, "scalar"), (32, "scalar")):
+        with phmm.Context(precision="fp32", cols_per_lane=N, variant=v) as ctx:
             out, flags, rc, st = ctx.run(b)
         _check(out, flags, oracle.batch(b))
 
