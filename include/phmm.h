@@ -186,6 +186,29 @@ int phmm_device_info(phmm_ctx *ctx, int *sms, double *max_clock_mhz, double *cup
  */
 int phmm_scan_test(phmm_ctx *ctx, const float *y, float *z, int n, float a);
 
+/*
+ * Allocation-free FP32 forward pass (the paper has no counterpart: this is an interface
+ * for callers that cannot allocate device memory at call time -- code inside a host
+ * framework that owns the device heap and forbids cudaMalloc/cudaFree on its threads, or
+ * a process that reserved all device memory up front).  It needs no context and calls no
+ * allocating routine: besides the caller's buffers it uses fixed scratch arrays built
+ * into the library (about 32 MiB of read-row records plus small tables), which every GPU
+ * that loads the library keeps until the process exits.
+ *   device   CUDA device ordinal; the call makes it current for its duration.  The first
+ *            call on a device looks up the scratch addresses (cudaGetSymbolAddress), so
+ *            make that first call outside any stream capture.
+ *   stream   cudaStream_t to run on (NULL = legacy default stream); the call waits for
+ *            its own work to finish before returning.
+ *   batch    as for phmm_submit_batch, with inputs_on_device = outputs_on_device = 1 (all
+ *            pointers are device pointers) and out_flags required.
+ * Limits: at most 2^20 read bases in the batch (PHMM_ENOMEM beyond) and haplotypes of at
+ * most 1024 bases (such pairs get NaN and PHMM_PAIR_ERROR; the call returns PHMM_EINVAL).
+ * FP32 only (no FP64 rescue pass): out_flags reports PHMM_PAIR_DANGER / NONFINITE /
+ * DEGENERATE where the regular API would rescue.  All calls share the scratch, so calls
+ * that overlap on the GPU (other streams or threads) race and must be serialised.
+ */
+int phmm_forward_noalloc(int device, void *stream, const phmm_batch *batch);
+
 #ifdef __cplusplus
 }
 #endif

@@ -13,7 +13,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libphmm.so")
-SOURCES = ["kernels_f32.cu", "kernels_f64.cu", "runtime.cu"]
+SOURCES = ["kernels_f32.cu", "kernels_f64.cu", "runtime.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "-diag-suppress", "177", "-I" + os.path.join(ROOT, "include"), "-I" + CSRC]

@@ -25,7 +25,8 @@ PAIR_DANGER, PAIR_NONFINITE, PAIR_SMALL_SUM, PAIR_DEGENERATE = 0x8, 0x10, 0x20, 
 
 # Every entry point declared in include/phmm.h.
 SYMBOLS = ["phmm_create", "phmm_submit_batch", "phmm_poll", "phmm_get_stats", "phmm_destroy",
-           "phmm_strerror", "phmm_abi_version", "phmm_device_info", "phmm_scan_test"]
+           "phmm_strerror", "phmm_abi_version", "phmm_device_info", "phmm_scan_test",
+           "phmm_forward_noalloc"]
 
 
 class PhmmError(RuntimeError):
@@ -82,6 +83,7 @@ def _load() -> ctypes.CDLL:
                                      ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
     lib.phmm_scan_test.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
                                    ctypes.c_float]
+    lib.phmm_forward_noalloc.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(Batch)]
     return lib
 
 
@@ -225,3 +227,15 @@ class Context:
         if rc != PHMM_OK:
             raise PhmmError(rc, "phmm_scan_test")
         return z
+
+
+def forward_noalloc(d: dict, out, out_flags, device: int = 0, stream=None) -> int:
+    """phmm_forward_noalloc: FP32 forward pass for callers that cannot allocate device
+    memory (see include/phmm.h).  ``d`` holds torch CUDA tensors (see to_device), ``out``
+    a float64 and ``out_flags`` a uint8 CUDA tensor of n_pairs.  Returns the status."""
+    ptr = {k: ctypes.c_void_p(v.data_ptr()) for k, v in d.items() if hasattr(v, "data_ptr")}
+    bb = Batch(len(d["read_off"]) - 1, ptr["read_bases"], ptr["read_off"], ptr["base_q"], ptr["ins_q"],
+               ptr["del_q"], ptr["gcp_q"], len(d["hap_off"]) - 1, ptr["hap_bases"], ptr["hap_off"],
+               len(d["pair_read"]), ptr["pair_read"], ptr["pair_hap"], ctypes.c_void_p(out.data_ptr()),
+               ctypes.c_void_p(out_flags.data_ptr()), 1, 1)
+    return _lib.phmm_forward_noalloc(device, ctypes.c_void_p(stream) if stream else None, ctypes.byref(bb))
