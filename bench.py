@@ -164,7 +164,8 @@ def run_ours(args):
     out = torch.empty(n, dtype=torch.float64, device="cuda")
     fl = torch.zeros(n, dtype=torch.uint8, device="cuda")
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # > L2 (129 MB)
-    ctx = phmm.Context(device=dev, precision="fp32", stream=stream.cuda_stream, max_inflight=2)
+    ctx = phmm.Context(device=dev, precision="fp32", stream=stream.cuda_stream, max_inflight=2,
+                       variant=args.variant, cols_per_lane=args.cols)
     info = ctx.device_info()
 
     def step():
@@ -277,6 +278,9 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--variant", default="auto", choices=["auto", "packed", "scalar"],
+                    help="short-pair kernel family (default: the built-in tuner decides)")
+    ap.add_argument("--cols", type=int, default=0, help="columns per lane (0: tuner)")
     ap.add_argument("--regions", type=int, default=2000,
                     help="active regions of the workload (2000 = the benchmark size; smaller "
                          "values only for profiling captures)")

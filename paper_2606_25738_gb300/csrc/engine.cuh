@@ -97,12 +97,15 @@ struct Num<double> {
     }
 };
 
-// x * 2^s for any s (two exact steps when 2^s alone is not representable).
+// x * 2^s (two exact steps when 2^s alone is not representable; shifts beyond twice the
+// exponent range saturate: to 0 downwards, to the largest factors upwards, where a
+// nonzero x overflows to inf and the next checkpoint flags it).
 template <typename T>
 __device__ __forceinline__ T scale2(T x, int s) {
     using NT = Num<T>;
     if (s >= NT::kMinExp && s <= NT::kMaxExp) return x * NT::pow2(s);
     if (s < 2 * NT::kMinExp) return T(0);
+    if (s > 2 * NT::kMaxExp) s = 2 * NT::kMaxExp;
     const int s1 = s / 2;
     return (x * NT::pow2(s1)) * NT::pow2(s - s1);
 }
@@ -252,6 +255,8 @@ struct SmemLink {
     unsigned long long* out_ring;  // next segment's ring
     volatile int* my_cons;         // rows I have consumed (written by me)
     volatile int* next_cons;       // rows the next segment consumed (read by me)
+    unsigned long long* in_g;      // strip boundary in global memory (row-indexed), or null
+    unsigned long long* out_g;     // ... outbound, or null
     bool has_left, has_right;
 };
 
@@ -334,6 +339,40 @@ __device__ bool link_recv(const SmemLink& L, int row, T& m, T& i, T& d, int& e) 
     }
     unpack_vals<T>(w, m, i, d, e);
     *L.my_cons = row;
+    return ok;
+}
+
+// Strip boundaries in global memory: one slot of kWords tagged words per row (no ring,
+// no back-pressure: the buffer holds every row), written once per launch.
+template <typename T>
+__device__ __forceinline__ void link_send_g(unsigned long long* base, int row, T m, T i, T d, int e) {
+    constexpr int W = Num<T>::kWords;
+    uint32_t w[W];
+    pack_vals<T>(m, i, d, e, w);
+    unsigned long long* slot = base + (size_t)(row - 1) * W;
+#pragma unroll
+    for (int q = 0; q < W; ++q) st_vol(slot + q, tagw(w[q], row));
+}
+template <typename T>
+__device__ bool link_recv_g(const unsigned long long* base, int row, T& m, T& i, T& d, int& e) {
+    constexpr int W = Num<T>::kWords;
+    const unsigned long long* slot = base + (size_t)(row - 1) * W;
+    uint32_t w[W];
+    bool ok = true;
+    long long spins = 0;
+    for (;;) {
+        bool all = true;
+#pragma unroll
+        for (int q = 0; q < W; ++q) {
+            const unsigned long long v = ld_vol(slot + q);
+            w[q] = (uint32_t)(v >> 32);
+            all &= ((uint32_t)v == (uint32_t)row);
+        }
+        if (all) break;
+        if (++spins > kSpinLimit) { ok = false; break; }
+        __nanosleep(64);
+    }
+    unpack_vals<T>(w, m, i, d, e);
     return ok;
 }
 
@@ -464,7 +503,9 @@ __device__ SegOut seg_run(const typename Num<T>::Rec* __restrict__ rec, int l, i
         if (LINKED && link.has_left) {
             int e_in = 0;
             if ((threadIdx.x & 31) == 0) {
-                if (!link_recv<T>(link, i, lM, lI, lD, e_in)) {
+                const bool ok = link.in_g ? link_recv_g<T>(link.in_g, i, lM, lI, lD, e_in)
+                                          : link_recv<T>(link, i, lM, lI, lD, e_in);
+                if (!ok) {
                     flags |= PF_TIMEOUT;
                     atomicOr(status, ST_TIMEOUT);
                 }
@@ -486,7 +527,12 @@ __device__ SegOut seg_run(const typename Num<T>::Rec* __restrict__ rec, int l, i
             int desired = E;
             if (e == INT_MAX) {
                 if (i <= l) flags |= PF_NONFINITE;
-            } else if (e != INT_MIN && (e > NT::kHi || e <= NT::kLo)) {
+            } else if (e == INT_MIN) {
+                // Nothing representable in this segment: follow the left neighbour's scale,
+                // so that mass arriving later from the left is not converted across a
+                // gap wider than the format's range.
+                if (LINKED && link.has_left) desired = INT_MIN;
+            } else if (e > NT::kHi || e <= NT::kLo) {
                 desired = E + (e - NT::kTarget);
             }
             Enew = desired;
@@ -495,6 +541,7 @@ __device__ SegOut seg_run(const typename Num<T>::Rec* __restrict__ rec, int l, i
                 Enew = Eleft;
                 forced = true;
             }
+            if (Enew == INT_MIN) Enew = E;
             // A segment whose largest value is zero or subnormal holds no mass of its
             // own (it sits beside the alignment band); an empty row as a whole is caught
             // by the underflow test on the final sum.
@@ -525,7 +572,9 @@ __device__ SegOut seg_run(const typename Num<T>::Rec* __restrict__ rec, int l, i
         const T Dlast = fma(Wd * pw.last1(), pw.last2(), yprev);
 
         if (LINKED && link.has_right && (threadIdx.x & 31) == 31) {
-            if (!link_send<T>(link, i, M[N - 1], I[N - 1], Dlast, E)) {
+            if (link.out_g) {
+                link_send_g<T>(link.out_g, i, M[N - 1], I[N - 1], Dlast, E);
+            } else if (!link_send<T>(link, i, M[N - 1], I[N - 1], Dlast, E)) {
                 flags |= PF_TIMEOUT;
                 atomicOr(status, ST_TIMEOUT);
             }

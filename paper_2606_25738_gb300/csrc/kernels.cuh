@@ -203,11 +203,15 @@ __device__ __forceinline__ void cta_clear(CtaShared<T>& sh) {
     if (threadIdx.x <= kCtaWarps) sh.cons[threadIdx.x] = 0;
 }
 
-// Warps w0 .. w0+W-1 of the CTA run pair `pair`, one column segment of 32 N each.
+// Warps w0 .. w0+W-1 of the CTA run one strip of a pair: segment (warp) s covers
+// columns col0 + s * 32 N .. + 32 N - 1.  Neighbouring warps link through the CTA's
+// shared-memory rings; the strip's first / last warp links to the previous / next strip
+// through global boundaries bnd_in / bnd_out (null: none).
 template <typename T, int N>
-__device__ __forceinline__ void cta_pair_run(const BatchHeader* __restrict__ H,
-                                             const PowRow<T>* __restrict__ pow, uint32_t pair,
-                                             int w0, int W, CtaShared<T>& sh, int R) {
+__device__ __forceinline__ void cta_strip_run(const BatchHeader* __restrict__ H,
+                                              const PowRow<T>* __restrict__ pow, uint32_t pair,
+                                              int w0, int W, uint32_t col0, unsigned long long* bnd_in,
+                                              unsigned long long* bnd_out, CtaShared<T>& sh, int R) {
     constexpr int KW = Num<T>::kWords;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int s = warp - w0;
@@ -218,11 +222,13 @@ __device__ __forceinline__ void cta_pair_run(const BatchHeader* __restrict__ H,
     L.out_ring = sh.ring + min(warp + 1, kCtaWarps - 1) * kRing * KW;
     L.my_cons = sh.cons + warp;
     L.next_cons = sh.cons + warp + 1;
-    L.has_left = s > 0;
-    L.has_right = s < W - 1;
-    const int col0 = (s * 32 + lane) * N;
+    L.in_g = (s == 0) ? bnd_in : nullptr;
+    L.out_g = (s == W - 1) ? bnd_out : nullptr;
+    L.has_left = s > 0 || bnd_in != nullptr;
+    L.has_right = s < W - 1 || bnd_out != nullptr;
+    const int c0 = (int)col0 + (s * 32 + lane) * N;
     const SegOut o = seg_run<T, N, true>(recs_of<T>(H) + d.roff, (int)d.l, (int)d.l,
-                                         H->hap_bases + d.hoff, (int)d.k, col0, lane, 31, 5,
+                                         H->hap_bases + d.hoff, (int)d.k, c0, lane, 31, 5,
                                          pow, R, L, H->status);
     if (lane == 0) sh.out[warp] = o;
 }
@@ -248,6 +254,71 @@ __device__ __forceinline__ Partial cta_combine(const CtaShared<T>& sh, int w0, i
     p.n_extra = 0;
     p.extra_base = 0;
     return p;
+}
+
+// Partial slot of a strip: strip 0 at the pair's slot (carrying where the other strips'
+// partials live), strip s >= 1 at extra_base + s - 1.
+__device__ __forceinline__ void write_strip_part(const BatchHeader* __restrict__ H, uint32_t pair,
+                                                 uint32_t strip, uint32_t nstrip, uint32_t extra_base,
+                                                 Partial p) {
+    if (strip == 0) {
+        p.n_extra = nstrip - 1;
+        p.extra_base = extra_base;
+        H->parts[pair] = p;
+    } else {
+        p.n_extra = 0;
+        p.extra_base = 0;
+        H->parts[extra_base + strip - 1] = p;
+    }
+}
+
+// A whole pair on this CTA, strip after strip (rescue pass, launch-per-pair comparator):
+// strip s reads boundary (s-1)&1 and writes boundary s&1 of this CTA's two scratch
+// boundaries; each strip finishes before the next starts.  Returns the combined partial
+// in thread 0.
+template <typename T, int N>
+__device__ Partial cta_pair_sequential(const BatchHeader* __restrict__ H, const PowRow<T>* __restrict__ pow,
+                                       uint32_t pair, CtaShared<T>& sh, int R, unsigned long long* scratch,
+                                       uint64_t half_words) {
+    const PairDesc d = H->desc[pair];
+    const uint32_t seg = 32u * N;
+    const uint32_t Wt = (d.k + seg - 1) / seg;
+    const uint32_t S = (Wt + kCtaWarps - 1) / kCtaWarps;
+    int Eref = INT_MIN;
+    double Sum = 0.0;
+    uint32_t fl = 0;
+    for (uint32_t st = 0; st < S; ++st) {
+        const int W = (int)min((uint32_t)kCtaWarps, Wt - st * kCtaWarps);
+        cta_clear<T>(sh);
+        __syncthreads();
+        unsigned long long* bin = st > 0 ? scratch + ((st - 1) & 1) * half_words : nullptr;
+        unsigned long long* bout = st + 1 < S ? scratch + (st & 1) * half_words : nullptr;
+        cta_strip_run<T, N>(H, pow, pair, 0, W, st * kCtaWarps * seg, bin, bout, sh, R);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const Partial q = cta_combine<T>(sh, 0, W);
+            fl |= q.flags;
+            if (q.S != 0.0) {
+                if (Eref == INT_MIN) {
+                    Eref = q.E;
+                    Sum = q.S;
+                } else if (q.E > Eref) {
+                    Sum = ldexp(Sum, Eref - q.E) + q.S;
+                    Eref = q.E;
+                } else {
+                    Sum += ldexp(q.S, q.E - Eref);
+                }
+            }
+        }
+        __syncthreads();
+    }
+    Partial r;
+    r.S = Sum;
+    r.E = Eref == INT_MIN ? 0 : Eref;
+    r.flags = fl | PF_DONE;
+    r.n_extra = 0;
+    r.extra_base = 0;
+    return r;
 }
 
 template <typename T>
@@ -333,13 +404,17 @@ k_forward(const BatchHeader* __restrict__ H, const PowRow<T>* __restrict__ pow) 
         for (uint32_t q = 0; q < ci.n; ++q) {
             const CtaPair cp = H->cpairs[ci.first + q];
             if (warp >= cp.w0 && warp < cp.w0 + cp.W)
-                cta_pair_run<T, N>(H, pow, cp.pair, cp.w0, cp.W, sh, R);
+                cta_strip_run<T, N>(H, pow, cp.pair, cp.w0, cp.W, cp.col0,
+                                    cp.bnd_in == kNoBnd ? nullptr : H->bnd + cp.bnd_in,
+                                    cp.bnd_out == kNoBnd ? nullptr : H->bnd + cp.bnd_out, sh, R);
         }
         __syncthreads();
         if ((threadIdx.x & 31) == 0) {
             for (uint32_t q = 0; q < ci.n; ++q) {
                 const CtaPair cp = H->cpairs[ci.first + q];
-                if (warp == cp.w0) H->parts[cp.pair] = cta_combine<T>(sh, cp.w0, cp.W);
+                if (warp == cp.w0)
+                    write_strip_part(H, cp.pair, cp.strip, cp.nstrip, cp.extra_base,
+                                     cta_combine<T>(sh, cp.w0, cp.W));
             }
         }
         __syncthreads();
@@ -386,9 +461,10 @@ __device__ __forceinline__ TeamOf team_of(const Team* __restrict__ teams, const 
 // Small CTAs: residency is set by registers, not by a CTA-wide shape.
 constexpr int kShortThreads = 128;
 
-// Lean scalar teams, N columns per lane (item list witems / counters[1]).
-template <int N>
-__global__ void __launch_bounds__(kShortThreads, 4)
+// Lean scalar teams, N columns per lane (item list witems / counters[1]); MINB resident
+// CTAs per SM bound the registers per thread.
+template <int N, int MINB>
+__global__ void __launch_bounds__(kShortThreads, MINB)
 k_short_scalar(const BatchHeader* __restrict__ H, const PowRow<float>* __restrict__ pow) {
     Rec32* const s_ring = nullptr;  // records are prefetched through registers
     const int R = checkpoint_interval<float>(H->dropgrow);
@@ -466,8 +542,28 @@ __global__ void k_finalize(const BatchHeader* __restrict__ H) {
     const uint32_t n = H->n_pairs;
     const uint32_t mode = H->mode;
     for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
-        const Partial q = H->parts[p];
+        Partial q = H->parts[p];
         const PairDesc d = H->desc[p];
+        if ((q.flags & PF_DONE) && q.n_extra > 0) {
+            // strips of a wide pair: L * C = sum_s S_s 2^(E_s)
+            int Eref = q.S != 0.0 ? q.E : INT_MIN;
+            for (uint32_t e = 0; e < q.n_extra; ++e) {
+                const Partial x = H->parts[q.extra_base + e];
+                q.flags |= x.flags;
+                if (!(x.flags & PF_DONE)) q.flags &= ~PF_DONE;
+                if (x.S != 0.0) Eref = max(Eref, x.E);
+            }
+            double Sum = 0.0;
+            if (Eref != INT_MIN) {
+                if (q.S != 0.0) Sum += ldexp(q.S, q.E - Eref);
+                for (uint32_t e = 0; e < q.n_extra; ++e) {
+                    const Partial x = H->parts[q.extra_base + e];
+                    if (x.S != 0.0) Sum += ldexp(x.S, x.E - Eref);
+                }
+                q.E = Eref;
+            }
+            q.S = Sum;
+        }
         uint32_t f = q.flags;
         double v;
         uint8_t of = 0;

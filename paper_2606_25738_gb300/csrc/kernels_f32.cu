@@ -11,13 +11,20 @@ __device__ Rec32 g_dummy32;
 template <>
 __device__ const Rec32* dummy_rec<float>() { return &g_dummy32; }
 
+// Zeroes the work counters and status words, and clears the strip boundary buffer (its
+// row tags must not survive from an earlier launch).
 __global__ void k_reset(const BatchHeader* __restrict__ H) {
-    if (threadIdx.x < 8) H->counters[threadIdx.x] = 0u;
-    if (threadIdx.x == 0) {
-        H->status[0] = 0u;
-        H->dropgrow[0] = 0u;
-        H->dropgrow[1] = 0u;
+    if (blockIdx.x == 0) {
+        if (threadIdx.x < 8) H->counters[threadIdx.x] = 0u;
+        if (threadIdx.x == 0) {
+            H->status[0] = 0u;
+            H->dropgrow[0] = 0u;
+            H->dropgrow[1] = 0u;
+        }
     }
+    const uint64_t n = H->n_bnd_words;
+    for (uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (uint64_t)gridDim.x * blockDim.x)
+        H->bnd[q] = 0ull;
 }
 
 // One record per read base, plus pair descriptors and the batch's drop / grow maxima.
@@ -55,8 +62,10 @@ __global__ void __launch_bounds__(256) k_prep32(const BatchHeader* __restrict__ 
 }
 
 template __global__ void k_forward<float, kNLong32, false>(const BatchHeader*, const PowRow<float>*);
-template __global__ void k_short_scalar<24>(const BatchHeader*, const PowRow<float>*);
-template __global__ void k_short_scalar<32>(const BatchHeader*, const PowRow<float>*);
+template __global__ void k_short_scalar<32, 4>(const BatchHeader*, const PowRow<float>*);
+template __global__ void k_short_scalar<24, 4>(const BatchHeader*, const PowRow<float>*);
+template __global__ void k_short_scalar<24, 5>(const BatchHeader*, const PowRow<float>*);
+template __global__ void k_short_scalar<16, 6>(const BatchHeader*, const PowRow<float>*);
 template __global__ void k_short_packed<12, 4>(const BatchHeader*, const PowRow<float>*);
 template __global__ void k_short_packed<16, 3>(const BatchHeader*, const PowRow<float>*);
 
@@ -87,7 +96,7 @@ __global__ void k_scan_test(const float* __restrict__ y, float* __restrict__ z, 
     }
 }
 
-void launch_reset(const BatchHeader* H, cudaStream_t s) { k_reset<<<1, 32, 0, s>>>(H); }
+void launch_reset(const BatchHeader* H, int grid, cudaStream_t s) { k_reset<<<grid, 256, 0, s>>>(H); }
 
 void launch_prep32(const BatchHeader* H, const PhredTables* T, int grid, cudaStream_t s) {
     k_prep32<<<grid, 256, 0, s>>>(H, T);
@@ -97,38 +106,45 @@ void launch_forward32_long(const BatchHeader* H, const void* pow, int grid, cuda
     k_forward<float, kNLong32, false><<<grid, kCtaThreads, 0, s>>>(H, static_cast<const PowRow<float>*>(pow));
 }
 
-void launch_short_scalar(int N, const BatchHeader* H, const void* pow, int grid, cudaStream_t s) {
-    const PowRow<float>* p = static_cast<const PowRow<float>*>(pow);
-    if (N == 24) k_short_scalar<24><<<grid, kShortThreads, 0, s>>>(H, p);
-    else k_short_scalar<32><<<grid, kShortThreads, 0, s>>>(H, p);
+// Short-pair kernel variants (ids used by the runtime's tuner):
+//   scalar id 0: N 32, 4 CTAs/SM   1: N 24, 4   2: N 24, 5   3: N 16, 6
+//   packed id 0: N 12, 4 CTAs/SM   1: N 16, 3
+template <typename K>
+static int occ_of(K kern) {
+    cudaFuncSetAttribute((const void*)kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                         cudaSharedmemCarveoutMaxShared);
+    int b = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, kShortThreads, 0);
+    return b > 0 ? b : 1;
 }
 
-void launch_short_packed(int N, const BatchHeader* H, const void* pow, int grid, cudaStream_t s) {
+void launch_short_scalar(int id, const BatchHeader* H, const void* pow, int grid, cudaStream_t s) {
     const PowRow<float>* p = static_cast<const PowRow<float>*>(pow);
-    if (N == 12) k_short_packed<12, 4><<<grid, kShortThreads, 0, s>>>(H, p);
+    switch (id) {
+    case 1: k_short_scalar<24, 4><<<grid, kShortThreads, 0, s>>>(H, p); break;
+    case 2: k_short_scalar<24, 5><<<grid, kShortThreads, 0, s>>>(H, p); break;
+    case 3: k_short_scalar<16, 6><<<grid, kShortThreads, 0, s>>>(H, p); break;
+    default: k_short_scalar<32, 4><<<grid, kShortThreads, 0, s>>>(H, p); break;
+    }
+}
+
+void launch_short_packed(int id, const BatchHeader* H, const void* pow, int grid, cudaStream_t s) {
+    const PowRow<float>* p = static_cast<const PowRow<float>*>(pow);
+    if (id == 0) k_short_packed<12, 4><<<grid, kShortThreads, 0, s>>>(H, p);
     else k_short_packed<16, 3><<<grid, kShortThreads, 0, s>>>(H, p);
 }
 
-static void prefer_smem(const void* f) {
-    cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+int occupancy_short_scalar(int id) {
+    switch (id) {
+    case 1: return occ_of(k_short_scalar<24, 4>);
+    case 2: return occ_of(k_short_scalar<24, 5>);
+    case 3: return occ_of(k_short_scalar<16, 6>);
+    default: return occ_of(k_short_scalar<32, 4>);
+    }
 }
 
-int occupancy_short_scalar(int N) {
-    prefer_smem((const void*)k_short_scalar<24>);
-    prefer_smem((const void*)k_short_scalar<32>);
-    int b = 0;
-    if (N == 24) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_short_scalar<24>, kShortThreads, 0);
-    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_short_scalar<32>, kShortThreads, 0);
-    return b > 0 ? b : 1;
-}
-
-int occupancy_short_packed(int N) {
-    prefer_smem((const void*)k_short_packed<12, 4>);
-    prefer_smem((const void*)k_short_packed<16, 3>);
-    int b = 0;
-    if (N == 12) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_short_packed<12, 4>, kShortThreads, 0);
-    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_short_packed<16, 3>, kShortThreads, 0);
-    return b > 0 ? b : 1;
+int occupancy_short_packed(int id) {
+    return id == 0 ? occ_of(k_short_packed<12, 4>) : occ_of(k_short_packed<16, 3>);
 }
 
 int occupancy_forward32_long() {

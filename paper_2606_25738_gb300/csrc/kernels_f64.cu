@@ -57,37 +57,28 @@ __device__ __forceinline__ double log10_of(const Partial& q) {
     return q.S == 0.0 ? -INFINITY : NAN;
 }
 
-// FP64 rescue pass: one CTA per selected pair, persistent over the rescue list.
+// FP64 rescue pass: one CTA per selected pair, persistent over the rescue list; pairs
+// wider than the CTA run strip after strip through this CTA's boundary scratch.
 __global__ void __launch_bounds__(kCtaThreads, 1)
 k_rescue(const BatchHeader* __restrict__ H, const PowRow<double>* __restrict__ pow) {
     __shared__ CtaShared<double> sh;
     const int R = checkpoint_interval<double>(H->dropgrow);
     const uint32_t n = H->counters[2];
+    unsigned long long* scratch = H->rbnd + (size_t)blockIdx.x * 2 * H->rbnd_words_per_cta;
     for (;;) {
         if (threadIdx.x == 0) sh.item = atomicAdd(&H->counters[3], 1u);
-        cta_clear<double>(sh);
         __syncthreads();
         const uint32_t r = sh.item;
+        __syncthreads();
         if (r >= n) break;
         const uint32_t p = H->rescue_list[r];
-        const PairDesc d = H->desc[p];
-        const int W = (int)((d.k + 32u * kN64 - 1u) / (32u * kN64));
-        if (W <= kCtaWarps) cta_pair_run<double, kN64>(H, pow, p, 0, W, sh, R);
-        __syncthreads();
+        const Partial q = cta_pair_sequential<double, kN64>(H, pow, p, sh, R, scratch, H->rbnd_words_per_cta);
         if (threadIdx.x == 0) {
             uint8_t of = (uint8_t)((H->out_flags[p] & 0x78u) | 0x1u | 0x4u);
-            double v;
-            if (W > kCtaWarps) {
-                v = NAN;
-                of |= 0x80u;
-                atomicOr(H->status, ST_TOO_LONG);
-            } else {
-                const Partial q = cta_combine<double>(sh, 0, W);
-                v = log10_of(q);
-                if (q.flags & PF_RESCALED) of |= 0x2u;
-                if (q.flags & (PF_TIMEOUT | PF_BAD)) of |= 0x80u;
-                if (!isfinite(q.S)) atomicOr(H->status, ST_NONFINITE);
-            }
+            const double v = log10_of(q);
+            if (q.flags & PF_RESCALED) of |= 0x2u;
+            if (q.flags & (PF_TIMEOUT | PF_BAD)) of |= 0x80u;
+            if (!isfinite(q.S)) atomicOr(H->status, ST_NONFINITE);
             H->out[p] = v;
             H->out_flags[p] = of;
         }
@@ -95,18 +86,13 @@ k_rescue(const BatchHeader* __restrict__ H, const PowRow<double>* __restrict__ p
     }
 }
 
-// Plain FP64 comparator: one launch (one CTA) per pair.
+// Plain FP64 comparator: one launch (one CTA) per pair, strips in sequence.
 __global__ void __launch_bounds__(kCtaThreads, 1)
 k_single(const BatchHeader* __restrict__ H, const PowRow<double>* __restrict__ pow, uint32_t pair) {
     __shared__ CtaShared<double> sh;
     const int R = checkpoint_interval<double>(H->dropgrow);
-    cta_clear<double>(sh);
-    __syncthreads();
-    const PairDesc d = H->desc[pair];
-    const int W = (int)((d.k + 32u * kN64 - 1u) / (32u * kN64));
-    if (W <= kCtaWarps) cta_pair_run<double, kN64>(H, pow, pair, 0, W, sh, R);
-    __syncthreads();
-    if (threadIdx.x == 0 && W <= kCtaWarps) H->parts[pair] = cta_combine<double>(sh, 0, W);
+    const Partial q = cta_pair_sequential<double, kN64>(H, pow, pair, sh, R, H->rbnd, H->rbnd_words_per_cta);
+    if (threadIdx.x == 0) H->parts[pair] = q;
 }
 
 void launch_prep64_all(const BatchHeader* H, const PhredTables* T, int grid, cudaStream_t s) {

@@ -10,15 +10,16 @@ namespace phmm {
 struct PhredTables;
 
 // FP32 unit
-void launch_reset(const BatchHeader* H, cudaStream_t s);
+void launch_reset(const BatchHeader* H, int grid, cudaStream_t s);
 void launch_prep32(const BatchHeader* H, const PhredTables* T, int grid, cudaStream_t s);
 void launch_forward32_long(const BatchHeader* H, const void* pow, int grid, cudaStream_t s);
-void launch_short_scalar(int N, const BatchHeader* H, const void* pow, int grid, cudaStream_t s);
-void launch_short_packed(int N, const BatchHeader* H, const void* pow, int grid, cudaStream_t s);
+// Short-pair kernels by variant id (see kShortScalar / kShortPacked).
+void launch_short_scalar(int id, const BatchHeader* H, const void* pow, int grid, cudaStream_t s);
+void launch_short_packed(int id, const BatchHeader* H, const void* pow, int grid, cudaStream_t s);
 void launch_finalize32(const BatchHeader* H, int grid, cudaStream_t s);
 int occupancy_forward32_long();          // resident CTAs per SM
-int occupancy_short_scalar(int N);
-int occupancy_short_packed(int N);
+int occupancy_short_scalar(int id);
+int occupancy_short_packed(int id);
 // pow_row: a device pointer to one PowRow<float>
 void launch_scan_test(const float* y, float* z, int n, const void* pow_row, cudaStream_t s);
 
@@ -33,7 +34,10 @@ int occupancy_forward64();
 
 constexpr int kN64 = 8;       // columns per lane of the FP64 kernels
 constexpr int kNLong32 = 32;  // columns per lane of FP32 multi-warp pairs
-constexpr int kPackedNs[2] = {12, 16};  // FP32 packed same-read team widths
-constexpr int kScalarNs[2] = {24, 32};  // FP32 scalar team widths  // columns per lane of the FP64 kernels
+// FP32 short-pair kernel variants: columns per lane of scalar teams / packed teams.
+constexpr int kNumScalar = 4;
+constexpr int kShortScalarN[kNumScalar] = {32, 24, 24, 16};
+constexpr int kNumPacked = 2;
+constexpr int kShortPackedN[kNumPacked] = {12, 16};  // columns per lane of the FP64 kernels
 
 }  // namespace phmm

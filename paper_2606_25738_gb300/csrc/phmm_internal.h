@@ -101,12 +101,21 @@ struct WarpItem {
     uint32_t first_team;
     uint32_t n_teams;
 };
+// One strip of a multi-warp pair in a CTA item: warps w0 .. w0+W-1 run columns
+// col0 .. col0 + W * 32 N - 1.  A pair wider than one CTA is split into nstrip strips
+// (consecutive CTA items, dequeued in order); strips pass each row's boundary values
+// through the global buffer `bnd` (bnd_in / bnd_out: word offsets, kNoBnd if none).
+constexpr uint64_t kNoBnd = ~0ull;
 struct CtaPair {
     uint32_t pair;
-    uint8_t w0;     // first warp
-    uint8_t W;      // warps
-    uint16_t pad;
-    uint32_t extra_base;  // partial slots of segments 1..W-1
+    uint8_t w0;          // first warp
+    uint8_t W;           // warps
+    uint16_t strip;      // strip index
+    uint32_t nstrip;     // strips of this pair
+    uint32_t col0;       // first column of the strip (0-based)
+    uint32_t extra_base; // partial slots of strips 1..nstrip-1
+    uint32_t pad;
+    uint64_t bnd_in, bnd_out;
 };
 struct CtaItem {
     uint32_t first;
@@ -155,7 +164,12 @@ struct BatchHeader {
     uint32_t n_witems, n_citems, n_witems2;
     uint32_t n_partials;
     uint32_t force_rescue;   // 1: every pair goes to the FP64 rescue pass
-    Partial *parts;
+    Partial *parts;          // n_pairs slots, then extra slots of strips 1.. of wide pairs
+    unsigned long long *bnd; // strip boundaries (tagged 64-bit words), cleared per launch
+    uint64_t n_bnd_words;
+    unsigned long long *rbnd;   // rescue / single-launch scratch: 2 boundaries per CTA
+    uint64_t rbnd_words_per_cta;
+    uint32_t l_max;          // longest read of the batch
     // outputs
     double *out;             // n_pairs log10 L
     uint8_t *out_flags;      // n_pairs PHMM_PAIR_* bits

@@ -8,6 +8,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <limits>
+#include <map>
 #include <mutex>
 #include <thread>
 #include <vector>
@@ -86,6 +87,10 @@ struct Plan {
     int N = 0;        // scalar team width (FP64: the only width)
     int NP = 0;       // packed team width (0: no packed teams)
     bool packed = false;
+    int scal_id = 0;  // FP32 short-pair kernel variants (launch.h)
+    int pack_id = -1;
+    uint64_t bnd_words = 0;   // strip boundary buffer (tagged words)
+    uint32_t n_extra = 0;     // extra partial slots (strips 1.. of wide pairs)
 };
 
 // Cost model constants (issue slots): per lane and cell of a row, and per lane and row
@@ -172,7 +177,7 @@ static void pack_teams(std::vector<Team>& run_teams, std::vector<uint32_t>& run_
 // ceil(max k / NP) lanes (x / y halves).  Long pairs: W = ceil(k / (32 Nl)) warps of one
 // CTA, packed best-fit into 16-warp CTAs.  Items are ordered longest first.
 void make_plan(const uint32_t* l, const uint32_t* k, const uint32_t* pr, uint32_t n, int Ns, int NP,
-               int Nl, Plan& P) {
+               int Nl, Plan& P, int kw = 4) {
     P = Plan();
     P.N = Ns;
     P.NP = NP;
@@ -197,8 +202,7 @@ void make_plan(const uint32_t* l, const uint32_t* k, const uint32_t* pr, uint32_
         else if (k[p] <= short_max) {
             st.push_back(mk(p, kNoPair, (k[p] + Ns - 1) / Ns));
             sl.push_back(l[p]);
-        } else if ((k[p] + seg - 1) / seg <= (uint32_t)kCtaWarps) lo.push_back(p);
-        else P.n_too_long++;
+        } else lo.push_back(p);
     }
     if (!pk.empty()) {
         std::stable_sort(pk.begin(), pk.end(), [&](uint32_t a, uint32_t b) {
@@ -216,12 +220,8 @@ void make_plan(const uint32_t* l, const uint32_t* k, const uint32_t* pr, uint32_
             }
             if (q < e) {  // odd one out: a scalar team
                 const uint32_t a = pk[q];
-                if (k[a] <= short_max) {
-                    st.push_back(mk(a, kNoPair, (k[a] + Ns - 1) / Ns));
-                    sl.push_back(l[a]);
-                } else {
-                    lo.push_back(a);
-                }
+                st.push_back(mk(a, kNoPair, (k[a] + Ns - 1) / Ns));
+                sl.push_back(l[a]);
                 ++q;
             }
         }
@@ -235,6 +235,51 @@ void make_plan(const uint32_t* l, const uint32_t* k, const uint32_t* pr, uint32_
         const double ca = (double)l[a] * W_of(a), cb = (double)l[b] * W_of(b);
         return ca > cb;
     });
+    auto cpair = [](uint32_t p, uint32_t w0, uint32_t W) {
+        CtaPair cp;
+        cp.pair = p;
+        cp.w0 = (uint8_t)w0;
+        cp.W = (uint8_t)W;
+        cp.strip = 0;
+        cp.nstrip = 1;
+        cp.col0 = 0;
+        cp.extra_base = 0;
+        cp.pad = 0;
+        cp.bnd_in = kNoBnd;
+        cp.bnd_out = kNoBnd;
+        return cp;
+    };
+    // Pairs wider than one CTA: one dedicated CTA item per strip, strips in order, so a
+    // strip is always dequeued after the strip it waits for.
+    std::vector<uint32_t> fit;
+    for (uint32_t p : lo) {
+        const uint32_t Wt = W_of(p);
+        if (Wt <= (uint32_t)kCtaWarps) {
+            fit.push_back(p);
+            continue;
+        }
+        const uint32_t S = (Wt + kCtaWarps - 1) / kCtaWarps;
+        const uint32_t extra = n + P.n_extra;
+        const uint64_t b0 = P.bnd_words;
+        for (uint32_t stp = 0; stp < S; ++stp) {
+            const uint32_t W = std::min((uint32_t)kCtaWarps, Wt - stp * kCtaWarps);
+            CtaPair cp = cpair(p, 0, W);
+            cp.strip = (uint16_t)stp;
+            cp.nstrip = S;
+            cp.col0 = stp * kCtaWarps * seg;
+            cp.extra_base = extra;
+            cp.bnd_in = stp > 0 ? b0 + (uint64_t)(stp - 1) * l[p] * kw : kNoBnd;
+            cp.bnd_out = stp + 1 < S ? b0 + (uint64_t)stp * l[p] * kw : kNoBnd;
+            CtaItem it;
+            it.first = (uint32_t)P.cpairs.size();
+            it.n = 1;
+            P.cpairs.push_back(cp);
+            P.citems.push_back(it);
+        }
+        P.bnd_words += (uint64_t)(S - 1) * l[p] * kw;
+        P.n_extra += S - 1;
+        P.cost += (double)l[p] * S * kCtaWarps * 32.0 * (Nl * kCellCost * 1.6 + kRowCost);
+    }
     struct CBin {
         std::vector<CtaPair> pairs;
         uint32_t rem, lmax;
@@ -242,14 +287,14 @@ void make_plan(const uint32_t* l, const uint32_t* k, const uint32_t* pr, uint32_
     std::vector<CBin> cb;
     std::vector<std::vector<uint32_t>> copen(kCtaWarps + 1);
     size_t a = 0;
-    while (a < lo.size()) {
-        const uint32_t l0 = l[lo[a]];
+    while (a < fit.size()) {
+        const uint32_t l0 = l[fit[a]];
         size_t b2 = a;
-        while (b2 < lo.size() && (double)l[lo[b2]] >= 0.9 * (double)l0) ++b2;
+        while (b2 < fit.size() && (double)l[fit[b2]] >= 0.9 * (double)l0) ++b2;
         cb.clear();
         for (auto& o : copen) o.clear();
         for (size_t q = a; q < b2; ++q) {
-            const uint32_t p = lo[q], W = W_of(p);
+            const uint32_t p = fit[q], W = W_of(p);
             int r = -1;
             for (uint32_t c = W; c <= (uint32_t)kCtaWarps; ++c)
                 if (!copen[c].empty()) {
@@ -264,13 +309,7 @@ void make_plan(const uint32_t* l, const uint32_t* k, const uint32_t* pr, uint32_
                 bi = copen[r].back();
                 copen[r].pop_back();
             }
-            CtaPair cp;
-            cp.pair = p;
-            cp.w0 = (uint8_t)(kCtaWarps - cb[bi].rem);
-            cp.W = (uint8_t)W;
-            cp.pad = 0;
-            cp.extra_base = 0;
-            cb[bi].pairs.push_back(cp);
+            cb[bi].pairs.push_back(cpair(p, kCtaWarps - cb[bi].rem, W));
             cb[bi].rem -= W;
             cb[bi].lmax = std::max(cb[bi].lmax, l[p]);
             if (cb[bi].rem > 0) copen[cb[bi].rem].push_back(bi);
@@ -339,7 +378,9 @@ void build_pow_table(int N, std::vector<PowRow<T>>& out) {
 struct Slot {
     DevBuf in_bases, in_bq, in_iq, in_dq, in_gq, in_hap, in_roff, in_hoff, in_pr, in_ph;
     DevBuf desc, rec32, rec64, teams, witems, witems2, cpairs, citems, parts, out, oflags, rescue;
-    DevBuf small;  // counters[4], status[1], dropgrow[2]
+    DevBuf small;  // counters[8], status[1], dropgrow[2]
+    DevBuf bnd;    // strip boundaries of the batch
+    DevBuf rbnd;   // rescue / launch-per-pair boundary scratch
     DevBuf hdr;
     HostBuf h_out, h_oflags, h_small, h_roff, h_hoff, h_pr, h_ph;
     BatchHeader hh;
@@ -377,7 +418,8 @@ struct phmm_ctx {
     DevBuf scan_row;                        // scan test: one PowRow<float> (global memory)
     DevBuf pow32[5];                        // N = 12, 16, 20, 24 (packed short), 32 (long)
     DevBuf pow64;
-    int occ_packed[2] = {1, 1}, occ_scalar[2] = {1, 1}, occ_long = 1, occ64 = 1;
+    int occ_packed[kNumPacked] = {}, occ_scalar[kNumScalar] = {}, occ_long = 1, occ64 = 1;
+    std::map<uint64_t, std::pair<int, int>> tuned;  // batch signature -> (scalar id, packed id)
     cudaStream_t stream2 = nullptr;         // graph branch: multi-warp pairs
     cudaStream_t stream3 = nullptr;         // graph branch: packed short teams
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_join3 = nullptr;
@@ -403,7 +445,7 @@ int pow_index(int N) { return N == 12 ? 0 : N == 16 ? 1 : N == 20 ? 2 : N == 24 
         }                                       \
     } while (0)
 
-int launch_sequence(phmm_ctx* ctx, Slot& S, int N, int NP, bool record_events) {
+int launch_sequence(phmm_ctx* ctx, Slot& S, int scal_id, int pack_id, bool record_events) {
     cudaStream_t s = ctx->stream;
     const BatchHeader* H = static_cast<const BatchHeader*>(S.hdr.p);
     const PhredTables* T = static_cast<const PhredTables*>(ctx->tables.p);
@@ -413,7 +455,7 @@ int launch_sequence(phmm_ctx* ctx, Slot& S, int N, int NP, bool record_events) {
         if (record_events) return cudaEventRecordWithFlags(ev, s, cudaEventRecordExternal);
         return cudaEventRecord(ev, s);
     };
-    launch_reset(H, s);
+    launch_reset(H, ctx->sms * 4, s);
     if (prec == PHMM_PREC_FP64) {
         launch_prep64_all(H, T, grid_pre, s);
         CK(rec(S.ev_fwd0));
@@ -431,9 +473,12 @@ int launch_sequence(phmm_ctx* ctx, Slot& S, int N, int NP, bool record_events) {
         CK(cudaStreamWaitEvent(ctx->stream3, ctx->ev_fork, 0));
         launch_forward32_long(H, ctx->pow32[pow_index(kNLong32)].p, ctx->sms * ctx->occ_long, ctx->stream2);
         CK(cudaEventRecord(ctx->ev_join, ctx->stream2));
-        if (NP > 0) launch_short_packed(NP, H, ctx->pow32[pow_index(NP)].p, ctx->sms * ctx->occ_packed[NP == 12 ? 0 : 1], ctx->stream3);
+        if (pack_id >= 0)
+            launch_short_packed(pack_id, H, ctx->pow32[pow_index(kShortPackedN[pack_id])].p,
+                                ctx->sms * ctx->occ_packed[pack_id], ctx->stream3);
         CK(cudaEventRecord(ctx->ev_join3, ctx->stream3));
-        launch_short_scalar(N, H, ctx->pow32[pow_index(N)].p, ctx->sms * ctx->occ_scalar[N == 24 ? 0 : 1], s);
+        launch_short_scalar(scal_id, H, ctx->pow32[pow_index(kShortScalarN[scal_id])].p,
+                            ctx->sms * ctx->occ_scalar[scal_id], s);
         CK(cudaStreamWaitEvent(s, ctx->ev_join, 0));
         CK(cudaStreamWaitEvent(s, ctx->ev_join3, 0));
         CK(rec(S.ev_fwd1));
@@ -455,6 +500,82 @@ int kernels_per_launch(int prec, int NP) {
 }
 
 uint64_t u64(const void* p) { return (uint64_t)(uintptr_t)p; }
+
+// Copies a plan's arrays into the slot's device arenas (growing them as needed).
+cudaError_t upload_plan(Slot& S, const Plan& P, cudaStream_t cs) {
+    cudaError_t e;
+    if ((e = ensure(S.teams, P.teams.size() * sizeof(Team))) != cudaSuccess) return e;
+    if ((e = ensure(S.witems, P.witems.size() * sizeof(WarpItem))) != cudaSuccess) return e;
+    if ((e = ensure(S.witems2, P.witems2.size() * sizeof(WarpItem))) != cudaSuccess) return e;
+    if ((e = ensure(S.cpairs, P.cpairs.size() * sizeof(CtaPair))) != cudaSuccess) return e;
+    if ((e = ensure(S.citems, P.citems.size() * sizeof(CtaItem))) != cudaSuccess) return e;
+    auto cp = [&](DevBuf& d, const void* src, size_t n) {
+        return n ? cudaMemcpyAsync(d.p, src, n, cudaMemcpyHostToDevice, cs) : cudaSuccess;
+    };
+    if ((e = cp(S.teams, P.teams.data(), P.teams.size() * sizeof(Team))) != cudaSuccess) return e;
+    if ((e = cp(S.witems, P.witems.data(), P.witems.size() * sizeof(WarpItem))) != cudaSuccess) return e;
+    if ((e = cp(S.witems2, P.witems2.data(), P.witems2.size() * sizeof(WarpItem))) != cudaSuccess) return e;
+    if ((e = cp(S.cpairs, P.cpairs.data(), P.cpairs.size() * sizeof(CtaPair))) != cudaSuccess) return e;
+    return cp(S.citems, P.citems.data(), P.citems.size() * sizeof(CtaItem));
+}
+
+// Plan fields of the batch header.
+void plan_header(const Slot& S, const Plan& P, BatchHeader& hh) {
+    hh.witems = (const WarpItem*)S.witems.p;
+    hh.witems2 = (const WarpItem*)S.witems2.p;
+    hh.n_witems2 = (uint32_t)P.witems2.size();
+    hh.teams = (const Team*)S.teams.p;
+    hh.citems = (const CtaItem*)S.citems.p;
+    hh.cpairs = (const CtaPair*)S.cpairs.p;
+    hh.n_witems = (uint32_t)P.witems.size();
+    hh.n_citems = (uint32_t)P.citems.size();
+    hh.n_partials = hh.n_pairs + P.n_extra;
+    hh.bnd = (unsigned long long*)S.bnd.p;
+    hh.n_bnd_words = P.bnd_words;
+}
+
+// FP32 short-pair kernel candidates (scalar id, packed id or -1) allowed by the config.
+std::vector<std::pair<int, int>> fp32_candidates(const phmm_config& cfg) {
+    std::vector<std::pair<int, int>> c;
+    const int v = cfg.kernel_variant, n = cfg.cols_per_lane;
+    for (int si = 0; si < kNumScalar; ++si)
+        for (int pi = -1; pi < kNumPacked; ++pi) {
+            if (v == 2 && pi >= 0) continue;
+            if (v == 1 && pi < 0) continue;
+            if ((n == 24 || n == 32 || n == 16) && v == 2 && kShortScalarN[si] != n) continue;
+            if ((n == 24 || n == 32) && v != 2 && kShortScalarN[si] != n) continue;
+            if ((n == 12 || n == 16) && v != 2 && (pi < 0 || kShortPackedN[pi] != n)) continue;
+            c.push_back({si, pi});
+        }
+    return c;
+}
+
+void make_plan_id(const uint32_t* l, const uint32_t* k, const uint32_t* pr, uint32_t n, int scal_id,
+                  int pack_id, Plan& P) {
+    make_plan(l, k, pr, n, kShortScalarN[scal_id], pack_id >= 0 ? kShortPackedN[pack_id] : 0, kNLong32, P);
+    P.scal_id = scal_id;
+    P.pack_id = pack_id;
+}
+
+// Coarse shape of a batch for the tuner cache: pair count, mean read and haplotype
+// lengths (quarter-octave buckets), share of pairs whose read has other pairs.
+uint64_t batch_signature(const uint32_t* l, const uint32_t* k, const uint32_t* pr, uint32_t n,
+                         const phmm_config& cfg) {
+    double sl = 0, sk = 0;
+    uint32_t shared = 0;
+    for (uint32_t p = 0; p < n; ++p) {
+        sl += l[p];
+        sk += k[p];
+        if ((p > 0 && pr[p - 1] == pr[p]) || (p + 1 < n && pr[p + 1] == pr[p])) shared++;
+    }
+    auto q = [](double x) { return (uint64_t)std::max(0.0, std::floor(4.0 * std::log2(std::max(x, 1.0)))); };
+    const uint64_t fs = n ? (uint64_t)(8.0 * shared / n) : 0;
+    return q(n) | (q(sl / std::max(n, 1u)) << 8) | (q(sk / std::max(n, 1u)) << 16) | (fs << 24) |
+           ((uint64_t)cfg.precision << 32) | ((uint64_t)cfg.kernel_variant << 36) |
+           ((uint64_t)cfg.cols_per_lane << 40);
+}
+
+constexpr uint64_t kTuneMinCells = 200000000ull;  // smaller batches keep the cost model's pick
 
 }  // namespace
 
@@ -485,7 +606,7 @@ int phmm_create(const phmm_config* cfg, phmm_ctx** out) {
     {
         const int n = cfg->cols_per_lane;
         const bool okp = n == 12 || n == 16;  // packed widths
-        const bool oks = n == 24 || n == 32;  // scalar widths
+        const bool oks = n == 16 || n == 24 || n == 32;  // scalar widths
         if (n != 0 && !(cfg->kernel_variant == 2 ? oks : (okp || oks))) return PHMM_EINVAL;
     }
     int ndev = 0;
@@ -528,13 +649,13 @@ int phmm_create(const phmm_config* cfg, phmm_ctx** out) {
         if (ensure(ctx->pow32[q], v.size() * sizeof(v[0])) != cudaSuccess) return fail(PHMM_ECUDA);
         cudaMemcpy(ctx->pow32[q].p, v.data(), v.size() * sizeof(v[0]), cudaMemcpyHostToDevice);
     }
-    for (int q = 0; q < 2; ++q) ctx->occ_packed[q] = occupancy_short_packed(kPackedNs[q]);
-    for (int q = 0; q < 2; ++q) ctx->occ_scalar[q] = occupancy_short_scalar(kScalarNs[q]);
+    for (int q = 0; q < kNumPacked; ++q) ctx->occ_packed[q] = occupancy_short_packed(q);
+    for (int q = 0; q < kNumScalar; ++q) ctx->occ_scalar[q] = occupancy_short_scalar(q);
     ctx->occ_long = occupancy_forward32_long();
     if (getenv("PHMM_DEBUG"))
-        fprintf(stderr, "phmm: sms %d occupancy packed12 %d packed16 %d scalar24 %d scalar32 %d long %d fp64 %d\n",
+        fprintf(stderr, "phmm: sms %d occupancy packed %d %d scalar %d %d %d %d long %d fp64 %d\n",
                 ctx->sms, ctx->occ_packed[0], ctx->occ_packed[1], ctx->occ_scalar[0], ctx->occ_scalar[1],
-                ctx->occ_long, ctx->occ64);
+                ctx->occ_scalar[2], ctx->occ_scalar[3], ctx->occ_long, ctx->occ64);
     if (cudaStreamCreateWithFlags(&ctx->stream2, cudaStreamNonBlocking) != cudaSuccess ||
         cudaStreamCreateWithFlags(&ctx->stream3, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
@@ -571,7 +692,7 @@ void phmm_destroy(phmm_ctx* ctx) {
         DevBuf* d[] = {&S.in_bases, &S.in_bq, &S.in_iq, &S.in_dq, &S.in_gq, &S.in_hap, &S.in_roff,
                        &S.in_hoff, &S.in_pr, &S.in_ph, &S.desc, &S.rec32, &S.rec64, &S.teams,
                        &S.witems, &S.witems2, &S.cpairs, &S.citems, &S.parts, &S.out, &S.oflags, &S.rescue,
-                       &S.small, &S.hdr};
+                       &S.small, &S.hdr, &S.bnd, &S.rbnd};
         for (auto* b : d) release(*b);
         HostBuf* h[] = {&S.h_out, &S.h_oflags, &S.h_small, &S.h_roff, &S.h_hoff, &S.h_pr, &S.h_ph};
         for (auto* b : h) release(*b);
@@ -669,35 +790,37 @@ int phmm_submit_batch(phmm_ctx* ctx, const phmm_batch* b, uint64_t* ticket) {
     hsh ^= np;
     Plan& P = S->plan;
     int N = kN64;
+    bool tune_now = false;
+    uint64_t tune_sig = 0;
+    std::vector<std::pair<int, int>> tune_cand;
     const bool reuse = S->plan_valid && S->plan_hash == hsh && S->plan_np == np;
     if (!reuse) {
         if (ctx->cfg.precision == PHMM_PREC_FP64) {
-            make_plan(L.data(), K.data(), pr, np, kN64, 0, kN64, P);
+            make_plan(L.data(), K.data(), pr, np, kN64, 0, kN64, P, 8);
         } else {
-            // kernel_variant 2: scalar teams only; otherwise pairs of the same read share
-            // packed teams.  cols_per_lane fixes the packed width (12, 16) or the scalar
-            // width (24, 32); anything left open is chosen by the cost model.
-            const int v = ctx->cfg.kernel_variant, n = ctx->cfg.cols_per_lane;
-            std::vector<std::pair<int, int>> cand;  // (Ns, NP)
-            for (int ns : {32, 24})
-                for (int npk : {16, 12, 0}) {
-                    if ((v == 2) != (npk == 0)) continue;
-                    if ((n == 24 || n == 32) && ns != n) continue;
-                    if ((n == 12 || n == 16) && npk != n) continue;
-                    cand.push_back({ns, npk});
+            const std::vector<std::pair<int, int>> cand = fp32_candidates(ctx->cfg);
+            const uint64_t sig = batch_signature(L.data(), K.data(), pr, np, ctx->cfg);
+            auto hit = ctx->tuned.find(sig);
+            if (hit != ctx->tuned.end()) {
+                make_plan_id(L.data(), K.data(), pr, np, hit->second.first, hit->second.second, P);
+            } else {
+                // cost-model choice first; measured tuning (below) may replace it
+                Plan best;
+                bool have = false;
+                for (auto& cd : cand) {
+                    Plan c;
+                    make_plan_id(L.data(), K.data(), pr, np, cd.first, cd.second, c);
+                    const double cost = c.cost + (double)c.n_too_long * 1e18;
+                    if (!have || cost < best.cost + (double)best.n_too_long * 1e18) {
+                        best = std::move(c);
+                        have = true;
+                    }
                 }
-            Plan best;
-            bool have = false;
-            for (auto& cd : cand) {
-                Plan c;
-                make_plan(L.data(), K.data(), pr, np, cd.first, cd.second, kNLong32, c);
-                const double cost = c.cost + (double)c.n_too_long * 1e18;
-                if (!have || cost < best.cost + (double)best.n_too_long * 1e18) {
-                    best = std::move(c);
-                    have = true;
-                }
+                P = std::move(best);
+                tune_now = cand.size() > 1 && cells >= kTuneMinCells;
+                tune_sig = sig;
+                tune_cand = cand;
             }
-            P = std::move(best);
         }
     }
     N = P.N;
@@ -708,7 +831,8 @@ int phmm_submit_batch(phmm_ctx* ctx, const phmm_batch* b, uint64_t* ticket) {
                           (ctx->cfg.precision == PHMM_PREC_FP64 ? 0 : nbases * sizeof(Rec32)) +
                           (need64 ? nbases * sizeof(Rec64) : 0) +
                           P.teams.size() * sizeof(Team) + (P.witems.size() + P.witems2.size()) * sizeof(WarpItem) +
-                          P.cpairs.size() * sizeof(CtaPair) + P.citems.size() * sizeof(CtaItem);
+                          P.cpairs.size() * sizeof(CtaPair) + P.citems.size() * sizeof(CtaItem) +
+                          P.bnd_words * 8ull + P.n_extra * sizeof(Partial);
     if (foot > ctx->budget) return PHMM_ENOMEM;
     // device arenas
     BatchHeader& hh = S->hh;
@@ -743,28 +867,21 @@ int phmm_submit_batch(phmm_ctx* ctx, const phmm_batch* b, uint64_t* ticket) {
     CK(ensure(S->desc, np * sizeof(PairDesc)));
     if (ctx->cfg.precision != PHMM_PREC_FP64) CK(ensure(S->rec32, nbases * sizeof(Rec32)));
     if (need64) CK(ensure(S->rec64, nbases * sizeof(Rec64)));
-    if (!reuse) CK(ensure(S->teams, P.teams.size() * sizeof(Team)));
-    if (!reuse) {
-        CK(ensure(S->witems, P.witems.size() * sizeof(WarpItem)));
-        CK(ensure(S->witems2, P.witems2.size() * sizeof(WarpItem)));
-        CK(ensure(S->cpairs, P.cpairs.size() * sizeof(CtaPair)));
-        CK(ensure(S->citems, P.citems.size() * sizeof(CtaItem)));
-    }
-    CK(ensure(S->parts, np * sizeof(Partial)));
+    CK(ensure(S->parts, (np + P.n_extra) * sizeof(Partial)));
+    CK(ensure(S->bnd, P.bnd_words * 8ull));
+    uint32_t lmax_b = 0;
+    for (uint32_t p = 0; p < np; ++p) lmax_b = std::max(lmax_b, L[p]);
+    const uint64_t rb_words = (uint64_t)lmax_b * 8;  // FP64 boundary: 8 words per row
+    const int rescue_ctas = ctx->sms * ctx->occ64;
+    if (ctx->cfg.precision != PHMM_PREC_FP32_ONLY) CK(ensure(S->rbnd, (uint64_t)rescue_ctas * 2 * rb_words * 8ull + 16));
     CK(ensure(S->out, np * 8ull));
     CK(ensure(S->oflags, np * 1ull));
     CK(ensure(S->rescue, np * 4ull));
     CK(ensure(S->h_out, np * 8ull));
     CK(ensure(S->h_oflags, np * 1ull));
     cudaStream_t cs = ctx->copy_stream;
-    if (!reuse) {
-        if (!P.teams.empty()) CK(cudaMemcpyAsync(S->teams.p, P.teams.data(), P.teams.size() * sizeof(Team), cudaMemcpyHostToDevice, cs));
-        if (!P.witems.empty()) CK(cudaMemcpyAsync(S->witems.p, P.witems.data(), P.witems.size() * sizeof(WarpItem), cudaMemcpyHostToDevice, cs));
-        if (!P.witems2.empty()) CK(cudaMemcpyAsync(S->witems2.p, P.witems2.data(), P.witems2.size() * sizeof(WarpItem), cudaMemcpyHostToDevice, cs));
-        if (!P.cpairs.empty()) CK(cudaMemcpyAsync(S->cpairs.p, P.cpairs.data(), P.cpairs.size() * sizeof(CtaPair), cudaMemcpyHostToDevice, cs));
-        if (!P.citems.empty()) CK(cudaMemcpyAsync(S->citems.p, P.citems.data(), P.citems.size() * sizeof(CtaItem), cudaMemcpyHostToDevice, cs));
-    }
-    CK(cudaMemsetAsync(S->parts.p, 0, np * sizeof(Partial), cs));
+    if (!reuse) CK(upload_plan(*S, P, cs));
+    CK(cudaMemsetAsync(S->parts.p, 0, (np + P.n_extra) * sizeof(Partial), cs));
     hh.n_read_bases = nbases;
     hh.n_reads = nr;
     hh.n_haps = nh;
@@ -772,15 +889,13 @@ int phmm_submit_batch(phmm_ctx* ctx, const phmm_batch* b, uint64_t* ticket) {
     hh.desc = (PairDesc*)S->desc.p;
     hh.rec32 = (Rec32*)S->rec32.p;
     hh.rec64 = (Rec64*)S->rec64.p;
-    hh.witems = (const WarpItem*)S->witems.p;
-    hh.witems2 = (const WarpItem*)S->witems2.p;
-    hh.n_witems2 = (uint32_t)P.witems2.size();
-    hh.teams = (const Team*)S->teams.p;
-    hh.citems = (const CtaItem*)S->citems.p;
-    hh.cpairs = (const CtaPair*)S->cpairs.p;
-    hh.n_witems = (uint32_t)P.witems.size();
-    hh.n_citems = (uint32_t)P.citems.size();
-    hh.n_partials = np;
+    plan_header(*S, P, hh);
+    hh.n_partials = np + P.n_extra;
+    hh.bnd = (unsigned long long*)S->bnd.p;
+    hh.n_bnd_words = P.bnd_words;
+    hh.rbnd = (unsigned long long*)S->rbnd.p;
+    hh.rbnd_words_per_cta = rb_words;
+    hh.l_max = lmax_b;
     hh.force_rescue = (ctx->cfg.flags & PHMM_F_FORCE_RESCUE) ? 1u : 0u;
     hh.parts = (Partial*)S->parts.p;
     hh.out = (double*)S->out.p;
@@ -795,6 +910,47 @@ int phmm_submit_batch(phmm_ctx* ctx, const phmm_batch* b, uint64_t* ticket) {
     CK(cudaEventRecord(S->ev_copy, cs));
     // host inputs may be released when submit returns
     CK(cudaEventSynchronize(S->ev_copy));
+    if (tune_now) {
+        // Measured tuning: run the FP32 pipeline once per candidate kernel pair on this
+        // batch (events around the forward kernels), keep the fastest for this shape.
+        cudaStream_t ts = ctx->stream;
+        CK(cudaStreamWaitEvent(ts, S->ev_copy, 0));
+        double best_ms = 1e30;
+        int bs = P.scal_id, bp = P.pack_id;
+        for (auto& cd : tune_cand) {
+            Plan c;
+            make_plan_id(L.data(), K.data(), pr, np, cd.first, cd.second, c);
+            if (c.n_too_long) continue;
+            CK(upload_plan(*S, c, cs));
+            CK(ensure(S->parts, (np + c.n_extra) * sizeof(Partial)));
+            CK(ensure(S->bnd, c.bnd_words * 8ull));
+            hh.parts = (Partial*)S->parts.p;
+            plan_header(*S, c, hh);
+            CK(cudaMemcpyAsync(S->hdr.p, &hh, sizeof(hh), cudaMemcpyHostToDevice, cs));
+            CK(cudaStreamSynchronize(cs));
+            const int rc = launch_sequence(ctx, *S, c.scal_id, c.pack_id, false);
+            if (rc != PHMM_OK) return rc;
+            CK(cudaStreamSynchronize(ts));
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, S->ev_fwd0, S->ev_fwd1));
+            if (ms < best_ms) {
+                best_ms = ms;
+                bs = cd.first;
+                bp = cd.second;
+            }
+        }
+        ctx->tuned[tune_sig] = {bs, bp};
+        make_plan_id(L.data(), K.data(), pr, np, bs, bp, P);
+        CK(upload_plan(*S, P, cs));
+        CK(ensure(S->parts, (np + P.n_extra) * sizeof(Partial)));
+        CK(ensure(S->bnd, P.bnd_words * 8ull));
+        hh.parts = (Partial*)S->parts.p;
+        plan_header(*S, P, hh);
+        CK(cudaMemcpyAsync(S->hdr.p, &hh, sizeof(hh), cudaMemcpyHostToDevice, cs));
+        CK(cudaMemsetAsync(S->parts.p, 0, (np + P.n_extra) * sizeof(Partial), cs));
+        CK(cudaStreamSynchronize(cs));
+        N = P.N;
+    }
     cudaStream_t s = ctx->stream;
     CK(cudaStreamWaitEvent(s, S->ev_copy, 0));
     CK(cudaEventRecord(S->ev_start, s));
@@ -804,7 +960,7 @@ int phmm_submit_batch(phmm_ctx* ctx, const phmm_batch* b, uint64_t* ticket) {
         const bool use_graph = !(ctx->cfg.flags & PHMM_F_NO_GRAPH) && !per_pair;
         if (per_pair) {
             const BatchHeader* H = static_cast<const BatchHeader*>(S->hdr.p);
-            launch_reset(H, s);
+            launch_reset(H, ctx->sms * 4, s);
             launch_prep64_all(H, static_cast<const PhredTables*>(ctx->tables.p), ctx->sms * 4, s);
             CK(cudaEventRecord(S->ev_fwd0, s));
             for (uint32_t p = 0; p < np; ++p) launch_single64(H, ctx->pow64.p, p, s);
@@ -815,13 +971,13 @@ int phmm_submit_batch(phmm_ctx* ctx, const phmm_batch* b, uint64_t* ticket) {
             CK(cudaGetLastError());
             launches = np + 3;
         } else if (use_graph) {
-            const int key = ctx->cfg.precision * 10000 + N * 100 + P.NP;
+            const int key = ctx->cfg.precision * 10000 + P.scal_id * 100 + (P.pack_id + 1);
             if (!S->gexec || S->g_key != key) {
                 if (S->gexec) cudaGraphExecDestroy(S->gexec);
                 S->gexec = nullptr;
                 cudaGraph_t g = nullptr;
                 CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-                const int rc = launch_sequence(ctx, *S, N, P.NP, true);
+                const int rc = launch_sequence(ctx, *S, P.scal_id, P.pack_id, true);
                 cudaError_t e2 = cudaStreamEndCapture(s, &g);
                 if (rc != PHMM_OK || e2 != cudaSuccess) {
                     if (g) cudaGraphDestroy(g);
@@ -836,7 +992,7 @@ int phmm_submit_batch(phmm_ctx* ctx, const phmm_batch* b, uint64_t* ticket) {
             CK(cudaGraphLaunch(S->gexec, s));
             launches = (uint32_t)kernels_per_launch(ctx->cfg.precision, P.NP);
         } else {
-            const int rc = launch_sequence(ctx, *S, N, P.NP, false);
+            const int rc = launch_sequence(ctx, *S, P.scal_id, P.pack_id, false);
             if (rc != PHMM_OK) return rc;
             launches = (uint32_t)kernels_per_launch(ctx->cfg.precision, P.NP);
         }

@@ -217,3 +217,66 @@ def test_launch_per_pair_fp64(phmm):
         out, flags, rc, st = ctx.run(b)
     assert st["kernel_launches"] == 8 + 3
     assert np.max(np.abs(out - oracle.batch(b))) <= TOL64
+
+
+def _wide_batch(seed=30):
+    """Pairs wider than one 16-warp CTA (strips), with moderate read lengths so the oracle
+    stays fast: haplotypes 16k-60k bp, reads 200-600 bp from a random offset."""
+    rng = np.random.default_rng(seed)
+    pairs = []
+    for k in (16385, 20000, 33000, 49153, 60000):
+        hap = "".join(rng.choice(list("ACGT"), size=k))
+        l = int(rng.integers(200, 601))
+        off = int(rng.integers(0, k - l))
+        read = list(hap[off:off + l])
+        for p in rng.choice(l, size=l // 40, replace=False):
+            read[p] = "ACGT"[("ACGT".index(read[p]) + 1) % 4]
+        pairs.append(("".join(read), hap, rng.integers(10, 41, size=l), 45, 45, 10))
+    return W.from_strings(pairs)
+
+
+def test_wide_pairs_fp32_strips(phmm):
+    """Concurrent strips (global row boundaries between CTAs), FP32 only."""
+    b = _wide_batch()
+    with phmm.Context(precision="fp32_only") as ctx:
+        out, flags, rc, st = ctx.run(b)
+    assert st["n_long"] == 5
+    assert np.all((flags & 0x78) == 0)
+    assert np.max(np.abs(out - oracle.batch(b))) <= TOL32
+
+
+def test_wide_pairs_fp64_strips(phmm):
+    """Concurrent strips in the batched FP64 engine (4096 columns per CTA)."""
+    b = _wide_batch(seed=31)
+    with phmm.Context(precision="fp64") as ctx:
+        out, flags, rc, st = ctx.run(b)
+    assert np.max(np.abs(out - oracle.batch(b))) <= TOL64
+
+
+def test_wide_pairs_rescue_sequential_strips(phmm):
+    """FP64 rescue of wide pairs: strips run one after another inside one CTA."""
+    b = _wide_batch(seed=32)
+    with phmm.Context(precision="fp32", flags=phmm.F_FORCE_RESCUE) as ctx:
+        out, flags, rc, st = ctx.run(b)
+    assert st["n_rescued"] == 5
+    assert np.max(np.abs(out - oracle.batch(b))) <= TOL64
+
+
+def test_long_reads_reduced(phmm):
+    """Long-read-like pairs (reads 90-100% of haplotypes of 1k-20k bp, 5% substitutions,
+    3% indels, quals 5-30): FP32 + rescue within 1e-3 including multi-warp and strip
+    pairs; checkpoint rescaling must have happened."""
+    b = W.long_pairs(10, seed=4, k_range=(1000, 20000))
+    with phmm.Context(precision="fp32") as ctx:
+        out, flags, rc, st = ctx.run(b)
+    ref = oracle.batch(b)
+    assert np.all(ref < -300)  # far below what a fixed 2^120 scale could hold
+    _check(out, flags, ref)
+    assert np.all(flags & phmm.PAIR_RESCALED)
+
+
+def test_launch_per_pair_wide(phmm):
+    b = _wide_batch(seed=33)
+    with phmm.Context(precision="fp64", flags=phmm.F_LAUNCH_PER_PAIR) as ctx:
+        out, flags, rc, st = ctx.run(b)
+    assert np.max(np.abs(out - oracle.batch(b))) <= TOL64
