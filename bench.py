@@ -142,6 +142,51 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def _fp64_comparators(b, d, dev, args):
+    """The all-FP64 GPU comparators on the same workload (outside the timed region):
+    the batched FP64 path of this library over the whole batch, and a plain FP64
+    one-launch-per-pair run over a bounded random sample of its pairs."""
+    import torch
+
+    from paper_2606_25738_gb300 import phmm
+    from paper_2606_25738_gb300 import workloads as W
+    n = len(b["pair_read"])
+    cells = W.cells(b)
+    res = {}
+    out = torch.empty(n, dtype=torch.float64, device="cuda")
+    fl = torch.zeros(n, dtype=torch.uint8, device="cuda")
+    with phmm.Context(device=dev, precision="fp64", max_inflight=1) as c64:
+        for _ in range(2):
+            c64.poll(c64.submit(d, out, fl), -1)
+        ms = []
+        for _ in range(3):
+            t = c64.submit(d, out, fl)
+            if c64.poll(t, -1) != 0:
+                raise RuntimeError("fp64 batched run failed")
+            ms.append(c64.stats(t)["ms_total"])
+        res["fp64_batched"] = {"value": cells / (float(np.mean(ms)) * 1e-3) / 1e9, "unit": "GCUPS",
+                               "ms_per_step": float(np.mean(ms)),
+                               "what": "this library, precision=fp64 (all pairs, one graph launch)"}
+    m = min(n, args.lpp_pairs)
+    pick = np.sort(np.random.default_rng(3).choice(n, m, replace=False))
+    sb = W.subset(b, pick)
+    sd = phmm.to_device(sb)
+    scells = W.cells(sb)
+    out2 = torch.empty(m, dtype=torch.float64, device="cuda")
+    fl2 = torch.zeros(m, dtype=torch.uint8, device="cuda")
+    with phmm.Context(device=dev, precision="fp64", flags=phmm.F_LAUNCH_PER_PAIR | phmm.F_NO_GRAPH,
+                      max_inflight=1) as cl:
+        cl.poll(cl.submit(sd, out2, fl2), -1)
+        t = cl.submit(sd, out2, fl2)
+        if cl.poll(t, -1) != 0:
+            raise RuntimeError("fp64 launch-per-pair run failed")
+        st = cl.stats(t)
+    res["fp64_launch_per_pair"] = {"value": scells / (st["ms_total"] * 1e-3) / 1e9, "unit": "GCUPS",
+                                   "ms": st["ms_total"], "sample_pairs": m, "sample_cells": scells,
+                                   "what": "plain FP64, one kernel launch (one CTA) per pair, in order"}
+    return res
+
+
 def run_ours(args):
     import torch
 
@@ -223,6 +268,7 @@ def run_ours(args):
     if rank != 0:
         ctx.close()
         return
+    comparators = _fp64_comparators(b, d, dev, args)
 
     peaks = _peaks()
     sm_max = float(peaks.get("sm_max_mhz", info["max_clock_mhz"]))
@@ -266,6 +312,7 @@ def run_ours(args):
         "accuracy": {"max_abs_dlog10_sample": err, "sample_pairs": 2000,
                      "rescued_pairs": int(sts[-1]["n_rescued"]),
                      "flagged": int(np.sum((flg & 0x78) != 0))},
+        "comparators": comparators,
         "ms_forward": fwd_ms, "wall_s": wall,
     }
     print(json.dumps(line), flush=True)
@@ -284,6 +331,8 @@ def main():
     ap.add_argument("--regions", type=int, default=2000,
                     help="active regions of the workload (2000 = the benchmark size; smaller "
                          "values only for profiling captures)")
+    ap.add_argument("--lpp-pairs", type=int, default=4000,
+                    help="pairs sampled for the FP64 launch-per-pair comparator")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

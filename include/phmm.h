@@ -148,11 +148,24 @@ typedef struct {
 int phmm_create(const phmm_config *cfg, phmm_ctx **out);
 
 /* Validate a batch, copy host inputs to device arenas (before returning, so the caller
- * may reuse host input buffers immediately), and enqueue the forward computation on the
- * context's stream.  *ticket identifies it for phmm_poll.  Device inputs and all
- * outputs must stay valid until phmm_poll returns a terminal status for the ticket.
- * PHMM_EINVAL / PHMM_ENOMEM (batch larger than the budget) / PHMM_EBUSY / PHMM_ECUDA. */
+ * may reuse host input buffers immediately), and enqueue the forward computation.
+ * *ticket identifies it for phmm_poll.  Device inputs and all outputs must stay valid
+ * until phmm_poll returns a terminal status for the ticket.
+ * Each in-flight batch occupies one of max_inflight slots with its own device arenas and
+ * streams, so batches submitted back to back run concurrently on the device.  They are
+ * ordered after work already queued on the context's stream (config.stream) at submit
+ * time, and work queued on that stream afterwards waits for their outputs.
+ * PHMM_EINVAL (bad offsets, index or length) / PHMM_ENOMEM (the batch alone exceeds the
+ * memory budget: it can never be admitted) / PHMM_EBUSY (no free slot, or the in-flight
+ * batches hold too much of the budget: retry after polling) / PHMM_ECUDA. */
 int phmm_submit_batch(phmm_ctx *ctx, const phmm_batch *batch, uint64_t *ticket);
+
+/* Upper bound of the device bytes a batch with host inputs needs while in flight (inputs,
+ * per-base coefficient records, per-pair descriptors and work items, strip boundaries
+ * of very wide pairs, FP64 rescue scratch), as counted against the memory budget.
+ * Offsets and pair indices must be valid (PHMM_EINVAL otherwise); bases and qualities
+ * are not read. */
+int phmm_batch_footprint(phmm_ctx *ctx, const phmm_batch *batch, uint64_t *bytes);
 
 /* Wait up to timeout_ms (0 = just test, < 0 = forever) for a ticket.  PHMM_OK when its
  * outputs are written, PHMM_PENDING if not finished, PHMM_EINVAL if a base or quality of
@@ -185,6 +198,60 @@ int phmm_device_info(phmm_ctx *ctx, int *sms, double *max_clock_mhz, double *cup
  * writes z[t] = sum_{s <= t} a^(t-s) y[s] (device pointer).  Runs synchronously.
  */
 int phmm_scan_test(phmm_ctx *ctx, const float *y, float *z, int n, float a);
+
+/*
+ * Serving: continuous batching of independent requests (an active region: R reads x H
+ * haplotypes, scored as one phmm_batch).  The paper has no serving layer; this loop is
+ * built on phmm_submit_batch / phmm_poll of one context.  A scheduler thread keeps a FIFO
+ * of waiting requests.  Whenever an epoch slot is free it admits waiting requests, in
+ * arrival order, while their summed footprint (phmm_batch_footprint) fits in the budget
+ * left by epochs still on the device and the epoch stays under max_epoch_pairs, joins
+ * them into one batch and submits it.  Up to max_inflight_epochs epochs run concurrently,
+ * so requests that arrive while others are on the GPU start as soon as a slot and memory
+ * free up.  When an epoch finishes, each request's results are copied to its own output
+ * buffers and the request completes.
+ */
+typedef struct phmm_server phmm_server;
+
+typedef struct {
+    uint64_t mem_budget_bytes;     /* device bytes admitted across in-flight epochs (0: 40 GiB) */
+    uint32_t max_epoch_pairs;      /* pairs per epoch (0: 2^20) */
+    uint32_t max_inflight_epochs;  /* concurrent epochs (0: 2); the context needs as many slots */
+    uint32_t max_pending;          /* waiting requests before enqueue returns PHMM_EBUSY (0: no limit) */
+} phmm_server_config;
+
+typedef struct {
+    uint64_t enqueued, admitted, completed, failed; /* requests */
+    uint64_t epochs;                                /* batches submitted */
+    uint64_t pending;                               /* requests waiting for admission */
+    uint64_t inflight;                              /* requests admitted, not completed */
+    uint64_t cells_completed;                       /* sum of l * k over completed requests */
+    uint64_t bytes_inflight;                        /* admitted footprint on the device */
+} phmm_server_stats;
+
+/* Start a server on ctx (which must outlive it and must not be used by the caller while
+ * the server runs).  PHMM_EINVAL on a bad argument. */
+int phmm_server_create(phmm_ctx *ctx, const phmm_server_config *cfg, phmm_server **out);
+
+/* Queue one request (a phmm_batch with host inputs and host outputs).  Inputs are copied
+ * before the call returns; out_log10 / out_flags must stay valid until phmm_server_poll
+ * returns a terminal status for *req_id.  PHMM_EINVAL (bad offsets, indices or lengths),
+ * PHMM_ENOMEM (footprint above the whole budget), PHMM_EBUSY (max_pending reached). */
+int phmm_server_enqueue(phmm_server *srv, const phmm_batch *request, uint64_t *req_id);
+
+/* Wait up to timeout_ms (0 = test, < 0 = forever) for a request.  PHMM_OK when its outputs
+ * are written, PHMM_PENDING, PHMM_EINVAL when one of its pairs had an invalid base or
+ * quality (that pair holds NaN and PHMM_PAIR_ERROR), or the error of its epoch.
+ * *latency_ms (optional) receives enqueue-to-completion time.  A terminal status retires
+ * the id (PHMM_ENOTFOUND afterwards). */
+int phmm_server_poll(phmm_server *srv, uint64_t req_id, int timeout_ms, double *latency_ms);
+
+/* Counters since creation. */
+int phmm_server_get_stats(phmm_server *srv, phmm_server_stats *out);
+
+/* Stop admitting, wait for epochs on the device, fail waiting requests with
+ * PHMM_ECANCELED, stop the scheduler and free the server (not the context). */
+void phmm_server_destroy(phmm_server *srv);
 
 /*
  * Allocation-free FP32 forward pass (the paper has no counterpart: this is an interface

@@ -1,5 +1,5 @@
 """Builds the CUDA library libphmm.so in-tree (paper_2606_25738_gb300/_lib/) with nvcc
-for sm_103a: three translation units compiled in parallel, then linked as a shared
+for sm_103a: the translation units compiled in parallel, then linked as a shared
 library exporting the C ABI of include/phmm.h."""
 from __future__ import annotations
 
@@ -13,7 +13,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libphmm.so")
-SOURCES = ["kernels_f32.cu", "kernels_f64.cu", "runtime.cu", "noalloc.cu"]
+SOURCES = ["kernels_f32.cu", "kernels_f64.cu", "runtime.cu", "noalloc.cu", "serve.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "-diag-suppress", "177", "-I" + os.path.join(ROOT, "include"), "-I" + CSRC]
@@ -44,7 +44,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     tag = str(os.getpid())
 
     def compile_one(src: str) -> str:
-        obj = os.path.join(LIBDIR, src.replace(".cu", ".%s.o" % tag))
+        obj = os.path.join(LIBDIR, os.path.splitext(src)[0] + ".%s.o" % tag)
         cmd = [nv, *ARCH, *FLAGS, "-c", os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:

@@ -36,10 +36,13 @@ struct HostBuf {
 cudaError_t ensure(DevBuf& b, size_t bytes) {
     if (bytes == 0) bytes = 16;
     if (bytes <= b.cap) return cudaSuccess;
+    const bool regrow = b.cap > 0;
     if (b.p) cudaFree(b.p);
     b.p = nullptr;
     b.cap = 0;
-    const size_t nb = std::max(bytes, (size_t)4096);
+    // regrowth keeps 1/8 headroom so that batches of slowly varying size reallocate rarely
+    // (cudaFree waits for the whole device, including other slots' work)
+    const size_t nb = std::max(regrow ? bytes + bytes / 8 : bytes, (size_t)4096);
     cudaError_t e = cudaMalloc(&b.p, nb);
     if (e != cudaSuccess) {
         b.p = nullptr;
@@ -386,6 +389,11 @@ struct Slot {
     BatchHeader hh;
     cudaEvent_t ev_copy = nullptr, ev_start = nullptr, ev_fwd0 = nullptr, ev_fwd1 = nullptr,
                 ev_res0 = nullptr, ev_res1 = nullptr, ev_end = nullptr;
+    // Per-slot streams: batches in different slots run concurrently on the device.
+    // sm carries the pipeline, sb2/sb3 the multi-warp and packed branches of the forward pass.
+    cudaStream_t sm = nullptr, sb2 = nullptr, sb3 = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_join3 = nullptr, ev_user = nullptr;
+    uint64_t foot = 0;  // admitted device footprint while pending
     cudaGraphExec_t gexec = nullptr;
     int g_key = -1;
     uint64_t ticket = 0;
@@ -420,9 +428,7 @@ struct phmm_ctx {
     DevBuf pow64;
     int occ_packed[kNumPacked] = {}, occ_scalar[kNumScalar] = {}, occ_long = 1, occ64 = 1;
     std::map<uint64_t, std::pair<int, int>> tuned;  // batch signature -> (scalar id, packed id)
-    cudaStream_t stream2 = nullptr;         // graph branch: multi-warp pairs
-    cudaStream_t stream3 = nullptr;         // graph branch: packed short teams
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_join3 = nullptr;
+    uint64_t inflight_foot = 0;             // sum of pending slots' footprints
     bool dead = false;
     uint32_t seed = 0x5eed1234u;
     uint64_t last_retired = 0;
@@ -445,8 +451,27 @@ int pow_index(int N) { return N == 12 ? 0 : N == 16 ? 1 : N == 20 ? 2 : N == 24 
         }                                       \
     } while (0)
 
+DevBuf* arena_bufs(Slot& S, int i) {
+    DevBuf* d[] = {&S.in_bases, &S.in_bq, &S.in_iq, &S.in_dq, &S.in_gq, &S.in_hap, &S.in_roff, &S.in_hoff,
+                   &S.in_pr, &S.in_ph, &S.desc, &S.rec32, &S.rec64, &S.teams, &S.witems, &S.witems2,
+                   &S.cpairs, &S.citems, &S.parts, &S.out, &S.oflags, &S.rescue, &S.bnd, &S.rbnd};
+    return i < (int)(sizeof(d) / sizeof(d[0])) ? d[i] : nullptr;
+}
+
+uint64_t slot_capacity(Slot& S) {
+    uint64_t c = 0;
+    for (int i = 0; DevBuf* b = arena_bufs(S, i); ++i) c += b->cap;
+    return c;
+}
+
+// Frees an idle slot's batch arenas (its header, counters and events stay).
+void release_arenas(Slot& S) {
+    for (int i = 0; DevBuf* b = arena_bufs(S, i); ++i) release(*b);
+    S.plan_valid = false;
+}
+
 int launch_sequence(phmm_ctx* ctx, Slot& S, int scal_id, int pack_id, bool record_events) {
-    cudaStream_t s = ctx->stream;
+    cudaStream_t s = S.sm;
     const BatchHeader* H = static_cast<const BatchHeader*>(S.hdr.p);
     const PhredTables* T = static_cast<const PhredTables*>(ctx->tables.p);
     const int prec = ctx->cfg.precision;
@@ -468,19 +493,19 @@ int launch_sequence(phmm_ctx* ctx, Slot& S, int scal_id, int pack_id, bool recor
         launch_prep32(H, T, grid_pre, s);
         CK(rec(S.ev_fwd0));
         // fork: multi-warp pairs and packed teams on two more branches, scalar teams here
-        CK(cudaEventRecord(ctx->ev_fork, s));
-        CK(cudaStreamWaitEvent(ctx->stream2, ctx->ev_fork, 0));
-        CK(cudaStreamWaitEvent(ctx->stream3, ctx->ev_fork, 0));
-        launch_forward32_long(H, ctx->pow32[pow_index(kNLong32)].p, ctx->sms * ctx->occ_long, ctx->stream2);
-        CK(cudaEventRecord(ctx->ev_join, ctx->stream2));
+        CK(cudaEventRecord(S.ev_fork, s));
+        CK(cudaStreamWaitEvent(S.sb2, S.ev_fork, 0));
+        CK(cudaStreamWaitEvent(S.sb3, S.ev_fork, 0));
+        launch_forward32_long(H, ctx->pow32[pow_index(kNLong32)].p, ctx->sms * ctx->occ_long, S.sb2);
+        CK(cudaEventRecord(S.ev_join, S.sb2));
         if (pack_id >= 0)
             launch_short_packed(pack_id, H, ctx->pow32[pow_index(kShortPackedN[pack_id])].p,
-                                ctx->sms * ctx->occ_packed[pack_id], ctx->stream3);
-        CK(cudaEventRecord(ctx->ev_join3, ctx->stream3));
+                                ctx->sms * ctx->occ_packed[pack_id], S.sb3);
+        CK(cudaEventRecord(S.ev_join3, S.sb3));
         launch_short_scalar(scal_id, H, ctx->pow32[pow_index(kShortScalarN[scal_id])].p,
                             ctx->sms * ctx->occ_scalar[scal_id], s);
-        CK(cudaStreamWaitEvent(s, ctx->ev_join, 0));
-        CK(cudaStreamWaitEvent(s, ctx->ev_join3, 0));
+        CK(cudaStreamWaitEvent(s, S.ev_join, 0));
+        CK(cudaStreamWaitEvent(s, S.ev_join3, 0));
         CK(rec(S.ev_fwd1));
         launch_finalize32(H, grid_pre, s);
         CK(rec(S.ev_res0));
@@ -656,12 +681,6 @@ int phmm_create(const phmm_config* cfg, phmm_ctx** out) {
         fprintf(stderr, "phmm: sms %d occupancy packed %d %d scalar %d %d %d %d long %d fp64 %d\n",
                 ctx->sms, ctx->occ_packed[0], ctx->occ_packed[1], ctx->occ_scalar[0], ctx->occ_scalar[1],
                 ctx->occ_scalar[2], ctx->occ_scalar[3], ctx->occ_long, ctx->occ64);
-    if (cudaStreamCreateWithFlags(&ctx->stream2, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaStreamCreateWithFlags(&ctx->stream3, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&ctx->ev_join3, cudaEventDisableTiming) != cudaSuccess)
-        return fail(PHMM_ECUDA);
     {
         std::vector<PowRow<double>> v;
         build_pow_table<double>(kN64, v);
@@ -674,6 +693,12 @@ int phmm_create(const phmm_config* cfg, phmm_ctx** out) {
         cudaEvent_t* evs[] = {&S.ev_copy, &S.ev_start, &S.ev_fwd0, &S.ev_fwd1, &S.ev_res0, &S.ev_res1, &S.ev_end};
         for (auto* e : evs)
             if (cudaEventCreate(e) != cudaSuccess) return fail(PHMM_ECUDA);
+        cudaEvent_t* evn[] = {&S.ev_fork, &S.ev_join, &S.ev_join3, &S.ev_user};
+        for (auto* e : evn)
+            if (cudaEventCreateWithFlags(e, cudaEventDisableTiming) != cudaSuccess) return fail(PHMM_ECUDA);
+        cudaStream_t* sts[] = {&S.sm, &S.sb2, &S.sb3};
+        for (auto* q : sts)
+            if (cudaStreamCreateWithFlags(q, cudaStreamNonBlocking) != cudaSuccess) return fail(PHMM_ECUDA);
         if (ensure(S.small, 64) != cudaSuccess || ensure(S.h_small, 64) != cudaSuccess ||
             ensure(S.hdr, sizeof(BatchHeader)) != cudaSuccess)
             return fail(PHMM_ECUDA);
@@ -689,6 +714,11 @@ void phmm_destroy(phmm_ctx* ctx) {
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     if (ctx->copy_stream) cudaStreamSynchronize(ctx->copy_stream);
     for (auto& S : ctx->slots) {
+        cudaStream_t sts[] = {S.sm, S.sb2, S.sb3};
+        for (auto q : sts)
+            if (q) cudaStreamSynchronize(q);
+    }
+    for (auto& S : ctx->slots) {
         DevBuf* d[] = {&S.in_bases, &S.in_bq, &S.in_iq, &S.in_dq, &S.in_gq, &S.in_hap, &S.in_roff,
                        &S.in_hoff, &S.in_pr, &S.in_ph, &S.desc, &S.rec32, &S.rec64, &S.teams,
                        &S.witems, &S.witems2, &S.cpairs, &S.citems, &S.parts, &S.out, &S.oflags, &S.rescue,
@@ -699,17 +729,16 @@ void phmm_destroy(phmm_ctx* ctx) {
         cudaEvent_t evs[] = {S.ev_copy, S.ev_start, S.ev_fwd0, S.ev_fwd1, S.ev_res0, S.ev_res1, S.ev_end};
         for (auto e : evs)
             if (e) cudaEventDestroy(e);
+        cudaEvent_t evn[] = {S.ev_fork, S.ev_join, S.ev_join3, S.ev_user};
+        for (auto e : evn)
+            if (e) cudaEventDestroy(e);
         if (S.gexec) cudaGraphExecDestroy(S.gexec);
+        cudaStream_t sts[] = {S.sm, S.sb2, S.sb3};
+        for (auto q : sts)
+            if (q) cudaStreamDestroy(q);
     }
     release(ctx->tables);
     release(ctx->scan_row);
-    if (ctx->stream2) cudaStreamSynchronize(ctx->stream2);
-    if (ctx->stream3) cudaStreamSynchronize(ctx->stream3);
-    if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
-    if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
-    if (ctx->ev_join3) cudaEventDestroy(ctx->ev_join3);
-    if (ctx->stream2) cudaStreamDestroy(ctx->stream2);
-    if (ctx->stream3) cudaStreamDestroy(ctx->stream3);
     for (auto& b : ctx->pow32) release(b);
     release(ctx->pow64);
     if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
@@ -749,6 +778,9 @@ int phmm_submit_batch(phmm_ctx* ctx, const phmm_batch* b, uint64_t* ticket) {
     const uint64_t *roff = b->read_off, *hoff = b->hap_off;
     const uint32_t *pr = b->pair_read, *ph = b->pair_hap;
     if (dev_in && np > 0) {
+        // device inputs are produced on the caller's stream: read them after its pending work
+        CK(cudaEventRecord(S->ev_user, ctx->stream));
+        CK(cudaStreamWaitEvent(ctx->copy_stream, S->ev_user, 0));
         CK(ensure(S->h_roff, (nr + 1) * 8ull));
         CK(ensure(S->h_hoff, (nh + 1) * 8ull));
         CK(ensure(S->h_pr, np * 4ull));
@@ -826,7 +858,13 @@ int phmm_submit_batch(phmm_ctx* ctx, const phmm_batch* b, uint64_t* ticket) {
     N = P.N;
     // footprint and admission
     const bool need64 = ctx->cfg.precision != PHMM_PREC_FP32_ONLY;
+    uint32_t lmax_b = 0;
+    for (uint32_t p = 0; p < np; ++p) lmax_b = std::max(lmax_b, L[p]);
+    const uint64_t rb_words = (uint64_t)lmax_b * 8;  // FP64 boundary: 8 words per row
+    const int rescue_ctas = ctx->sms * ctx->occ64;
+    const uint64_t rb_bytes = (uint64_t)rescue_ctas * 2 * rb_words * 8ull + 16;
     const uint64_t foot = (dev_in ? 0 : nbases * 5 + nhb + (nr + 1) * 8ull + (nh + 1) * 8ull + np * 8ull) +
+                          (ctx->cfg.precision != PHMM_PREC_FP32_ONLY ? rb_bytes : 0) +
                           np * (sizeof(PairDesc) + sizeof(Partial) + 8 + 1 + 4) +
                           (ctx->cfg.precision == PHMM_PREC_FP64 ? 0 : nbases * sizeof(Rec32)) +
                           (need64 ? nbases * sizeof(Rec64) : 0) +
@@ -834,6 +872,16 @@ int phmm_submit_batch(phmm_ctx* ctx, const phmm_batch* b, uint64_t* ticket) {
                           P.cpairs.size() * sizeof(CtaPair) + P.citems.size() * sizeof(CtaItem) +
                           P.bnd_words * 8ull + P.n_extra * sizeof(Partial);
     if (foot > ctx->budget) return PHMM_ENOMEM;
+    if (foot + ctx->inflight_foot > ctx->budget) return PHMM_EBUSY;  // admissible once others retire
+    {
+        // arenas persist across batches; give back idle slots' arenas when the budget needs them
+        uint64_t held = 0;
+        for (auto& o : ctx->slots)
+            if (&o != S) held += slot_capacity(o);
+        if (held + std::max<uint64_t>(foot, slot_capacity(*S)) > ctx->budget)
+            for (auto& o : ctx->slots)
+                if (&o != S && o.state == 0) release_arenas(o);
+    }
     // device arenas
     BatchHeader& hh = S->hh;
     memset(&hh, 0, sizeof(hh));
@@ -869,11 +917,7 @@ int phmm_submit_batch(phmm_ctx* ctx, const phmm_batch* b, uint64_t* ticket) {
     if (need64) CK(ensure(S->rec64, nbases * sizeof(Rec64)));
     CK(ensure(S->parts, (np + P.n_extra) * sizeof(Partial)));
     CK(ensure(S->bnd, P.bnd_words * 8ull));
-    uint32_t lmax_b = 0;
-    for (uint32_t p = 0; p < np; ++p) lmax_b = std::max(lmax_b, L[p]);
-    const uint64_t rb_words = (uint64_t)lmax_b * 8;  // FP64 boundary: 8 words per row
-    const int rescue_ctas = ctx->sms * ctx->occ64;
-    if (ctx->cfg.precision != PHMM_PREC_FP32_ONLY) CK(ensure(S->rbnd, (uint64_t)rescue_ctas * 2 * rb_words * 8ull + 16));
+    if (ctx->cfg.precision != PHMM_PREC_FP32_ONLY) CK(ensure(S->rbnd, rb_bytes));
     CK(ensure(S->out, np * 8ull));
     CK(ensure(S->oflags, np * 1ull));
     CK(ensure(S->rescue, np * 4ull));
@@ -910,11 +954,14 @@ int phmm_submit_batch(phmm_ctx* ctx, const phmm_batch* b, uint64_t* ticket) {
     CK(cudaEventRecord(S->ev_copy, cs));
     // host inputs may be released when submit returns
     CK(cudaEventSynchronize(S->ev_copy));
+    // this slot's pipeline runs after the caller's pending work and the uploads
+    CK(cudaEventRecord(S->ev_user, ctx->stream));
+    CK(cudaStreamWaitEvent(S->sm, S->ev_user, 0));
+    CK(cudaStreamWaitEvent(S->sm, S->ev_copy, 0));
     if (tune_now) {
         // Measured tuning: run the FP32 pipeline once per candidate kernel pair on this
         // batch (events around the forward kernels), keep the fastest for this shape.
-        cudaStream_t ts = ctx->stream;
-        CK(cudaStreamWaitEvent(ts, S->ev_copy, 0));
+        cudaStream_t ts = S->sm;
         double best_ms = 1e30;
         int bs = P.scal_id, bp = P.pack_id;
         for (auto& cd : tune_cand) {
@@ -951,8 +998,7 @@ int phmm_submit_batch(phmm_ctx* ctx, const phmm_batch* b, uint64_t* ticket) {
         CK(cudaStreamSynchronize(cs));
         N = P.N;
     }
-    cudaStream_t s = ctx->stream;
-    CK(cudaStreamWaitEvent(s, S->ev_copy, 0));
+    cudaStream_t s = S->sm;
     CK(cudaEventRecord(S->ev_start, s));
     uint32_t launches = 0;
     if (np > 0) {
@@ -1013,6 +1059,10 @@ int phmm_submit_batch(phmm_ctx* ctx, const phmm_batch* b, uint64_t* ticket) {
         CK(cudaEventRecord(S->ev_res1, s));
     }
     CK(cudaEventRecord(S->ev_end, s));
+    // later work on the caller's stream sees the outputs
+    CK(cudaStreamWaitEvent(ctx->stream, S->ev_end, 0));
+    S->foot = foot;
+    ctx->inflight_foot += foot;
     S->ticket = ++ctx->next_ticket;
     S->state = 1;
     S->user_out = b->out_log10;
@@ -1032,6 +1082,43 @@ int phmm_submit_batch(phmm_ctx* ctx, const phmm_batch* b, uint64_t* ticket) {
     S->plan_np = np;
     S->st.ms_host = (float)std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - th0).count();
     *ticket = S->ticket;
+    return PHMM_OK;
+}
+
+int phmm_batch_footprint(phmm_ctx* ctx, const phmm_batch* b, uint64_t* bytes) {
+    if (!ctx || !b || !bytes || b->inputs_on_device) return PHMM_EINVAL;
+    *bytes = 0;
+    const uint32_t nr = b->n_reads, nh = b->n_haps, np = b->n_pairs;
+    if (np == 0) return PHMM_OK;
+    if (!b->read_off || !b->hap_off || !b->pair_read || !b->pair_hap || nr == 0 || nh == 0) return PHMM_EINVAL;
+    const uint64_t *roff = b->read_off, *hoff = b->hap_off;
+    if (roff[0] != 0 || hoff[0] != 0) return PHMM_EINVAL;
+    for (uint32_t r = 0; r < nr; ++r)
+        if (roff[r + 1] <= roff[r] || roff[r + 1] - roff[r] > 0xffffffull) return PHMM_EINVAL;
+    for (uint32_t h = 0; h < nh; ++h)
+        if (hoff[h + 1] <= hoff[h] || hoff[h + 1] - hoff[h] > 0xffffffull) return PHMM_EINVAL;
+    const int prec = ctx->cfg.precision;
+    const bool need64 = prec != PHMM_PREC_FP32_ONLY;
+    const uint64_t nbases = roff[nr], nhb = hoff[nh];
+    const uint64_t seg = 32ull * (prec == PHMM_PREC_FP64 ? kN64 : kNLong32);
+    uint64_t f = nbases * 5 + nhb + (nr + 1) * 8ull + (nh + 1) * 8ull + np * 8ull;
+    f += nbases * ((prec != PHMM_PREC_FP64 ? sizeof(Rec32) : 0) + (need64 ? sizeof(Rec64) : 0));
+    f += (uint64_t)np * (sizeof(PairDesc) + sizeof(Partial) + 8 + 1 + 4 + sizeof(Team) + 2 * sizeof(WarpItem) +
+                         sizeof(CtaPair) + sizeof(CtaItem));
+    uint64_t lmax = 0;
+    for (uint32_t p = 0; p < np; ++p) {
+        if (b->pair_read[p] >= nr || b->pair_hap[p] >= nh) return PHMM_EINVAL;
+        const uint64_t l = roff[b->pair_read[p] + 1] - roff[b->pair_read[p]];
+        const uint64_t k = hoff[b->pair_hap[p] + 1] - hoff[b->pair_hap[p]];
+        lmax = std::max(lmax, l);
+        const uint64_t Wt = (k + seg - 1) / seg;
+        if (Wt > (uint64_t)kCtaWarps) {  // strips of a very wide pair
+            const uint64_t S = (Wt + kCtaWarps - 1) / kCtaWarps;
+            f += (S - 1) * (l * (prec == PHMM_PREC_FP64 ? 8 : 4) * 8 + sizeof(Partial) + sizeof(CtaPair) + sizeof(CtaItem));
+        }
+    }
+    if (need64) f += (uint64_t)ctx->sms * ctx->occ64 * 2 * lmax * 8 * 8 + 16;
+    *bytes = f;
     return PHMM_OK;
 }
 
@@ -1079,6 +1166,8 @@ int phmm_poll(phmm_ctx* ctx, uint64_t ticket, int timeout_ms) {
     S->st.ms_rescue = ms;
     ctx->last_stats = S->st;
     ctx->last_retired = S->ticket;
+    ctx->inflight_foot -= S->foot;
+    S->foot = 0;
     S->state = 0;
     int rc = S->host_status;
     if (sm[8] & ST_TIMEOUT) rc = PHMM_ETIMEOUT;

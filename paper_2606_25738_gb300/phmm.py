@@ -26,7 +26,8 @@ PAIR_DANGER, PAIR_NONFINITE, PAIR_SMALL_SUM, PAIR_DEGENERATE = 0x8, 0x10, 0x20, 
 # Every entry point declared in include/phmm.h.
 SYMBOLS = ["phmm_create", "phmm_submit_batch", "phmm_poll", "phmm_get_stats", "phmm_destroy",
            "phmm_strerror", "phmm_abi_version", "phmm_device_info", "phmm_scan_test",
-           "phmm_forward_noalloc"]
+           "phmm_forward_noalloc", "phmm_batch_footprint", "phmm_server_create",
+           "phmm_server_enqueue", "phmm_server_poll", "phmm_server_get_stats", "phmm_server_destroy"]
 
 
 class PhmmError(RuntimeError):
@@ -66,6 +67,19 @@ class Stats(ctypes.Structure):
         return {name: getattr(self, name) for name, _ in self._fields_}
 
 
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("mem_budget_bytes", ctypes.c_uint64), ("max_epoch_pairs", ctypes.c_uint32),
+                ("max_inflight_epochs", ctypes.c_uint32), ("max_pending", ctypes.c_uint32)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint64) for n in ("enqueued", "admitted", "completed", "failed", "epochs",
+                                               "pending", "inflight", "cells_completed", "bytes_inflight")]
+
+    def as_dict(self) -> dict:
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
 def _load() -> ctypes.CDLL:
     if not os.path.exists(LIB_PATH):
         raise RuntimeError("libphmm.so is not built (%s); run __graft_entry__.build() or "
@@ -84,6 +98,15 @@ def _load() -> ctypes.CDLL:
     lib.phmm_scan_test.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
                                    ctypes.c_float]
     lib.phmm_forward_noalloc.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(Batch)]
+    lib.phmm_batch_footprint.argtypes = [ctypes.c_void_p, ctypes.POINTER(Batch), ctypes.POINTER(ctypes.c_uint64)]
+    lib.phmm_server_create.argtypes = [ctypes.c_void_p, ctypes.POINTER(ServerConfig),
+                                       ctypes.POINTER(ctypes.c_void_p)]
+    lib.phmm_server_enqueue.argtypes = [ctypes.c_void_p, ctypes.POINTER(Batch), ctypes.POINTER(ctypes.c_uint64)]
+    lib.phmm_server_poll.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int,
+                                     ctypes.POINTER(ctypes.c_double)]
+    lib.phmm_server_get_stats.argtypes = [ctypes.c_void_p, ctypes.POINTER(ServerStats)]
+    lib.phmm_server_destroy.argtypes = [ctypes.c_void_p]
+    lib.phmm_server_destroy.restype = None
     return lib
 
 
@@ -104,6 +127,18 @@ def _host_arrays(b: dict) -> dict:
     a["pair_read"] = np.ascontiguousarray(b["pair_read"], dtype=np.uint32)
     a["pair_hap"] = np.ascontiguousarray(b["pair_hap"], dtype=np.uint32)
     return a
+
+
+def _host_batch(b: dict, out, out_flags):
+    """ctypes Batch over host numpy arrays; returns (batch, arrays kept alive)."""
+    arrs = _host_arrays(b)
+    ptr = {k: ctypes.c_void_p(v.ctypes.data) for k, v in arrs.items()}
+    bb = Batch(len(arrs["read_off"]) - 1, ptr["read_bases"], ptr["read_off"], ptr["base_q"], ptr["ins_q"],
+               ptr["del_q"], ptr["gcp_q"], len(arrs["hap_off"]) - 1, ptr["hap_bases"], ptr["hap_off"],
+               len(arrs["pair_read"]), ptr["pair_read"], ptr["pair_hap"],
+               ctypes.c_void_p(out.ctypes.data) if out is not None else None,
+               ctypes.c_void_p(out_flags.ctypes.data) if out_flags is not None else None, 0, 0)
+    return bb, arrs
 
 
 def to_device(b: dict, device: str = "cuda"):
@@ -217,6 +252,15 @@ class Context:
             raise PhmmError(rc, "phmm_poll")
         return out, out_flags, rc, st
 
+    def footprint(self, b: dict) -> int:
+        """phmm_batch_footprint: device bytes a host batch may hold while in flight."""
+        bb, _arrs = _host_batch(b, None, None)
+        v = ctypes.c_uint64()
+        rc = _lib.phmm_batch_footprint(self._h, ctypes.byref(bb), ctypes.byref(v))
+        if rc != PHMM_OK:
+            raise PhmmError(rc, "phmm_batch_footprint")
+        return v.value
+
     def scan_test(self, y, a: float):
         """The lane + warp linear-recurrence scan on a torch CUDA float32 tensor y
         (1..1024 values): z[t] = sum_{s<=t} a^(t-s) y[s]."""
@@ -239,3 +283,63 @@ def forward_noalloc(d: dict, out, out_flags, device: int = 0, stream=None) -> in
                len(d["pair_read"]), ptr["pair_read"], ptr["pair_hap"], ctypes.c_void_p(out.data_ptr()),
                ctypes.c_void_p(out_flags.data_ptr()), 1, 1)
     return _lib.phmm_forward_noalloc(device, ctypes.c_void_p(stream) if stream else None, ctypes.byref(bb))
+
+
+class Server:
+    """Continuous-batching request loop of the library (phmm_server_*), on a Context it
+    takes over while it runs.  Requests are host batches; results land in numpy arrays."""
+
+    def __init__(self, ctx: Context, mem_budget: int = 40 << 30, max_epoch_pairs: int = 0,
+                 max_inflight_epochs: int = 2, max_pending: int = 0):
+        self.ctx = ctx
+        cfg = ServerConfig(mem_budget, max_epoch_pairs, max_inflight_epochs, max_pending)
+        h = ctypes.c_void_p()
+        rc = _lib.phmm_server_create(ctx._h, ctypes.byref(cfg), ctypes.byref(h))
+        if rc != PHMM_OK:
+            raise PhmmError(rc, "phmm_server_create")
+        self._h = h
+        self._out = {}
+
+    def enqueue(self, b: dict) -> int:
+        """Queue a request; returns its id.  Raises PhmmError on rejection."""
+        n = len(b["pair_read"])
+        out = np.full(n, np.nan, dtype=np.float64)
+        fl = np.zeros(n, dtype=np.uint8)
+        bb, _arrs = _host_batch(b, out, fl)
+        rid = ctypes.c_uint64()
+        rc = _lib.phmm_server_enqueue(self._h, ctypes.byref(bb), ctypes.byref(rid))
+        if rc != PHMM_OK:
+            raise PhmmError(rc, "phmm_server_enqueue")
+        self._out[rid.value] = (out, fl)
+        return rid.value
+
+    def poll(self, rid: int, timeout_ms: int = -1):
+        """(status, latency_ms, log10 L, flags); results are None while pending."""
+        lat = ctypes.c_double()
+        rc = _lib.phmm_server_poll(self._h, rid, timeout_ms, ctypes.byref(lat))
+        if rc == PHMM_PENDING:
+            return rc, None, None, None
+        out, fl = self._out.pop(rid, (None, None))
+        return rc, lat.value, out, fl
+
+    def stats(self) -> dict:
+        s = ServerStats()
+        _lib.phmm_server_get_stats(self._h, ctypes.byref(s))
+        return s.as_dict()
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.phmm_server_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -246,6 +246,69 @@ def uneven_pairs(n_pairs: int = 1_000_000, seed: int = 0, len_range=(50, 20000))
     return _pack(reads, quals, haps, idx, idx)
 
 
+def _short_read_quals(rng, n: int):
+    """Base quals 85% U{30..41} / 15% U{2..29}; ins/del U{40..45}; gcp 10."""
+    hi = rng.random(n) < 0.85
+    bq = np.where(hi, rng.integers(30, 42, size=n), rng.integers(2, 30, size=n)).astype(np.uint8)
+    return (bq, rng.integers(40, 46, size=n).astype(np.uint8),
+            rng.integers(40, 46, size=n).astype(np.uint8), np.full(n, 10, np.uint8))
+
+
+def region_request(rng, reads_range=(10, 500), haps_range=(2, 16), long_frac=0.2,
+                   long_range=(1000, 20000), short_len=150, hap_factor=(1.5, 3.0)) -> dict:
+    """One serving request: an active region of R ~ U{reads_range} reads x H ~
+    U{haps_range} haplotypes, scored as all R x H pairs.  With probability ``long_frac``
+    every read of the region has one length drawn log-uniform in ``long_range``, else
+    ``short_len``.  The reference window is U[hap_factor] x the read length; haplotypes
+    are the reference with SNPs (1e-3 per base) and 1 bp indels (1e-4 per base); reads
+    come from a random haplotype at a random offset with the short-read error and
+    quality model (substitutions U[0.5%, 2%], then 1% N)."""
+    R = int(rng.integers(reads_range[0], reads_range[1] + 1))
+    H = int(rng.integers(haps_range[0], haps_range[1] + 1))
+    if rng.random() < long_frac:
+        rl = int(round(np.exp(rng.uniform(np.log(long_range[0]), np.log(long_range[1])))))
+    else:
+        rl = short_len
+    wl = max(rl, int(round(rl * rng.uniform(hap_factor[0], hap_factor[1]))))
+    ref = _random_bases(rng, wl)
+    haps = []
+    for _ in range(H):
+        hap = _substitute(rng, ref, 1e-3)
+        ev = np.flatnonzero(rng.random(wl) < 1e-4)
+        if len(ev):
+            keep = np.ones(len(hap), bool)
+            ins_at, ins_b = [], []
+            for p in ev:
+                if rng.random() < 0.5:
+                    ins_at.append(p)
+                    ins_b.append(_random_bases(rng, 1)[0])
+                else:
+                    keep[p] = False
+            hap = np.insert(hap, ins_at, ins_b) if ins_at else hap
+            if not keep.all():
+                keep = np.insert(keep, ins_at, True) if ins_at else keep
+                hap = hap[keep]
+        haps.append(hap)
+    reads, quals = [], []
+    src = rng.integers(0, H, size=R)
+    for r in range(R):
+        hap = haps[int(src[r])]
+        off = int(rng.integers(0, max(len(hap) - rl, 0) + 1))
+        read = _mutate(rng, hap, off, rl, float(rng.uniform(0.005, 0.02)), 0.0)
+        read[rng.random(rl) < 0.01] = ord("N")
+        reads.append(read)
+        quals.append(_short_read_quals(rng, rl))
+    pr = np.repeat(np.arange(R), H)
+    ph = np.tile(np.arange(H), R)
+    return _pack(reads, quals, haps, pr, ph)
+
+
+def serving_requests(n: int, seed: int = 0, **kw) -> list:
+    """``n`` independent region requests (see region_request), seeded."""
+    rng = _rng(seed, 5)
+    return [region_request(rng, **kw) for _ in range(n)]
+
+
 def equal_length(n_pairs: int, length: int, seed: int = 0) -> dict:
     """Equal-length synthetic pairs (read length = haplotype length), the shape of the
     paper's scalability sweep (Section 4.3): random haplotype, read = haplotype with 1%
