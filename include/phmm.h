@@ -84,9 +84,13 @@ typedef struct {
                                  pairs: 12 or 16 fixes the packed-team width, 24 or 32 the
                                  scalar-team width, 0 = chosen by the built-in tuner.
                                  Multi-warp pairs use 32 (FP32); FP64 kernels use 8. */
-    int kernel_variant;       /* FP32 short pairs: 0 or 1 = pairs of the same read share
-                                 packed teams (two haplotypes per thread in float2 halves),
-                                 the rest run in scalar teams; 2 = scalar teams only */
+    int kernel_variant;       /* FP32 short-pair kernels the tuner may use: 0 = any; 1 =
+                                 pairs of the same read share packed teams (two haplotypes
+                                 per thread in float2 halves), the rest run in scalar
+                                 teams; 2 = scalar teams only (lean or pipelined engine);
+                                 3 = lean scalar engine only; 4 = pipelined scalar engine
+                                 only (the next row's scan-independent work overlaps the
+                                 deletion scan) */
 } phmm_config;
 
 /*

@@ -118,6 +118,14 @@ __device__ __forceinline__ Rec32 load_rec(const Rec32* p) {
     r.mi = b.x; r.g = b.y; r.gm = b.z; r.meta = __float_as_uint(b.w);
     return r;
 }
+__device__ __forceinline__ Rec32J load_recj(const Rec32J* p) {
+    const float4 a = __ldg(reinterpret_cast<const float4*>(p));
+    const float4 b = __ldg(reinterpret_cast<const float4*>(p) + 1);
+    Rec32J r;
+    r.pm = a.x; r.px = a.y; r.a = a.z; r.b = a.w;
+    r.h = b.x; r.g = b.y; r.mi = b.z; r.meta = __float_as_uint(b.w);
+    return r;
+}
 __device__ __forceinline__ Rec64 load_rec(const Rec64* p) {
     const double2* q = reinterpret_cast<const double2*>(p);
     const double2 a = __ldg(q), b = __ldg(q + 1), c = __ldg(q + 2), d = __ldg(q + 3);
@@ -1000,6 +1008,184 @@ __device__ SegOut team_run_lean(const Rec32* __restrict__ rec, int l, int lmax,
 }  // namespace phmm
 
 namespace phmm {
+
+// ------------------------------------------------------------------------------------
+// Pipelined scalar FP32 team (short pairs, no neighbour link).  Same recurrences as
+// team_run_lean (Eq. 2 in the row-wise form of Eq. 7), rearranged so that the part of
+// row i+1 that does not depend on row i's deletion scan runs while that scan's shuffles
+// are in flight:
+//   phase B (row i):  u = b D-hat_{i-1,j-1} + U_ij,  M_ij = P' u,  D-hat_{i-1} chain
+//                     (carry from the left lane), lane-local D-hat_i chain y;
+//   scan of y over the team (Algorithm 1), and alongside it
+//   phase A (row i+1): U_{i+1,j} = a M_{i,j-1} + J_{i,j-1},  J_{i+1,j} = M_{i,j} + h J_{i,j}.
+// J = I / T_MI (see Rec32J) makes the insertion update a single FMA.  The scan always
+// takes five steps (steps beyond the team width change nothing), so it is one basic
+// block that the compiler can interleave with phase A.
+// ------------------------------------------------------------------------------------
+template <int N>
+__device__ SegOut team_run_pipe(const Rec32J* __restrict__ rec, int l, int lmax,
+                                const uint8_t* __restrict__ hap, int k, int col0, int lt,
+                                int tlast, int nsteps, const PowRow<float>* __restrict__ pow_tab,
+                                int R) {
+    using NT = Num<float>;
+    static_assert(N <= 32, "match masks hold 32 columns");
+    uint32_t bmA = 0, bmC = 0, bmG = 0, bmT = 0, flags = 0, mflags = 0;
+    const int nvalid = max(0, min(k - col0, N));
+#pragma unroll
+    for (int c = 0; c < N; ++c) {
+        if (c < nvalid) {
+            const int code = base_code(hap[col0 + c]);
+            const uint32_t bit = 1u << c;
+            if (code < 0) flags |= PF_BAD;
+            if (code == 0 || code == 4) bmA |= bit;
+            if (code == 1 || code == 4) bmC |= bit;
+            if (code == 2 || code == 4) bmG |= bit;
+            if (code == 3 || code == 4) bmT |= bit;
+        }
+    }
+    float M[N], J[N], U[N];
+    int E = 0;
+    float ml = 0.f, dt = 0.f, gprev = 0.f;
+    float sp1[5], sp2[5], last1 = 0.f, last2 = 0.f;
+    int gcp = -1;
+    SegOut out;
+    out.S = 0.0;
+    out.E = 0;
+    out.flags = 0;
+    const float cinit = l > 0 && k > 0 ? (float)(0x1p120 / (double)k) : 0.f;
+    const int l1 = max(l, 1) - 1;
+    Rec32J cur = load_recj(rec);
+    int until = 0;
+    for (int i = 1; i <= lmax; ++i) {
+        Rec32J nxt = cur;
+        if (i < lmax) nxt = load_recj(rec + min(i, l1));
+        const uint32_t meta = cur.meta;
+        mflags |= meta;
+        const int gq = (int)((meta >> META_GCP_SHIFT) & 0xffu);
+        if (gq != gcp) {
+            const PowRow<float>* pr = pow_tab + min(gq, kMaxPhred);
+#pragma unroll
+            for (int s = 0; s < 5; ++s) {
+                sp1[s] = __ldg(&pr->sp1[s]);
+                sp2[s] = __ldg(&pr->sp2[s]);
+            }
+            last1 = __ldg(&pr->last1);
+            last2 = __ldg(&pr->last2);
+            gcp = gq;
+        }
+        const int code = (int)(meta & META_CODE_MASK);
+        const uint32_t mask = code == 0 ? bmA : code == 1 ? bmC : code == 2 ? bmG
+                            : code == 3 ? bmT : 0xffffffffu;
+        const float pim = cur.pm, pix = cur.px, rg = cur.g;
+        float y = 0.f, yprev = 0.f;
+        // phase B
+        if (i == 1) {
+#pragma unroll
+            for (int c = 0; c < N; ++c) {
+                M[c] = (((mask >> c) & 1u) ? pim : pix) * cinit;
+                J[c] = 0.f;
+                if (c == N - 1) yprev = y;
+                y = fmaf(rg, y, M[c]);
+            }
+        } else {
+            const float rb = cur.b;
+#pragma unroll
+            for (int c = 0; c < N; ++c) {
+                const float u = fmaf(rb, dt, U[c]);
+                dt = fmaf(gprev, dt, ml);
+                ml = M[c];
+                const float mn = (((mask >> c) & 1u) ? pim : pix) * u;
+                M[c] = mn;
+                if (c == N - 1) yprev = y;
+                y = fmaf(rg, y, mn);
+            }
+        }
+        // Eq. 4 when a pair of this warp finishes (I = T_MI J on the last row)
+        if (__any_sync(kFull, i == l)) {
+            const double rmi = (double)cur.mi;
+            double s = 0.0;
+#pragma unroll
+            for (int c = 0; c < N; ++c)
+                if (c < nvalid) s += (double)M[c] + rmi * (double)J[c];
+            s = team_sum<double>(s, lt, tlast, nsteps);
+            uint32_t f = flags;
+            if (mflags & META_BAD) f |= PF_BAD;
+            if (mflags & META_DEGEN) f |= PF_DEGEN;
+            f = team_or(f, lt, tlast, nsteps);
+            if (i == l) {
+                out.S = s;
+                out.E = E;
+                out.flags = f;
+            }
+        }
+        // the deletion scan of row i and, independent of it, phase A of row i+1
+        float nm = __shfl_up_sync(kFull, M[N - 1], 1);
+        float nj = __shfl_up_sync(kFull, J[N - 1], 1);
+        if (lt == 0) {
+            nm = 0.f;
+            nj = 0.f;
+        }
+        float Z = y;
+#pragma unroll
+        for (int s = 0; s < 5; ++s) {
+            const int off = 1 << s;
+            const float up = __shfl_up_sync(kFull, Z, off);
+            const float t = fmaf(up * sp1[s], sp2[s], Z);
+            Z = lt >= off ? t : Z;
+        }
+        {
+            const float na = nxt.a, nh = nxt.h;
+#pragma unroll
+            for (int c = N - 1; c >= 1; --c) {
+                U[c] = fmaf(na, M[c - 1], J[c - 1]);
+                J[c] = fmaf(nh, J[c], M[c]);
+            }
+            U[0] = fmaf(na, nm, nj);
+            J[0] = fmaf(nh, J[0], M[0]);
+        }
+        float Wd = __shfl_up_sync(kFull, Z, 1);
+        if (lt == 0) Wd = 0.f;
+        if (until == 0) {
+            // checkpoint: M holds row i, J and U row i+1 (linear in row i, so they take
+            // the same power of two)
+            until = R;
+            float m = 0.f;
+#pragma unroll
+            for (int c = 0; c < N; ++c) m = fmaxf(m, fmaxf(fabsf(M[c]), fabsf(J[c])));
+            m = team_max<float>(m, lt, tlast, nsteps);
+            const int e = NT::expo(m);
+            if (e == INT_MAX) {
+                flags |= PF_NONFINITE;
+            } else if (e != INT_MIN) {
+                if (e <= NT::kDanger) flags |= PF_DANGER;
+                if (e > NT::kHi || e <= NT::kLo) {
+                    const int sh = e - NT::kTarget;  // multiply by 2^-sh in two exact steps
+                    const float f1 = NT::pow2((-sh) / 2), f2v = NT::pow2(-sh - (-sh) / 2);
+#pragma unroll
+                    for (int c = 0; c < N; ++c) {
+                        M[c] = (M[c] * f1) * f2v;
+                        J[c] = (J[c] * f1) * f2v;
+                        U[c] = (U[c] * f1) * f2v;
+                    }
+                    Wd = (Wd * f1) * f2v;
+                    yprev = (yprev * f1) * f2v;
+                    nm = (nm * f1) * f2v;
+                    flags |= PF_RESCALED;
+                    E += sh;
+                }
+            }
+        }
+        --until;
+        const float Dlast = fmaf(Wd * last1, last2, yprev);
+        float nd = __shfl_up_sync(kFull, Dlast, 1);
+        if (lt == 0) nd = 0.f;
+        ml = nm;
+        dt = nd;
+        gprev = rg;
+        cur = nxt;
+    }
+    return out;
+}
 
 // ------------------------------------------------------------------------------------
 // Packed FP32 team for two haplotypes of the SAME read (pair A in x, pair B in y halves).

@@ -58,7 +58,7 @@ __device__ __forceinline__ int read_code(uint32_t c) { return base_code(c); }
 
 // Per-base record inputs with validation.  Returns META_BAD-tagged meta on bad input.
 struct BaseQ {
-    int code, Q, ins, del, gcp, delp;
+    int code, Q, ins, del, gcp, delp, insp;  // delp / insp: previous base of the batch
     bool bad;
 };
 __device__ __forceinline__ BaseQ base_inputs(const BatchHeader* __restrict__ H, uint64_t b) {
@@ -69,6 +69,7 @@ __device__ __forceinline__ BaseQ base_inputs(const BatchHeader* __restrict__ H, 
     r.del = H->del_q[b];
     r.gcp = H->gcp_q[b];
     r.delp = b > 0 ? H->del_q[b - 1] : 0;
+    r.insp = b > 0 ? H->ins_q[b - 1] : 0;
     r.bad = r.code < 0 || r.Q > kMaxPhred || r.ins > kMaxPhred || r.del > kMaxPhred ||
             r.gcp > kMaxPhred;
     r.code = r.code < 0 ? 4 : r.code;
@@ -77,6 +78,7 @@ __device__ __forceinline__ BaseQ base_inputs(const BatchHeader* __restrict__ H, 
     r.del = min(r.del, kMaxPhred);
     r.gcp = min(r.gcp, kMaxPhred);
     r.delp = min(r.delp, kMaxPhred);
+    r.insp = min(r.insp, kMaxPhred);
     return r;
 }
 
@@ -103,6 +105,43 @@ __device__ __forceinline__ Rec32 make_rec32(const BaseQ& x, const float2* tq, co
     uint32_t meta = (uint32_t)x.code | ((uint32_t)x.gcp << META_GCP_SHIFT);
     if (x.bad) meta |= META_BAD;
     if (!(om_g.hi >= 0x1p-20f) || !isfinite(r.a)) meta |= META_DEGEN;
+    r.meta = meta;
+    return r;
+}
+
+// Record of the pipelined FP32 engine (see Rec32J).  first: row 1 of a read, where the
+// previous row's T_MI is taken as 1.  All products in double-float, then stochastically
+// rounded to FP32 (unbiased, so per-row rounding errors do not add up to a drift over
+// long reads with constant qualities).
+__device__ __forceinline__ Rec32J make_rec32j(const BaseQ& x, const float2* tq, const float2* tom,
+                                              const float2* tq3, const float2* tinv, const float2* tiq,
+                                              uint32_t seed, uint64_t b, bool first) {
+    const df one = {1.0f, 0.0f};
+    const df q_i = {tq[x.ins].x, tq[x.ins].y};
+    const df q_d = {tq[x.del].x, tq[x.del].y};
+    const df q_g = {tq[x.gcp].x, tq[x.gcp].y};
+    const df om_g = {tom[x.gcp].x, tom[x.gcp].y};
+    const df om_Q = {tom[x.Q].x, tom[x.Q].y};
+    const df q3_Q = {tq3[x.Q].x, tq3[x.Q].y};
+    const df inv_g = {tinv[x.gcp].x, tinv[x.gcp].y};
+    const df iq_i = {tiq[x.ins].x, tiq[x.ins].y};
+    const df q_dp = {tq[x.delp].x, tq[x.delp].y};
+    const df mi_p = first ? one : df{tq[x.insp].x, tq[x.insp].y};    // mi_{i-1}
+    const df imi_p = first ? one : df{tiq[x.insp].x, tiq[x.insp].y}; // 1 / mi_{i-1}
+    const df tmm = df_sub(df_sub(one, q_i), q_d);
+    const uint64_t h1 = mix64(((uint64_t)seed << 40) ^ (b * 4u + 1u));
+    const uint64_t h2 = mix64(((uint64_t)seed << 40) ^ (b * 4u + 2u));
+    Rec32J r;
+    r.pm = sround(df_mul(df_mul(om_Q, om_g), mi_p), (uint32_t)(h1 & 0xffffffu));
+    r.px = sround(df_mul(df_mul(q3_Q, om_g), mi_p), (uint32_t)((h1 >> 24) & 0xffffffu));
+    r.a = sround(df_mul(df_mul(tmm, inv_g), imi_p), (uint32_t)((h1 >> 40) & 0xffffffu));
+    r.b = sround(df_mul(q_dp, imi_p), (uint32_t)(h2 & 0xffffffu));
+    r.h = sround(df_mul(df_mul(q_g, mi_p), iq_i), (uint32_t)((h2 >> 24) & 0xffffffu));
+    r.g = q_g.hi;
+    r.mi = q_i.hi;
+    uint32_t meta = (uint32_t)x.code | ((uint32_t)x.gcp << META_GCP_SHIFT);
+    if (x.bad) meta |= META_BAD;
+    if (!(om_g.hi >= 0x1p-20f) || !isfinite(r.a) || !isfinite(r.b) || !isfinite(r.h)) meta |= META_DEGEN;
     r.meta = meta;
     return r;
 }
@@ -161,6 +200,7 @@ __device__ __forceinline__ void load_tables(const PhredTables* __restrict__ G, P
         S.om[i] = G->om[i];
         S.q3[i] = G->q3[i];
         S.inv[i] = G->inv[i];
+        S.iq[i] = G->iq[i];
     }
 }
 
@@ -489,6 +529,36 @@ k_short_scalar(const BatchHeader* __restrict__ H, const PowRow<float>* __restric
         const int lmax = (int)__reduce_max_sync(kFull, (unsigned)l);
         const SegOut o = team_run_lean<N>(rec, l, lmax, hap, k, t.lt * N, t.lt, t.tlast, t.nsteps, pow, R,
                                           s_ring);
+        if (t.pair != kNoPair && t.lt == 0) write_part(H, t.pair, o);
+    }
+}
+
+// Pipelined scalar teams (team_run_pipe, Rec32J records), same work list as
+// k_short_scalar.
+template <int N, int MINB>
+__global__ void __launch_bounds__(kShortThreads, MINB)
+k_short_pipe(const BatchHeader* __restrict__ H, const PowRow<float>* __restrict__ pow) {
+    const int R = checkpoint_interval<float>(H->dropgrow);
+    const uint32_t n_w = H->n_witems;
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+        uint32_t wi = 0;
+        if (lane == 0) wi = atomicAdd(&H->counters[1], 1u);
+        wi = __shfl_sync(kFull, wi, 0);
+        if (wi >= n_w) break;
+        const TeamOf t = team_of(H->teams, H->witems[wi]);
+        int l = 0, k = 0;
+        const Rec32J* rec = reinterpret_cast<const Rec32J*>(dummy_rec<float>());
+        const uint8_t* hap = H->hap_bases;
+        if (t.pair != kNoPair) {
+            const PairDesc d = H->desc[t.pair];
+            l = (int)d.l;
+            k = (int)d.k;
+            rec = H->rec32j + d.roff;
+            hap = H->hap_bases + d.hoff;
+        }
+        const int lmax = (int)__reduce_max_sync(kFull, (unsigned)l);
+        const SegOut o = team_run_pipe<N>(rec, l, lmax, hap, k, t.lt * N, t.lt, t.tlast, t.nsteps, pow, R);
         if (t.pair != kNoPair && t.lt == 0) write_part(H, t.pair, o);
     }
 }

@@ -27,19 +27,37 @@ __global__ void k_reset(const BatchHeader* __restrict__ H) {
         H->bnd[q] = 0ull;
 }
 
-// One record per read base, plus pair descriptors and the batch's drop / grow maxima.
-__global__ void __launch_bounds__(256) k_prep32(const BatchHeader* __restrict__ H,
-                                                const PhredTables* __restrict__ TG) {
-    __shared__ float2 tq[kPhredTab], tom[kPhredTab], tq3[kPhredTab], tinv[kPhredTab];
+// Phred tables as double-float pairs in shared memory.
+struct Tables32 {
+    float2 tq[kPhredTab], tom[kPhredTab], tq3[kPhredTab], tinv[kPhredTab], tiq[kPhredTab];
+};
+__device__ __forceinline__ void stage_tables32(const PhredTables* __restrict__ TG, Tables32& T) {
     for (int i = threadIdx.x; i < kPhredTab; i += blockDim.x) {
         const df a = to_df(TG->q[i]), b = to_df(TG->om[i]), c = to_df(TG->q3[i]),
-                 d = to_df(TG->inv[i]);
-        tq[i] = make_float2(a.hi, a.lo);
-        tom[i] = make_float2(b.hi, b.lo);
-        tq3[i] = make_float2(c.hi, c.lo);
-        tinv[i] = make_float2(d.hi, d.lo);
+                 d = to_df(TG->inv[i]), e = to_df(TG->iq[i]);
+        T.tq[i] = make_float2(a.hi, a.lo);
+        T.tom[i] = make_float2(b.hi, b.lo);
+        T.tq3[i] = make_float2(c.hi, c.lo);
+        T.tinv[i] = make_float2(d.hi, d.lo);
+        T.tiq[i] = make_float2(e.hi, e.lo);
     }
     __syncthreads();
+}
+
+__device__ __forceinline__ void store_rec32j(Rec32J* dst, const Rec32J& r) {
+    float4* d = reinterpret_cast<float4*>(dst);
+    d[0] = make_float4(r.pm, r.px, r.a, r.b);
+    d[1] = make_float4(r.h, r.g, r.mi, __uint_as_float(r.meta));
+}
+
+// One record per read base (both FP32 layouts), plus pair descriptors and the batch's
+// drop / grow maxima.
+__global__ void __launch_bounds__(256) k_prep32(const BatchHeader* __restrict__ H,
+                                                const PhredTables* __restrict__ TG) {
+    __shared__ Tables32 T;
+    stage_tables32(TG, T);
+    const float2 *tq = T.tq, *tom = T.tom, *tq3 = T.tq3, *tinv = T.tinv;
+    Rec32J* const rj = H->rec32j;
     uint32_t dmax = 0, gmax = 0;
     const uint64_t n = H->n_read_bases;
     const uint32_t seed = H->seed;
@@ -50,6 +68,7 @@ __global__ void __launch_bounds__(256) k_prep32(const BatchHeader* __restrict__ 
         float4* dst = reinterpret_cast<float4*>(H->rec32 + b);
         dst[0] = make_float4(r.pm, r.px, r.a, r.b);
         dst[1] = make_float4(r.mi, r.g, r.gm, __uint_as_float(r.meta));
+        if (rj) store_rec32j(rj + b, make_rec32j(x, tq, tom, tq3, tinv, T.tiq, seed, b, false));
         if (x.bad) atomicOr(H->status, ST_BAD_INPUT);
         const float qi = tq[x.ins].x, qd = tq[x.del].x, qg = tq[x.gcp].x;
         const float drop = -log2f(fminf(qi, qg));
@@ -61,11 +80,30 @@ __global__ void __launch_bounds__(256) k_prep32(const BatchHeader* __restrict__ 
     build_desc(H);
 }
 
+// Row 1 of every read in the pipelined-engine records: the previous row's T_MI is 1
+// there (k_prep32 used the previous base of the batch).  Runs after k_prep32.
+__global__ void __launch_bounds__(256) k_prep32_first(const BatchHeader* __restrict__ H,
+                                                      const PhredTables* __restrict__ TG) {
+    __shared__ Tables32 T;
+    stage_tables32(TG, T);
+    Rec32J* const rj = H->rec32j;
+    if (!rj) return;
+    for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < H->n_reads; r += gridDim.x * blockDim.x) {
+        const uint64_t b = H->read_off[r];
+        if (b >= H->read_off[r + 1]) continue;
+        const BaseQ x = base_inputs(H, b);
+        store_rec32j(rj + b, make_rec32j(x, T.tq, T.tom, T.tq3, T.tinv, T.tiq, H->seed, b, true));
+    }
+}
+
 template __global__ void k_forward<float, kNLong32, false>(const BatchHeader*, const PowRow<float>*);
 template __global__ void k_short_scalar<32, 4>(const BatchHeader*, const PowRow<float>*);
 template __global__ void k_short_scalar<24, 4>(const BatchHeader*, const PowRow<float>*);
 template __global__ void k_short_scalar<24, 5>(const BatchHeader*, const PowRow<float>*);
 template __global__ void k_short_scalar<16, 6>(const BatchHeader*, const PowRow<float>*);
+template __global__ void k_short_pipe<32, 3>(const BatchHeader*, const PowRow<float>*);
+template __global__ void k_short_pipe<24, 4>(const BatchHeader*, const PowRow<float>*);
+template __global__ void k_short_pipe<16, 4>(const BatchHeader*, const PowRow<float>*);
 template __global__ void k_short_packed<12, 4>(const BatchHeader*, const PowRow<float>*);
 template __global__ void k_short_packed<16, 3>(const BatchHeader*, const PowRow<float>*);
 
@@ -102,12 +140,17 @@ void launch_prep32(const BatchHeader* H, const PhredTables* T, int grid, cudaStr
     k_prep32<<<grid, 256, 0, s>>>(H, T);
 }
 
+void launch_prep32_first(const BatchHeader* H, const PhredTables* T, int grid, cudaStream_t s) {
+    k_prep32_first<<<grid, 256, 0, s>>>(H, T);
+}
+
 void launch_forward32_long(const BatchHeader* H, const void* pow, int grid, cudaStream_t s) {
     k_forward<float, kNLong32, false><<<grid, kCtaThreads, 0, s>>>(H, static_cast<const PowRow<float>*>(pow));
 }
 
 // Short-pair kernel variants (ids used by the runtime's tuner):
-//   scalar id 0: N 32, 4 CTAs/SM   1: N 24, 4   2: N 24, 5   3: N 16, 6
+//   scalar id 0: N 32, 4 CTAs/SM   1: N 24, 4   2: N 24, 5   3: N 16, 6   (lean)
+//             4: N 32, 3            5: N 24, 4   6: N 16, 4                 (pipelined)
 //   packed id 0: N 12, 4 CTAs/SM   1: N 16, 3
 template <typename K>
 static int occ_of(K kern) {
@@ -124,6 +167,9 @@ void launch_short_scalar(int id, const BatchHeader* H, const void* pow, int grid
     case 1: k_short_scalar<24, 4><<<grid, kShortThreads, 0, s>>>(H, p); break;
     case 2: k_short_scalar<24, 5><<<grid, kShortThreads, 0, s>>>(H, p); break;
     case 3: k_short_scalar<16, 6><<<grid, kShortThreads, 0, s>>>(H, p); break;
+    case 4: k_short_pipe<32, 3><<<grid, kShortThreads, 0, s>>>(H, p); break;
+    case 5: k_short_pipe<24, 4><<<grid, kShortThreads, 0, s>>>(H, p); break;
+    case 6: k_short_pipe<16, 4><<<grid, kShortThreads, 0, s>>>(H, p); break;
     default: k_short_scalar<32, 4><<<grid, kShortThreads, 0, s>>>(H, p); break;
     }
 }
@@ -139,6 +185,9 @@ int occupancy_short_scalar(int id) {
     case 1: return occ_of(k_short_scalar<24, 4>);
     case 2: return occ_of(k_short_scalar<24, 5>);
     case 3: return occ_of(k_short_scalar<16, 6>);
+    case 4: return occ_of(k_short_pipe<32, 3>);
+    case 5: return occ_of(k_short_pipe<24, 4>);
+    case 6: return occ_of(k_short_pipe<16, 4>);
     default: return occ_of(k_short_scalar<32, 4>);
     }
 }

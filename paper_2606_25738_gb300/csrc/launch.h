@@ -12,6 +12,7 @@ struct PhredTables;
 // FP32 unit
 void launch_reset(const BatchHeader* H, int grid, cudaStream_t s);
 void launch_prep32(const BatchHeader* H, const PhredTables* T, int grid, cudaStream_t s);
+void launch_prep32_first(const BatchHeader* H, const PhredTables* T, int grid, cudaStream_t s);
 void launch_forward32_long(const BatchHeader* H, const void* pow, int grid, cudaStream_t s);
 // Short-pair kernels by variant id (see kShortScalar / kShortPacked).
 void launch_short_scalar(int id, const BatchHeader* H, const void* pow, int grid, cudaStream_t s);
@@ -35,9 +36,11 @@ int occupancy_forward64();
 constexpr int kN64 = 8;       // columns per lane of the FP64 kernels
 constexpr int kNLong32 = 32;  // columns per lane of FP32 multi-warp pairs
 // FP32 short-pair kernel variants: columns per lane of scalar teams / packed teams.
-constexpr int kNumScalar = 4;
-constexpr int kShortScalarN[kNumScalar] = {32, 24, 24, 16};
+constexpr int kNumScalar = 7;
+constexpr int kShortScalarN[kNumScalar] = {32, 24, 24, 16, 32, 24, 16};
+// scalar ids whose kernel is the pipelined engine (Rec32J records)
+constexpr bool kShortScalarPipe[kNumScalar] = {false, false, false, false, true, true, true};
 constexpr int kNumPacked = 2;
-constexpr int kShortPackedN[kNumPacked] = {12, 16};  // columns per lane of the FP64 kernels
+constexpr int kShortPackedN[kNumPacked] = {12, 16};
 
 }  // namespace phmm

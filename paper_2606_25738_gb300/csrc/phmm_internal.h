@@ -31,6 +31,18 @@ struct alignas(16) Rec64 {
     double pm, px, a, b, mi, g, gm;
     uint64_t meta;
 };
+// FP32 record of the pipelined engine, which carries J_i = I_i / T_MI_i instead of I_i,
+// so that Eq. 2's insertion update becomes J_ij = M_{i-1,j} + h_i J_{i-1,j} (one FMA) and
+// the factor T_MI_{i-1} of the I term of the match update moves into the coefficients
+// (mi_0 := 1 for the first row of a read):
+//   pm = (1 - e_i)(1 - g_i) mi_{i-1},  px = (e_i / 3)(1 - g_i) mi_{i-1}
+//   a  = T_MM_i / ((1 - g_i) mi_{i-1}),  b = T_MD_{i-1} / mi_{i-1}
+//   h  = g_i mi_{i-1} / mi_i,  g = g_i,  mi = T_MI_i
+// so that M_ij = P' (a M' + J' + b D-hat'), with the primes on row i-1, column j-1.
+struct alignas(16) Rec32J {
+    float pm, px, a, b, h, g, mi;
+    uint32_t meta;
+};
 
 constexpr uint32_t META_CODE_MASK = 0x7u;
 constexpr int META_GCP_SHIFT = 8;
@@ -139,7 +151,7 @@ struct PowRow {
 //   q[x] = 10^(-x/10)      om[x] = 1 - q[x]      q3[x] = q[x] / 3      inv[x] = 1 / om[x]
 // ------------------------------------------------------------------------------------
 struct PhredTables {
-    double q[kPhredTab], om[kPhredTab], q3[kPhredTab], inv[kPhredTab];
+    double q[kPhredTab], om[kPhredTab], q3[kPhredTab], inv[kPhredTab], iq[kPhredTab];  // iq = 1 / q
 };
 
 // Everything a batch's kernels read, in one device-resident header (so a captured CUDA
@@ -154,6 +166,7 @@ struct BatchHeader {
     // derived
     PairDesc *desc;
     Rec32 *rec32;
+    Rec32J *rec32j;  // pipelined-engine records (nullptr when no kernel of the plan uses them)
     Rec64 *rec64;
     // plan
     const WarpItem *witems;   // FP32: scalar teams; FP64: all teams

@@ -340,6 +340,7 @@ void build_phred_tables(PhredTables& T) {
         T.om[x] = 1.0 - v;
         T.q3[x] = v / 3.0;
         T.inv[x] = 1.0 / (1.0 - v);  // inf for x = 0 (g = 1): flagged as degenerate
+        T.iq[x] = std::pow(10.0, (double)q / 10.0);
     }
 }
 
@@ -380,7 +381,7 @@ void build_pow_table(int N, std::vector<PowRow<T>>& out) {
 // ------------------------------------------------------------------------------------
 struct Slot {
     DevBuf in_bases, in_bq, in_iq, in_dq, in_gq, in_hap, in_roff, in_hoff, in_pr, in_ph;
-    DevBuf desc, rec32, rec64, teams, witems, witems2, cpairs, citems, parts, out, oflags, rescue;
+    DevBuf desc, rec32, rec32j, rec64, teams, witems, witems2, cpairs, citems, parts, out, oflags, rescue;
     DevBuf small;  // counters[8], status[1], dropgrow[2]
     DevBuf bnd;    // strip boundaries of the batch
     DevBuf rbnd;   // rescue / launch-per-pair boundary scratch
@@ -453,7 +454,7 @@ int pow_index(int N) { return N == 12 ? 0 : N == 16 ? 1 : N == 20 ? 2 : N == 24 
 
 DevBuf* arena_bufs(Slot& S, int i) {
     DevBuf* d[] = {&S.in_bases, &S.in_bq, &S.in_iq, &S.in_dq, &S.in_gq, &S.in_hap, &S.in_roff, &S.in_hoff,
-                   &S.in_pr, &S.in_ph, &S.desc, &S.rec32, &S.rec64, &S.teams, &S.witems, &S.witems2,
+                   &S.in_pr, &S.in_ph, &S.desc, &S.rec32, &S.rec32j, &S.rec64, &S.teams, &S.witems, &S.witems2,
                    &S.cpairs, &S.citems, &S.parts, &S.out, &S.oflags, &S.rescue, &S.bnd, &S.rbnd};
     return i < (int)(sizeof(d) / sizeof(d[0])) ? d[i] : nullptr;
 }
@@ -491,6 +492,7 @@ int launch_sequence(phmm_ctx* ctx, Slot& S, int scal_id, int pack_id, bool recor
         CK(rec(S.ev_res1));
     } else {
         launch_prep32(H, T, grid_pre, s);
+        launch_prep32_first(H, T, grid_pre, s);
         CK(rec(S.ev_fwd0));
         // fork: multi-warp pairs and packed teams on two more branches, scalar teams here
         CK(cudaEventRecord(S.ev_fork, s));
@@ -521,7 +523,7 @@ int launch_sequence(phmm_ctx* ctx, Slot& S, int scal_id, int pack_id, bool recor
 
 int kernels_per_launch(int prec, int NP) {
     const int packed = NP > 0 ? 1 : 0;
-    return prec == PHMM_PREC_FP64 ? 4 : prec == PHMM_PREC_FP32_RESCUE ? 7 + packed : 5 + packed;
+    return prec == PHMM_PREC_FP64 ? 4 : prec == PHMM_PREC_FP32_RESCUE ? 8 + packed : 6 + packed;
 }
 
 uint64_t u64(const void* p) { return (uint64_t)(uintptr_t)p; }
@@ -565,11 +567,14 @@ std::vector<std::pair<int, int>> fp32_candidates(const phmm_config& cfg) {
     const int v = cfg.kernel_variant, n = cfg.cols_per_lane;
     for (int si = 0; si < kNumScalar; ++si)
         for (int pi = -1; pi < kNumPacked; ++pi) {
-            if (v == 2 && pi >= 0) continue;
+            const bool scal_only = v >= 2;
+            if (scal_only && pi >= 0) continue;
             if (v == 1 && pi < 0) continue;
-            if ((n == 24 || n == 32 || n == 16) && v == 2 && kShortScalarN[si] != n) continue;
-            if ((n == 24 || n == 32) && v != 2 && kShortScalarN[si] != n) continue;
-            if ((n == 12 || n == 16) && v != 2 && (pi < 0 || kShortPackedN[pi] != n)) continue;
+            if (v == 3 && kShortScalarPipe[si]) continue;
+            if (v == 4 && !kShortScalarPipe[si]) continue;
+            if ((n == 24 || n == 32 || n == 16) && scal_only && kShortScalarN[si] != n) continue;
+            if ((n == 24 || n == 32) && !scal_only && kShortScalarN[si] != n) continue;
+            if ((n == 12 || n == 16) && !scal_only && (pi < 0 || kShortPackedN[pi] != n)) continue;
             c.push_back({si, pi});
         }
     return c;
@@ -627,12 +632,12 @@ int phmm_create(const phmm_config* cfg, phmm_ctx** out) {
     if (!cfg || !out) return PHMM_EINVAL;
     *out = nullptr;
     if (cfg->precision < 0 || cfg->precision > 2) return PHMM_EINVAL;
-    if (cfg->kernel_variant < 0 || cfg->kernel_variant > 2) return PHMM_EINVAL;
+    if (cfg->kernel_variant < 0 || cfg->kernel_variant > 4) return PHMM_EINVAL;
     {
         const int n = cfg->cols_per_lane;
         const bool okp = n == 12 || n == 16;  // packed widths
         const bool oks = n == 16 || n == 24 || n == 32;  // scalar widths
-        if (n != 0 && !(cfg->kernel_variant == 2 ? oks : (okp || oks))) return PHMM_EINVAL;
+        if (n != 0 && !(cfg->kernel_variant >= 2 ? oks : (okp || oks))) return PHMM_EINVAL;
     }
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || cfg->device < 0 || cfg->device >= ndev)
@@ -866,7 +871,7 @@ int phmm_submit_batch(phmm_ctx* ctx, const phmm_batch* b, uint64_t* ticket) {
     const uint64_t foot = (dev_in ? 0 : nbases * 5 + nhb + (nr + 1) * 8ull + (nh + 1) * 8ull + np * 8ull) +
                           (ctx->cfg.precision != PHMM_PREC_FP32_ONLY ? rb_bytes : 0) +
                           np * (sizeof(PairDesc) + sizeof(Partial) + 8 + 1 + 4) +
-                          (ctx->cfg.precision == PHMM_PREC_FP64 ? 0 : nbases * sizeof(Rec32)) +
+                          (ctx->cfg.precision == PHMM_PREC_FP64 ? 0 : nbases * (sizeof(Rec32) + sizeof(Rec32J))) +
                           (need64 ? nbases * sizeof(Rec64) : 0) +
                           P.teams.size() * sizeof(Team) + (P.witems.size() + P.witems2.size()) * sizeof(WarpItem) +
                           P.cpairs.size() * sizeof(CtaPair) + P.citems.size() * sizeof(CtaItem) +
@@ -913,7 +918,10 @@ int phmm_submit_batch(phmm_ctx* ctx, const phmm_batch* b, uint64_t* ticket) {
         hh.pair_read = (const uint32_t*)S->in_pr.p; hh.pair_hap = (const uint32_t*)S->in_ph.p;
     }
     CK(ensure(S->desc, np * sizeof(PairDesc)));
-    if (ctx->cfg.precision != PHMM_PREC_FP64) CK(ensure(S->rec32, nbases * sizeof(Rec32)));
+    if (ctx->cfg.precision != PHMM_PREC_FP64) {
+        CK(ensure(S->rec32, nbases * sizeof(Rec32)));
+        CK(ensure(S->rec32j, nbases * sizeof(Rec32J)));
+    }
     if (need64) CK(ensure(S->rec64, nbases * sizeof(Rec64)));
     CK(ensure(S->parts, (np + P.n_extra) * sizeof(Partial)));
     CK(ensure(S->bnd, P.bnd_words * 8ull));
@@ -932,6 +940,7 @@ int phmm_submit_batch(phmm_ctx* ctx, const phmm_batch* b, uint64_t* ticket) {
     hh.n_pairs = np;
     hh.desc = (PairDesc*)S->desc.p;
     hh.rec32 = (Rec32*)S->rec32.p;
+    hh.rec32j = ctx->cfg.precision != PHMM_PREC_FP64 ? (Rec32J*)S->rec32j.p : nullptr;
     hh.rec64 = (Rec64*)S->rec64.p;
     plan_header(*S, P, hh);
     hh.n_partials = np + P.n_extra;
@@ -1102,7 +1111,7 @@ int phmm_batch_footprint(phmm_ctx* ctx, const phmm_batch* b, uint64_t* bytes) {
     const uint64_t nbases = roff[nr], nhb = hoff[nh];
     const uint64_t seg = 32ull * (prec == PHMM_PREC_FP64 ? kN64 : kNLong32);
     uint64_t f = nbases * 5 + nhb + (nr + 1) * 8ull + (nh + 1) * 8ull + np * 8ull;
-    f += nbases * ((prec != PHMM_PREC_FP64 ? sizeof(Rec32) : 0) + (need64 ? sizeof(Rec64) : 0));
+    f += nbases * ((prec != PHMM_PREC_FP64 ? sizeof(Rec32) + sizeof(Rec32J) : 0) + (need64 ? sizeof(Rec64) : 0));
     f += (uint64_t)np * (sizeof(PairDesc) + sizeof(Partial) + 8 + 1 + 4 + sizeof(Team) + 2 * sizeof(WarpItem) +
                          sizeof(CtaPair) + sizeof(CtaItem));
     uint64_t lmax = 0;

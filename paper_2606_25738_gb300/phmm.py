@@ -19,6 +19,7 @@ PHMM_OK, PHMM_PENDING = 0, 1
 PHMM_EINVAL, PHMM_ENOMEM, PHMM_EBUSY, PHMM_ECUDA = -1, -2, -3, -4
 PHMM_ETIMEOUT, PHMM_ECANCELED, PHMM_ENOTFOUND = -5, -6, -7
 PREC = {"fp32": 0, "fp64": 1, "fp32_only": 2}
+VARIANTS = {"auto": 0, "packed": 1, "scalar": 2, "lean": 3, "pipe": 4}
 F_NO_GRAPH, F_LAUNCH_PER_PAIR, F_FORCE_RESCUE = 0x1, 0x2, 0x4
 PAIR_RESCUED, PAIR_RESCALED, PAIR_FP64, PAIR_ERROR = 0x1, 0x2, 0x4, 0x80
 PAIR_DANGER, PAIR_NONFINITE, PAIR_SMALL_SUM, PAIR_DEGENERATE = 0x8, 0x10, 0x20, 0x40
@@ -161,7 +162,7 @@ class Context:
                  variant: str = "auto"):
         cfg = Config(device, PREC[precision], mem_budget, max_inflight, flags,
                      ctypes.c_void_p(stream) if stream else None, cols_per_lane,
-                     {"auto": 0, "packed": 1, "scalar": 2}[variant])
+                     VARIANTS[variant])
         h = ctypes.c_void_p()
         rc = _lib.phmm_create(ctypes.byref(cfg), ctypes.byref(h))
         if rc != PHMM_OK:

@@ -67,7 +67,8 @@ def test_force_rescue_fp64_pass(phmm):
     assert np.max(np.abs(out - oracle.batch(b))) <= TOL64
 
 
-VARIANTS = [("packed", 12), ("packed", 16), ("scalar", 24), ("scalar", 32)]
+VARIANTS = [("packed", 12), ("packed", 16), ("lean", 24), ("lean", 32), ("pipe", 16), ("pipe", 24),
+            ("pipe", 32)]
 
 
 @pytest.mark.parametrize("variant,N", [("packed", 12), ("packed", 16)])
@@ -135,10 +136,11 @@ def _edge_batch(N=16):
     return W.from_strings(pairs)
 
 
-@pytest.mark.parametrize("prec,variant", [("fp32", "packed"), ("fp32", "scalar"), ("fp64", "auto")])
+@pytest.mark.parametrize("prec,variant", [("fp32", "packed"), ("fp32", "scalar"), ("fp32", "lean"),
+                                          ("fp32", "pipe"), ("fp64", "auto")])
 def test_edge_cases(phmm, prec, variant):
-    b = _edge_batch()
-    n = {"packed": 16, "scalar": 24}.get(variant, 0) if prec == "fp32" else 0
+    n = {"packed": 16, "scalar": 24, "lean": 32, "pipe": 32}.get(variant, 0) if prec == "fp32" else 0
+    b = _edge_batch(max(n, 16))
     with phmm.Context(precision=prec, cols_per_lane=n, variant=variant) as ctx:
         out, flags, rc, st = ctx.run(b)
     ref = oracle.batch(b)
@@ -157,7 +159,8 @@ def test_long_deletion_50bp(phmm):
     hap = "".join(rng.choice(list("ACGT"), size=2000))
     read = hap[100:700] + hap[750:1350]
     b = W.from_strings([(read, hap, 30, 45, 45, 10)])
-    for N, v in ((12, "packed"), (16, "packed"), (24, "scalar"), (32, "scalar")):
+    for N, v in ((12, "packed"), (16, "packed"), (24, "lean"), (32, "lean"), (16, "pipe"), (24, "pipe"),
+                 (32, "pipe")):
         with phmm.Context(precision="fp32", cols_per_lane=N, variant=v) as ctx:
             out, flags, rc, st = ctx.run(b)
         _check(out, flags, oracle.batch(b))
