@@ -1066,7 +1066,7 @@ __device__ SegOut team_run_pipe(const Rec32J* __restrict__ rec, int l, int lmax,
             const PowRow<float>* pr = pow_tab + min(gq, kMaxPhred);
 #pragma unroll
             for (int s = 0; s < 5; ++s) {
-                sp1[s] = __ldg(&pr->sp1[s]);
+                sp1[s] = lt >= (1 << s) ? __ldg(&pr->sp1[s]) : 0.f;
                 sp2[s] = __ldg(&pr->sp2[s]);
             }
             last1 = __ldg(&pr->last1);
@@ -1121,17 +1121,18 @@ __device__ SegOut team_run_pipe(const Rec32J* __restrict__ rec, int l, int lmax,
         // the deletion scan of row i and, independent of it, phase A of row i+1
         float nm = __shfl_up_sync(kFull, M[N - 1], 1);
         float nj = __shfl_up_sync(kFull, J[N - 1], 1);
+        float yp = __shfl_up_sync(kFull, yprev, 1);
         if (lt == 0) {
             nm = 0.f;
             nj = 0.f;
+            yp = 0.f;
         }
         float Z = y;
 #pragma unroll
         for (int s = 0; s < 5; ++s) {
             const int off = 1 << s;
             const float up = __shfl_up_sync(kFull, Z, off);
-            const float t = fmaf(up * sp1[s], sp2[s], Z);
-            Z = lt >= off ? t : Z;
+            Z = fmaf(up * sp1[s], sp2[s], Z);
         }
         {
             const float na = nxt.a, nh = nxt.h;
@@ -1143,8 +1144,8 @@ __device__ SegOut team_run_pipe(const Rec32J* __restrict__ rec, int l, int lmax,
             U[0] = fmaf(na, nm, nj);
             J[0] = fmaf(nh, J[0], M[0]);
         }
-        float Wd = __shfl_up_sync(kFull, Z, 1);
-        if (lt == 0) Wd = 0.f;
+        float zz = __shfl_up_sync(kFull, Z, 2);
+        if (lt < 2) zz = 0.f;
         if (until == 0) {
             // checkpoint: M holds row i, J and U row i+1 (linear in row i, so they take
             // the same power of two)
@@ -1167,8 +1168,8 @@ __device__ SegOut team_run_pipe(const Rec32J* __restrict__ rec, int l, int lmax,
                         J[c] = (J[c] * f1) * f2v;
                         U[c] = (U[c] * f1) * f2v;
                     }
-                    Wd = (Wd * f1) * f2v;
-                    yprev = (yprev * f1) * f2v;
+                    zz = (zz * f1) * f2v;
+                    yp = (yp * f1) * f2v;
                     nm = (nm * f1) * f2v;
                     flags |= PF_RESCALED;
                     E += sh;
@@ -1176,11 +1177,8 @@ __device__ SegOut team_run_pipe(const Rec32J* __restrict__ rec, int l, int lmax,
             }
         }
         --until;
-        const float Dlast = fmaf(Wd * last1, last2, yprev);
-        float nd = __shfl_up_sync(kFull, Dlast, 1);
-        if (lt == 0) nd = 0.f;
         ml = nm;
-        dt = nd;
+        dt = fmaf(zz * last1, last2, yp);
         gprev = rg;
         cur = nxt;
     }
