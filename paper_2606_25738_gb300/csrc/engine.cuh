@@ -397,6 +397,31 @@ __device__ __forceinline__ int checkpoint_interval(const uint32_t* dropgrow) {
     return max(1, min(r, 64));
 }
 
+// Range control of the pipelined FP32 engine.  Its match-update partial U = a M' + J' and
+// the term b D-hat' are up to 2^rbits times the row maximum (rbits from prep: a, b/(1-g)
+// and 1/T_MI of the previous row), and M can sit 2^rbits below J; so the rescale ceiling
+// leaves rbits + 16 bits of headroom, the danger level rises by rbits, and the checkpoint
+// interval R keeps the worst-case drift of the maximum within both budgets (J grows by at
+// most 1 + h per row).  ok = false: the range does not fit (the pairs go to the rescue).
+struct PipeRange {
+    int R, hi, target, danger;
+    bool ok;
+};
+__device__ __forceinline__ PipeRange pipe_range(const uint32_t* dropgrow) {
+    using NT = Num<float>;
+    const int rbits = (int)min(dropgrow[2], 200u);
+    PipeRange r;
+    r.hi = min(NT::kHi, 110 - rbits);
+    r.target = r.hi - 4;
+    r.danger = NT::kDanger + rbits;
+    r.ok = r.hi >= NT::kLo + 16 && r.danger <= NT::kLo - 32;
+    const uint32_t d = max(dropgrow[0], 1u), g = max(max(dropgrow[1], dropgrow[3]), 1u);
+    const int drop_budget = max(NT::kLo - r.danger, 1), grow_budget = max(126 - rbits - r.hi, 1);
+    const int r1 = (int)((uint64_t)drop_budget * 64u / d), r2 = (int)((uint64_t)grow_budget * 64u / g);
+    r.R = max(1, min(min(r1, r2), 64));
+    return r;
+}
+
 struct SegOut {
     double S;
     int E;
@@ -1026,10 +1051,10 @@ template <int N>
 __device__ SegOut team_run_pipe(const Rec32J* __restrict__ rec, int l, int lmax,
                                 const uint8_t* __restrict__ hap, int k, int col0, int lt,
                                 int tlast, int nsteps, const PowRow<float>* __restrict__ pow_tab,
-                                int R) {
+                                const PipeRange& rng) {
     using NT = Num<float>;
     static_assert(N <= 32, "match masks hold 32 columns");
-    uint32_t bmA = 0, bmC = 0, bmG = 0, bmT = 0, flags = 0, mflags = 0;
+    uint32_t bmA = 0, bmC = 0, bmG = 0, bmT = 0, flags = rng.ok ? 0u : PF_DEGEN, mflags = 0;
     const int nvalid = max(0, min(k - col0, N));
 #pragma unroll
     for (int c = 0; c < N; ++c) {
@@ -1044,7 +1069,7 @@ __device__ SegOut team_run_pipe(const Rec32J* __restrict__ rec, int l, int lmax,
         }
     }
     float M[N], J[N], U[N];
-    int E = 0;
+    int E = 120 - rng.target;  // see cinit
     float ml = 0.f, dt = 0.f, gprev = 0.f;
     float sp1[5], sp2[5], last1 = 0.f, last2 = 0.f;
     int gcp = -1;
@@ -1052,7 +1077,9 @@ __device__ SegOut team_run_pipe(const Rec32J* __restrict__ rec, int l, int lmax,
     out.S = 0.0;
     out.E = 0;
     out.flags = 0;
-    const float cinit = l > 0 && k > 0 ? (float)(0x1p120 / (double)k) : 0.f;
+    // Eq. 1's scale C = 2^120 taken as already rescaled to 2^target (E records the
+    // difference), so that row 1 and the partials U formed from it start in range
+    const float cinit = l > 0 && k > 0 ? (float)(ldexp(1.0, rng.target) / (double)k) : 0.f;
     const int l1 = max(l, 1) - 1;
     Rec32J cur = load_recj(rec);
     int until = 0;
@@ -1147,9 +1174,10 @@ __device__ SegOut team_run_pipe(const Rec32J* __restrict__ rec, int l, int lmax,
         float zz = __shfl_up_sync(kFull, Z, 2);
         if (lt < 2) zz = 0.f;
         if (until == 0) {
-            // checkpoint: M holds row i, J and U row i+1 (linear in row i, so they take
-            // the same power of two)
-            until = R;
+            // checkpoint: M holds row i, J and U row i+1 (linear in row i, so they take the
+            // same power of two); U was formed before this test, which the headroom of the
+            // range bounds covers
+            until = rng.R;
             float m = 0.f;
 #pragma unroll
             for (int c = 0; c < N; ++c) m = fmaxf(m, fmaxf(fabsf(M[c]), fabsf(J[c])));
@@ -1158,19 +1186,32 @@ __device__ SegOut team_run_pipe(const Rec32J* __restrict__ rec, int l, int lmax,
             if (e == INT_MAX) {
                 flags |= PF_NONFINITE;
             } else if (e != INT_MIN) {
-                if (e <= NT::kDanger) flags |= PF_DANGER;
-                if (e > NT::kHi || e <= NT::kLo) {
-                    const int sh = e - NT::kTarget;  // multiply by 2^-sh in two exact steps
-                    const float f1 = NT::pow2((-sh) / 2), f2v = NT::pow2(-sh - (-sh) / 2);
+                if (e <= rng.danger) flags |= PF_DANGER;
+                if (e > rng.hi || e <= NT::kLo) {
+                    const int sh = e - rng.target;  // multiply by 2^-sh
+                    if (sh >= -126 && sh <= 126) {
+                        const float f = NT::pow2(-sh);
 #pragma unroll
-                    for (int c = 0; c < N; ++c) {
-                        M[c] = (M[c] * f1) * f2v;
-                        J[c] = (J[c] * f1) * f2v;
-                        U[c] = (U[c] * f1) * f2v;
+                        for (int c = 0; c < N; ++c) {
+                            M[c] *= f;
+                            J[c] *= f;
+                            U[c] *= f;
+                        }
+                        nm *= f;
+                        zz *= f;
+                        yp *= f;
+                    } else {  // two exact steps
+                        const float f1 = NT::pow2((-sh) / 2), f2v = NT::pow2(-sh - (-sh) / 2);
+#pragma unroll
+                        for (int c = 0; c < N; ++c) {
+                            M[c] = (M[c] * f1) * f2v;
+                            J[c] = (J[c] * f1) * f2v;
+                            U[c] = (U[c] * f1) * f2v;
+                        }
+                        nm = (nm * f1) * f2v;
+                        zz = (zz * f1) * f2v;
+                        yp = (yp * f1) * f2v;
                     }
-                    zz = (zz * f1) * f2v;
-                    yp = (yp * f1) * f2v;
-                    nm = (nm * f1) * f2v;
                     flags |= PF_RESCALED;
                     E += sh;
                 }

@@ -69,7 +69,10 @@ __device__ __forceinline__ BaseQ base_inputs(const BatchHeader* __restrict__ H, 
     r.del = H->del_q[b];
     r.gcp = H->gcp_q[b];
     r.delp = b > 0 ? H->del_q[b - 1] : 0;
-    r.insp = b > 0 ? H->ins_q[b - 1] : 0;
+    // the batch's first base has no predecessor: take its own insertion quality (its
+    // record is a row 1, whose previous-row terms are never used; this keeps the prep's
+    // range statistics free of an artificial T_MI = 1)
+    r.insp = b > 0 ? H->ins_q[b - 1] : H->ins_q[b];
     r.bad = r.code < 0 || r.Q > kMaxPhred || r.ins > kMaxPhred || r.del > kMaxPhred ||
             r.gcp > kMaxPhred;
     r.code = r.code < 0 ? 4 : r.code;
@@ -538,7 +541,7 @@ k_short_scalar(const BatchHeader* __restrict__ H, const PowRow<float>* __restric
 template <int N, int MINB>
 __global__ void __launch_bounds__(kShortThreads, MINB)
 k_short_pipe(const BatchHeader* __restrict__ H, const PowRow<float>* __restrict__ pow) {
-    const int R = checkpoint_interval<float>(H->dropgrow);
+    const PipeRange rng = pipe_range(H->dropgrow);
     const uint32_t n_w = H->n_witems;
     const int lane = threadIdx.x & 31;
     for (;;) {
@@ -558,7 +561,7 @@ k_short_pipe(const BatchHeader* __restrict__ H, const PowRow<float>* __restrict_
             hap = H->hap_bases + d.hoff;
         }
         const int lmax = (int)__reduce_max_sync(kFull, (unsigned)l);
-        const SegOut o = team_run_pipe<N>(rec, l, lmax, hap, k, t.lt * N, t.lt, t.tlast, t.nsteps, pow, R);
+        const SegOut o = team_run_pipe<N>(rec, l, lmax, hap, k, t.lt * N, t.lt, t.tlast, t.nsteps, pow, rng);
         if (t.pair != kNoPair && t.lt == 0) write_part(H, t.pair, o);
     }
 }

@@ -20,6 +20,8 @@ __global__ void k_reset(const BatchHeader* __restrict__ H) {
             H->status[0] = 0u;
             H->dropgrow[0] = 0u;
             H->dropgrow[1] = 0u;
+            H->dropgrow[2] = 0u;
+            H->dropgrow[3] = 0u;
         }
     }
     const uint64_t n = H->n_bnd_words;
@@ -58,7 +60,7 @@ __global__ void __launch_bounds__(256) k_prep32(const BatchHeader* __restrict__ 
     stage_tables32(TG, T);
     const float2 *tq = T.tq, *tom = T.tom, *tq3 = T.tq3, *tinv = T.tinv;
     Rec32J* const rj = H->rec32j;
-    uint32_t dmax = 0, gmax = 0;
+    uint32_t dmax = 0, gmax = 0, jmax = 0, hmax = 0;
     const uint64_t n = H->n_read_bases;
     const uint32_t seed = H->seed;
     for (uint64_t b = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; b < n;
@@ -68,7 +70,15 @@ __global__ void __launch_bounds__(256) k_prep32(const BatchHeader* __restrict__ 
         float4* dst = reinterpret_cast<float4*>(H->rec32 + b);
         dst[0] = make_float4(r.pm, r.px, r.a, r.b);
         dst[1] = make_float4(r.mi, r.g, r.gm, __uint_as_float(r.meta));
-        if (rj) store_rec32j(rj + b, make_rec32j(x, tq, tom, tq3, tinv, T.tiq, seed, b, false));
+        if (rj) {
+            const Rec32J r2 = make_rec32j(x, tq, tom, tq3, tinv, T.tiq, seed, b, false);
+            store_rec32j(rj + b, r2);
+            // range of the pipelined engine's intermediates relative to the row maximum
+            const float om = fmaxf(1.0f - r2.g, 0x1p-60f);
+            const float big = fmaxf(fmaxf(fabsf(r2.a), fabsf(r2.b) / om), T.tiq[x.insp].x);
+            jmax = max(jmax, (uint32_t)fmaxf(ceilf(log2f(fmaxf(big, 1.0f))), 0.0f));
+            hmax = max(hmax, (uint32_t)ceilf(log2f(1.0f + fabsf(r2.h)) * 64.0f) + 1u);
+        }
         if (x.bad) atomicOr(H->status, ST_BAD_INPUT);
         const float qi = tq[x.ins].x, qd = tq[x.del].x, qg = tq[x.gcp].x;
         const float drop = -log2f(fminf(qi, qg));
@@ -77,6 +87,8 @@ __global__ void __launch_bounds__(256) k_prep32(const BatchHeader* __restrict__ 
         gmax = max(gmax, (uint32_t)ceilf(fmaxf(grow, 0.0f) * 64.0f) + 1u);
     }
     block_max2(dmax, gmax, H->dropgrow);
+    __syncthreads();
+    block_max2(jmax, hmax, H->dropgrow + 2);
     build_desc(H);
 }
 

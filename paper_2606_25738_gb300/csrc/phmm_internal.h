@@ -191,7 +191,9 @@ struct BatchHeader {
     uint32_t *counters;      // 8 words: [0] CTA items [1] warp items [2] rescue count
                              // [3] rescue items [4] packed warp items
     uint32_t *status;        // ST_* bits
-    uint32_t *dropgrow;      // [0] max drop bits * 64, [1] max grow bits * 64 (prep)
+    uint32_t *dropgrow;      // [0] max drop bits * 64, [1] max grow bits * 64 (prep);
+                             // pipelined-engine records: [2] range bits (ceil log2 of the
+                             // largest of a, b / (1 - g), 1 / mi_{i-1}), [3] J growth bits * 64
     uint32_t seed;
     uint32_t mode;           // 0 FP32+rescue, 1 FP64, 2 FP32 only
 };

@@ -382,7 +382,7 @@ void build_pow_table(int N, std::vector<PowRow<T>>& out) {
 struct Slot {
     DevBuf in_bases, in_bq, in_iq, in_dq, in_gq, in_hap, in_roff, in_hoff, in_pr, in_ph;
     DevBuf desc, rec32, rec32j, rec64, teams, witems, witems2, cpairs, citems, parts, out, oflags, rescue;
-    DevBuf small;  // counters[8], status[1], dropgrow[2]
+    DevBuf small;  // counters[8], status[1], dropgrow[4]
     DevBuf bnd;    // strip boundaries of the batch
     DevBuf rbnd;   // rescue / launch-per-pair boundary scratch
     DevBuf hdr;
@@ -956,7 +956,7 @@ int phmm_submit_batch(phmm_ctx* ctx, const phmm_batch* b, uint64_t* ticket) {
     hh.rescue_list = (uint32_t*)S->rescue.p;
     hh.counters = (uint32_t*)S->small.p;          // words 0..7
     hh.status = (uint32_t*)S->small.p + 8;        // word 8
-    hh.dropgrow = (uint32_t*)S->small.p + 9;      // words 9, 10
+    hh.dropgrow = (uint32_t*)S->small.p + 9;      // words 9 .. 12
     hh.seed = ctx->seed;
     hh.mode = (uint32_t)ctx->cfg.precision;
     CK(cudaMemcpyAsync(S->hdr.p, &hh, sizeof(hh), cudaMemcpyHostToDevice, cs));
@@ -989,6 +989,9 @@ int phmm_submit_batch(phmm_ctx* ctx, const phmm_batch* b, uint64_t* ticket) {
             CK(cudaStreamSynchronize(ts));
             float ms = 0.f;
             CK(cudaEventElapsedTime(&ms, S->ev_fwd0, S->ev_fwd1));
+            if (getenv("PHMM_DEBUG"))
+                fprintf(stderr, "phmm tuner: scalar %d (N %d%s) packed %d: forward %.3f ms\n", cd.first,
+                        kShortScalarN[cd.first], kShortScalarPipe[cd.first] ? " pipelined" : "", cd.second, ms);
             if (ms < best_ms) {
                 best_ms = ms;
                 bs = cd.first;

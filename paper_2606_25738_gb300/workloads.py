@@ -312,9 +312,25 @@ def serving_requests(n: int, seed: int = 0, **kw) -> list:
 def equal_length(n_pairs: int, length: int, seed: int = 0) -> dict:
     """Equal-length synthetic pairs (read length = haplotype length), the shape of the
     paper's scalability sweep (Section 4.3): random haplotype, read = haplotype with 1%
-    substitutions; quals U{10..40}, ins/del 45, gcp 10."""
-    return plain_pairs(n_pairs, seed=seed + 1000 * length, k_range=(length, length),
-                       l_range=(length, length), sub_rate=0.01, indel_rate=0.0)
+    substitutions; quals U{10..40}, ins/del 45, gcp 10.  Vectorised (one array draw per
+    field), so a million short pairs take seconds."""
+    rng = _rng(seed + 1000 * length, 6)
+    n, L = int(n_pairs), int(length)
+    hap = ACGT[rng.integers(0, 4, size=n * L)]
+    read = hap.copy()
+    m = rng.random(n * L) < 0.01
+    if m.any():
+        codes = np.searchsorted(ACGT, read[m])
+        read[m] = ACGT[(codes + rng.integers(1, 4, size=int(m.sum()))) % 4]
+    off = np.arange(n + 1, dtype=np.uint64) * np.uint64(L)
+    idx = np.arange(n, dtype=np.uint32)
+    return {
+        "read_bases": read, "read_off": off.copy(), "hap_bases": hap, "hap_off": off.copy(),
+        "pair_read": idx, "pair_hap": idx.copy(),
+        "base_q": rng.integers(10, 41, size=n * L).astype(np.uint8),
+        "ins_q": np.full(n * L, 45, np.uint8), "del_q": np.full(n * L, 45, np.uint8),
+        "gcp_q": np.full(n * L, 10, np.uint8),
+    }
 
 
 def subset(b: dict, pairs) -> dict:

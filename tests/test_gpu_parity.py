@@ -283,3 +283,42 @@ def test_launch_per_pair_wide(phmm):
     with phmm.Context(precision="fp64", flags=phmm.F_LAUNCH_PER_PAIR) as ctx:
         out, flags, rc, st = ctx.run(b)
     assert np.max(np.abs(out - oracle.batch(b))) <= TOL64
+
+
+@pytest.mark.parametrize("L", [32, 64, 128])
+def test_short_equal_length_no_spurious_rescue(phmm, L):
+    """Short equal-length pairs (the first lengths of the scalability sweep): the initial
+    scale 2^120 / k is largest here, and no FP32 kernel may overflow on it, so no pair
+    needs the rescue pass."""
+    b = W.equal_length(1500, L, seed=1)
+    ref = oracle.batch(b)
+    for v, N in (("pipe", 32), ("pipe", 16), ("lean", 32), ("packed", 12)):
+        with phmm.Context(precision="fp32", variant=v, cols_per_lane=N) as ctx:
+            out, flags, rc, st = ctx.run(b)
+        assert st["n_rescued"] == 0, (v, N, np.unique(flags, return_counts=True))
+        _check(out, flags, ref)
+
+
+def test_pipelined_engine_extreme_gap_qualities(phmm):
+    """The pipelined engine carries J = I / T_MI: insertion Phred 93 next to 1, gap
+    continuation 1-2 and mixed rows stress its range; every pair is within 1e-3 or
+    flagged and rescued (then within 1e-9)."""
+    rng = np.random.default_rng(5)
+    hap = "".join(rng.choice(list("ACGT"), size=900))
+    read = hap[100:400] + hap[410:700]
+    l = len(read)
+    alt = np.where(np.arange(l) % 2 == 0, 93, 1)
+    pairs = [
+        (read, hap, 30, 93, 93, 10),
+        (read, hap, 30, alt, 45, 10),
+        (read, hap, 30, 45, alt, 10),
+        (read, hap, 30, 45, 45, 1),
+        (read, hap, 30, 93, 0, 2),
+        (read, hap, 30, np.arange(l) % 94, 40, np.arange(l) % 20 + 1),
+        (read[:60], hap[:64], 30, 93, 93, 10),
+    ]
+    b = W.from_strings(pairs)
+    for N in (16, 24, 32):
+        with phmm.Context(precision="fp32", variant="pipe", cols_per_lane=N) as ctx:
+            out, flags, rc, st = ctx.run(b)
+        _check(out, flags, oracle.batch(b))
