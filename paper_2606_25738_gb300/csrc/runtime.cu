@@ -854,7 +854,13 @@ int phmm_submit_batch(phmm_ctx* ctx, const phmm_batch* b, uint64_t* ticket) {
                     }
                 }
                 P = std::move(best);
-                tune_now = cand.size() > 1 && cells >= kTuneMinCells;
+                // the candidates differ only in the short-pair kernels: tune when those
+                // hold a real share of the batch's cells
+                uint64_t short_cells = 0;
+                const uint64_t wmax = 32ull * 32ull;  // widest short team: 32 lanes x 32 columns
+                for (uint32_t p = 0; p < np; ++p)
+                    if (K[p] <= wmax) short_cells += (uint64_t)L[p] * K[p];
+                tune_now = cand.size() > 1 && short_cells >= kTuneMinCells && short_cells * 10 >= cells;
                 tune_sig = sig;
                 tune_cand = cand;
             }

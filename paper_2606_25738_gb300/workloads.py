@@ -218,32 +218,54 @@ def long_pairs(n_pairs: int = 64, seed: int = 0, k_range=(1000, 100000), read_fr
     return _pack(reads, quals, haps, idx, idx)
 
 
-def uneven_pairs(n_pairs: int = 1_000_000, seed: int = 0, len_range=(50, 20000)) -> dict:
+def uneven_pairs(n_pairs: int = 1_000_000, seed: int = 0, len_range=(50, 20000),
+                 chunk: int = 65536) -> dict:
     """Uneven-length batch: read and haplotype lengths each log-uniform in
     ``len_range``, drawn independently and swapped so that haplotype >= read; the read
     is copied from a random haplotype offset with the short-read error and quality model
-    (substitutions U[0.5%, 2%], 1% N, quals 85% U{30..41} / 15% U{2..29}, ins/del
-    U{40..45}, gcp 10)."""
+    (substitutions at a per-read rate U[0.5%, 2%], 1% N, quals 85% U{30..41} / 15%
+    U{2..29}, ins/del U{40..45}, gcp 10).  Vectorised over chunks of pairs, so the full
+    million pairs (about 1.1e9 read and 5.6e9 haplotype bases) take memory in proportion
+    to the output only."""
     rng = _rng(seed, 4)
     lo, hi = np.log(len_range[0]), np.log(len_range[1])
     a = np.rint(np.exp(rng.uniform(lo, hi, size=n_pairs))).astype(np.int64)
     c = np.rint(np.exp(rng.uniform(lo, hi, size=n_pairs))).astype(np.int64)
     ls, ks = np.minimum(a, c), np.maximum(a, c)
-    reads, quals, haps = [], [], []
-    for p in range(n_pairs):
-        l, k = int(ls[p]), int(ks[p])
-        hap = _random_bases(rng, k)
-        off = int(rng.integers(0, k - l + 1))
-        read = _substitute(rng, hap[off:off + l], float(rng.uniform(0.005, 0.02)))
-        read[rng.random(l) < 0.01] = ord("N")
-        hi_q = rng.random(l) < 0.85
-        bq = np.where(hi_q, rng.integers(30, 42, size=l), rng.integers(2, 30, size=l)).astype(np.uint8)
-        quals.append((bq, rng.integers(40, 46, size=l).astype(np.uint8),
-                      rng.integers(40, 46, size=l).astype(np.uint8), np.full(l, 10, np.uint8)))
-        reads.append(read)
-        haps.append(hap)
-    idx = np.arange(n_pairs)
-    return _pack(reads, quals, haps, idx, idx)
+    roff = np.zeros(n_pairs + 1, np.uint64)
+    hoff = np.zeros(n_pairs + 1, np.uint64)
+    roff[1:] = np.cumsum(ls)
+    hoff[1:] = np.cumsum(ks)
+    nb, nh = int(roff[-1]), int(hoff[-1])
+    hap = ACGT[rng.integers(0, 4, size=nh, dtype=np.uint8)]
+    read = np.empty(nb, np.uint8)
+    bq = np.empty(nb, np.uint8)
+    iq = np.empty(nb, np.uint8)
+    dq = np.empty(nb, np.uint8)
+    off = (rng.random(n_pairs) * (ks - ls + 1)).astype(np.int64)
+    rate = rng.uniform(0.005, 0.02, size=n_pairs)
+    for p0 in range(0, n_pairs, chunk):
+        p1 = min(n_pairs, p0 + chunk)
+        L = ls[p0:p1]
+        b0, b1 = int(roff[p0]), int(roff[p1])
+        n = b1 - b0
+        first = np.repeat(hoff[p0:p1].astype(np.int64) + off[p0:p1], L)
+        within = np.arange(n, dtype=np.int64) - np.repeat(roff[p0:p1].astype(np.int64) - b0, L)
+        r = hap[first + within]
+        m = rng.random(n) < np.repeat(rate[p0:p1], L)
+        if m.any():
+            codes = np.searchsorted(ACGT, r[m])
+            r[m] = ACGT[(codes + rng.integers(1, 4, size=int(m.sum()))) % 4]
+        r[rng.random(n) < 0.01] = ord("N")
+        read[b0:b1] = r
+        hq = rng.random(n) < 0.85
+        bq[b0:b1] = np.where(hq, rng.integers(30, 42, size=n), rng.integers(2, 30, size=n))
+        iq[b0:b1] = rng.integers(40, 46, size=n)
+        dq[b0:b1] = rng.integers(40, 46, size=n)
+    idx = np.arange(n_pairs, dtype=np.uint32)
+    return {"read_bases": read, "read_off": roff, "hap_bases": hap, "hap_off": hoff,
+            "pair_read": idx, "pair_hap": idx.copy(), "base_q": bq, "ins_q": iq, "del_q": dq,
+            "gcp_q": np.full(nb, 10, np.uint8)}
 
 
 def _short_read_quals(rng, n: int):
