@@ -331,7 +331,8 @@ def run_ours(args):
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                      "frac": achieved / peak_tflops, "traffic": traffic,
-                     "kernel": "k_forward (FP32)", "flop_per_cell": 12,
+                     "kernel": "FP32 forward branches (k_short_pipe short teams; k_forward multi-warp pairs)",
+                     "flop_per_cell": 12,
                      "peak_note": "2 x 128 FP32 lanes x %d SMs x %.0f MHz (max SM clock, MEASURED_PEAKS)" % (info["sms"], sm_max)},
         "cpu_baseline": {"value": cpu_v, "unit": "GCUPS", "cores": cores, "kind": "oracle",
                          "sample": sdesc},
@@ -364,7 +365,7 @@ def main():
                          "values only for profiling captures)")
     ap.add_argument("--lpp-pairs", type=int, default=4000,
                     help="pairs sampled for the FP64 launch-per-pair comparator")
-    ap.add_argument("--serve-rate", type=float, default=20.0, help="requests per second of the serving leg")
+    ap.add_argument("--serve-rate", type=float, default=12.0, help="requests per second of the serving leg")
     ap.add_argument("--serve-seconds", type=float, default=8.0, help="arrival window of the serving leg (0: skip)")
     ap.add_argument("--serve-pool", type=int, default=32, help="distinct region requests in the serving pool")
     args = ap.parse_args()
