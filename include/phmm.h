@@ -69,6 +69,12 @@ typedef enum {
 #define PHMM_F_LAUNCH_PER_PAIR 0x2u /* with PHMM_PREC_FP64: one kernel launch per pair
                                        (the plain FP64 comparator) */
 #define PHMM_F_FORCE_RESCUE 0x4u    /* flag every pair for the FP64 rescue pass (tests) */
+/* FP32 multi-warp pairs (k > 1024): force one kernel instead of the tuner's choice --
+ * the lean engine (16-warp CTAs), the pipelined engine with 32 columns per lane
+ * (12-warp CTAs) or with 24 columns per lane (16-warp CTAs).  At most one may be set. */
+#define PHMM_F_LONG_LEAN 0x10u
+#define PHMM_F_LONG_PIPE32 0x20u
+#define PHMM_F_LONG_PIPE24 0x40u
 
 typedef struct {
     int device;               /* CUDA device ordinal */

@@ -257,6 +257,9 @@ __device__ __forceinline__ int base_code(uint32_t c) {
 // Word = (payload32 << 32) | row tag; a row is complete when every word carries its tag.
 // ------------------------------------------------------------------------------------
 constexpr long long kSpinLimit = 1ll << 22;  // polls (with backoff) before giving up
+constexpr long long kSpinFast = 256;         // polls without backoff first: a neighbour
+                                             // segment is usually a few hundred cycles
+                                             // behind, far less than one sleep
 
 struct SmemLink {
     unsigned long long* in_ring;   // my inbound ring  [kRing][words]
@@ -315,7 +318,7 @@ __device__ bool link_send(const SmemLink& L, int row, T m, T i, T d, int e) {
     long long spins = 0;
     while (*L.next_cons < row - kRing) {
         if (++spins > kSpinLimit) { ok = false; break; }
-        __nanosleep(64);
+        if (spins > kSpinFast) __nanosleep(64);
     }
     uint32_t w[W];
     pack_vals<T>(m, i, d, e, w);
@@ -343,7 +346,7 @@ __device__ bool link_recv(const SmemLink& L, int row, T& m, T& i, T& d, int& e) 
         }
         if (all) break;
         if (++spins > kSpinLimit) { ok = false; break; }
-        __nanosleep(32);
+        if (spins > kSpinFast) __nanosleep(32);
     }
     unpack_vals<T>(w, m, i, d, e);
     *L.my_cons = row;
@@ -378,7 +381,7 @@ __device__ bool link_recv_g(const unsigned long long* base, int row, T& m, T& i,
         }
         if (all) break;
         if (++spins > kSpinLimit) { ok = false; break; }
-        __nanosleep(64);
+        if (spins > kSpinFast) __nanosleep(64);
     }
     unpack_vals<T>(w, m, i, d, e);
     return ok;
@@ -1220,6 +1223,236 @@ __device__ SegOut team_run_pipe(const Rec32J* __restrict__ rec, int l, int lmax,
         --until;
         ml = nm;
         dt = fmaf(zz * last1, last2, yp);
+        gprev = rg;
+        cur = nxt;
+    }
+    return out;
+}
+
+// ------------------------------------------------------------------------------------
+// Pipelined FP32 engine for one warp segment of a multi-warp pair (32 N columns, all 32
+// lanes; rows 1..l).  The row work is team_run_pipe's; the segment exchange is
+// seg_run<LINKED>'s: after the scan and phase A of row i, lane 0 takes the left segment's
+// (M, J, D-hat, E) of its last column for row i (shared-memory ring, or the global
+// boundary of the previous strip), the checkpoint keeps E >= E_left, the left values are
+// brought into this segment's scale, and lane 31 hands this segment's last column on.
+// The segment carry enters lane t's previous column with the power g^(N t - 1).
+// ------------------------------------------------------------------------------------
+template <int N>
+__device__ SegOut seg_link_pipe(const Rec32J* __restrict__ rec, int l, const uint8_t* __restrict__ hap,
+                                int k, int col0, int lane, const PowRow<float>* __restrict__ pow_tab,
+                                const PipeRange& rng, const SmemLink& link, uint32_t* __restrict__ status) {
+    using NT = Num<float>;
+    static_assert(N <= 32, "match masks hold 32 columns");
+    uint32_t bmA = 0, bmC = 0, bmG = 0, bmT = 0, flags = rng.ok ? 0u : PF_DEGEN, mflags = 0;
+    const int nvalid = max(0, min(k - col0, N));
+    const bool has_left = link.has_left, has_right = link.has_right;
+#pragma unroll
+    for (int c = 0; c < N; ++c) {
+        if (c < nvalid) {
+            const int code = base_code(hap[col0 + c]);
+            const uint32_t bit = 1u << c;
+            if (code < 0) flags |= PF_BAD;
+            if (code == 0 || code == 4) bmA |= bit;
+            if (code == 1 || code == 4) bmC |= bit;
+            if (code == 2 || code == 4) bmG |= bit;
+            if (code == 3 || code == 4) bmT |= bit;
+        }
+    }
+    float M[N], J[N], U[N];
+    int E = 120 - rng.target;  // see team_run_pipe's cinit
+    float ml = 0.f, dt = 0.f, gprev = 0.f;
+    float sp1[5], sp2[5], last1 = 0.f, last2 = 0.f, qa1 = 0.f, qa2 = 0.f, qb1 = 0.f, qb2 = 0.f;
+    int gcp = -1;
+    SegOut out;
+    out.S = 0.0;
+    out.E = 0;
+    out.flags = 0;
+    const float cinit = l > 0 && k > 0 ? (float)(ldexp(1.0, rng.target) / (double)k) : 0.f;
+    const int l1 = max(l, 1) - 1;
+    Rec32J cur = load_recj(rec);
+    int until = 0;
+    for (int i = 1; i <= l; ++i) {
+        Rec32J nxt = cur;
+        if (i < l) nxt = load_recj(rec + min(i, l1));
+        const uint32_t meta = cur.meta;
+        mflags |= meta;
+        const int gq = (int)((meta >> META_GCP_SHIFT) & 0xffu);
+        if (gq != gcp) {
+            const PowRow<float>* pr = pow_tab + min(gq, kMaxPhred);
+#pragma unroll
+            for (int s = 0; s < 5; ++s) {
+                sp1[s] = lane >= (1 << s) ? __ldg(&pr->sp1[s]) : 0.f;
+                sp2[s] = __ldg(&pr->sp2[s]);
+            }
+            last1 = __ldg(&pr->last1);
+            last2 = __ldg(&pr->last2);
+            qa1 = __ldg(&pr->lq1[lane]);      // g^(N lane - 1) (lane 0: unused)
+            qa2 = __ldg(&pr->lq2[lane]);
+            qb1 = __ldg(&pr->lq1[lane + 1]);  // g^(N (lane + 1) - 1): this lane's last column
+            qb2 = __ldg(&pr->lq2[lane + 1]);
+            gcp = gq;
+        }
+        const int code = (int)(meta & META_CODE_MASK);
+        const uint32_t mask = code == 0 ? bmA : code == 1 ? bmC : code == 2 ? bmG
+                            : code == 3 ? bmT : 0xffffffffu;
+        const float pim = cur.pm, pix = cur.px, rg = cur.g;
+        float y = 0.f, yprev = 0.f;
+        // phase B
+        if (i == 1) {
+#pragma unroll
+            for (int c = 0; c < N; ++c) {
+                M[c] = (((mask >> c) & 1u) ? pim : pix) * cinit;
+                J[c] = 0.f;
+                if (c == N - 1) yprev = y;
+                y = fmaf(rg, y, M[c]);
+            }
+        } else {
+            const float rb = cur.b;
+#pragma unroll
+            for (int c = 0; c < N; ++c) {
+                const float u = fmaf(rb, dt, U[c]);
+                dt = fmaf(gprev, dt, ml);
+                ml = M[c];
+                const float mn = (((mask >> c) & 1u) ? pim : pix) * u;
+                M[c] = mn;
+                if (c == N - 1) yprev = y;
+                y = fmaf(rg, y, mn);
+            }
+        }
+        // Eq. 4 on the last row (I = T_MI J); all lanes of the warp run the same pair
+        if (i == l) {
+            const double rmi = (double)cur.mi;
+            double s = 0.0;
+#pragma unroll
+            for (int c = 0; c < N; ++c)
+                if (c < nvalid) s += (double)M[c] + rmi * (double)J[c];
+            s = team_sum<double>(s, lane, 31, 5);
+            uint32_t f = flags;
+            if (mflags & META_BAD) f |= PF_BAD;
+            if (mflags & META_DEGEN) f |= PF_DEGEN;
+            f = team_or(f, lane, 31, 5);
+            out.S = s;
+            out.E = E;
+            out.flags = f;
+        }
+        // deletion scan of row i, phase A of row i+1 (all but lane 0's first partial)
+        float nm = __shfl_up_sync(kFull, M[N - 1], 1);
+        float nj = __shfl_up_sync(kFull, J[N - 1], 1);
+        float yp = __shfl_up_sync(kFull, yprev, 1);
+        float jl = J[N - 1];  // this segment's last J of row i (sent right)
+        float Z = y;
+#pragma unroll
+        for (int s = 0; s < 5; ++s) {
+            const float up = __shfl_up_sync(kFull, Z, 1 << s);
+            Z = fmaf(up * sp1[s], sp2[s], Z);
+        }
+        const float na = nxt.a, nh = nxt.h;
+        {
+#pragma unroll
+            for (int c = N - 1; c >= 1; --c) {
+                U[c] = fmaf(na, M[c - 1], J[c - 1]);
+                J[c] = fmaf(nh, J[c], M[c]);
+            }
+            U[0] = fmaf(na, nm, nj);  // lane 0: replaced from the left segment below
+            J[0] = fmaf(nh, J[0], M[0]);
+        }
+        float zz = __shfl_up_sync(kFull, Z, 2);
+        float Wd = __shfl_up_sync(kFull, Z, 1);
+        if (lane < 2) zz = 0.f;
+        if (lane == 0) {
+            Wd = 0.f;
+            yp = 0.f;
+        }
+        // the left segment's last column of row i: lane 0 waits for it, then the whole
+        // (converged) warp takes it
+        float lM = 0.f, lJ = 0.f, lD = 0.f;
+        int e_in = INT_MIN;
+        if (has_left && lane == 0) {
+            const bool ok = link.in_g ? link_recv_g<float>(link.in_g, i, lM, lJ, lD, e_in)
+                                      : link_recv<float>(link, i, lM, lJ, lD, e_in);
+            if (!ok) {
+                flags |= PF_TIMEOUT;
+                atomicOr(status, ST_TIMEOUT);
+            }
+        }
+        __syncwarp();
+        lM = __shfl_sync(kFull, lM, 0);
+        lJ = __shfl_sync(kFull, lJ, 0);
+        lD = __shfl_sync(kFull, lD, 0);
+        const int Eleft = __shfl_sync(kFull, e_in, 0);
+        // checkpoint (same rows in every segment of the pair): power-of-two rescaling,
+        // with E >= E_left so that left values only ever scale down
+        int Enew = E;
+        if (until == 0) {
+            until = rng.R;
+            float m = 0.f;
+#pragma unroll
+            for (int c = 0; c < N; ++c) m = fmaxf(m, fmaxf(fabsf(M[c]), fabsf(J[c])));
+            m = team_max<float>(m, lane, 31, 5);
+            const int e = NT::expo(m);
+            int desired = E;
+            if (e == INT_MAX) {
+                if (i <= l) flags |= PF_NONFINITE;
+            } else if (e == INT_MIN) {
+                // nothing representable here: follow the left neighbour's scale
+                if (has_left) desired = INT_MIN;
+            } else if (e > rng.hi || e <= NT::kLo) {
+                desired = E + (e - rng.target);
+            }
+            Enew = desired;
+            bool forced = false;
+            if (has_left && Eleft > Enew) {
+                Enew = Eleft;
+                forced = true;
+            }
+            if (Enew == INT_MIN) Enew = E;
+            if (!forced && e != INT_MIN && e <= rng.danger) flags |= PF_DANGER;
+        }
+        --until;
+        if (Enew != E) {
+            const int sdn = E - Enew;
+#pragma unroll
+            for (int c = 0; c < N; ++c) {
+                M[c] = scale2(M[c], sdn);
+                J[c] = scale2(J[c], sdn);
+                U[c] = scale2(U[c], sdn);
+            }
+            nm = scale2(nm, sdn);
+            yp = scale2(yp, sdn);
+            zz = scale2(zz, sdn);
+            Wd = scale2(Wd, sdn);
+            yprev = scale2(yprev, sdn);
+            jl = scale2(jl, sdn);
+            flags |= PF_RESCALED;
+            E = Enew;
+        }
+        // left values into this segment's scale (E >= E_left here; no left: zeros stay zero)
+        const int dsh = has_left ? Eleft - E : 0;
+        lM = scale2(lM, dsh);
+        lJ = scale2(lJ, dsh);
+        lD = scale2(lD, dsh);
+        const float Wseg = fmaf(rg, lD, lM);  // D-hat at the segment's first column
+        // D-hat at the column before this lane: the left lanes' part plus the carry
+        float nd = fmaf(zz * last1, last2, yp);
+        nd = fmaf(Wseg * qa1, qa2, nd);
+        if (lane == 0) {
+            nd = lD;
+            nm = lM;
+            U[0] = fmaf(na, lM, lJ);
+        }
+        if (has_right && lane == 31) {
+            // D-hat at the segment's last column
+            const float dl = fmaf(Wseg * qb1, qb2, fmaf(Wd * last1, last2, yprev));
+            if (link.out_g) {
+                link_send_g<float>(link.out_g, i, M[N - 1], jl, dl, E);
+            } else if (!link_send<float>(link, i, M[N - 1], jl, dl, E)) {
+                flags |= PF_TIMEOUT;
+                atomicOr(status, ST_TIMEOUT);
+            }
+        }
+        ml = nm;
+        dt = nd;
         gprev = rg;
         cur = nxt;
     }

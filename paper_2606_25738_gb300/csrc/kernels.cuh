@@ -475,6 +475,71 @@ k_forward(const BatchHeader* __restrict__ H, const PowRow<T>* __restrict__ pow) 
     }
 }
 
+// Multi-warp FP32 pairs on the pipelined engine: one warp per 32 N-column segment, up to
+// kCtaWarpsPipe warps per CTA item (register budget of the engine), strips beyond that.
+template <int N>
+__device__ __forceinline__ void cta_strip_run_pipe(const BatchHeader* __restrict__ H,
+                                                   const PowRow<float>* __restrict__ pow, uint32_t pair,
+                                                   int w0, int W, uint32_t col0, unsigned long long* bnd_in,
+                                                   unsigned long long* bnd_out, CtaShared<float>& sh,
+                                                   const PipeRange& rng) {
+    constexpr int KW = Num<float>::kWords;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int s = warp - w0;
+    if (s < 0 || s >= W) return;
+    const PairDesc d = H->desc[pair];
+    SmemLink L;
+    L.in_ring = sh.ring + warp * kRing * KW;
+    L.out_ring = sh.ring + min(warp + 1, kCtaWarps - 1) * kRing * KW;
+    L.my_cons = sh.cons + warp;
+    L.next_cons = sh.cons + warp + 1;
+    L.in_g = (s == 0) ? bnd_in : nullptr;
+    L.out_g = (s == W - 1) ? bnd_out : nullptr;
+    L.has_left = s > 0 || bnd_in != nullptr;
+    L.has_right = s < W - 1 || bnd_out != nullptr;
+    const int c0 = (int)col0 + (s * 32 + lane) * N;
+    const SegOut o = seg_link_pipe<N>(H->rec32j + d.roff, (int)d.l, H->hap_bases + d.hoff, (int)d.k, c0,
+                                      lane, pow, rng, L, H->status);
+    if (lane == 0) sh.out[warp] = o;
+}
+
+constexpr int kCtaThreadsPipe = kCtaWarpsPipe * 32;
+
+// CW warps per CTA: 12 at N = 32 (168 registers), 16 at N = 24 (128 registers).
+template <int N, int CW>
+__global__ void __launch_bounds__(CW * 32, 1)
+k_forward_pipe(const BatchHeader* __restrict__ H, const PowRow<float>* __restrict__ pow) {
+    __shared__ CtaShared<float> sh;
+    const PipeRange rng = pipe_range(H->dropgrow);
+    const uint32_t n_c = H->n_citems;
+    for (;;) {
+        if (threadIdx.x == 0) sh.item = atomicAdd(&H->counters[0], 1u);
+        cta_clear<float>(sh);
+        __syncthreads();
+        const uint32_t it = sh.item;
+        if (it >= n_c) break;
+        const CtaItem ci = H->citems[it];
+        const int warp = threadIdx.x >> 5;
+        for (uint32_t q = 0; q < ci.n; ++q) {
+            const CtaPair cp = H->cpairs[ci.first + q];
+            if (warp >= cp.w0 && warp < cp.w0 + cp.W)
+                cta_strip_run_pipe<N>(H, pow, cp.pair, cp.w0, cp.W, cp.col0,
+                                      cp.bnd_in == kNoBnd ? nullptr : H->bnd + cp.bnd_in,
+                                      cp.bnd_out == kNoBnd ? nullptr : H->bnd + cp.bnd_out, sh, rng);
+        }
+        __syncthreads();
+        if ((threadIdx.x & 31) == 0) {
+            for (uint32_t q = 0; q < ci.n; ++q) {
+                const CtaPair cp = H->cpairs[ci.first + q];
+                if (warp == cp.w0)
+                    write_strip_part(H, cp.pair, cp.strip, cp.nstrip, cp.extra_base,
+                                     cta_combine<float>(sh, cp.w0, cp.W));
+            }
+        }
+        __syncthreads();
+    }
+}
+
 // Team lookup of a warp item: this lane's team (first lane, size, pairs) and the scan
 // steps of the widest team.
 struct TeamOf {

@@ -109,6 +109,8 @@ __global__ void __launch_bounds__(256) k_prep32_first(const BatchHeader* __restr
 }
 
 template __global__ void k_forward<float, kNLong32, false>(const BatchHeader*, const PowRow<float>*);
+template __global__ void k_forward_pipe<32, kCtaWarpsPipe>(const BatchHeader*, const PowRow<float>*);
+template __global__ void k_forward_pipe<24, kCtaWarps>(const BatchHeader*, const PowRow<float>*);
 template __global__ void k_short_scalar<32, 4>(const BatchHeader*, const PowRow<float>*);
 template __global__ void k_short_scalar<24, 4>(const BatchHeader*, const PowRow<float>*);
 template __global__ void k_short_scalar<24, 5>(const BatchHeader*, const PowRow<float>*);
@@ -158,6 +160,12 @@ void launch_prep32_first(const BatchHeader* H, const PhredTables* T, int grid, c
 
 void launch_forward32_long(const BatchHeader* H, const void* pow, int grid, cudaStream_t s) {
     k_forward<float, kNLong32, false><<<grid, kCtaThreads, 0, s>>>(H, static_cast<const PowRow<float>*>(pow));
+}
+
+void launch_forward32_long_pipe(int kind, const BatchHeader* H, const void* pow, int grid, cudaStream_t s) {
+    const PowRow<float>* p = static_cast<const PowRow<float>*>(pow);
+    if (kind == 2) k_forward_pipe<24, kCtaWarps><<<grid, kCtaWarps * 32, 0, s>>>(H, p);
+    else k_forward_pipe<32, kCtaWarpsPipe><<<grid, kCtaWarpsPipe * 32, 0, s>>>(H, p);
 }
 
 // Short-pair kernel variants (ids used by the runtime's tuner):
@@ -211,6 +219,15 @@ int occupancy_short_packed(int id) {
 int occupancy_forward32_long() {
     int b = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_forward<float, kNLong32, false>, kCtaThreads, 0);
+    return b > 0 ? b : 1;
+}
+
+int occupancy_forward32_long_pipe(int kind) {
+    int b = 0;
+    if (kind == 2)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_forward_pipe<24, kCtaWarps>, kCtaWarps * 32, 0);
+    else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_forward_pipe<32, kCtaWarpsPipe>, kCtaWarpsPipe * 32, 0);
     return b > 0 ? b : 1;
 }
 

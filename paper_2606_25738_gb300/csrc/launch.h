@@ -14,11 +14,18 @@ void launch_reset(const BatchHeader* H, int grid, cudaStream_t s);
 void launch_prep32(const BatchHeader* H, const PhredTables* T, int grid, cudaStream_t s);
 void launch_prep32_first(const BatchHeader* H, const PhredTables* T, int grid, cudaStream_t s);
 void launch_forward32_long(const BatchHeader* H, const void* pow, int grid, cudaStream_t s);
+// FP32 multi-warp kernels: kind 0 = lean engine (N 32, 16-warp CTAs), 1 = pipelined
+// (N 32, 12-warp CTAs), 2 = pipelined (N 24, 16-warp CTAs).
+constexpr int kNumLong = 3;
+constexpr int kLongN[kNumLong] = {32, 32, 24};
+constexpr int kLongCW[kNumLong] = {16, 12, 16};
+void launch_forward32_long_pipe(int kind, const BatchHeader* H, const void* pow, int grid, cudaStream_t s);
 // Short-pair kernels by variant id (see kShortScalar / kShortPacked).
 void launch_short_scalar(int id, const BatchHeader* H, const void* pow, int grid, cudaStream_t s);
 void launch_short_packed(int id, const BatchHeader* H, const void* pow, int grid, cudaStream_t s);
 void launch_finalize32(const BatchHeader* H, int grid, cudaStream_t s);
 int occupancy_forward32_long();          // resident CTAs per SM
+int occupancy_forward32_long_pipe(int kind);
 int occupancy_short_scalar(int id);
 int occupancy_short_packed(int id);
 // pow_row: a device pointer to one PowRow<float>

@@ -95,6 +95,7 @@ constexpr uint32_t ST_NONFINITE = 1u << 3;
 //   lists pairs with their warp ranges.
 // ----------------------------------------------------------------------------------
 constexpr int kCtaWarps = 16;
+constexpr int kCtaWarpsPipe = 12;  // FP32 multi-warp CTAs of the pipelined engine (register budget)
 constexpr int kCtaThreads = kCtaWarps * 32;
 constexpr int kRing = 8;  // rows buffered between two warp segments
 
@@ -143,6 +144,8 @@ struct PowRow {
     T lp1[32], lp2[32]; // g^(N * t), t = 0..31: segment carry into lane t
     T last1, last2;     // g^(N - 1): from a lane's first column to its last
     T pad1, pad2;
+    T lq1[33], lq2[33]; // g^(N * t - 1), t = 1..32 (t = 0 unused): segment carry to the
+                        // column before lane t (t = 32: the segment's last column)
 };
 
 // Phred tables staged in shared memory by the prep kernels.  Each value is a pair

@@ -8,6 +8,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <limits>
+#include <array>
 #include <map>
 #include <mutex>
 #include <thread>
@@ -94,6 +95,7 @@ struct Plan {
     int pack_id = -1;
     uint64_t bnd_words = 0;   // strip boundary buffer (tagged words)
     uint32_t n_extra = 0;     // extra partial slots (strips 1.. of wide pairs)
+    int long_kind = 0;        // FP32 multi-warp kernel (launch.h: kLongN / kLongCW)
 };
 
 // Cost model constants (issue slots): per lane and cell of a row, and per lane and row
@@ -178,9 +180,10 @@ static void pack_teams(std::vector<Team>& run_teams, std::vector<uint32_t>& run_
 // Work plan.  Short pairs: a scalar team of G = ceil(k / Ns) lanes (k <= 32 Ns); with
 // NP > 0 (FP32), two pairs of the same read with k <= 32 NP share a packed team of
 // ceil(max k / NP) lanes (x / y halves).  Long pairs: W = ceil(k / (32 Nl)) warps of one
-// CTA, packed best-fit into 16-warp CTAs.  Items are ordered longest first.
+// CTA, packed best-fit into CTAs of CW warps (wider pairs: strips of CW warps).  Items
+// are ordered longest first.
 void make_plan(const uint32_t* l, const uint32_t* k, const uint32_t* pr, uint32_t n, int Ns, int NP,
-               int Nl, Plan& P, int kw = 4) {
+               int Nl, Plan& P, int kw = 4, int CW = kCtaWarps) {
     P = Plan();
     P.N = Ns;
     P.NP = NP;
@@ -257,19 +260,19 @@ void make_plan(const uint32_t* l, const uint32_t* k, const uint32_t* pr, uint32_
     std::vector<uint32_t> fit;
     for (uint32_t p : lo) {
         const uint32_t Wt = W_of(p);
-        if (Wt <= (uint32_t)kCtaWarps) {
+        if (Wt <= (uint32_t)CW) {
             fit.push_back(p);
             continue;
         }
-        const uint32_t S = (Wt + kCtaWarps - 1) / kCtaWarps;
+        const uint32_t S = (Wt + CW - 1) / CW;
         const uint32_t extra = n + P.n_extra;
         const uint64_t b0 = P.bnd_words;
         for (uint32_t stp = 0; stp < S; ++stp) {
-            const uint32_t W = std::min((uint32_t)kCtaWarps, Wt - stp * kCtaWarps);
+            const uint32_t W = std::min((uint32_t)CW, Wt - stp * CW);
             CtaPair cp = cpair(p, 0, W);
             cp.strip = (uint16_t)stp;
             cp.nstrip = S;
-            cp.col0 = stp * kCtaWarps * seg;
+            cp.col0 = stp * CW * seg;
             cp.extra_base = extra;
             cp.bnd_in = stp > 0 ? b0 + (uint64_t)(stp - 1) * l[p] * kw : kNoBnd;
             cp.bnd_out = stp + 1 < S ? b0 + (uint64_t)stp * l[p] * kw : kNoBnd;
@@ -281,14 +284,14 @@ void make_plan(const uint32_t* l, const uint32_t* k, const uint32_t* pr, uint32_
         }
         P.bnd_words += (uint64_t)(S - 1) * l[p] * kw;
         P.n_extra += S - 1;
-        P.cost += (double)l[p] * S * kCtaWarps * 32.0 * (Nl * kCellCost * 1.6 + kRowCost);
+        P.cost += (double)l[p] * S * CW * 32.0 * (Nl * kCellCost * 1.6 + kRowCost);
     }
     struct CBin {
         std::vector<CtaPair> pairs;
         uint32_t rem, lmax;
     };
     std::vector<CBin> cb;
-    std::vector<std::vector<uint32_t>> copen(kCtaWarps + 1);
+    std::vector<std::vector<uint32_t>> copen(CW + 1);
     size_t a = 0;
     while (a < fit.size()) {
         const uint32_t l0 = l[fit[a]];
@@ -299,7 +302,7 @@ void make_plan(const uint32_t* l, const uint32_t* k, const uint32_t* pr, uint32_
         for (size_t q = a; q < b2; ++q) {
             const uint32_t p = fit[q], W = W_of(p);
             int r = -1;
-            for (uint32_t c = W; c <= (uint32_t)kCtaWarps; ++c)
+            for (uint32_t c = W; c <= (uint32_t)CW; ++c)
                 if (!copen[c].empty()) {
                     r = (int)c;
                     break;
@@ -307,12 +310,12 @@ void make_plan(const uint32_t* l, const uint32_t* k, const uint32_t* pr, uint32_
             uint32_t bi;
             if (r < 0) {
                 bi = (uint32_t)cb.size();
-                cb.push_back({{}, (uint32_t)kCtaWarps, 0});
+                cb.push_back({{}, (uint32_t)CW, 0});
             } else {
                 bi = copen[r].back();
                 copen[r].pop_back();
             }
-            cb[bi].pairs.push_back(cpair(p, kCtaWarps - cb[bi].rem, W));
+            cb[bi].pairs.push_back(cpair(p, CW - cb[bi].rem, W));
             cb[bi].rem -= W;
             cb[bi].lmax = std::max(cb[bi].lmax, l[p]);
             if (cb[bi].rem > 0) copen[cb[bi].rem].push_back(bi);
@@ -323,7 +326,7 @@ void make_plan(const uint32_t* l, const uint32_t* k, const uint32_t* pr, uint32_
             it.n = (uint32_t)c.pairs.size();
             for (auto& cp : c.pairs) P.cpairs.push_back(cp);
             P.citems.push_back(it);
-            P.cost += (double)c.lmax * kCtaWarps * 32.0 * (Nl * kCellCost * 1.6 + kRowCost);
+            P.cost += (double)c.lmax * CW * 32.0 * (Nl * kCellCost * 1.6 + kRowCost);
         }
         a = b2;
     }
@@ -368,6 +371,8 @@ void build_pow_table(int N, std::vector<PowRow<T>>& out) {
         PowRow<T>& r = out[x];
         for (int s = 0; s < 5; ++s) split_pow<T>(gq, (double)N * (double)(1 << s), r.sp1[s], r.sp2[s]);
         for (int t = 0; t < 32; ++t) split_pow<T>(gq, (double)N * t, r.lp1[t], r.lp2[t]);
+        r.lq1[0] = r.lq2[0] = (T)0;
+        for (int t = 1; t <= 32; ++t) split_pow<T>(gq, (double)N * t - 1.0, r.lq1[t], r.lq2[t]);
         split_pow<T>(gq, (double)(N - 1), r.last1, r.last2);
         r.pad1 = (T)std::pow(10.0, -(double)gq / 10.0);
         r.pad2 = (T)0;
@@ -427,8 +432,8 @@ struct phmm_ctx {
     DevBuf scan_row;                        // scan test: one PowRow<float> (global memory)
     DevBuf pow32[5];                        // N = 12, 16, 20, 24 (packed short), 32 (long)
     DevBuf pow64;
-    int occ_packed[kNumPacked] = {}, occ_scalar[kNumScalar] = {}, occ_long = 1, occ64 = 1;
-    std::map<uint64_t, std::pair<int, int>> tuned;  // batch signature -> (scalar id, packed id)
+    int occ_packed[kNumPacked] = {}, occ_scalar[kNumScalar] = {}, occ_longk[kNumLong] = {1, 1, 1}, occ64 = 1;
+    std::map<uint64_t, std::array<int, 3>> tuned;  // batch signature -> (scalar id, packed id, long kind)
     uint64_t inflight_foot = 0;             // sum of pending slots' footprints
     bool dead = false;
     uint32_t seed = 0x5eed1234u;
@@ -471,7 +476,7 @@ void release_arenas(Slot& S) {
     S.plan_valid = false;
 }
 
-int launch_sequence(phmm_ctx* ctx, Slot& S, int scal_id, int pack_id, bool record_events) {
+int launch_sequence(phmm_ctx* ctx, Slot& S, int scal_id, int pack_id, int long_kind, bool record_events) {
     cudaStream_t s = S.sm;
     const BatchHeader* H = static_cast<const BatchHeader*>(S.hdr.p);
     const PhredTables* T = static_cast<const PhredTables*>(ctx->tables.p);
@@ -498,7 +503,11 @@ int launch_sequence(phmm_ctx* ctx, Slot& S, int scal_id, int pack_id, bool recor
         CK(cudaEventRecord(S.ev_fork, s));
         CK(cudaStreamWaitEvent(S.sb2, S.ev_fork, 0));
         CK(cudaStreamWaitEvent(S.sb3, S.ev_fork, 0));
-        launch_forward32_long(H, ctx->pow32[pow_index(kNLong32)].p, ctx->sms * ctx->occ_long, S.sb2);
+        const void* lpow = ctx->pow32[pow_index(kLongN[long_kind])].p;
+        if (long_kind > 0)
+            launch_forward32_long_pipe(long_kind, H, lpow, ctx->sms * ctx->occ_longk[long_kind], S.sb2);
+        else
+            launch_forward32_long(H, lpow, ctx->sms * ctx->occ_longk[0], S.sb2);
         CK(cudaEventRecord(S.ev_join, S.sb2));
         if (pack_id >= 0)
             launch_short_packed(pack_id, H, ctx->pow32[pow_index(kShortPackedN[pack_id])].p,
@@ -581,10 +590,26 @@ std::vector<std::pair<int, int>> fp32_candidates(const phmm_config& cfg) {
 }
 
 void make_plan_id(const uint32_t* l, const uint32_t* k, const uint32_t* pr, uint32_t n, int scal_id,
-                  int pack_id, Plan& P) {
-    make_plan(l, k, pr, n, kShortScalarN[scal_id], pack_id >= 0 ? kShortPackedN[pack_id] : 0, kNLong32, P);
+                  int pack_id, int long_kind, Plan& P) {
+    make_plan(l, k, pr, n, kShortScalarN[scal_id], pack_id >= 0 ? kShortPackedN[pack_id] : 0,
+              kLongN[long_kind], P, 4, kLongCW[long_kind]);
     P.scal_id = scal_id;
     P.pack_id = pack_id;
+    P.long_kind = long_kind;
+}
+
+// FP32 multi-warp kernels the configuration allows (the lean variant keeps the lean
+// engine), and the one used without measurement.
+std::vector<int> long_kinds_of(const phmm_config& cfg) {
+    if (cfg.flags & PHMM_F_LONG_LEAN) return {0};
+    if (cfg.flags & PHMM_F_LONG_PIPE32) return {1};
+    if (cfg.flags & PHMM_F_LONG_PIPE24) return {2};
+    if (cfg.kernel_variant == 3) return {0};
+    return {0, 1};  // kind 2 only when forced: measured slower than kind 1 everywhere
+}
+int default_long_kind(const phmm_config& cfg) {
+    const std::vector<int> k = long_kinds_of(cfg);
+    return k.size() == 1 ? k[0] : 1;
 }
 
 // Coarse shape of a batch for the tuner cache: pair count, mean read and haplotype
@@ -634,6 +659,10 @@ int phmm_create(const phmm_config* cfg, phmm_ctx** out) {
     if (cfg->precision < 0 || cfg->precision > 2) return PHMM_EINVAL;
     if (cfg->kernel_variant < 0 || cfg->kernel_variant > 4) return PHMM_EINVAL;
     {
+        const unsigned lk = cfg->flags & (PHMM_F_LONG_LEAN | PHMM_F_LONG_PIPE32 | PHMM_F_LONG_PIPE24);
+        if (lk & (lk - 1)) return PHMM_EINVAL;  // more than one forced multi-warp kernel
+    }
+    {
         const int n = cfg->cols_per_lane;
         const bool okp = n == 12 || n == 16;  // packed widths
         const bool oks = n == 16 || n == 24 || n == 32;  // scalar widths
@@ -681,11 +710,13 @@ int phmm_create(const phmm_config* cfg, phmm_ctx** out) {
     }
     for (int q = 0; q < kNumPacked; ++q) ctx->occ_packed[q] = occupancy_short_packed(q);
     for (int q = 0; q < kNumScalar; ++q) ctx->occ_scalar[q] = occupancy_short_scalar(q);
-    ctx->occ_long = occupancy_forward32_long();
+    ctx->occ_longk[0] = occupancy_forward32_long();
+    ctx->occ_longk[1] = occupancy_forward32_long_pipe(1);
+    ctx->occ_longk[2] = occupancy_forward32_long_pipe(2);
     if (getenv("PHMM_DEBUG"))
         fprintf(stderr, "phmm: sms %d occupancy packed %d %d scalar %d %d %d %d long %d fp64 %d\n",
                 ctx->sms, ctx->occ_packed[0], ctx->occ_packed[1], ctx->occ_scalar[0], ctx->occ_scalar[1],
-                ctx->occ_scalar[2], ctx->occ_scalar[3], ctx->occ_long, ctx->occ64);
+                ctx->occ_scalar[2], ctx->occ_scalar[3], ctx->occ_longk[1], ctx->occ64);
     {
         std::vector<PowRow<double>> v;
         build_pow_table<double>(kN64, v);
@@ -827,7 +858,7 @@ int phmm_submit_batch(phmm_ctx* ctx, const phmm_batch* b, uint64_t* ticket) {
     hsh ^= np;
     Plan& P = S->plan;
     int N = kN64;
-    bool tune_now = false;
+    bool tune_short = false, tune_long = false;
     uint64_t tune_sig = 0;
     std::vector<std::pair<int, int>> tune_cand;
     const bool reuse = S->plan_valid && S->plan_hash == hsh && S->plan_np == np;
@@ -839,14 +870,14 @@ int phmm_submit_batch(phmm_ctx* ctx, const phmm_batch* b, uint64_t* ticket) {
             const uint64_t sig = batch_signature(L.data(), K.data(), pr, np, ctx->cfg);
             auto hit = ctx->tuned.find(sig);
             if (hit != ctx->tuned.end()) {
-                make_plan_id(L.data(), K.data(), pr, np, hit->second.first, hit->second.second, P);
+                make_plan_id(L.data(), K.data(), pr, np, hit->second[0], hit->second[1], hit->second[2], P);
             } else {
                 // cost-model choice first; measured tuning (below) may replace it
                 Plan best;
                 bool have = false;
                 for (auto& cd : cand) {
                     Plan c;
-                    make_plan_id(L.data(), K.data(), pr, np, cd.first, cd.second, c);
+                    make_plan_id(L.data(), K.data(), pr, np, cd.first, cd.second, default_long_kind(ctx->cfg), c);
                     const double cost = c.cost + (double)c.n_too_long * 1e18;
                     if (!have || cost < best.cost + (double)best.n_too_long * 1e18) {
                         best = std::move(c);
@@ -854,13 +885,16 @@ int phmm_submit_batch(phmm_ctx* ctx, const phmm_batch* b, uint64_t* ticket) {
                     }
                 }
                 P = std::move(best);
-                // the candidates differ only in the short-pair kernels: tune when those
-                // hold a real share of the batch's cells
+                // measure the short-pair kernels when short pairs, and the multi-warp
+                // kernels when multi-warp pairs, hold a real share of the batch's cells
                 uint64_t short_cells = 0;
                 const uint64_t wmax = 32ull * 32ull;  // widest short team: 32 lanes x 32 columns
                 for (uint32_t p = 0; p < np; ++p)
                     if (K[p] <= wmax) short_cells += (uint64_t)L[p] * K[p];
-                tune_now = cand.size() > 1 && short_cells >= kTuneMinCells && short_cells * 10 >= cells;
+                const uint64_t long_cells = cells - short_cells;
+                tune_short = cand.size() > 1 && short_cells >= kTuneMinCells && short_cells * 10 >= cells;
+                tune_long = long_kinds_of(ctx->cfg).size() > 1 && long_cells >= kTuneMinCells &&
+                            long_cells * 10 >= cells;
                 tune_sig = sig;
                 tune_cand = cand;
             }
@@ -973,15 +1007,28 @@ int phmm_submit_batch(phmm_ctx* ctx, const phmm_batch* b, uint64_t* ticket) {
     CK(cudaEventRecord(S->ev_user, ctx->stream));
     CK(cudaStreamWaitEvent(S->sm, S->ev_user, 0));
     CK(cudaStreamWaitEvent(S->sm, S->ev_copy, 0));
-    if (tune_now) {
-        // Measured tuning: run the FP32 pipeline once per candidate kernel pair on this
-        // batch (events around the forward kernels), keep the fastest for this shape.
+    if (tune_short || tune_long) {
+        // Measured tuning: run the FP32 pipeline once per candidate on this batch (events
+        // around the forward kernels), keep the fastest for this shape: first the short-
+        // pair kernels, then the multi-warp kernel.
         cudaStream_t ts = S->sm;
         double best_ms = 1e30;
-        int bs = P.scal_id, bp = P.pack_id;
-        for (auto& cd : tune_cand) {
+        int bs = P.scal_id, bp = P.pack_id, bl = P.long_kind;
+        std::vector<std::array<int, 3>> runs;
+        if (tune_short)
+            for (auto& cd : tune_cand) runs.push_back({cd.first, cd.second, bl});
+        const size_t n_short = runs.size();
+        if (tune_long)
+            for (int lk : long_kinds_of(ctx->cfg)) runs.push_back({-1, -1, lk});
+        for (size_t ri = 0; ri < runs.size(); ++ri) {
+            if (ri == n_short) best_ms = 1e30;  // second stage: the short choice is fixed
+            std::array<int, 3> cd = runs[ri];
+            if (cd[0] < 0) {
+                cd[0] = bs;
+                cd[1] = bp;
+            }
             Plan c;
-            make_plan_id(L.data(), K.data(), pr, np, cd.first, cd.second, c);
+            make_plan_id(L.data(), K.data(), pr, np, cd[0], cd[1], cd[2], c);
             if (c.n_too_long) continue;
             CK(upload_plan(*S, c, cs));
             CK(ensure(S->parts, (np + c.n_extra) * sizeof(Partial)));
@@ -990,22 +1037,23 @@ int phmm_submit_batch(phmm_ctx* ctx, const phmm_batch* b, uint64_t* ticket) {
             plan_header(*S, c, hh);
             CK(cudaMemcpyAsync(S->hdr.p, &hh, sizeof(hh), cudaMemcpyHostToDevice, cs));
             CK(cudaStreamSynchronize(cs));
-            const int rc = launch_sequence(ctx, *S, c.scal_id, c.pack_id, false);
+            const int rc = launch_sequence(ctx, *S, c.scal_id, c.pack_id, c.long_kind, false);
             if (rc != PHMM_OK) return rc;
             CK(cudaStreamSynchronize(ts));
             float ms = 0.f;
             CK(cudaEventElapsedTime(&ms, S->ev_fwd0, S->ev_fwd1));
             if (getenv("PHMM_DEBUG"))
-                fprintf(stderr, "phmm tuner: scalar %d (N %d%s) packed %d: forward %.3f ms\n", cd.first,
-                        kShortScalarN[cd.first], kShortScalarPipe[cd.first] ? " pipelined" : "", cd.second, ms);
+                fprintf(stderr, "phmm tuner: scalar %d (N %d%s) packed %d long %d: forward %.3f ms\n", cd[0],
+                        kShortScalarN[cd[0]], kShortScalarPipe[cd[0]] ? " pipelined" : "", cd[1], cd[2], ms);
             if (ms < best_ms) {
                 best_ms = ms;
-                bs = cd.first;
-                bp = cd.second;
+                bs = cd[0];
+                bp = cd[1];
+                bl = cd[2];
             }
         }
-        ctx->tuned[tune_sig] = {bs, bp};
-        make_plan_id(L.data(), K.data(), pr, np, bs, bp, P);
+        ctx->tuned[tune_sig] = {bs, bp, bl};
+        make_plan_id(L.data(), K.data(), pr, np, bs, bp, bl, P);
         CK(upload_plan(*S, P, cs));
         CK(ensure(S->parts, (np + P.n_extra) * sizeof(Partial)));
         CK(ensure(S->bnd, P.bnd_words * 8ull));
@@ -1035,13 +1083,13 @@ int phmm_submit_batch(phmm_ctx* ctx, const phmm_batch* b, uint64_t* ticket) {
             CK(cudaGetLastError());
             launches = np + 3;
         } else if (use_graph) {
-            const int key = ctx->cfg.precision * 10000 + P.scal_id * 100 + (P.pack_id + 1);
+            const int key = P.long_kind * 100000 + ctx->cfg.precision * 10000 + P.scal_id * 100 + (P.pack_id + 1);
             if (!S->gexec || S->g_key != key) {
                 if (S->gexec) cudaGraphExecDestroy(S->gexec);
                 S->gexec = nullptr;
                 cudaGraph_t g = nullptr;
                 CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-                const int rc = launch_sequence(ctx, *S, P.scal_id, P.pack_id, true);
+                const int rc = launch_sequence(ctx, *S, P.scal_id, P.pack_id, P.long_kind, true);
                 cudaError_t e2 = cudaStreamEndCapture(s, &g);
                 if (rc != PHMM_OK || e2 != cudaSuccess) {
                     if (g) cudaGraphDestroy(g);
@@ -1056,7 +1104,7 @@ int phmm_submit_batch(phmm_ctx* ctx, const phmm_batch* b, uint64_t* ticket) {
             CK(cudaGraphLaunch(S->gexec, s));
             launches = (uint32_t)kernels_per_launch(ctx->cfg.precision, P.NP);
         } else {
-            const int rc = launch_sequence(ctx, *S, P.scal_id, P.pack_id, false);
+            const int rc = launch_sequence(ctx, *S, P.scal_id, P.pack_id, P.long_kind, false);
             if (rc != PHMM_OK) return rc;
             launches = (uint32_t)kernels_per_launch(ctx->cfg.precision, P.NP);
         }
@@ -1130,8 +1178,9 @@ int phmm_batch_footprint(phmm_ctx* ctx, const phmm_batch* b, uint64_t* bytes) {
         const uint64_t k = hoff[b->pair_hap[p] + 1] - hoff[b->pair_hap[p]];
         lmax = std::max(lmax, l);
         const uint64_t Wt = (k + seg - 1) / seg;
-        if (Wt > (uint64_t)kCtaWarps) {  // strips of a very wide pair
-            const uint64_t S = (Wt + kCtaWarps - 1) / kCtaWarps;
+        const uint64_t cw = prec == PHMM_PREC_FP64 ? (uint64_t)kCtaWarps : (uint64_t)kCtaWarpsPipe;
+        if (Wt > cw) {  // strips of a very wide pair
+            const uint64_t S = (Wt + cw - 1) / cw;
             f += (S - 1) * (l * (prec == PHMM_PREC_FP64 ? 8 : 4) * 8 + sizeof(Partial) + sizeof(CtaPair) + sizeof(CtaItem));
         }
     }

@@ -21,6 +21,7 @@ PHMM_ETIMEOUT, PHMM_ECANCELED, PHMM_ENOTFOUND = -5, -6, -7
 PREC = {"fp32": 0, "fp64": 1, "fp32_only": 2}
 VARIANTS = {"auto": 0, "packed": 1, "scalar": 2, "lean": 3, "pipe": 4}
 F_NO_GRAPH, F_LAUNCH_PER_PAIR, F_FORCE_RESCUE = 0x1, 0x2, 0x4
+F_LONG_LEAN, F_LONG_PIPE32, F_LONG_PIPE24 = 0x10, 0x20, 0x40
 PAIR_RESCUED, PAIR_RESCALED, PAIR_FP64, PAIR_ERROR = 0x1, 0x2, 0x4, 0x80
 PAIR_DANGER, PAIR_NONFINITE, PAIR_SMALL_SUM, PAIR_DEGENERATE = 0x8, 0x10, 0x20, 0x40
 

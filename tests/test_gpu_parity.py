@@ -93,12 +93,24 @@ def test_columns_per_lane(phmm, variant, N):
     _check(out, flags, oracle.batch(b))
 
 
+LONG_KINDS = ["lean", "pipe32", "pipe24"]
+
+
+def _long_flag(phmm, kind):
+    return {"lean": phmm.F_LONG_LEAN, "pipe32": phmm.F_LONG_PIPE32, "pipe24": phmm.F_LONG_PIPE24}[kind]
+
+
 @pytest.mark.parametrize("variant,N", VARIANTS)
-def test_fp32_path_without_rescue(phmm, variant, N):
-    """The FP32 engine alone (no FP64 rescue pass): packed short teams and multi-warp
-    pairs up to 16 warps x 1024 columns stay within 1e-3 and none is flagged for rescue."""
+@pytest.mark.parametrize("kind", LONG_KINDS)
+def test_fp32_path_without_rescue(phmm, variant, N, kind):
+    """The FP32 engines alone (no FP64 rescue pass): short teams and multi-warp pairs up to
+    16384 columns (every multi-warp kernel, strips included) stay within 1e-3 and none is
+    flagged for rescue."""
+    if variant == "lean" and kind != "lean":
+        pytest.skip("the lean variant keeps the lean multi-warp engine")
     b = W.plain_pairs(48, seed=12, k_range=(1, 16384), l_range=(1, 400), indel_rate=0.01)
-    with phmm.Context(precision="fp32_only", cols_per_lane=N, variant=variant) as ctx:
+    with phmm.Context(precision="fp32_only", cols_per_lane=N, variant=variant,
+                      flags=_long_flag(phmm, kind)) as ctx:
         out, flags, rc, st = ctx.run(b)
     assert st["n_long"] > 0
     assert np.all((flags & 0x78) == 0), flags[(flags & 0x78) != 0]
@@ -238,10 +250,11 @@ def _wide_batch(seed=30):
     return W.from_strings(pairs)
 
 
-def test_wide_pairs_fp32_strips(phmm):
+@pytest.mark.parametrize("kind", LONG_KINDS)
+def test_wide_pairs_fp32_strips(phmm, kind):
     """Concurrent strips (global row boundaries between CTAs), FP32 only."""
     b = _wide_batch()
-    with phmm.Context(precision="fp32_only") as ctx:
+    with phmm.Context(precision="fp32_only", flags=_long_flag(phmm, kind)) as ctx:
         out, flags, rc, st = ctx.run(b)
     assert st["n_long"] == 5
     assert np.all((flags & 0x78) == 0)
@@ -265,12 +278,13 @@ def test_wide_pairs_rescue_sequential_strips(phmm):
     assert np.max(np.abs(out - oracle.batch(b))) <= TOL64
 
 
-def test_long_reads_reduced(phmm):
+@pytest.mark.parametrize("kind", LONG_KINDS)
+def test_long_reads_reduced(phmm, kind):
     """Long-read-like pairs (reads 90-100% of haplotypes of 1k-20k bp, 5% substitutions,
     3% indels, quals 5-30): FP32 + rescue within 1e-3 including multi-warp and strip
     pairs; checkpoint rescaling must have happened."""
     b = W.long_pairs(10, seed=4, k_range=(1000, 20000))
-    with phmm.Context(precision="fp32") as ctx:
+    with phmm.Context(precision="fp32", flags=_long_flag(phmm, kind)) as ctx:
         out, flags, rc, st = ctx.run(b)
     ref = oracle.batch(b)
     assert np.all(ref < -300)  # far below what a fixed 2^120 scale could hold
