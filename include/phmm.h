@@ -96,7 +96,8 @@ typedef struct {
                                  teams; 2 = scalar teams only (lean or pipelined engine);
                                  3 = lean scalar engine only; 4 = pipelined scalar engine
                                  only (the next row's scan-independent work overlaps the
-                                 deletion scan) */
+                                 deletion scan); 5 = pipelined engine with each lane's two
+                                 column halves in packed FP32 pairs */
 } phmm_config;
 
 /*

@@ -1230,6 +1230,207 @@ __device__ SegOut team_run_pipe(const Rec32J* __restrict__ rec, int l, int lmax,
 }
 
 // ------------------------------------------------------------------------------------
+// team_run_pipe with each lane's columns split in two halves that advance side by side in
+// the two halves of float2 registers (packed FFMA2 / FMUL2): column q of the first half
+// and column N/2 + q of the second share an instruction.  Both halves run the D-hat chains
+// of phase B at once, each from its own carry: the first half's comes from the left lane
+// (as in team_run_pipe), the second half's is the first half's D-hat at its last column,
+// formed after the scan.  The lane's scan aggregate joins the two half chains with
+// g^(N/2).  Same results as team_run_pipe up to rounding order.
+// ------------------------------------------------------------------------------------
+template <int N>
+__device__ SegOut team_run_pipe2(const Rec32J* __restrict__ rec, int l, int lmax,
+                                 const uint8_t* __restrict__ hap, int k, int col0, int lt,
+                                 int tlast, int nsteps, const PowRow<float>* __restrict__ pow_tab,
+                                 const PipeRange& rng) {
+    using NT = Num<float>;
+    static_assert(N <= 32 && N % 2 == 0, "match masks hold 32 columns; two halves");
+    constexpr int H = N / 2;
+    uint32_t bmA = 0, bmC = 0, bmG = 0, bmT = 0, flags = rng.ok ? 0u : PF_DEGEN, mflags = 0;
+    const int nvalid = max(0, min(k - col0, N));
+#pragma unroll
+    for (int c = 0; c < N; ++c) {
+        if (c < nvalid) {
+            const int code = base_code(hap[col0 + c]);
+            const uint32_t bit = 1u << c;
+            if (code < 0) flags |= PF_BAD;
+            if (code == 0 || code == 4) bmA |= bit;
+            if (code == 1 || code == 4) bmC |= bit;
+            if (code == 2 || code == 4) bmG |= bit;
+            if (code == 3 || code == 4) bmT |= bit;
+        }
+    }
+    float2 M2[H], J2[H], U2[H];  // .x: column q, .y: column H + q of the lane
+    int E = 120 - rng.target;    // see team_run_pipe's cinit
+    float2 dt2 = make_float2(0.f, 0.f), ml2 = make_float2(0.f, 0.f);
+    float gprev = 0.f;
+    float sp1[5], sp2[5], last1 = 0.f, last2 = 0.f, hh1 = 0.f, hh2 = 0.f, hm1 = 0.f, hm2 = 0.f;
+    int gcp = -1;
+    SegOut out;
+    out.S = 0.0;
+    out.E = 0;
+    out.flags = 0;
+    const float cinit = l > 0 && k > 0 ? (float)(ldexp(1.0, rng.target) / (double)k) : 0.f;
+    const int l1 = max(l, 1) - 1;
+    Rec32J cur = load_recj(rec);
+    int until = 0;
+    for (int i = 1; i <= lmax; ++i) {
+        Rec32J nxt = cur;
+        if (i < lmax) nxt = load_recj(rec + min(i, l1));
+        const uint32_t meta = cur.meta;
+        mflags |= meta;
+        const int gq = (int)((meta >> META_GCP_SHIFT) & 0xffu);
+        if (gq != gcp) {
+            const PowRow<float>* pr = pow_tab + min(gq, kMaxPhred);
+#pragma unroll
+            for (int s = 0; s < 5; ++s) {
+                sp1[s] = lt >= (1 << s) ? __ldg(&pr->sp1[s]) : 0.f;
+                sp2[s] = __ldg(&pr->sp2[s]);
+            }
+            last1 = __ldg(&pr->last1);
+            last2 = __ldg(&pr->last2);
+            hh1 = __ldg(&pr->hh1);
+            hh2 = __ldg(&pr->hh2);
+            hm1 = __ldg(&pr->hm1);
+            hm2 = __ldg(&pr->hm2);
+            gcp = gq;
+        }
+        const int code = (int)(meta & META_CODE_MASK);
+        const uint32_t mask = code == 0 ? bmA : code == 1 ? bmC : code == 2 ? bmG
+                            : code == 3 ? bmT : 0xffffffffu;
+        const float pim = cur.pm, pix = cur.px, rg = cur.g;
+        const float2 rg2 = make_float2(rg, rg);
+        float2 y2 = make_float2(0.f, 0.f), yp2 = make_float2(0.f, 0.f);
+        // phase B (both halves at once)
+        if (i == 1) {
+#pragma unroll
+            for (int q = 0; q < H; ++q) {
+                const float2 mn = make_float2((((mask >> q) & 1u) ? pim : pix) * cinit,
+                                              (((mask >> (q + H)) & 1u) ? pim : pix) * cinit);
+                M2[q] = mn;
+                J2[q] = make_float2(0.f, 0.f);
+                if (q == H - 1) yp2 = y2;
+                y2 = __ffma2_rn(rg2, y2, mn);
+            }
+        } else {
+            const float2 rb2 = make_float2(cur.b, cur.b), gp2 = make_float2(gprev, gprev);
+#pragma unroll
+            for (int q = 0; q < H; ++q) {
+                const float2 u2 = __ffma2_rn(rb2, dt2, U2[q]);
+                dt2 = __ffma2_rn(gp2, dt2, ml2);
+                ml2 = M2[q];
+                const float2 p2 = make_float2(((mask >> q) & 1u) ? pim : pix,
+                                              ((mask >> (q + H)) & 1u) ? pim : pix);
+                const float2 mn = __fmul2_rn(p2, u2);
+                M2[q] = mn;
+                if (q == H - 1) yp2 = y2;
+                y2 = __ffma2_rn(rg2, y2, mn);
+            }
+        }
+        // Eq. 4 when a pair of this warp finishes (I = T_MI J on the last row)
+        if (__any_sync(kFull, i == l)) {
+            const double rmi = (double)cur.mi;
+            double s = 0.0;
+#pragma unroll
+            for (int q = 0; q < H; ++q) {
+                if (q < nvalid) s += (double)M2[q].x + rmi * (double)J2[q].x;
+                if (q + H < nvalid) s += (double)M2[q].y + rmi * (double)J2[q].y;
+            }
+            s = team_sum<double>(s, lt, tlast, nsteps);
+            uint32_t f = flags;
+            if (mflags & META_BAD) f |= PF_BAD;
+            if (mflags & META_DEGEN) f |= PF_DEGEN;
+            f = team_or(f, lt, tlast, nsteps);
+            if (i == l) {
+                out.S = s;
+                out.E = E;
+                out.flags = f;
+            }
+        }
+        // lane aggregates of the local (zero-carry) D-hat chain: one past the lane's last
+        // column (scan input) and at its last column (the right neighbour's carry)
+        const float zl = fmaf(y2.x * hh1, hh2, y2.y);
+        const float ypl = fmaf(y2.x * hm1, hm2, yp2.y);
+        float yA = yp2.x;  // first half, at its last column
+        float nm = __shfl_up_sync(kFull, M2[H - 1].y, 1);
+        float nj = __shfl_up_sync(kFull, J2[H - 1].y, 1);
+        float yp = __shfl_up_sync(kFull, ypl, 1);
+        if (lt == 0) {
+            nm = 0.f;
+            nj = 0.f;
+            yp = 0.f;
+        }
+        float Z = zl;
+#pragma unroll
+        for (int s = 0; s < 5; ++s) {
+            const float up = __shfl_up_sync(kFull, Z, 1 << s);
+            Z = fmaf(up * sp1[s], sp2[s], Z);
+        }
+        {
+            const float2 na2 = make_float2(nxt.a, nxt.a), nh2 = make_float2(nxt.h, nxt.h);
+            const float mal = M2[H - 1].x, jal = J2[H - 1].x;
+#pragma unroll
+            for (int q = H - 1; q >= 1; --q) {
+                U2[q] = __ffma2_rn(na2, M2[q - 1], J2[q - 1]);
+                J2[q] = __ffma2_rn(nh2, J2[q], M2[q]);
+            }
+            U2[0] = __ffma2_rn(na2, make_float2(nm, mal), make_float2(nj, jal));
+            J2[0] = __ffma2_rn(nh2, J2[0], M2[0]);
+        }
+        float zz = __shfl_up_sync(kFull, Z, 2);
+        if (lt < 2) zz = 0.f;
+        if (until == 0) {
+            until = rng.R;
+            float2 m2 = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int q = 0; q < H; ++q) {
+                m2.x = fmaxf(m2.x, fmaxf(fabsf(M2[q].x), fabsf(J2[q].x)));
+                m2.y = fmaxf(m2.y, fmaxf(fabsf(M2[q].y), fabsf(J2[q].y)));
+            }
+            const float m = team_max<float>(fmaxf(m2.x, m2.y), lt, tlast, nsteps);
+            const int e = NT::expo(m);
+            if (e == INT_MAX) {
+                flags |= PF_NONFINITE;
+            } else if (e != INT_MIN) {
+                if (e <= rng.danger) flags |= PF_DANGER;
+                if (e > rng.hi || e <= NT::kLo) {
+                    const int sh = e - rng.target;
+                    float f1 = 1.f, f2v;
+                    if (sh >= -126 && sh <= 126) {
+                        f2v = NT::pow2(-sh);
+                    } else {
+                        f1 = NT::pow2((-sh) / 2);
+                        f2v = NT::pow2(-sh - (-sh) / 2);
+                    }
+                    const float2 a2 = make_float2(f1, f1), b2 = make_float2(f2v, f2v);
+#pragma unroll
+                    for (int q = 0; q < H; ++q) {
+                        M2[q] = __fmul2_rn(__fmul2_rn(M2[q], a2), b2);
+                        J2[q] = __fmul2_rn(__fmul2_rn(J2[q], a2), b2);
+                        U2[q] = __fmul2_rn(__fmul2_rn(U2[q], a2), b2);
+                    }
+                    nm = (nm * f1) * f2v;
+                    zz = (zz * f1) * f2v;
+                    yp = (yp * f1) * f2v;
+                    yA = (yA * f1) * f2v;
+                    flags |= PF_RESCALED;
+                    E += sh;
+                }
+            }
+        }
+        --until;
+        const float ndA = fmaf(zz * last1, last2, yp);  // D-hat at the column before the lane
+        const float wl = fmaf(rg, ndA, nm);              // D-hat at the lane's first column
+        const float ndB = fmaf(wl * hm1, hm2, yA);       // D-hat at the first half's last column
+        dt2 = make_float2(ndA, ndB);
+        ml2 = make_float2(nm, M2[H - 1].x);
+        gprev = rg;
+        cur = nxt;
+    }
+    return out;
+}
+
+// ------------------------------------------------------------------------------------
 // Pipelined FP32 engine for one warp segment of a multi-warp pair (32 N columns, all 32
 // lanes; rows 1..l).  The row work is team_run_pipe's; the segment exchange is
 // seg_run<LINKED>'s: after the scan and phase A of row i, lane 0 takes the left segment's

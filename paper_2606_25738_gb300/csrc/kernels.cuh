@@ -631,6 +631,35 @@ k_short_pipe(const BatchHeader* __restrict__ H, const PowRow<float>* __restrict_
     }
 }
 
+// Pipelined scalar teams with packed column halves (team_run_pipe2).
+template <int N, int MINB>
+__global__ void __launch_bounds__(kShortThreads, MINB)
+k_short_pipe2(const BatchHeader* __restrict__ H, const PowRow<float>* __restrict__ pow) {
+    const PipeRange rng = pipe_range(H->dropgrow);
+    const uint32_t n_w = H->n_witems;
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+        uint32_t wi = 0;
+        if (lane == 0) wi = atomicAdd(&H->counters[1], 1u);
+        wi = __shfl_sync(kFull, wi, 0);
+        if (wi >= n_w) break;
+        const TeamOf t = team_of(H->teams, H->witems[wi]);
+        int l = 0, k = 0;
+        const Rec32J* rec = reinterpret_cast<const Rec32J*>(dummy_rec<float>());
+        const uint8_t* hap = H->hap_bases;
+        if (t.pair != kNoPair) {
+            const PairDesc d = H->desc[t.pair];
+            l = (int)d.l;
+            k = (int)d.k;
+            rec = H->rec32j + d.roff;
+            hap = H->hap_bases + d.hoff;
+        }
+        const int lmax = (int)__reduce_max_sync(kFull, (unsigned)l);
+        const SegOut o = team_run_pipe2<N>(rec, l, lmax, hap, k, t.lt * N, t.lt, t.tlast, t.nsteps, pow, rng);
+        if (t.pair != kNoPair && t.lt == 0) write_part(H, t.pair, o);
+    }
+}
+
 // Packed teams of two haplotypes of the same read, N columns per lane (item list
 // witems2 / counters[4]).
 template <int N, int MINB>

@@ -66,10 +66,12 @@ __global__ void __launch_bounds__(256) k_prep32(const BatchHeader* __restrict__ 
     for (uint64_t b = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; b < n;
          b += (uint64_t)gridDim.x * blockDim.x) {
         const BaseQ x = base_inputs(H, b);
-        const Rec32 r = make_rec32(x, tq, tom, tq3, tinv, seed, b);
-        float4* dst = reinterpret_cast<float4*>(H->rec32 + b);
-        dst[0] = make_float4(r.pm, r.px, r.a, r.b);
-        dst[1] = make_float4(r.mi, r.g, r.gm, __uint_as_float(r.meta));
+        if (H->rec32) {
+            const Rec32 r = make_rec32(x, tq, tom, tq3, tinv, seed, b);
+            float4* dst = reinterpret_cast<float4*>(H->rec32 + b);
+            dst[0] = make_float4(r.pm, r.px, r.a, r.b);
+            dst[1] = make_float4(r.mi, r.g, r.gm, __uint_as_float(r.meta));
+        }
         if (rj) {
             const Rec32J r2 = make_rec32j(x, tq, tom, tq3, tinv, T.tiq, seed, b, false);
             store_rec32j(rj + b, r2);
@@ -118,6 +120,8 @@ template __global__ void k_short_scalar<16, 6>(const BatchHeader*, const PowRow<
 template __global__ void k_short_pipe<32, 3>(const BatchHeader*, const PowRow<float>*);
 template __global__ void k_short_pipe<24, 4>(const BatchHeader*, const PowRow<float>*);
 template __global__ void k_short_pipe<16, 4>(const BatchHeader*, const PowRow<float>*);
+template __global__ void k_short_pipe2<32, 3>(const BatchHeader*, const PowRow<float>*);
+template __global__ void k_short_pipe2<24, 4>(const BatchHeader*, const PowRow<float>*);
 template __global__ void k_short_packed<12, 4>(const BatchHeader*, const PowRow<float>*);
 template __global__ void k_short_packed<16, 3>(const BatchHeader*, const PowRow<float>*);
 
@@ -190,6 +194,8 @@ void launch_short_scalar(int id, const BatchHeader* H, const void* pow, int grid
     case 4: k_short_pipe<32, 3><<<grid, kShortThreads, 0, s>>>(H, p); break;
     case 5: k_short_pipe<24, 4><<<grid, kShortThreads, 0, s>>>(H, p); break;
     case 6: k_short_pipe<16, 4><<<grid, kShortThreads, 0, s>>>(H, p); break;
+    case 7: k_short_pipe2<32, 3><<<grid, kShortThreads, 0, s>>>(H, p); break;
+    case 8: k_short_pipe2<24, 4><<<grid, kShortThreads, 0, s>>>(H, p); break;
     default: k_short_scalar<32, 4><<<grid, kShortThreads, 0, s>>>(H, p); break;
     }
 }
@@ -208,6 +214,8 @@ int occupancy_short_scalar(int id) {
     case 4: return occ_of(k_short_pipe<32, 3>);
     case 5: return occ_of(k_short_pipe<24, 4>);
     case 6: return occ_of(k_short_pipe<16, 4>);
+    case 7: return occ_of(k_short_pipe2<32, 3>);
+    case 8: return occ_of(k_short_pipe2<24, 4>);
     default: return occ_of(k_short_scalar<32, 4>);
     }
 }

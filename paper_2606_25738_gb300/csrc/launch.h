@@ -43,10 +43,12 @@ int occupancy_forward64();
 constexpr int kN64 = 8;       // columns per lane of the FP64 kernels
 constexpr int kNLong32 = 32;  // columns per lane of FP32 multi-warp pairs
 // FP32 short-pair kernel variants: columns per lane of scalar teams / packed teams.
-constexpr int kNumScalar = 7;
-constexpr int kShortScalarN[kNumScalar] = {32, 24, 24, 16, 32, 24, 16};
+constexpr int kNumScalar = 9;
+constexpr int kShortScalarN[kNumScalar] = {32, 24, 24, 16, 32, 24, 16, 32, 24};
 // scalar ids whose kernel is the pipelined engine (Rec32J records)
-constexpr bool kShortScalarPipe[kNumScalar] = {false, false, false, false, true, true, true};
+constexpr bool kShortScalarPipe[kNumScalar] = {false, false, false, false, true, true, true, true, true};
+// scalar ids whose pipelined engine packs the two column halves of a lane (FFMA2)
+constexpr bool kShortScalarHalves[kNumScalar] = {false, false, false, false, false, false, false, true, true};
 constexpr int kNumPacked = 2;
 constexpr int kShortPackedN[kNumPacked] = {12, 16};
 

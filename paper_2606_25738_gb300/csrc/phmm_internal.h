@@ -146,6 +146,8 @@ struct PowRow {
     T pad1, pad2;
     T lq1[33], lq2[33]; // g^(N * t - 1), t = 1..32 (t = 0 unused): segment carry to the
                         // column before lane t (t = 32: the segment's last column)
+    T hh1, hh2;         // g^(N/2): across the first half of a lane's columns
+    T hm1, hm2;         // g^(N/2 - 1)
 };
 
 // Phred tables staged in shared memory by the prep kernels.  Each value is a pair

@@ -373,6 +373,8 @@ void build_pow_table(int N, std::vector<PowRow<T>>& out) {
         for (int t = 0; t < 32; ++t) split_pow<T>(gq, (double)N * t, r.lp1[t], r.lp2[t]);
         r.lq1[0] = r.lq2[0] = (T)0;
         for (int t = 1; t <= 32; ++t) split_pow<T>(gq, (double)N * t - 1.0, r.lq1[t], r.lq2[t]);
+        split_pow<T>(gq, (double)(N / 2), r.hh1, r.hh2);
+        split_pow<T>(gq, (double)(N / 2 - 1), r.hm1, r.hm2);
         split_pow<T>(gq, (double)(N - 1), r.last1, r.last2);
         r.pad1 = (T)std::pow(10.0, -(double)gq / 10.0);
         r.pad2 = (T)0;
@@ -568,6 +570,10 @@ void plan_header(const Slot& S, const Plan& P, BatchHeader& hh) {
     hh.n_partials = hh.n_pairs + P.n_extra;
     hh.bnd = (unsigned long long*)S.bnd.p;
     hh.n_bnd_words = P.bnd_words;
+    // the Rec32 layout is read by the lean and packed short kernels and the lean
+    // multi-warp kernel only; without them prep skips it
+    const bool need32 = P.pack_id >= 0 || !kShortScalarPipe[P.scal_id] || (P.long_kind == 0 && !P.citems.empty());
+    if (hh.rec32 || hh.rec32j) hh.rec32 = need32 ? (Rec32*)S.rec32.p : nullptr;
 }
 
 // FP32 short-pair kernel candidates (scalar id, packed id or -1) allowed by the config.
@@ -581,6 +587,7 @@ std::vector<std::pair<int, int>> fp32_candidates(const phmm_config& cfg) {
             if (v == 1 && pi < 0) continue;
             if (v == 3 && kShortScalarPipe[si]) continue;
             if (v == 4 && !kShortScalarPipe[si]) continue;
+            if (v == 5 && !kShortScalarHalves[si]) continue;
             if ((n == 24 || n == 32 || n == 16) && scal_only && kShortScalarN[si] != n) continue;
             if ((n == 24 || n == 32) && !scal_only && kShortScalarN[si] != n) continue;
             if ((n == 12 || n == 16) && !scal_only && (pi < 0 || kShortPackedN[pi] != n)) continue;
@@ -657,7 +664,7 @@ int phmm_create(const phmm_config* cfg, phmm_ctx** out) {
     if (!cfg || !out) return PHMM_EINVAL;
     *out = nullptr;
     if (cfg->precision < 0 || cfg->precision > 2) return PHMM_EINVAL;
-    if (cfg->kernel_variant < 0 || cfg->kernel_variant > 4) return PHMM_EINVAL;
+    if (cfg->kernel_variant < 0 || cfg->kernel_variant > 5) return PHMM_EINVAL;
     {
         const unsigned lk = cfg->flags & (PHMM_F_LONG_LEAN | PHMM_F_LONG_PIPE32 | PHMM_F_LONG_PIPE24);
         if (lk & (lk - 1)) return PHMM_EINVAL;  // more than one forced multi-warp kernel

@@ -19,7 +19,7 @@ PHMM_OK, PHMM_PENDING = 0, 1
 PHMM_EINVAL, PHMM_ENOMEM, PHMM_EBUSY, PHMM_ECUDA = -1, -2, -3, -4
 PHMM_ETIMEOUT, PHMM_ECANCELED, PHMM_ENOTFOUND = -5, -6, -7
 PREC = {"fp32": 0, "fp64": 1, "fp32_only": 2}
-VARIANTS = {"auto": 0, "packed": 1, "scalar": 2, "lean": 3, "pipe": 4}
+VARIANTS = {"auto": 0, "packed": 1, "scalar": 2, "lean": 3, "pipe": 4, "pipe2": 5}
 F_NO_GRAPH, F_LAUNCH_PER_PAIR, F_FORCE_RESCUE = 0x1, 0x2, 0x4
 F_LONG_LEAN, F_LONG_PIPE32, F_LONG_PIPE24 = 0x10, 0x20, 0x40
 PAIR_RESCUED, PAIR_RESCALED, PAIR_FP64, PAIR_ERROR = 0x1, 0x2, 0x4, 0x80

@@ -68,7 +68,7 @@ def test_force_rescue_fp64_pass(phmm):
 
 
 VARIANTS = [("packed", 12), ("packed", 16), ("lean", 24), ("lean", 32), ("pipe", 16), ("pipe", 24),
-            ("pipe", 32)]
+            ("pipe", 32), ("pipe2", 24), ("pipe2", 32)]
 
 
 @pytest.mark.parametrize("variant,N", [("packed", 12), ("packed", 16)])
@@ -149,9 +149,9 @@ def _edge_batch(N=16):
 
 
 @pytest.mark.parametrize("prec,variant", [("fp32", "packed"), ("fp32", "scalar"), ("fp32", "lean"),
-                                          ("fp32", "pipe"), ("fp64", "auto")])
+                                          ("fp32", "pipe"), ("fp32", "pipe2"), ("fp64", "auto")])
 def test_edge_cases(phmm, prec, variant):
-    n = {"packed": 16, "scalar": 24, "lean": 32, "pipe": 32}.get(variant, 0) if prec == "fp32" else 0
+    n = {"packed": 16, "scalar": 24, "lean": 32, "pipe": 32, "pipe2": 32}.get(variant, 0) if prec == "fp32" else 0
     b = _edge_batch(max(n, 16))
     with phmm.Context(precision=prec, cols_per_lane=n, variant=variant) as ctx:
         out, flags, rc, st = ctx.run(b)
@@ -172,7 +172,7 @@ def test_long_deletion_50bp(phmm):
     read = hap[100:700] + hap[750:1350]
     b = W.from_strings([(read, hap, 30, 45, 45, 10)])
     for N, v in ((12, "packed"), (16, "packed"), (24, "lean"), (32, "lean"), (16, "pipe"), (24, "pipe"),
-                 (32, "pipe")):
+                 (32, "pipe"), (24, "pipe2"), (32, "pipe2")):
         with phmm.Context(precision="fp32", cols_per_lane=N, variant=v) as ctx:
             out, flags, rc, st = ctx.run(b)
         _check(out, flags, oracle.batch(b))
@@ -306,7 +306,7 @@ def test_short_equal_length_no_spurious_rescue(phmm, L):
     needs the rescue pass."""
     b = W.equal_length(1500, L, seed=1)
     ref = oracle.batch(b)
-    for v, N in (("pipe", 32), ("pipe", 16), ("lean", 32), ("packed", 12)):
+    for v, N in (("pipe", 32), ("pipe", 16), ("lean", 32), ("packed", 12), ("pipe2", 32)):
         with phmm.Context(precision="fp32", variant=v, cols_per_lane=N) as ctx:
             out, flags, rc, st = ctx.run(b)
         assert st["n_rescued"] == 0, (v, N, np.unique(flags, return_counts=True))
@@ -332,7 +332,7 @@ def test_pipelined_engine_extreme_gap_qualities(phmm):
         (read[:60], hap[:64], 30, 93, 93, 10),
     ]
     b = W.from_strings(pairs)
-    for N in (16, 24, 32):
-        with phmm.Context(precision="fp32", variant="pipe", cols_per_lane=N) as ctx:
+    for v, N in (("pipe", 16), ("pipe", 24), ("pipe", 32), ("pipe2", 24), ("pipe2", 32)):
+        with phmm.Context(precision="fp32", variant=v, cols_per_lane=N) as ctx:
             out, flags, rc, st = ctx.run(b)
         _check(out, flags, oracle.batch(b))
