@@ -82,6 +82,15 @@ def run_config(name: str, b: dict, precision: str, steps: int = 3, per_decile: i
         t = time.perf_counter()
         ref = oracle.batch(b, pairs=pick)
         row["oracle_s"] = time.perf_counter() - t
+        rl, hl = W.pair_lengths(b)
+        row["oracle_gcups_all_cores"] = float((rl[pick] * hl[pick]).sum()) / row["oracle_s"] / 1e9
+        # one core, on a slice of the sample worth about a second
+        order = pick[np.argsort(rl[pick] * hl[pick])]
+        csum = np.cumsum(rl[order] * hl[order])
+        one = order[: max(1, int(np.searchsorted(csum, 3e8)))]
+        t = time.perf_counter()
+        oracle.batch(b, pairs=one, n_threads=1)
+        row["oracle_gcups_1core"] = float((rl[one] * hl[one]).sum()) / (time.perf_counter() - t) / 1e9
         dd = np.abs(res[pick] - ref)
         fp64 = (flags[pick] & (phmm.PAIR_RESCUED | phmm.PAIR_FP64)) != 0
         row["checked_pairs"] = int(len(pick))

@@ -255,70 +255,97 @@ void make_plan(const uint32_t* l, const uint32_t* k, const uint32_t* pr, uint32_
         cp.bnd_out = kNoBnd;
         return cp;
     };
-    // Pairs wider than one CTA: one dedicated CTA item per strip, strips in order, so a
-    // strip is always dequeued after the strip it waits for.
-    std::vector<uint32_t> fit;
+    // Units: a pair that fits one CTA, or one strip of a wider pair (S = ceil(W / CW)
+    // strips of near-equal width, the wider ones first).  Units are best-fit packed into
+    // CTAs of CW warps, in runs of similar read length (the CTA waits for its longest
+    // unit).  A pair's strips go into bins in order, never into an earlier bin than the
+    // strip before, so a strip is always dequeued no earlier than the strip it waits for
+    // (the persistent kernel takes items in order: no strip waits on a strip that has not
+    // been started).
+    struct Unit {
+        CtaPair cp;
+        uint32_t l;
+    };
+    std::vector<Unit> units;
     for (uint32_t p : lo) {
         const uint32_t Wt = W_of(p);
         if (Wt <= (uint32_t)CW) {
-            fit.push_back(p);
+            units.push_back({cpair(p, 0, Wt), l[p]});
             continue;
         }
         const uint32_t S = (Wt + CW - 1) / CW;
         const uint32_t extra = n + P.n_extra;
         const uint64_t b0 = P.bnd_words;
+        uint32_t wcol = 0;
         for (uint32_t stp = 0; stp < S; ++stp) {
-            const uint32_t W = std::min((uint32_t)CW, Wt - stp * CW);
+            const uint32_t W = Wt / S + (stp < Wt % S ? 1u : 0u);
             CtaPair cp = cpair(p, 0, W);
             cp.strip = (uint16_t)stp;
             cp.nstrip = S;
-            cp.col0 = stp * CW * seg;
+            cp.col0 = wcol * seg;
             cp.extra_base = extra;
             cp.bnd_in = stp > 0 ? b0 + (uint64_t)(stp - 1) * l[p] * kw : kNoBnd;
             cp.bnd_out = stp + 1 < S ? b0 + (uint64_t)stp * l[p] * kw : kNoBnd;
-            CtaItem it;
-            it.first = (uint32_t)P.cpairs.size();
-            it.n = 1;
-            P.cpairs.push_back(cp);
-            P.citems.push_back(it);
+            units.push_back({cp, l[p]});
+            wcol += W;
         }
         P.bnd_words += (uint64_t)(S - 1) * l[p] * kw;
         P.n_extra += S - 1;
-        P.cost += (double)l[p] * S * CW * 32.0 * (Nl * kCellCost * 1.6 + kRowCost);
     }
+    // runs of similar length, longest first; inside a run widest first (a pair's strips
+    // keep their order: their widths do not increase)
+    std::stable_sort(units.begin(), units.end(), [](const Unit& x, const Unit& y) { return x.l > y.l; });
     struct CBin {
         std::vector<CtaPair> pairs;
         uint32_t rem, lmax;
     };
     std::vector<CBin> cb;
     std::vector<std::vector<uint32_t>> copen(CW + 1);
+    std::vector<uint32_t> last_bin;  // per unit index of a wide pair: bin of its previous strip
     size_t a = 0;
-    while (a < fit.size()) {
-        const uint32_t l0 = l[fit[a]];
+    while (a < units.size()) {
+        const uint32_t l0 = units[a].l;
         size_t b2 = a;
-        while (b2 < fit.size() && (double)l[fit[b2]] >= 0.9 * (double)l0) ++b2;
+        while (b2 < units.size() && (double)units[b2].l >= 0.9 * (double)l0) ++b2;
+        std::stable_sort(units.begin() + a, units.begin() + b2,
+                         [](const Unit& x, const Unit& y) { return x.cp.W > y.cp.W; });
         cb.clear();
         for (auto& o : copen) o.clear();
+        std::map<uint32_t, uint32_t> prev_bin;  // pair -> bin of its latest strip in this run
         for (size_t q = a; q < b2; ++q) {
-            const uint32_t p = fit[q], W = W_of(p);
+            const Unit& u = units[q];
+            const uint32_t W = u.cp.W;
+            uint32_t minb = 0;
+            if (u.cp.nstrip > 1) {
+                auto it = prev_bin.find(u.cp.pair);
+                if (it != prev_bin.end()) minb = it->second;
+            }
             int r = -1;
-            for (uint32_t c = W; c <= (uint32_t)CW; ++c)
-                if (!copen[c].empty()) {
-                    r = (int)c;
-                    break;
-                }
+            size_t pos = 0;
+            for (uint32_t c = W; c <= (uint32_t)CW && r < 0; ++c) {
+                auto& lst = copen[c];
+                for (size_t z = lst.size(); z-- > 0;)
+                    if (lst[z] >= minb) {
+                        r = (int)c;
+                        pos = z;
+                        break;
+                    }
+            }
             uint32_t bi;
             if (r < 0) {
                 bi = (uint32_t)cb.size();
                 cb.push_back({{}, (uint32_t)CW, 0});
             } else {
-                bi = copen[r].back();
-                copen[r].pop_back();
+                bi = copen[r][pos];
+                copen[r].erase(copen[r].begin() + pos);
             }
-            cb[bi].pairs.push_back(cpair(p, CW - cb[bi].rem, W));
+            CtaPair cp = u.cp;
+            cp.w0 = (uint8_t)(CW - cb[bi].rem);
+            cb[bi].pairs.push_back(cp);
             cb[bi].rem -= W;
-            cb[bi].lmax = std::max(cb[bi].lmax, l[p]);
+            cb[bi].lmax = std::max(cb[bi].lmax, u.l);
             if (cb[bi].rem > 0) copen[cb[bi].rem].push_back(bi);
+            if (u.cp.nstrip > 1) prev_bin[u.cp.pair] = bi;
         }
         for (auto& c : cb) {
             CtaItem it;
@@ -603,6 +630,9 @@ void make_plan_id(const uint32_t* l, const uint32_t* k, const uint32_t* pr, uint
     P.scal_id = scal_id;
     P.pack_id = pack_id;
     P.long_kind = long_kind;
+    // the cost model counts slots of the lean engine; the pipelined engines measured ~1.3x
+    // faster per cell on every short shape
+    if (!kShortScalarPipe[scal_id]) P.cost *= 1.3;
 }
 
 // FP32 multi-warp kernels the configuration allows (the lean variant keeps the lean
