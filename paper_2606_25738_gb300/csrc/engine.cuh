@@ -1230,15 +1230,29 @@ __device__ SegOut team_run_pipe(const Rec32J* __restrict__ rec, int l, int lmax,
 }
 
 // ------------------------------------------------------------------------------------
-// team_run_pipe with each lane's columns split in two halves that advance side by side in
-// the two halves of float2 registers (packed FFMA2 / FMUL2): column q of the first half
-// and column N/2 + q of the second share an instruction.  Both halves run the D-hat chains
+// team_run_pipe with each lane's columns split in two halves that advance side by side:
+// column q of the first half and column N/2 + q of the second sit in one float2 and share
+// a packed FFMA2 / FMUL2 (PACKED) or go through two scalar instructions (two independent
+// dependency chains per lane).  Both halves run the D-hat chains
 // of phase B at once, each from its own carry: the first half's comes from the left lane
 // (as in team_run_pipe), the second half's is the first half's D-hat at its last column,
 // formed after the scan.  The lane's scan aggregate joins the two half chains with
 // g^(N/2).  Same results as team_run_pipe up to rounding order.
 // ------------------------------------------------------------------------------------
-template <int N>
+// float2 FMA / multiply as one packed instruction (PACKED) or as two scalar ones (two
+// independent dependency chains for the scheduler to interleave).
+template <bool PACKED>
+__device__ __forceinline__ float2 ffma2_sel(float2 a, float2 b, float2 c) {
+    if constexpr (PACKED) return __ffma2_rn(a, b, c);
+    else return make_float2(fmaf(a.x, b.x, c.x), fmaf(a.y, b.y, c.y));
+}
+template <bool PACKED>
+__device__ __forceinline__ float2 fmul2_sel(float2 a, float2 b) {
+    if constexpr (PACKED) return __fmul2_rn(a, b);
+    else return make_float2(a.x * b.x, a.y * b.y);
+}
+
+template <int N, bool PACKED>
 __device__ SegOut team_run_pipe2(const Rec32J* __restrict__ rec, int l, int lmax,
                                  const uint8_t* __restrict__ hap, int k, int col0, int lt,
                                  int tlast, int nsteps, const PowRow<float>* __restrict__ pow_tab,
@@ -1310,21 +1324,21 @@ __device__ SegOut team_run_pipe2(const Rec32J* __restrict__ rec, int l, int lmax
                 M2[q] = mn;
                 J2[q] = make_float2(0.f, 0.f);
                 if (q == H - 1) yp2 = y2;
-                y2 = __ffma2_rn(rg2, y2, mn);
+                y2 = ffma2_sel<PACKED>(rg2, y2, mn);
             }
         } else {
             const float2 rb2 = make_float2(cur.b, cur.b), gp2 = make_float2(gprev, gprev);
 #pragma unroll
             for (int q = 0; q < H; ++q) {
-                const float2 u2 = __ffma2_rn(rb2, dt2, U2[q]);
-                dt2 = __ffma2_rn(gp2, dt2, ml2);
+                const float2 u2 = ffma2_sel<PACKED>(rb2, dt2, U2[q]);
+                dt2 = ffma2_sel<PACKED>(gp2, dt2, ml2);
                 ml2 = M2[q];
                 const float2 p2 = make_float2(((mask >> q) & 1u) ? pim : pix,
                                               ((mask >> (q + H)) & 1u) ? pim : pix);
-                const float2 mn = __fmul2_rn(p2, u2);
+                const float2 mn = fmul2_sel<PACKED>(p2, u2);
                 M2[q] = mn;
                 if (q == H - 1) yp2 = y2;
-                y2 = __ffma2_rn(rg2, y2, mn);
+                y2 = ffma2_sel<PACKED>(rg2, y2, mn);
             }
         }
         // Eq. 4 when a pair of this warp finishes (I = T_MI J on the last row)
@@ -1371,11 +1385,11 @@ __device__ SegOut team_run_pipe2(const Rec32J* __restrict__ rec, int l, int lmax
             const float mal = M2[H - 1].x, jal = J2[H - 1].x;
 #pragma unroll
             for (int q = H - 1; q >= 1; --q) {
-                U2[q] = __ffma2_rn(na2, M2[q - 1], J2[q - 1]);
-                J2[q] = __ffma2_rn(nh2, J2[q], M2[q]);
+                U2[q] = ffma2_sel<PACKED>(na2, M2[q - 1], J2[q - 1]);
+                J2[q] = ffma2_sel<PACKED>(nh2, J2[q], M2[q]);
             }
-            U2[0] = __ffma2_rn(na2, make_float2(nm, mal), make_float2(nj, jal));
-            J2[0] = __ffma2_rn(nh2, J2[0], M2[0]);
+            U2[0] = ffma2_sel<PACKED>(na2, make_float2(nm, mal), make_float2(nj, jal));
+            J2[0] = ffma2_sel<PACKED>(nh2, J2[0], M2[0]);
         }
         float zz = __shfl_up_sync(kFull, Z, 2);
         if (lt < 2) zz = 0.f;
@@ -1405,9 +1419,9 @@ __device__ SegOut team_run_pipe2(const Rec32J* __restrict__ rec, int l, int lmax
                     const float2 a2 = make_float2(f1, f1), b2 = make_float2(f2v, f2v);
 #pragma unroll
                     for (int q = 0; q < H; ++q) {
-                        M2[q] = __fmul2_rn(__fmul2_rn(M2[q], a2), b2);
-                        J2[q] = __fmul2_rn(__fmul2_rn(J2[q], a2), b2);
-                        U2[q] = __fmul2_rn(__fmul2_rn(U2[q], a2), b2);
+                        M2[q] = fmul2_sel<PACKED>(fmul2_sel<PACKED>(M2[q], a2), b2);
+                        J2[q] = fmul2_sel<PACKED>(fmul2_sel<PACKED>(J2[q], a2), b2);
+                        U2[q] = fmul2_sel<PACKED>(fmul2_sel<PACKED>(U2[q], a2), b2);
                     }
                     nm = (nm * f1) * f2v;
                     zz = (zz * f1) * f2v;

@@ -632,7 +632,7 @@ k_short_pipe(const BatchHeader* __restrict__ H, const PowRow<float>* __restrict_
 }
 
 // Pipelined scalar teams with packed column halves (team_run_pipe2).
-template <int N, int MINB>
+template <int N, int MINB, bool PACKED>
 __global__ void __launch_bounds__(kShortThreads, MINB)
 k_short_pipe2(const BatchHeader* __restrict__ H, const PowRow<float>* __restrict__ pow) {
     const PipeRange rng = pipe_range(H->dropgrow);
@@ -655,7 +655,7 @@ k_short_pipe2(const BatchHeader* __restrict__ H, const PowRow<float>* __restrict
             hap = H->hap_bases + d.hoff;
         }
         const int lmax = (int)__reduce_max_sync(kFull, (unsigned)l);
-        const SegOut o = team_run_pipe2<N>(rec, l, lmax, hap, k, t.lt * N, t.lt, t.tlast, t.nsteps, pow, rng);
+        const SegOut o = team_run_pipe2<N, PACKED>(rec, l, lmax, hap, k, t.lt * N, t.lt, t.tlast, t.nsteps, pow, rng);
         if (t.pair != kNoPair && t.lt == 0) write_part(H, t.pair, o);
     }
 }

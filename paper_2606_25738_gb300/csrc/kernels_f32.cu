@@ -120,8 +120,9 @@ template __global__ void k_short_scalar<16, 6>(const BatchHeader*, const PowRow<
 template __global__ void k_short_pipe<32, 3>(const BatchHeader*, const PowRow<float>*);
 template __global__ void k_short_pipe<24, 4>(const BatchHeader*, const PowRow<float>*);
 template __global__ void k_short_pipe<16, 4>(const BatchHeader*, const PowRow<float>*);
-template __global__ void k_short_pipe2<32, 3>(const BatchHeader*, const PowRow<float>*);
-template __global__ void k_short_pipe2<24, 4>(const BatchHeader*, const PowRow<float>*);
+template __global__ void k_short_pipe2<32, 3, true>(const BatchHeader*, const PowRow<float>*);
+template __global__ void k_short_pipe2<24, 4, true>(const BatchHeader*, const PowRow<float>*);
+
 template __global__ void k_short_packed<12, 4>(const BatchHeader*, const PowRow<float>*);
 template __global__ void k_short_packed<16, 3>(const BatchHeader*, const PowRow<float>*);
 
@@ -194,8 +195,9 @@ void launch_short_scalar(int id, const BatchHeader* H, const void* pow, int grid
     case 4: k_short_pipe<32, 3><<<grid, kShortThreads, 0, s>>>(H, p); break;
     case 5: k_short_pipe<24, 4><<<grid, kShortThreads, 0, s>>>(H, p); break;
     case 6: k_short_pipe<16, 4><<<grid, kShortThreads, 0, s>>>(H, p); break;
-    case 7: k_short_pipe2<32, 3><<<grid, kShortThreads, 0, s>>>(H, p); break;
-    case 8: k_short_pipe2<24, 4><<<grid, kShortThreads, 0, s>>>(H, p); break;
+    case 7: k_short_pipe2<32, 3, true><<<grid, kShortThreads, 0, s>>>(H, p); break;
+    case 8: k_short_pipe2<24, 4, true><<<grid, kShortThreads, 0, s>>>(H, p); break;
+
     default: k_short_scalar<32, 4><<<grid, kShortThreads, 0, s>>>(H, p); break;
     }
 }
@@ -214,8 +216,9 @@ int occupancy_short_scalar(int id) {
     case 4: return occ_of(k_short_pipe<32, 3>);
     case 5: return occ_of(k_short_pipe<24, 4>);
     case 6: return occ_of(k_short_pipe<16, 4>);
-    case 7: return occ_of(k_short_pipe2<32, 3>);
-    case 8: return occ_of(k_short_pipe2<24, 4>);
+    case 7: return occ_of(k_short_pipe2<32, 3, true>);
+    case 8: return occ_of(k_short_pipe2<24, 4, true>);
+
     default: return occ_of(k_short_scalar<32, 4>);
     }
 }
