@@ -278,21 +278,37 @@ def run_ours(args):
     res = out.cpu().numpy()
     flg = fl.cpu().numpy()
 
-    # end to end through the C ABI with host buffers (H2D / D2H inside the timed region)
-    e2e_ms = []
-    hout = np.empty(n, dtype=np.float64)
-    hfl = np.zeros(n, dtype=np.uint8)
-    h2d = int(sum(np.asarray(b[k]).nbytes for k in ("read_bases", "base_q", "ins_q", "del_q", "gcp_q",
-                                                      "hap_bases", "read_off", "hap_off", "pair_read",
-                                                      "pair_hap")))
+    # End to end through the C ABI with host buffers: every step copies its inputs from
+    # pinned host memory to the device and its results back, both inside the timed region.
+    # The caller keeps two batches in flight (two slots), as a pipelined client would, so
+    # one step's copies overlap the previous step's kernels.
+    keys = ("read_bases", "base_q", "ins_q", "del_q", "gcp_q", "hap_bases", "read_off", "hap_off",
+            "pair_read", "pair_hap")
+    hb = dict(b)
+    for k in keys:
+        hb[k] = torch.from_numpy(np.ascontiguousarray(b[k])).pin_memory().numpy()
+    h2d = int(sum(hb[k].nbytes for k in keys))
     d2h = n * 9
+    bufs = [(np.empty(n, dtype=np.float64), np.zeros(n, dtype=np.uint8)) for _ in range(2)]
+    n_e2e = max(4, args.steps // 2)
     with phmm.Context(device=dev, precision="fp32", max_inflight=2) as hctx:
-        for _ in range(2):
-            hctx.run(b, hout, hfl)
-        for _ in range(max(2, args.steps // 2)):
-            t = time.perf_counter()
-            hctx.run(b, hout, hfl)
-            e2e_ms.append((time.perf_counter() - t) * 1e3)
+
+        def pipelined(count):
+            pending = []
+            for q in range(count):
+                if len(pending) == 2:
+                    if hctx.poll(pending.pop(0), -1) != 0:
+                        raise RuntimeError("e2e step failed")
+                o, f = bufs[q % 2]
+                pending.append(hctx.submit(hb, o, f))
+            for t in pending:
+                if hctx.poll(t, -1) != 0:
+                    raise RuntimeError("e2e step failed")
+
+        pipelined(4)  # plans, tuning and graphs of both slots
+        t0 = time.perf_counter()
+        pipelined(n_e2e)
+        e2e_ms = [(time.perf_counter() - t0) * 1e3 / n_e2e]
     e2e_value = cells * world / (float(np.median(e2e_ms)) * 1e-3) / 1e9
     if rank != 0:
         ctx.close()
@@ -337,7 +353,9 @@ def run_ours(args):
         "cpu_baseline": {"value": cpu_v, "unit": "GCUPS", "cores": cores, "kind": "oracle",
                          "sample": sdesc},
         "e2e": {"value": e2e_value, "unit": "GCUPS", "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h, "ms_per_step": float(np.median(e2e_ms))},
+                "d2h_bytes_per_step": d2h, "ms_per_step": float(np.median(e2e_ms)),
+                "how": "phmm_submit_batch/phmm_poll with pinned host inputs and host outputs, "
+                       "2 batches in flight, %d steps" % n_e2e},
         "gpu_launches": int(sum(s["kernel_launches"] for s in sts)),
         "clocks": clocks,
         "accuracy": {"max_abs_dlog10_sample": err, "sample_pairs": 2000,
@@ -365,7 +383,7 @@ def main():
                          "values only for profiling captures)")
     ap.add_argument("--lpp-pairs", type=int, default=4000,
                     help="pairs sampled for the FP64 launch-per-pair comparator")
-    ap.add_argument("--serve-rate", type=float, default=12.0, help="requests per second of the serving leg")
+    ap.add_argument("--serve-rate", type=float, default=8.0, help="requests per second of the serving leg")
     ap.add_argument("--serve-seconds", type=float, default=8.0, help="arrival window of the serving leg (0: skip)")
     ap.add_argument("--serve-pool", type=int, default=32, help="distinct region requests in the serving pool")
     args = ap.parse_args()
