@@ -211,6 +211,21 @@ int phmm_device_info(phmm_ctx *ctx, int *sms, double *max_clock_mhz, double *cup
 int phmm_scan_test(phmm_ctx *ctx, const float *y, float *z, int n, float a);
 
 /*
+ * Test entry (host only, no device needed): builds the work plan the runtime would use
+ * for a batch with read lengths l[p], haplotype lengths k[p] and read index pair_read[p]
+ * (n pairs), for precision (PHMM_PREC_*) and, in FP32, the short-pair kernel ids (scalar
+ * 0..8, packed -1..1) and the multi-warp kernel kind (0..2), and checks it: every pair
+ * scheduled exactly once; teams inside their warp, disjoint and wide enough, packed pairs
+ * sharing a read; CTA warp ranges inside the CTA and disjoint; a wide pair's strips tiling
+ * its columns in order, never placed in an earlier work item than the strip to their left,
+ * with matching and disjoint boundary buffers and partial slots.  stats[8] receives:
+ * teams, warp items, packed warp items, CTA items, CTA pairs, striped pairs, pairs too
+ * long, and the number of the failed check (0 = none).  PHMM_OK or PHMM_EINVAL.
+ */
+int phmm_plan_check(const uint32_t *l, const uint32_t *k, const uint32_t *pair_read, uint32_t n,
+                    int precision, int scal_id, int pack_id, int long_kind, uint64_t *stats);
+
+/*
  * Serving: continuous batching of independent requests (an active region: R reads x H
  * haplotypes, scored as one phmm_batch).  The paper has no serving layer; this loop is
  * built on phmm_submit_batch / phmm_poll of one context.  A scheduler thread keeps a FIFO

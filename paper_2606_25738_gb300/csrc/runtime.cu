@@ -1301,6 +1301,147 @@ int phmm_get_stats(phmm_ctx* ctx, uint64_t ticket, phmm_stats* out) {
     return PHMM_ENOTFOUND;
 }
 
+int phmm_plan_check(const uint32_t* l, const uint32_t* k, const uint32_t* pair_read, uint32_t n,
+                    int precision, int scal_id, int pack_id, int long_kind, uint64_t* stats) {
+    if (!l || !k || !pair_read || !stats) return PHMM_EINVAL;
+    if (precision < 0 || precision > 2) return PHMM_EINVAL;
+    for (int q = 0; q < 8; ++q) stats[q] = 0;
+    Plan P;
+    int CW = kCtaWarps, Nl = kN64, kw = 8;
+    if (precision == PHMM_PREC_FP64) {
+        make_plan(l, k, pair_read, n, kN64, 0, kN64, P, 8);
+    } else {
+        if (scal_id < 0 || scal_id >= kNumScalar || pack_id < -1 || pack_id >= kNumPacked || long_kind < 0 ||
+            long_kind >= kNumLong)
+            return PHMM_EINVAL;
+        make_plan_id(l, k, pair_read, n, scal_id, pack_id, long_kind, P);
+        CW = kLongCW[long_kind];
+        Nl = kLongN[long_kind];
+        kw = 4;
+    }
+    const uint64_t seg = 32ull * (uint64_t)Nl;
+    auto fail = [&](uint64_t code) {
+        stats[7] = code;
+        return PHMM_EINVAL;
+    };
+    std::vector<uint32_t> seen(n, 0);
+    // teams: inside their warp, disjoint, wide enough, packed pairs share a read
+    auto check_items = [&](const std::vector<WarpItem>& items, bool packed) -> int {
+        for (const WarpItem& w : items) {
+            uint64_t used = 0;
+            for (uint32_t t = 0; t < w.n_teams; ++t) {
+                if (w.first_team + t >= P.teams.size()) return 1;
+                const Team& tm = P.teams[w.first_team + t];
+                if (tm.size == 0 || tm.base + tm.size > 32) return 2;
+                const uint64_t bits = ((tm.size == 32 ? ~0ull : ((1ull << tm.size) - 1)) << tm.base) & 0xffffffffull;
+                if (used & bits) return 3;
+                used |= bits;
+                const int Nw = packed ? P.NP : P.N;
+                if (tm.pair >= n) return 4;
+                if ((uint64_t)tm.size * Nw < k[tm.pair]) return 5;
+                seen[tm.pair]++;
+                if (tm.pair2 != kNoPair) {
+                    if (!packed || tm.pair2 >= n) return 6;
+                    if (pair_read[tm.pair2] != pair_read[tm.pair]) return 7;
+                    if ((uint64_t)tm.size * Nw < k[tm.pair2]) return 5;
+                    seen[tm.pair2]++;
+                }
+            }
+        }
+        return 0;
+    };
+    if (int e = check_items(P.witems, false)) return fail(e);
+    if (int e = check_items(P.witems2, true)) return fail(e);
+    // CTA items: warp ranges fit and are disjoint; strips tile their pair in item order
+    struct StripSeen {
+        uint32_t nstrip = 0, count = 0, extra_base = 0;
+        std::vector<int64_t> col0, width, item;
+        std::vector<uint64_t> bin, bout;
+    };
+    std::map<uint32_t, StripSeen> strips;
+    for (size_t it = 0; it < P.citems.size(); ++it) {
+        const CtaItem& ci = P.citems[it];
+        uint32_t used = 0;
+        for (uint32_t q = 0; q < ci.n; ++q) {
+            if (ci.first + q >= P.cpairs.size()) return fail(10);
+            const CtaPair& cp = P.cpairs[ci.first + q];
+            if (cp.W == 0 || cp.w0 + cp.W > CW) return fail(11);
+            const uint32_t bits = ((cp.W == 32 ? ~0u : ((1u << cp.W) - 1)) << cp.w0);
+            if (used & bits) return fail(12);
+            used |= bits;
+            if (cp.pair >= n) return fail(13);
+            const uint64_t Wt = (k[cp.pair] + seg - 1) / seg;
+            if (cp.nstrip <= 1) {
+                if (cp.W != Wt || cp.col0 != 0 || cp.bnd_in != kNoBnd || cp.bnd_out != kNoBnd) return fail(14);
+                seen[cp.pair]++;
+                continue;
+            }
+            StripSeen& sv = strips[cp.pair];
+            if (sv.count == 0) {
+                sv.nstrip = cp.nstrip;
+                sv.extra_base = cp.extra_base;
+                sv.col0.assign(cp.nstrip, -1);
+                sv.width.assign(cp.nstrip, -1);
+                sv.item.assign(cp.nstrip, -1);
+                sv.bin.assign(cp.nstrip, 0);
+                sv.bout.assign(cp.nstrip, 0);
+            }
+            if (cp.nstrip != sv.nstrip || cp.extra_base != sv.extra_base || cp.strip >= sv.nstrip ||
+                sv.item[cp.strip] >= 0)
+                return fail(15);
+            sv.col0[cp.strip] = cp.col0;
+            sv.width[cp.strip] = cp.W;
+            sv.item[cp.strip] = (int64_t)it;
+            sv.bin[cp.strip] = cp.bnd_in;
+            sv.bout[cp.strip] = cp.bnd_out;
+            sv.count++;
+        }
+    }
+    std::vector<std::pair<uint64_t, uint64_t>> bnd_ranges, extra_ranges;
+    for (auto& kv : strips) {
+        const uint32_t p = kv.first;
+        StripSeen& sv = kv.second;
+        if (sv.count != sv.nstrip) return fail(20);
+        int64_t col = 0, warps = 0;
+        for (uint32_t st = 0; st < sv.nstrip; ++st) {
+            if (sv.col0[st] != col) return fail(21);
+            col += sv.width[st] * (int64_t)seg;
+            warps += sv.width[st];
+            if (st > 0 && sv.item[st] < sv.item[st - 1]) return fail(22);  // never before its left strip
+            if ((st == 0) != (sv.bin[st] == kNoBnd)) return fail(23);
+            if ((st + 1 == sv.nstrip) != (sv.bout[st] == kNoBnd)) return fail(23);
+            if (st > 0 && sv.bin[st] != sv.bout[st - 1]) return fail(24);
+            if (st + 1 < sv.nstrip) {
+                const uint64_t a = sv.bout[st], b = a + (uint64_t)l[p] * kw;
+                if (b > P.bnd_words) return fail(25);
+                bnd_ranges.push_back({a, b});
+            }
+        }
+        if ((uint64_t)warps != (k[p] + seg - 1) / seg) return fail(26);
+        if (sv.extra_base < n || sv.extra_base + sv.nstrip - 1 > n + P.n_extra) return fail(27);
+        extra_ranges.push_back({sv.extra_base, sv.extra_base + sv.nstrip - 1});
+        seen[p]++;
+        stats[5]++;
+    }
+    auto disjoint = [](std::vector<std::pair<uint64_t, uint64_t>>& r) {
+        std::sort(r.begin(), r.end());
+        for (size_t q = 1; q < r.size(); ++q)
+            if (r[q].first < r[q - 1].second) return false;
+        return true;
+    };
+    if (!disjoint(bnd_ranges)) return fail(28);
+    if (!disjoint(extra_ranges)) return fail(29);
+    for (uint32_t p = 0; p < n; ++p)
+        if (seen[p] != 1) return fail(30);
+    stats[0] = P.teams.size();
+    stats[1] = P.witems.size();
+    stats[2] = P.witems2.size();
+    stats[3] = P.citems.size();
+    stats[4] = P.cpairs.size();
+    stats[6] = P.n_too_long;
+    return PHMM_OK;
+}
+
 int phmm_scan_test(phmm_ctx* ctx, const float* y, float* z, int n, float a) {
     if (!ctx || !y || !z || n < 1 || n > 1024 || !(a >= 0.0f) || !(a <= 1.0f)) return PHMM_EINVAL;
     std::lock_guard<std::mutex> lock(ctx->mu);

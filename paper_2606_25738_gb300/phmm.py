@@ -29,7 +29,8 @@ PAIR_DANGER, PAIR_NONFINITE, PAIR_SMALL_SUM, PAIR_DEGENERATE = 0x8, 0x10, 0x20, 
 SYMBOLS = ["phmm_create", "phmm_submit_batch", "phmm_poll", "phmm_get_stats", "phmm_destroy",
            "phmm_strerror", "phmm_abi_version", "phmm_device_info", "phmm_scan_test",
            "phmm_forward_noalloc", "phmm_batch_footprint", "phmm_server_create",
-           "phmm_server_enqueue", "phmm_server_poll", "phmm_server_get_stats", "phmm_server_destroy"]
+           "phmm_server_enqueue", "phmm_server_poll", "phmm_server_get_stats", "phmm_server_destroy",
+           "phmm_plan_check"]
 
 
 class PhmmError(RuntimeError):
@@ -109,6 +110,9 @@ def _load() -> ctypes.CDLL:
     lib.phmm_server_get_stats.argtypes = [ctypes.c_void_p, ctypes.POINTER(ServerStats)]
     lib.phmm_server_destroy.argtypes = [ctypes.c_void_p]
     lib.phmm_server_destroy.restype = None
+    lib.phmm_plan_check.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint32,
+                                    ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                    ctypes.POINTER(ctypes.c_uint64)]
     return lib
 
 
@@ -273,6 +277,22 @@ class Context:
         if rc != PHMM_OK:
             raise PhmmError(rc, "phmm_scan_test")
         return z
+
+
+def plan_check(l, k, pair_read, precision: str = "fp32", scal_id: int = 4, pack_id: int = -1,
+               long_kind: int = 1):
+    """phmm_plan_check (host only): builds and checks the work plan for the given read /
+    haplotype lengths.  Returns (status, stats dict)."""
+    l = np.ascontiguousarray(l, dtype=np.uint32)
+    k = np.ascontiguousarray(k, dtype=np.uint32)
+    pr = np.ascontiguousarray(pair_read, dtype=np.uint32)
+    st = (ctypes.c_uint64 * 8)()
+    rc = _lib.phmm_plan_check(ctypes.c_void_p(l.ctypes.data), ctypes.c_void_p(k.ctypes.data),
+                              ctypes.c_void_p(pr.ctypes.data), len(l), PREC[precision], scal_id, pack_id,
+                              long_kind, st)
+    names = ("teams", "warp_items", "packed_warp_items", "cta_items", "cta_pairs", "striped_pairs",
+             "too_long", "failed_check")
+    return rc, dict(zip(names, [int(v) for v in st]))
 
 
 def forward_noalloc(d: dict, out, out_flags, device: int = 0, stream=None) -> int:
