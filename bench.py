@@ -138,7 +138,10 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GCUPS",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic (seeded)", "config": {"workload": WORKLOAD},
+            "data": "synthetic (seeded short-read regions)",
+            "config": {"workload": WORKLOAD if args.regions == 2000 else WORKLOAD.replace("2000", str(args.regions)),
+                       "pairs": int(len(b["pair_read"])), "reads": int(len(b["read_off"]) - 1),
+                       "cells": int(W.cells(b))},
             "cpu_baseline": {"value": value, "unit": "GCUPS", "cores": cores, "kind": "oracle",
                              "sample": desc},
             "e2e": {"value": value, "unit": "GCUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
