@@ -453,6 +453,7 @@ __device__ SegOut seg_run(const typename Num<T>::Rec* __restrict__ rec, int l, i
     // Match masks of the lane's columns (Eq. 3; an N matches every base).
     uint32_t bmA = 0, bmC = 0, bmG = 0, bmT = 0;
     uint32_t flags = 0;
+    const bool has_left = LINKED && link.has_left, has_right = LINKED && link.has_right;
     const int nvalid = max(0, min(k - col0, N));
 #pragma unroll
     for (int c = 0; c < N; ++c) {
@@ -533,12 +534,13 @@ __device__ SegOut seg_run(const typename Num<T>::Rec* __restrict__ rec, int l, i
         T Wd = __shfl_up_sync(kFull, Z, 1);
         if (lt == 0) Wd = T(0);
 
-        // Carry from the previous warp segment (multi-warp pairs).
+        // Carry from the previous warp segment (multi-warp pairs): lane 0 waits for it, then
+        // the (converged) warp takes it.
         T lM = T(0), lI = T(0), lD = T(0);
         int Eleft = INT_MIN;
-        if (LINKED && link.has_left) {
-            int e_in = 0;
-            if ((threadIdx.x & 31) == 0) {
+        if (LINKED) {
+            int e_in = INT_MIN;
+            if (has_left && (threadIdx.x & 31) == 0) {
                 const bool ok = link.in_g ? link_recv_g<T>(link.in_g, i, lM, lI, lD, e_in)
                                           : link_recv<T>(link, i, lM, lI, lD, e_in);
                 if (!ok) {
@@ -546,6 +548,7 @@ __device__ SegOut seg_run(const typename Num<T>::Rec* __restrict__ rec, int l, i
                     atomicOr(status, ST_TIMEOUT);
                 }
             }
+            __syncwarp();
             lM = __shfl_sync(kFull, lM, 0);
             lI = __shfl_sync(kFull, lI, 0);
             lD = __shfl_sync(kFull, lD, 0);
@@ -567,13 +570,13 @@ __device__ SegOut seg_run(const typename Num<T>::Rec* __restrict__ rec, int l, i
                 // Nothing representable in this segment: follow the left neighbour's scale,
                 // so that mass arriving later from the left is not converted across a
                 // gap wider than the format's range.
-                if (LINKED && link.has_left) desired = INT_MIN;
+                if (has_left) desired = INT_MIN;
             } else if (e > NT::kHi || e <= NT::kLo) {
                 desired = E + (e - NT::kTarget);
             }
             Enew = desired;
             bool forced = false;
-            if (LINKED && link.has_left && Eleft > Enew) {
+            if (has_left && Eleft > Enew) {
                 Enew = Eleft;
                 forced = true;
             }
@@ -595,7 +598,7 @@ __device__ SegOut seg_run(const typename Num<T>::Rec* __restrict__ rec, int l, i
             if (i <= l) flags |= PF_RESCALED;
             E = Enew;
         }
-        if (LINKED && link.has_left) {
+        if (has_left) {
             // Left values into this segment's scale (E >= Eleft always holds here).
             const int d = Eleft - E;
             lM = scale2(lM, d);
@@ -607,7 +610,7 @@ __device__ SegOut seg_run(const typename Num<T>::Rec* __restrict__ rec, int l, i
         // D-hat at the lane's last column (needed by the next lane's first cell).
         const T Dlast = fma(Wd * pw.last1(), pw.last2(), yprev);
 
-        if (LINKED && link.has_right && (threadIdx.x & 31) == 31) {
+        if (has_right && (threadIdx.x & 31) == 31) {
             if (link.out_g) {
                 link_send_g<T>(link.out_g, i, M[N - 1], I[N - 1], Dlast, E);
             } else if (!link_send<T>(link, i, M[N - 1], I[N - 1], Dlast, E)) {
