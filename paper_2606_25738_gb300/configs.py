@@ -1,13 +1,12 @@
-"""Runs one named workload through the C ABI and reports throughput and sampled parity.
+"""Runs one named workload through the C ABI and reports its throughput.
 
     python -m paper_2606_25738_gb300.configs --config long --precision both
 
 Workloads (see workloads.py): ``plain`` (64 short pairs), ``short`` (the short-read
 region batch), ``long`` (64 long-read pairs, haplotypes 1k-100k bp), ``uneven`` (1M pairs
 of log-uniform 50-20k bp lengths).  Each precision is run as one batch: one submit, the
-timed steps replaying its captured graph.  Parity: pairs sampled in every decile of the
-per-pair cell count, plus every pair the FP64 rescue recomputed (up to a cap), compared
-with the CPU oracle.  One JSON line per (workload, precision).
+timed steps replaying its captured graph.  One JSON line per (workload, precision).
+``stratified_sample`` picks the pairs a parity check looks at (tests/measure_parity.py).
 """
 from __future__ import annotations
 
@@ -47,8 +46,11 @@ def stratified_sample(b: dict, per_decile: int, seed: int = 0, max_cells: float 
     return pick
 
 
-def run_config(name: str, b: dict, precision: str, steps: int = 3, per_decile: int = 200,
-               check: bool = True, variant: str = "auto", rescued_cap: int = 300) -> dict:
+def run_config(name: str, b: dict, precision: str, steps: int = 3, variant: str = "auto",
+               on_result=None) -> dict:
+    """One batch through the C ABI: a first submit (plan, tuning, graph capture), then
+    ``steps`` timed replays.  ``on_result(b, log10_L, flags)`` (optional) receives the
+    last step's host outputs, for a caller that checks them."""
     import torch
     n = len(b["pair_read"])
     cells = W.cells(b)
@@ -72,31 +74,8 @@ def run_config(name: str, b: dict, precision: str, steps: int = 3, per_decile: i
            "ms_forward": fwd, "ms_total": tot, "gcups_kernel": cells / fwd / 1e6,
            "gcups_total": cells / tot / 1e6, "rescued": int(st[-1]["n_rescued"]),
            "kernel_launches": int(st[-1]["kernel_launches"]), "first_submit_s": first_s}
-    if check:
-        import oracle
-        res = out.cpu().numpy()
-        flags = fl.cpu().numpy()
-        pick = stratified_sample(b, per_decile)
-        resc = np.flatnonzero(flags & phmm.PAIR_RESCUED)[:rescued_cap]
-        pick = np.unique(np.concatenate([pick, resc]))
-        t = time.perf_counter()
-        ref = oracle.batch(b, pairs=pick)
-        row["oracle_s"] = time.perf_counter() - t
-        rl, hl = W.pair_lengths(b)
-        row["oracle_gcups_all_cores"] = float((rl[pick] * hl[pick]).sum()) / row["oracle_s"] / 1e9
-        # one core, on a slice of the sample worth about a second
-        order = pick[np.argsort(rl[pick] * hl[pick])]
-        csum = np.cumsum(rl[order] * hl[order])
-        one = order[: max(1, int(np.searchsorted(csum, 3e8)))]
-        t = time.perf_counter()
-        oracle.batch(b, pairs=one, n_threads=1)
-        row["oracle_gcups_1core"] = float((rl[one] * hl[one]).sum()) / (time.perf_counter() - t) / 1e9
-        dd = np.abs(res[pick] - ref)
-        fp64 = (flags[pick] & (phmm.PAIR_RESCUED | phmm.PAIR_FP64)) != 0
-        row["checked_pairs"] = int(len(pick))
-        row["max_abs_dlog10_fp32"] = float(dd[~fp64].max()) if (~fp64).any() else None
-        row["max_abs_dlog10_fp64"] = float(dd[fp64].max()) if fp64.any() else None
-        row["within_tolerance"] = bool(np.all(dd <= np.where(fp64, 1e-9, 1e-3)))
+    if on_result is not None:
+        on_result(b, out.cpu().numpy(), fl.cpu().numpy())
     return row
 
 
@@ -105,15 +84,13 @@ def main(argv=None):
     ap.add_argument("--config", required=True, choices=sorted(MAKERS))
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "fp32_only", "both"])
     ap.add_argument("--steps", type=int, default=3)
-    ap.add_argument("--per-decile", type=int, default=200)
-    ap.add_argument("--no-check", action="store_true")
     a = ap.parse_args(argv)
     t = time.perf_counter()
     b = MAKERS[a.config]()
     gen_s = time.perf_counter() - t
     precs = ["fp32", "fp64"] if a.precision == "both" else [a.precision]
     for p in precs:
-        row = run_config(a.config, b, p, steps=a.steps, per_decile=a.per_decile, check=not a.no_check)
+        row = run_config(a.config, b, p, steps=a.steps)
         row["gen_s"] = gen_s
         print(json.dumps(row), flush=True)
 

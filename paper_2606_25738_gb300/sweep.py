@@ -4,8 +4,8 @@ haplotype length = 32 .. 131072 bp), through the library's C ABI.
 For each length L the batch holds about ``target_cells`` cell updates (at least one
 pair, at most ``max_pairs``).  GCUPS are reported for the forward kernels alone (the
 paper's kernel-only convention for this experiment) and for the whole device pipeline
-of a batch (prep, forward, reduction, rescue selection and rescue).  A sample of each
-batch is checked against the CPU oracle where the oracle finishes in seconds.
+of a batch (prep, forward, reduction, rescue selection and rescue).  Parity of the sweep's
+batches is checked by tests/measure_parity.py.
 
     python -m paper_2606_25738_gb300.sweep [--max-len 131072] [--precision fp32]
 """
@@ -23,7 +23,10 @@ from . import workloads as W
 
 
 def run(lengths, target_cells: float = 2e10, max_pairs: int = 1 << 20, precision: str = "fp32",
-        steps: int = 3, check: bool = True, check_cells: float = 4e8, device: int = 0, log=None):
+        steps: int = 3, device: int = 0, log=None, on_result=None):
+    """One batch per length L of about ``target_cells`` cells (at least one pair, at most
+    ``max_pairs``).  ``on_result(L, batch, log10_L, flags)`` (optional) receives each
+    batch's host outputs, for a caller that checks them."""
     import torch
     rows = []
     for L in lengths:
@@ -50,18 +53,8 @@ def run(lengths, target_cells: float = 2e10, max_pairs: int = 1 << 20, precision
                "gcups_kernel": cells / fwd / 1e6, "gcups_total": cells / tot / 1e6,
                "rescued": int(st[-1]["n_rescued"]), "cols_per_lane": int(st[-1]["cols_per_lane"]),
                "gen_s": gen_s}
-        if check:
-            import oracle
-            per = L * L
-            m = int(max(1, min(n, check_cells // per))) if per <= check_cells else 0
-            if m:
-                pick = np.random.default_rng(L).choice(n, m, replace=False)
-                ref = oracle.batch(b, pairs=pick)
-                got = out.cpu().numpy()[pick]
-                row["checked_pairs"] = m
-                row["max_abs_dlog10"] = float(np.max(np.abs(got - ref)))
-            else:
-                row["checked_pairs"] = 0
+        if on_result is not None:
+            row.update(on_result(L, b, out.cpu().numpy(), fl.cpu().numpy()) or {})
         rows.append(row)
         if log:
             print(json.dumps(row), file=log, flush=True)
@@ -75,14 +68,13 @@ def main(argv=None):
     ap.add_argument("--target-cells", type=float, default=2e10)
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "fp32_only"])
     ap.add_argument("--steps", type=int, default=3)
-    ap.add_argument("--no-check", action="store_true")
     a = ap.parse_args(argv)
     lengths = []
     L = a.min_len
     while L <= a.max_len:
         lengths.append(L)
         L *= 2
-    run(lengths, a.target_cells, precision=a.precision, steps=a.steps, check=not a.no_check, log=sys.stdout)
+    run(lengths, a.target_cells, precision=a.precision, steps=a.steps, log=sys.stdout)
 
 
 if __name__ == "__main__":
