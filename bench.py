@@ -82,6 +82,25 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def max_over_ranks(values, world: int):
+    """Element-wise maximum of per-rank values (step time, wall time) over the job's ranks:
+    the job is as slow as its slowest rank.  NCCL jobs reduce on the GPU, gloo on the CPU."""
+    if world <= 1:
+        return [float(v) for v in values]
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t.cpu()]
+
+
+def job_throughput(cells_per_rank: float, world: int, step_ms: float) -> float:
+    """Whole-job GCUPS: every rank scores its own replica of the batch (pairs are
+    independent; no exchange), so the job updates world x cells per slowest-rank step."""
+    return cells_per_rank * world / (step_ms * 1e-3) / 1e9
+
+
 def _peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -274,11 +293,8 @@ def run_ours(args):
     ms = np.array([s["ms_total"] for s in sts])
     ms_fwd = np.array([s["ms_forward"] for s in sts])
     step_ms = float(ms.mean())
-    if world > 1:
-        tt = torch.tensor([step_ms, wall], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        step_ms, wall = float(tt[0]), float(tt[1])
-    value = cells * world / (step_ms * 1e-3) / 1e9
+    step_ms, wall = max_over_ranks([step_ms, wall], world)
+    value = job_throughput(cells, world, step_ms)
     # accuracy gate on a sample of this run's outputs
     res = out.cpu().numpy()
     flg = fl.cpu().numpy()
@@ -314,7 +330,7 @@ def run_ours(args):
         t0 = time.perf_counter()
         pipelined(n_e2e)
         e2e_ms = [(time.perf_counter() - t0) * 1e3 / n_e2e]
-    e2e_value = cells * world / (float(np.median(e2e_ms)) * 1e-3) / 1e9
+    e2e_value = job_throughput(cells, world, max_over_ranks([float(np.median(e2e_ms))], world)[0])
     if rank != 0:
         ctx.close()
         return
