@@ -211,6 +211,14 @@ int phmm_device_info(phmm_ctx *ctx, int *sms, double *max_clock_mhz, double *cup
 int phmm_scan_test(phmm_ctx *ctx, const float *y, float *z, int n, float a);
 
 /*
+ * Test entry: the bounded device-side wait that links column strips (and, in shared
+ * memory, warp segments) run on a boundary that is never written.  The wait gives up
+ * after its poll limit (about a second) instead of hanging, and the call returns
+ * PHMM_ETIMEOUT; the context stays usable.  Runs synchronously on the context's stream.
+ */
+int phmm_wait_test(phmm_ctx *ctx);
+
+/*
  * Test entry (host only, no device needed): builds the work plan the runtime would use
  * for a batch with read lengths l[p], haplotype lengths k[p] and read index pair_read[p]
  * (n pairs), for precision (PHMM_PREC_*) and, in FP32, the short-pair kernel ids (scalar

@@ -153,6 +153,20 @@ __global__ void k_scan_test(const float* __restrict__ y, float* __restrict__ z, 
     }
 }
 
+// Bounded-wait test: lane 0 waits for row 1 of a strip boundary that nothing writes (the
+// words hold tag 0); the wait gives up after its poll limit and reports ST_TIMEOUT.
+__global__ void k_wait_test(const unsigned long long* __restrict__ bnd, uint32_t* __restrict__ status) {
+    if (threadIdx.x == 0) {
+        float m, i, d;
+        int e;
+        if (!link_recv_g<float>(bnd, 1, m, i, d, e)) atomicOr(status, ST_TIMEOUT);
+    }
+}
+
+void launch_wait_test(const void* bnd, uint32_t* status, cudaStream_t s) {
+    k_wait_test<<<1, 32, 0, s>>>(static_cast<const unsigned long long*>(bnd), status);
+}
+
 void launch_reset(const BatchHeader* H, int grid, cudaStream_t s) { k_reset<<<grid, 256, 0, s>>>(H); }
 
 void launch_prep32(const BatchHeader* H, const PhredTables* T, int grid, cudaStream_t s) {

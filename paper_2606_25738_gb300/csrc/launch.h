@@ -30,6 +30,8 @@ int occupancy_short_scalar(int id);
 int occupancy_short_packed(int id);
 // pow_row: a device pointer to one PowRow<float>
 void launch_scan_test(const float* y, float* z, int n, const void* pow_row, cudaStream_t s);
+// bnd: device buffer of at least 4 zero words; status: device word
+void launch_wait_test(const void* bnd, uint32_t* status, cudaStream_t s);
 
 // FP64 unit
 void launch_prep64_all(const BatchHeader* H, const PhredTables* T, int grid, cudaStream_t s);

@@ -1442,6 +1442,24 @@ int phmm_plan_check(const uint32_t* l, const uint32_t* k, const uint32_t* pair_r
     return PHMM_OK;
 }
 
+int phmm_wait_test(phmm_ctx* ctx) {
+    if (!ctx) return PHMM_EINVAL;
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    if (ctx->dead) return PHMM_ECUDA;
+    cudaSetDevice(ctx->dev);
+    DevBuf buf;
+    CK(ensure(buf, 64));
+    CK(cudaMemsetAsync(buf.p, 0, 64, ctx->stream));
+    uint32_t* status = static_cast<uint32_t*>(buf.p) + 12;  // word after the 4 boundary words
+    launch_wait_test(buf.p, status, ctx->stream);
+    CK(cudaGetLastError());
+    uint32_t st = 0;
+    CK(cudaMemcpyAsync(&st, status, sizeof(st), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    release(buf);
+    return (st & ST_TIMEOUT) ? PHMM_ETIMEOUT : PHMM_OK;
+}
+
 int phmm_scan_test(phmm_ctx* ctx, const float* y, float* z, int n, float a) {
     if (!ctx || !y || !z || n < 1 || n > 1024 || !(a >= 0.0f) || !(a <= 1.0f)) return PHMM_EINVAL;
     std::lock_guard<std::mutex> lock(ctx->mu);

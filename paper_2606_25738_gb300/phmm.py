@@ -30,7 +30,7 @@ SYMBOLS = ["phmm_create", "phmm_submit_batch", "phmm_poll", "phmm_get_stats", "p
            "phmm_strerror", "phmm_abi_version", "phmm_device_info", "phmm_scan_test",
            "phmm_forward_noalloc", "phmm_batch_footprint", "phmm_server_create",
            "phmm_server_enqueue", "phmm_server_poll", "phmm_server_get_stats", "phmm_server_destroy",
-           "phmm_plan_check"]
+           "phmm_plan_check", "phmm_wait_test"]
 
 
 class PhmmError(RuntimeError):
@@ -110,6 +110,7 @@ def _load() -> ctypes.CDLL:
     lib.phmm_server_get_stats.argtypes = [ctypes.c_void_p, ctypes.POINTER(ServerStats)]
     lib.phmm_server_destroy.argtypes = [ctypes.c_void_p]
     lib.phmm_server_destroy.restype = None
+    lib.phmm_wait_test.argtypes = [ctypes.c_void_p]
     lib.phmm_plan_check.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint32,
                                     ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                     ctypes.POINTER(ctypes.c_uint64)]
@@ -266,6 +267,11 @@ class Context:
         if rc != PHMM_OK:
             raise PhmmError(rc, "phmm_batch_footprint")
         return v.value
+
+    def wait_test(self) -> int:
+        """phmm_wait_test: a bounded device wait on a boundary nothing writes; returns
+        PHMM_ETIMEOUT when the wait gave up as designed."""
+        return _lib.phmm_wait_test(self._h)
 
     def scan_test(self, y, a: float):
         """The lane + warp linear-recurrence scan on a torch CUDA float32 tensor y

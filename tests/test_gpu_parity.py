@@ -336,3 +336,17 @@ def test_pipelined_engine_extreme_gap_qualities(phmm):
         with phmm.Context(precision="fp32", variant=v, cols_per_lane=N) as ctx:
             out, flags, rc, st = ctx.run(b)
         _check(out, flags, oracle.batch(b))
+
+
+def test_bounded_wait_times_out_and_context_survives(phmm):
+    """A device-side wait that can never be satisfied gives up within its poll limit and
+    reports PHMM_ETIMEOUT; the same context then still scores a batch correctly."""
+    import time
+    b = W.plain_pairs(8, seed=40)
+    with phmm.Context() as ctx:
+        t = time.perf_counter()
+        assert ctx.wait_test() == phmm.PHMM_ETIMEOUT
+        assert time.perf_counter() - t < 30.0
+        out, flags, rc, st = ctx.run(b)
+    assert rc == 0
+    _check(out, flags, oracle.batch(b))
