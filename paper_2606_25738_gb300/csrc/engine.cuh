@@ -135,36 +135,6 @@ __device__ __forceinline__ Rec64 load_rec(const Rec64* p) {
     return r;
 }
 
-// Asynchronous global -> shared copies (cp.async): the per-row records of a team are
-// fetched three rows ahead into a 4-slot shared-memory ring, without holding registers.
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int K>
-__device__ __forceinline__ void cp_async_wait() {
-    asm volatile("cp.async.wait_group %0;\n" ::"n"(K) : "memory");
-}
-constexpr int kRecRing = 4;  // slots per team
-// Row `row` (1-based, clamped to the read) of a team's records into its ring slot.
-__device__ __forceinline__ void rec_fetch(Rec32* ring, const Rec32* rec, int row, int l1, int lt) {
-    if (lt == 0) {
-        const Rec32* src = rec + min(row - 1, l1);
-        Rec32* dst = ring + (row & (kRecRing - 1));
-        cp_async16(dst, src);
-        cp_async16(reinterpret_cast<char*>(dst) + 16, reinterpret_cast<const char*>(src) + 16);
-    }
-    cp_async_commit();
-}
-__device__ __forceinline__ Rec32 rec_read(const Rec32* ring, int row) {
-    const float4* q = reinterpret_cast<const float4*>(ring + (row & (kRecRing - 1)));
-    const float4 a = q[0], b = q[1];
-    Rec32 r;
-    r.pm = a.x; r.px = a.y; r.a = a.z; r.b = a.w;
-    r.mi = b.x; r.g = b.y; r.gm = b.z; r.meta = __float_as_uint(b.w);
-    return r;
-}
 
 // Powers of g for the lane's scan (see PowRow): a pointer to the table row of the
 // current gcp; the factors are read through L1 when used (uniform addresses), which
@@ -656,12 +626,13 @@ __device__ SegOut seg_run(const typename Num<T>::Rec* __restrict__ rec, int l, i
 
 namespace phmm {
 
+
+}  // namespace phmm
+
+namespace phmm {
+
 // ------------------------------------------------------------------------------------
-// Packed FP32 teams: two short pairs per lane, pair A in the x halves and pair B in the
-// y halves of float2 registers, so each cell operation of Eq. 2 issues once (FFMA2 /
-// FMUL2) for two cells and the per-row work of a lane (records, scan, shuffles,
-// checkpoints) serves 2N cells.  Same algorithm as seg_run (unlinked teams only), with
-// one exponent per pair.
+// Helpers of the packed FP32 engines (float2 halves) and of the double-float prep.
 // ------------------------------------------------------------------------------------
 __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
 
@@ -682,200 +653,6 @@ struct PairOut2 {
     SegOut a, b;
 };
 
-template <int N>
-__device__ PairOut2 team_run_x2(const Rec32* __restrict__ recA, int lA, const uint8_t* __restrict__ hapA,
-                                int kA, const Rec32* __restrict__ recB, int lB,
-                                const uint8_t* __restrict__ hapB, int kB, int lmax, int col0, int lt,
-                                int tlast, int nsteps, const PowRow<float>* __restrict__ pow_tab,
-                                int R, uint32_t* __restrict__ status) {
-    using NT = Num<float>;
-    static_assert(N <= 32, "match masks hold 32 columns");
-    uint32_t xA = 0, xC = 0, xG = 0, xT = 0, yA = 0, yC = 0, yG = 0, yT = 0;
-    uint32_t flA = 0, flB = 0;
-    const int nvA = max(0, min(kA - col0, N)), nvB = max(0, min(kB - col0, N));
-#pragma unroll
-    for (int c = 0; c < N; ++c) {
-        const uint32_t bit = 1u << c;
-        if (c < nvA) {
-            const int code = base_code(hapA[col0 + c]);
-            if (code < 0) flA |= PF_BAD;
-            if (code == 0 || code == 4) xA |= bit;
-            if (code == 1 || code == 4) xC |= bit;
-            if (code == 2 || code == 4) xG |= bit;
-            if (code == 3 || code == 4) xT |= bit;
-        }
-        if (c < nvB) {
-            const int code = base_code(hapB[col0 + c]);
-            if (code < 0) flB |= PF_BAD;
-            if (code == 0 || code == 4) yA |= bit;
-            if (code == 1 || code == 4) yC |= bit;
-            if (code == 2 || code == 4) yG |= bit;
-            if (code == 3 || code == 4) yT |= bit;
-        }
-    }
-    float2 M[N], I[N];
-    int EA = 0, EB = 0;
-    float2 ml = f2(0.f, 0.f), sl = f2(0.f, 0.f), dt = f2(0.f, 0.f), gprev = f2(0.f, 0.f);
-    const float2 cinit = f2(lA > 0 && kA > 0 ? (float)(0x1p120 / (double)kA) : 0.f,
-                            lB > 0 && kB > 0 ? (float)(0x1p120 / (double)kB) : 0.f);
-    PairOut2 out;
-    out.a = {0.0, 0, 0};
-    out.b = {0.0, 0, 0};
-    const int lA1 = max(lA, 1) - 1, lB1 = max(lB, 1) - 1;
-    Rec32 ca = load_rec(recA), cb = load_rec(recB);
-    int until = 0;  // rows to the next checkpoint
-    for (int i = 1; i <= lmax; ++i) {
-        Rec32 na = ca, nb = cb;
-        if (i < lmax) {
-            na = load_rec(recA + min(i, lA1));
-            nb = load_rec(recB + min(i, lB1));
-        }
-        const int cA = (int)(ca.meta & META_CODE_MASK), cB = (int)(cb.meta & META_CODE_MASK);
-        const uint32_t mx = cA == 0 ? xA : cA == 1 ? xC : cA == 2 ? xG : cA == 3 ? xT : 0xffffffffu;
-        const uint32_t my = cB == 0 ? yA : cB == 1 ? yC : cB == 2 ? yG : cB == 3 ? yT : 0xffffffffu;
-        if (i <= lA) {
-            if (ca.meta & META_BAD) flA |= PF_BAD;
-            if (ca.meta & META_DEGEN) flA |= PF_DEGEN;
-        }
-        if (i <= lB) {
-            if (cb.meta & META_BAD) flB |= PF_BAD;
-            if (cb.meta & META_DEGEN) flB |= PF_DEGEN;
-        }
-        const float2 pim = f2(ca.pm, cb.pm), pix = f2(ca.px, cb.px), rg = f2(ca.g, cb.g);
-        float2 y = f2(0.f, 0.f), yprev = f2(0.f, 0.f);
-        if (i == 1) {
-#pragma unroll
-            for (int c = 0; c < N; ++c) {
-                const float2 p = f2(((mx >> c) & 1u) ? pim.x : pix.x, ((my >> c) & 1u) ? pim.y : pix.y);
-                M[c] = __fmul2_rn(p, cinit);
-                I[c] = f2(0.f, 0.f);
-                if (c == N - 1) yprev = y;
-                y = __ffma2_rn(rg, y, M[c]);
-            }
-        } else {
-            const float2 ra = f2(ca.a, cb.a), rb = f2(ca.b, cb.b), rmi = f2(ca.mi, cb.mi);
-#pragma unroll
-            for (int c = 0; c < N; ++c) {
-                const float2 S = __ffma2_rn(rb, dt, sl);
-                const float2 u = __ffma2_rn(ra, ml, S);
-                const float2 p = f2(((mx >> c) & 1u) ? pim.x : pix.x, ((my >> c) & 1u) ? pim.y : pix.y);
-                const float2 mn = __fmul2_rn(p, u);
-                const float2 in = __ffma2_rn(rmi, M[c], __fmul2_rn(rg, I[c]));
-                dt = __ffma2_rn(gprev, dt, ml);
-                ml = M[c];
-                sl = I[c];
-                M[c] = mn;
-                I[c] = in;
-                if (c == N - 1) yprev = y;
-                y = __ffma2_rn(rg, y, mn);
-            }
-        }
-        // Deletion scan over the team (both pairs at once).
-        const int gqA = (int)((ca.meta >> META_GCP_SHIFT) & 0xffu), gqB = (int)((cb.meta >> META_GCP_SHIFT) & 0xffu);
-        const PowRow<float>* pa = pow_tab + min(gqA, kMaxPhred);
-        const PowRow<float>* pb = pow_tab + min(gqB, kMaxPhred);
-        float2 sp1[5], sp2[5];
-#pragma unroll
-        for (int s = 0; s < 5; ++s) {
-            sp1[s] = f2(__ldg(&pa->sp1[s]), __ldg(&pb->sp1[s]));
-            sp2[s] = f2(__ldg(&pa->sp2[s]), __ldg(&pb->sp2[s]));
-        }
-        const float2 last1 = f2(__ldg(&pa->last1), __ldg(&pb->last1));
-        const float2 last2 = f2(__ldg(&pa->last2), __ldg(&pb->last2));
-        float2 Z = y;
-#pragma unroll
-        for (int s = 0; s < 5; ++s) {
-            if (s < nsteps) {
-                const int off = 1 << s;
-                const float2 up = shfl_up2(Z, off);
-                const float2 t = __fmul2_rn(up, sp1[s]);
-                if (lt >= off) Z = __ffma2_rn(t, sp2[s], Z);
-            }
-        }
-        float2 Wd = shfl_up2(Z, 1);
-        if (lt == 0) Wd = f2(0.f, 0.f);
-
-        // Checkpoint (per pair exponent).
-        if (until == 0) {
-            until = R;
-            float mA = 0.f, mB = 0.f;
-#pragma unroll
-            for (int c = 0; c < N; ++c) {
-                mA = fmaxf(mA, fmaxf(fabsf(M[c].x), fabsf(I[c].x)));
-                mB = fmaxf(mB, fmaxf(fabsf(M[c].y), fabsf(I[c].y)));
-            }
-            mA = team_max<float>(mA, lt, tlast, nsteps);
-            mB = team_max<float>(mB, lt, tlast, nsteps);
-            const int eA = NT::expo(mA), eB = NT::expo(mB);
-            int sA = 0, sB = 0;
-            if (eA == INT_MAX) {
-                if (i <= lA) flA |= PF_NONFINITE;
-            } else if (eA != INT_MIN) {
-                if (eA > NT::kHi || eA <= NT::kLo) sA = eA - NT::kTarget;
-                if (eA <= NT::kDanger && i <= lA) flA |= PF_DANGER;
-            }
-            if (eB == INT_MAX) {
-                if (i <= lB) flB |= PF_NONFINITE;
-            } else if (eB != INT_MIN) {
-                if (eB > NT::kHi || eB <= NT::kLo) sB = eB - NT::kTarget;
-                if (eB <= NT::kDanger && i <= lB) flB |= PF_DANGER;
-            }
-            if (sA != 0 || sB != 0) {
-                // multiply by 2^-s (two exact steps when one is not representable)
-                const int hA = (-sA) / 2, hB = (-sB) / 2;
-                const float2 f1 = f2(NT::pow2(hA), NT::pow2(hB));
-                const float2 f2_ = f2(NT::pow2(-sA - hA), NT::pow2(-sB - hB));
-#pragma unroll
-                for (int c = 0; c < N; ++c) {
-                    M[c] = __fmul2_rn(__fmul2_rn(M[c], f1), f2_);
-                    I[c] = __fmul2_rn(__fmul2_rn(I[c], f1), f2_);
-                }
-                Wd = __fmul2_rn(__fmul2_rn(Wd, f1), f2_);
-                yprev = __fmul2_rn(__fmul2_rn(yprev, f1), f2_);
-                if (sA != 0 && i <= lA) flA |= PF_RESCALED;
-                if (sB != 0 && i <= lB) flB |= PF_RESCALED;
-                EA += sA;
-                EB += sB;
-            }
-        }
-        --until;
-        const float2 Dlast = __ffma2_rn(__fmul2_rn(Wd, last1), last2, yprev);
-
-        // Eq. 4 when a pair of this warp finishes.
-        if (__any_sync(kFull, i == lA || i == lB)) {
-            double sa = 0.0, sb = 0.0;
-#pragma unroll
-            for (int c = 0; c < N; ++c) {
-                if (c < nvA) sa += (double)M[c].x + (double)I[c].x;
-                if (c < nvB) sb += (double)M[c].y + (double)I[c].y;
-            }
-            sa = team_sum<double>(sa, lt, tlast, nsteps);
-            sb = team_sum<double>(sb, lt, tlast, nsteps);
-            const uint32_t fa = team_or(flA, lt, tlast, nsteps), fb = team_or(flB, lt, tlast, nsteps);
-            if (i == lA) out.a = {sa, EA, fa};
-            if (i == lB) out.b = {sb, EB, fb};
-        }
-        float2 nm = shfl_up2(M[N - 1], 1), ni = shfl_up2(I[N - 1], 1), nd = shfl_up2(Dlast, 1);
-        if (lt == 0) {
-            nm = f2(0.f, 0.f);
-            ni = f2(0.f, 0.f);
-            nd = f2(0.f, 0.f);
-        }
-        ml = nm;
-        sl = ni;
-        dt = nd;
-        gprev = rg;
-        ca = na;
-        cb = nb;
-    }
-    (void)status;
-    return out;
-}
-
-}  // namespace phmm
-
-namespace phmm {
-
 // ------------------------------------------------------------------------------------
 // Lean scalar FP32 team (short pairs, no neighbour link): seg_run's algorithm with the
 // per-row work cut down -- scan powers cached in registers (reloaded only when gcp
@@ -885,7 +662,7 @@ template <int N>
 __device__ SegOut team_run_lean(const Rec32* __restrict__ rec, int l, int lmax,
                                 const uint8_t* __restrict__ hap, int k, int col0, int lt,
                                 int tlast, int nsteps, const PowRow<float>* __restrict__ pow_tab,
-                                int R, Rec32* ring) {
+                                int R) {
     using NT = Num<float>;
     static_assert(N <= 32, "match masks hold 32 columns");
     uint32_t bmA = 0, bmC = 0, bmG = 0, bmT = 0, flags = 0, mflags = 0;
@@ -913,7 +690,6 @@ __device__ SegOut team_run_lean(const Rec32* __restrict__ rec, int l, int lmax,
     out.flags = 0;
     const float cinit = l > 0 && k > 0 ? (float)(0x1p120 / (double)k) : 0.f;
     const int l1 = max(l, 1) - 1;
-    (void)ring;
     Rec32 cur = load_rec(rec);
     int until = 0;
     for (int i = 1; i <= lmax; ++i) {
@@ -1688,7 +1464,7 @@ __device__ PairOut2 team_run_sr2(const Rec32* __restrict__ rec, int l, int lmax,
                                  const uint8_t* __restrict__ hapA, int kA,
                                  const uint8_t* __restrict__ hapB, int kB, int col0, int lt,
                                  int tlast, int nsteps, const PowRow<float>* __restrict__ pow_tab,
-                                 int R, Rec32* ring) {
+                                 int R) {
     using NT = Num<float>;
     static_assert(N <= 16, "two 16-bit match masks per register");
     uint32_t mA = 0, mC = 0, mG = 0, mT = 0, flA = 0, flB = 0, mflags = 0;
@@ -1726,7 +1502,6 @@ __device__ PairOut2 team_run_sr2(const Rec32* __restrict__ rec, int l, int lmax,
     out.a = {0.0, 0, 0};
     out.b = {0.0, 0, 0};
     const int l1 = max(l, 1) - 1;
-    (void)ring;
     Rec32 cur = load_rec(rec);
     int until = 0;
     for (int i = 1; i <= lmax; ++i) {

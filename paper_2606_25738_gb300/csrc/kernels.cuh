@@ -574,7 +574,6 @@ constexpr int kShortThreads = 128;
 template <int N, int MINB>
 __global__ void __launch_bounds__(kShortThreads, MINB)
 k_short_scalar(const BatchHeader* __restrict__ H, const PowRow<float>* __restrict__ pow) {
-    Rec32* const s_ring = nullptr;  // records are prefetched through registers
     const int R = checkpoint_interval<float>(H->dropgrow);
     const uint32_t n_w = H->n_witems;
     const int lane = threadIdx.x & 31;
@@ -595,8 +594,7 @@ k_short_scalar(const BatchHeader* __restrict__ H, const PowRow<float>* __restric
             hap = H->hap_bases + d.hoff;
         }
         const int lmax = (int)__reduce_max_sync(kFull, (unsigned)l);
-        const SegOut o = team_run_lean<N>(rec, l, lmax, hap, k, t.lt * N, t.lt, t.tlast, t.nsteps, pow, R,
-                                          s_ring);
+        const SegOut o = team_run_lean<N>(rec, l, lmax, hap, k, t.lt * N, t.lt, t.tlast, t.nsteps, pow, R);
         if (t.pair != kNoPair && t.lt == 0) write_part(H, t.pair, o);
     }
 }
@@ -665,7 +663,6 @@ k_short_pipe2(const BatchHeader* __restrict__ H, const PowRow<float>* __restrict
 template <int N, int MINB>
 __global__ void __launch_bounds__(kShortThreads, MINB)
 k_short_packed(const BatchHeader* __restrict__ H, const PowRow<float>* __restrict__ pow) {
-    Rec32* const s_ring = nullptr;  // records are prefetched through registers
     const int R = checkpoint_interval<float>(H->dropgrow);
     const uint32_t n_w = H->n_witems2;
     const int lane = threadIdx.x & 31;
@@ -693,7 +690,7 @@ k_short_packed(const BatchHeader* __restrict__ H, const PowRow<float>* __restric
         }
         const int lmax = (int)__reduce_max_sync(kFull, (unsigned)l);
         const PairOut2 o = team_run_sr2<N>(rec, l, lmax, hap, k, hap2, k2, t.lt * N, t.lt, t.tlast,
-                                           t.nsteps, pow, R, s_ring);
+                                           t.nsteps, pow, R);
         if (t.lt == 0) {
             if (t.pair != kNoPair) write_part(H, t.pair, o.a);
             if (t.pair2 != kNoPair) write_part(H, t.pair2, o.b);

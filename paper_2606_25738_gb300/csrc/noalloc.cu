@@ -164,7 +164,7 @@ __global__ void __launch_bounds__(128) k_na_forward(const uint8_t* __restrict__ 
             continue;
         }
         const SegOut o = team_run_lean<kNaN>(rec + roff, l, l, hap_bases + hoff, k, lane * kNaN, lane, 31, 5,
-                                             pw, R, nullptr);
+                                             pw, R);
         if (lane == 0) {
             uint8_t f = 0;
             double v;
