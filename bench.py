@@ -186,7 +186,7 @@ def _serve_leg(dev, args):
     from paper_2606_25738_gb300 import phmm
     from paper_2606_25738_gb300 import serving
     pool = serving.make_pool(args.serve_pool, seed=0)
-    with phmm.Context(device=dev, precision="fp32", max_inflight=3, variant="scalar", cols_per_lane=32) as c:
+    with phmm.Context(device=dev, precision="fp32", max_inflight=3, flags=phmm.F_NO_TUNE) as c:
         r = serving.run(c, pool, rate=args.serve_rate, duration=args.serve_seconds, drain_s=60.0,
                         max_inflight_epochs=3)
     r["pool"] = "%d seeded region requests, mean %.3g cells" % (len(pool), sum(p[1] for p in pool) / len(pool))
@@ -347,11 +347,15 @@ def run_ours(args):
     fp64 = (flg[pick] & 0x5) != 0
     err = float(np.max(np.abs(res[pick] - ref)[~fp64])) if (~fp64).any() else 0.0
     clocks = clk.summary()
+    # the dominant kernel is the short-team kernel the plan ran; its DRAM bytes per launch
+    # come from an ncu capture of that same kernel (null for any other kernel)
+    sk = int(sts[-1]["short_kernel"])
+    kname = phmm.SHORT_KERNELS[sk] if 0 <= sk < len(phmm.SHORT_KERNELS) else "none"
     traffic = None
     tfile = os.path.join(ROOT, "profiles", "forward_traffic.json")
     if os.path.exists(tfile):
         try:
-            traffic = json.load(open(tfile)).get("bytes_per_launch")
+            traffic = json.load(open(tfile)).get(kname, {}).get("bytes_per_launch")
         except Exception:
             traffic = None
     line = {
@@ -365,7 +369,7 @@ def run_ours(args):
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                      "frac": achieved / peak_tflops, "traffic": traffic,
-                     "kernel": "FP32 forward branches (k_short_pipe short teams; k_forward multi-warp pairs)",
+                     "kernel": "FP32 forward branches; short teams on %s" % kname,
                      "flop_per_cell": 12,
                      "peak_note": "2 x 128 FP32 lanes x %d SMs x %.0f MHz (max SM clock, MEASURED_PEAKS)" % (info["sms"], sm_max)},
         "cpu_baseline": {"value": cpu_v, "unit": "GCUPS", "cores": cores, "kind": "oracle",

@@ -37,7 +37,7 @@
 extern "C" {
 #endif
 
-#define PHMM_ABI_VERSION 1
+#define PHMM_ABI_VERSION 2
 
 /* Opaque context: device arenas, stream, captured graphs, pending tickets. */
 typedef struct phmm_ctx phmm_ctx;
@@ -75,6 +75,9 @@ typedef enum {
 #define PHMM_F_LONG_LEAN 0x10u
 #define PHMM_F_LONG_PIPE32 0x20u
 #define PHMM_F_LONG_PIPE24 0x40u
+/* No measured tuning: the built-in cost model and defaults choose the kernels.  For
+ * serving, where nearly every batch (epoch) has a new shape and tuning would re-run it. */
+#define PHMM_F_NO_TUNE 0x80u
 
 typedef struct {
     int device;               /* CUDA device ordinal */
@@ -152,6 +155,15 @@ typedef struct {
     uint32_t kernel_launches; /* kernels launched for the ticket */
     uint32_t status_bits;     /* device status word (0 = clean) */
     float ms_host;            /* host time of phmm_submit_batch's planning and enqueue */
+    /* FP32 kernels the plan ran (-1: that branch had no work or the precision is FP64):
+     * short_kernel = scalar-team variant 0..8 (k_short_scalar<32,4>, <24,4>, <24,5>,
+     * <16,6>, k_short_pipe<32,3>, <24,4>, <16,4>, k_short_pipe2<32,3>, <24,4>);
+     * packed_kernel = packed-team variant 0..1 (k_short_packed<12,4>, <16,3>);
+     * long_kernel = multi-warp kind 0..2 (lean k_forward<32>, k_forward_pipe<32,12>,
+     * k_forward_pipe<24,16>). */
+    int32_t short_kernel;
+    int32_t packed_kernel;
+    int32_t long_kernel;
 } phmm_stats;
 
 /* Create a context on cfg->device.  *out receives the handle.  PHMM_EINVAL on a bad

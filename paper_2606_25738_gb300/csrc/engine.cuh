@@ -1045,7 +1045,9 @@ __device__ SegOut team_run_pipe2(const Rec32J* __restrict__ rec, int l, int lmax
     for (int c = 0; c < N; ++c) {
         if (c < nvalid) {
             const int code = base_code(hap[col0 + c]);
-            const uint32_t bit = 1u << c;
+            // match bits in the order phase B reads them: bit 2q for column q of the first
+            // half, bit 2q + 1 for column H + q of the second
+            const uint32_t bit = 1u << (c < H ? 2 * c : 2 * (c - H) + 1);
             if (code < 0) flags |= PF_BAD;
             if (code == 0 || code == 4) bmA |= bit;
             if (code == 1 || code == 4) bmC |= bit;
@@ -1098,8 +1100,8 @@ __device__ SegOut team_run_pipe2(const Rec32J* __restrict__ rec, int l, int lmax
         if (i == 1) {
 #pragma unroll
             for (int q = 0; q < H; ++q) {
-                const float2 mn = make_float2((((mask >> q) & 1u) ? pim : pix) * cinit,
-                                              (((mask >> (q + H)) & 1u) ? pim : pix) * cinit);
+                const float2 mn = make_float2((((mask >> (2 * q)) & 1u) ? pim : pix) * cinit,
+                                              (((mask >> (2 * q + 1)) & 1u) ? pim : pix) * cinit);
                 M2[q] = mn;
                 J2[q] = make_float2(0.f, 0.f);
                 if (q == H - 1) yp2 = y2;
@@ -1112,8 +1114,8 @@ __device__ SegOut team_run_pipe2(const Rec32J* __restrict__ rec, int l, int lmax
                 const float2 u2 = ffma2_sel<PACKED>(rb2, dt2, U2[q]);
                 dt2 = ffma2_sel<PACKED>(gp2, dt2, ml2);
                 ml2 = M2[q];
-                const float2 p2 = make_float2(((mask >> q) & 1u) ? pim : pix,
-                                              ((mask >> (q + H)) & 1u) ? pim : pix);
+                const float2 p2 = make_float2(((mask >> (2 * q)) & 1u) ? pim : pix,
+                                              ((mask >> (2 * q + 1)) & 1u) ? pim : pix);
                 const float2 mn = fmul2_sel<PACKED>(p2, u2);
                 M2[q] = mn;
                 if (q == H - 1) yp2 = y2;

@@ -929,8 +929,9 @@ int phmm_submit_batch(phmm_ctx* ctx, const phmm_batch* b, uint64_t* ticket) {
                 for (uint32_t p = 0; p < np; ++p)
                     if (K[p] <= wmax) short_cells += (uint64_t)L[p] * K[p];
                 const uint64_t long_cells = cells - short_cells;
-                tune_short = cand.size() > 1 && short_cells >= kTuneMinCells && short_cells * 10 >= cells;
-                tune_long = long_kinds_of(ctx->cfg).size() > 1 && long_cells >= kTuneMinCells &&
+                const bool may_tune = !(ctx->cfg.flags & PHMM_F_NO_TUNE);
+                tune_short = may_tune && cand.size() > 1 && short_cells >= kTuneMinCells && short_cells * 10 >= cells;
+                tune_long = may_tune && long_kinds_of(ctx->cfg).size() > 1 && long_cells >= kTuneMinCells &&
                             long_cells * 10 >= cells;
                 tune_sig = sig;
                 tune_cand = cand;
@@ -1186,6 +1187,12 @@ int phmm_submit_batch(phmm_ctx* ctx, const phmm_batch* b, uint64_t* ticket) {
     S->st.n_long = P.n_long;
     S->st.cols_per_lane = (uint32_t)(P.NP > 0 ? P.NP : N);
     S->st.kernel_launches = launches;
+    {
+        const bool f32 = ctx->cfg.precision != PHMM_PREC_FP64;
+        S->st.short_kernel = f32 && !P.witems.empty() ? P.scal_id : -1;
+        S->st.packed_kernel = f32 && !P.witems2.empty() ? P.pack_id : -1;
+        S->st.long_kernel = f32 && !P.citems.empty() ? P.long_kind : -1;
+    }
     S->host_status = P.n_too_long ? PHMM_EINVAL : PHMM_OK;
     S->plan_valid = true;
     S->plan_hash = hsh;

@@ -21,7 +21,7 @@ PHMM_ETIMEOUT, PHMM_ECANCELED, PHMM_ENOTFOUND = -5, -6, -7
 PREC = {"fp32": 0, "fp64": 1, "fp32_only": 2}
 VARIANTS = {"auto": 0, "packed": 1, "scalar": 2, "lean": 3, "pipe": 4, "pipe2": 5}
 F_NO_GRAPH, F_LAUNCH_PER_PAIR, F_FORCE_RESCUE = 0x1, 0x2, 0x4
-F_LONG_LEAN, F_LONG_PIPE32, F_LONG_PIPE24 = 0x10, 0x20, 0x40
+F_LONG_LEAN, F_LONG_PIPE32, F_LONG_PIPE24, F_NO_TUNE = 0x10, 0x20, 0x40, 0x80
 PAIR_RESCUED, PAIR_RESCALED, PAIR_FP64, PAIR_ERROR = 0x1, 0x2, 0x4, 0x80
 PAIR_DANGER, PAIR_NONFINITE, PAIR_SMALL_SUM, PAIR_DEGENERATE = 0x8, 0x10, 0x20, 0x40
 
@@ -58,13 +58,25 @@ class Batch(ctypes.Structure):
                 ("inputs_on_device", ctypes.c_int), ("outputs_on_device", ctypes.c_int)]
 
 
+ABI_VERSION = 2  # PHMM_ABI_VERSION of include/phmm.h
+
+# Kernel names behind phmm_stats.short_kernel / packed_kernel / long_kernel.
+SHORT_KERNELS = ["k_short_scalar<32, 4>", "k_short_scalar<24, 4>", "k_short_scalar<24, 5>",
+                 "k_short_scalar<16, 6>", "k_short_pipe<32, 3>", "k_short_pipe<24, 4>",
+                 "k_short_pipe<16, 4>", "k_short_pipe2<32, 3, 1>", "k_short_pipe2<24, 4, 1>"]
+PACKED_KERNELS = ["k_short_packed<12, 4>", "k_short_packed<16, 3>"]
+LONG_KERNELS = ["k_forward<float, 32, 0>", "k_forward_pipe<32, 12>", "k_forward_pipe<24, 16>"]
+
+
 class Stats(ctypes.Structure):
     _fields_ = [("cells", ctypes.c_uint64), ("n_pairs", ctypes.c_uint32),
                 ("n_rescued", ctypes.c_uint32), ("n_long", ctypes.c_uint32),
                 ("cols_per_lane", ctypes.c_uint32), ("ms_total", ctypes.c_float),
                 ("ms_forward", ctypes.c_float), ("ms_rescue", ctypes.c_float),
                 ("ms_h2d", ctypes.c_float), ("kernel_launches", ctypes.c_uint32),
-                ("status_bits", ctypes.c_uint32), ("ms_host", ctypes.c_float)]
+                ("status_bits", ctypes.c_uint32), ("ms_host", ctypes.c_float),
+                ("short_kernel", ctypes.c_int32), ("packed_kernel", ctypes.c_int32),
+                ("long_kernel", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -88,6 +100,9 @@ def _load() -> ctypes.CDLL:
         raise RuntimeError("libphmm.so is not built (%s); run __graft_entry__.build() or "
                            "python -m paper_2606_25738_gb300.build" % LIB_PATH)
     lib = ctypes.CDLL(LIB_PATH)
+    if lib.phmm_abi_version() != ABI_VERSION:
+        raise RuntimeError("libphmm.so has ABI version %d, this binding expects %d: rebuild it"
+                           % (lib.phmm_abi_version(), ABI_VERSION))
     lib.phmm_create.argtypes = [ctypes.POINTER(Config), ctypes.POINTER(ctypes.c_void_p)]
     lib.phmm_submit_batch.argtypes = [ctypes.c_void_p, ctypes.POINTER(Batch), ctypes.POINTER(ctypes.c_uint64)]
     lib.phmm_poll.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int]

@@ -8,7 +8,8 @@ lagging submitter counts too.  Request data comes from a seeded pool of distinct
 regions (request i uses pool entry i mod pool size).
 
 All scheduling, admission and batching happen in the library; this module only drives
-arrivals and collects timings.
+arrivals and collects timings.  Give the context PHMM_F_NO_TUNE: every epoch is a batch of
+a new shape, and measured tuning would re-run each one.
 """
 from __future__ import annotations
 

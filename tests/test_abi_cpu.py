@@ -86,3 +86,33 @@ def test_null_arguments(lib):
     assert so.phmm_submit_batch(None, None, ctypes.byref(t)) == lib.PHMM_EINVAL
     assert so.phmm_poll(None, 1, 0) == lib.PHMM_EINVAL
     so.phmm_destroy(None)
+
+
+def test_ctypes_structs_match_header(lib, tmp_path):
+    """The binding's ctypes structs have the C header's sizes and field offsets (gcc)."""
+    import ctypes
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    assert lib.ABI_VERSION == lib.library().phmm_abi_version()
+    pairs = [("phmm_config", lib.Config), ("phmm_batch", lib.Batch), ("phmm_stats", lib.Stats),
+             ("phmm_server_config", lib.ServerConfig), ("phmm_server_stats", lib.ServerStats)]
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "phmm.h"', "int main(void) {"]
+    for cname, cls in pairs:
+        lines.append('printf("%%zu\\n", sizeof(%s));' % cname)
+        for f, _ in cls._fields_:
+            lines.append('printf("%%zu\\n", offsetof(%s, %s));' % (cname, f))
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True,
+                                          check=True).stdout.split()]
+    want = []
+    for _, cls in pairs:
+        want.append(ctypes.sizeof(cls))
+        want += [getattr(cls, f).offset for f, _ in cls._fields_]
+    assert got == want

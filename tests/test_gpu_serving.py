@@ -104,7 +104,7 @@ def test_open_loop_run(phmm):
     from paper_2606_25738_gb300 import serving
     pool = serving.make_pool(8, seed=5, reads_range=(4, 32), haps_range=(2, 6), long_frac=0.2,
                              long_range=(1000, 3000))
-    with phmm.Context(max_inflight=2, variant="scalar", cols_per_lane=32) as ctx:
+    with phmm.Context(max_inflight=2, flags=phmm.F_NO_TUNE) as ctx:
         r = serving.run(ctx, pool, rate=40.0, duration=1.5, drain_s=60.0)
     assert r["enqueued"] == r["arrivals"] and r["completed"] == r["enqueued"]
     assert r["p50_ms"] > 0 and r["p99_ms"] >= r["p50_ms"] and r["gcups"] > 0
