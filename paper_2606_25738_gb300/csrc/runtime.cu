@@ -750,10 +750,13 @@ int phmm_create(const phmm_config* cfg, phmm_ctx** out) {
     ctx->occ_longk[0] = occupancy_forward32_long();
     ctx->occ_longk[1] = occupancy_forward32_long_pipe(1);
     ctx->occ_longk[2] = occupancy_forward32_long_pipe(2);
-    if (getenv("PHMM_DEBUG"))
-        fprintf(stderr, "phmm: sms %d occupancy packed %d %d scalar %d %d %d %d long %d fp64 %d\n",
-                ctx->sms, ctx->occ_packed[0], ctx->occ_packed[1], ctx->occ_scalar[0], ctx->occ_scalar[1],
-                ctx->occ_scalar[2], ctx->occ_scalar[3], ctx->occ_longk[1], ctx->occ64);
+    if (getenv("PHMM_DEBUG")) {
+        fprintf(stderr, "phmm: sms %d occupancy packed %d %d long %d %d %d fp64 %d scalar", ctx->sms,
+                ctx->occ_packed[0], ctx->occ_packed[1], ctx->occ_longk[0], ctx->occ_longk[1],
+                ctx->occ_longk[2], ctx->occ64);
+        for (int q = 0; q < kNumScalar; ++q) fprintf(stderr, " %d", ctx->occ_scalar[q]);
+        fprintf(stderr, "\n");
+    }
     {
         std::vector<PowRow<double>> v;
         build_pow_table<double>(kN64, v);
