@@ -871,7 +871,7 @@ __device__ SegOut team_run_pipe(const Rec32J* __restrict__ rec, int l, int lmax,
         const uint32_t meta = cur.meta;
         mflags |= meta;
         const int gq = (int)((meta >> META_GCP_SHIFT) & 0xffu);
-        if (__any_sync(kFull, gq != gcp)) {  // warp-uniform: every lane reloads its own row
+        if (gq != gcp) {
             const PowRow<float>* pr = pow_tab + min(gq, kMaxPhred);
 #pragma unroll
             for (int s = 0; s < 5; ++s) {
@@ -955,7 +955,7 @@ __device__ SegOut team_run_pipe(const Rec32J* __restrict__ rec, int l, int lmax,
         }
         float zz = __shfl_up_sync(kFull, Z, 2);
         if (lt < 2) zz = 0.f;
-        if (__any_sync(kFull, until == 0)) {  // (until is the same in every lane)
+        if (until == 0) {
             // checkpoint: M holds row i, J and U row i+1 (linear in row i, so they take the
             // same power of two); U was formed before this test, which the headroom of the
             // range bounds covers
