@@ -71,10 +71,14 @@ typedef enum {
 #define PHMM_F_FORCE_RESCUE 0x4u    /* flag every pair for the FP64 rescue pass (tests) */
 /* FP32 multi-warp pairs (k > 1024): force one kernel instead of the tuner's choice --
  * the lean engine (16-warp CTAs), the pipelined engine with 32 columns per lane
- * (12-warp CTAs) or with 24 columns per lane (16-warp CTAs).  At most one may be set. */
+ * (12-warp CTAs) or with 24 columns per lane (16-warp CTAs), or the serial one below.
+ * At most one may be set. */
 #define PHMM_F_LONG_LEAN 0x10u
 #define PHMM_F_LONG_PIPE32 0x20u
 #define PHMM_F_LONG_PIPE24 0x40u
+/* ... or one warp per multi-warp pair, running its 1024-column strips one after
+ * another (no warp waits on another; for batches with many long pairs). */
+#define PHMM_F_LONG_SERIAL 0x100u
 /* No measured tuning: the built-in cost model and defaults choose the kernels.  For
  * serving, where nearly every batch (epoch) has a new shape and tuning would re-run it. */
 #define PHMM_F_NO_TUNE 0x80u
@@ -159,8 +163,8 @@ typedef struct {
      * short_kernel = scalar-team variant 0..8 (k_short_scalar<32,4>, <24,4>, <24,5>,
      * <16,6>, k_short_pipe<32,3>, <24,4>, <16,4>, k_short_pipe2<32,3>, <24,4>);
      * packed_kernel = packed-team variant 0..1 (k_short_packed<12,4>, <16,3>);
-     * long_kernel = multi-warp kind 0..2 (lean k_forward<32>, k_forward_pipe<32,12>,
-     * k_forward_pipe<24,16>). */
+     * long_kernel = multi-warp kind 0..3 (lean k_forward<32>, k_forward_pipe<32,12>,
+     * k_forward_pipe<24,16>, k_forward_serial<32,3>). */
     int32_t short_kernel;
     int32_t packed_kernel;
     int32_t long_kernel;

@@ -1233,11 +1233,18 @@ __device__ SegOut team_run_pipe2(const Rec32J* __restrict__ rec, int l, int lmax
 // boundary of the previous strip), the checkpoint keeps E >= E_left, the left values are
 // brought into this segment's scale, and lane 31 hands this segment's last column on.
 // The segment carry enters lane t's previous column with the power g^(N t - 1).
+//
+// SER: the strips of a pair run one after another on the same warp.  The left strip is
+// complete before this one starts, so its boundary (one float4 per row: M, J, D-hat and
+// the exponent E of its last column) is read without waiting: every 32 rows each lane
+// loads one row of it, and row i comes from lane (i - 1) mod 32 by shuffle.  Lane 31
+// stores this strip's boundary row by row for the next strip.
 // ------------------------------------------------------------------------------------
-template <int N>
+template <int N, bool SER = false>
 __device__ SegOut seg_link_pipe(const Rec32J* __restrict__ rec, int l, const uint8_t* __restrict__ hap,
                                 int k, int col0, int lane, const PowRow<float>* __restrict__ pow_tab,
-                                const PipeRange& rng, const SmemLink& link, uint32_t* __restrict__ status) {
+                                const PipeRange& rng, const SmemLink& link, uint32_t* __restrict__ status,
+                                const float4* sin = nullptr, float4* sout = nullptr) {
     using NT = Num<float>;
     static_assert(N <= 32, "match masks hold 32 columns");
     uint32_t bmA = 0, bmC = 0, bmG = 0, bmT = 0, flags = rng.ok ? 0u : PF_DEGEN, mflags = 0;
@@ -1268,6 +1275,7 @@ __device__ SegOut seg_link_pipe(const Rec32J* __restrict__ rec, int l, const uin
     const int l1 = max(l, 1) - 1;
     Rec32J cur = load_recj(rec);
     int until = 0;
+    float4 bnd4 = make_float4(0.f, 0.f, 0.f, 0.f);  // SER: this lane's row of the left boundary
     for (int i = 1; i <= l; ++i) {
         Rec32J nxt = cur;
         if (i < l) nxt = load_recj(rec + min(i, l1));
@@ -1363,20 +1371,36 @@ __device__ SegOut seg_link_pipe(const Rec32J* __restrict__ rec, int l, const uin
         // the left segment's last column of row i: lane 0 waits for it, then the whole
         // (converged) warp takes it
         float lM = 0.f, lJ = 0.f, lD = 0.f;
-        int e_in = INT_MIN;
-        if (has_left && lane == 0) {
-            const bool ok = link.in_g ? link_recv_g<float>(link.in_g, i, lM, lJ, lD, e_in)
-                                      : link_recv<float>(link, i, lM, lJ, lD, e_in);
-            if (!ok) {
-                flags |= PF_TIMEOUT;
-                atomicOr(status, ST_TIMEOUT);
+        int Eleft = INT_MIN;
+        if constexpr (SER) {
+            if (has_left) {
+                if (((i - 1) & 31) == 0) {  // next 32 rows of the finished left strip
+                    const int r = i + lane;
+                    // L2 load (.cg): written earlier in this launch by this warp's lane 31
+                    bnd4 = r <= l ? __ldcg(sin + (r - 1)) : make_float4(0.f, 0.f, 0.f, __int_as_float(INT_MIN));
+                }
+                const int src = (i - 1) & 31;
+                lM = __shfl_sync(kFull, bnd4.x, src);
+                lJ = __shfl_sync(kFull, bnd4.y, src);
+                lD = __shfl_sync(kFull, bnd4.z, src);
+                Eleft = __float_as_int(__shfl_sync(kFull, bnd4.w, src));
             }
+        } else {
+            int e_in = INT_MIN;
+            if (has_left && lane == 0) {
+                const bool ok = link.in_g ? link_recv_g<float>(link.in_g, i, lM, lJ, lD, e_in)
+                                          : link_recv<float>(link, i, lM, lJ, lD, e_in);
+                if (!ok) {
+                    flags |= PF_TIMEOUT;
+                    atomicOr(status, ST_TIMEOUT);
+                }
+            }
+            __syncwarp();
+            lM = __shfl_sync(kFull, lM, 0);
+            lJ = __shfl_sync(kFull, lJ, 0);
+            lD = __shfl_sync(kFull, lD, 0);
+            Eleft = __shfl_sync(kFull, e_in, 0);
         }
-        __syncwarp();
-        lM = __shfl_sync(kFull, lM, 0);
-        lJ = __shfl_sync(kFull, lJ, 0);
-        lD = __shfl_sync(kFull, lD, 0);
-        const int Eleft = __shfl_sync(kFull, e_in, 0);
         // checkpoint (same rows in every segment of the pair): power-of-two rescaling,
         // with E >= E_left so that left values only ever scale down
         int Enew = E;
@@ -1440,7 +1464,9 @@ __device__ SegOut seg_link_pipe(const Rec32J* __restrict__ rec, int l, const uin
         if (has_right && lane == 31) {
             // D-hat at the segment's last column
             const float dl = fmaf(Wseg * qb1, qb2, fmaf(Wd * last1, last2, yprev));
-            if (link.out_g) {
+            if constexpr (SER) {
+                __stcg(sout + (i - 1), make_float4(M[N - 1], jl, dl, __int_as_float(E)));
+            } else if (link.out_g) {
                 link_send_g<float>(link.out_g, i, M[N - 1], jl, dl, E);
             } else if (!link_send<float>(link, i, M[N - 1], jl, dl, E)) {
                 flags |= PF_TIMEOUT;

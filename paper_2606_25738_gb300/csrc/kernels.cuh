@@ -540,6 +540,53 @@ k_forward_pipe(const BatchHeader* __restrict__ H, const PowRow<float>* __restric
     }
 }
 
+// Multi-warp pairs one warp at a time (long kind 3): each warp takes a whole pair and
+// runs its strips of 32 N columns one after another (seg_link_pipe<N, true>), strip s
+// reading the boundary strip s - 1 left in this warp's scratch.  No warp ever waits on
+// another; the pair's S strips leave S partials, combined by the finalize kernel as for
+// CTA strips.
+template <int N, int MINB>
+__global__ void __launch_bounds__(128, MINB)
+k_forward_serial(const BatchHeader* __restrict__ H, const PowRow<float>* __restrict__ pow) {
+    const PipeRange rng = pipe_range(H->dropgrow);
+    const uint32_t n_c = H->n_citems;
+    const int lane = threadIdx.x & 31;
+    const uint32_t gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (gw >= H->sbnd_warps) return;  // no scratch for this warp (grid larger than planned)
+    float4* buf0 = H->sbnd + (size_t)gw * 2 * H->sbnd_rows;
+    float4* buf1 = buf0 + H->sbnd_rows;
+    SmemLink L;
+    L.in_ring = L.out_ring = nullptr;
+    L.my_cons = L.next_cons = nullptr;
+    L.in_g = L.out_g = nullptr;
+    for (;;) {
+        uint32_t wi = 0;
+        if (lane == 0) wi = atomicAdd(&H->counters[0], 1u);
+        wi = __shfl_sync(kFull, wi, 0);
+        if (wi >= n_c) break;
+        const CtaPair cp = H->cpairs[H->citems[wi].first];
+        const PairDesc d = H->desc[cp.pair];
+        const uint32_t S = cp.nstrip;
+        for (uint32_t s = 0; s < S; ++s) {
+            L.has_left = s > 0;
+            L.has_right = s + 1 < S;
+            const float4* in = (s & 1u) ? buf0 : buf1;  // what strip s - 1 wrote
+            float4* outb = (s & 1u) ? buf1 : buf0;
+            const int c0 = (int)(s * 32u * N) + lane * N;
+            const SegOut o = seg_link_pipe<N, true>(H->rec32j + d.roff, (int)d.l, H->hap_bases + d.hoff,
+                                                    (int)d.k, c0, lane, pow, rng, L, H->status, in, outb);
+            __syncwarp();  // this strip's boundary stores before the next strip's loads
+            if (lane == 0) {
+                Partial p;
+                p.S = o.S;
+                p.E = o.E;
+                p.flags = o.flags | PF_DONE;
+                write_strip_part(H, cp.pair, s, S, cp.extra_base, p);
+            }
+        }
+    }
+}
+
 // Team lookup of a warp item: this lane's team (first lane, size, pairs) and the scan
 // steps of the widest team.
 struct TeamOf {

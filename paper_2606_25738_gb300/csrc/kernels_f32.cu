@@ -113,6 +113,7 @@ __global__ void __launch_bounds__(256) k_prep32_first(const BatchHeader* __restr
 template __global__ void k_forward<float, kNLong32, false>(const BatchHeader*, const PowRow<float>*);
 template __global__ void k_forward_pipe<32, kCtaWarpsPipe>(const BatchHeader*, const PowRow<float>*);
 template __global__ void k_forward_pipe<24, kCtaWarps>(const BatchHeader*, const PowRow<float>*);
+template __global__ void k_forward_serial<32, 3>(const BatchHeader*, const PowRow<float>*);
 template __global__ void k_short_scalar<32, 4>(const BatchHeader*, const PowRow<float>*);
 template __global__ void k_short_scalar<24, 4>(const BatchHeader*, const PowRow<float>*);
 template __global__ void k_short_scalar<24, 5>(const BatchHeader*, const PowRow<float>*);
@@ -183,7 +184,8 @@ void launch_forward32_long(const BatchHeader* H, const void* pow, int grid, cuda
 
 void launch_forward32_long_pipe(int kind, const BatchHeader* H, const void* pow, int grid, cudaStream_t s) {
     const PowRow<float>* p = static_cast<const PowRow<float>*>(pow);
-    if (kind == 2) k_forward_pipe<24, kCtaWarps><<<grid, kCtaWarps * 32, 0, s>>>(H, p);
+    if (kind == 3) k_forward_serial<32, 3><<<grid, kSerialThreads, 0, s>>>(H, p);
+    else if (kind == 2) k_forward_pipe<24, kCtaWarps><<<grid, kCtaWarps * 32, 0, s>>>(H, p);
     else k_forward_pipe<32, kCtaWarpsPipe><<<grid, kCtaWarpsPipe * 32, 0, s>>>(H, p);
 }
 
@@ -249,7 +251,9 @@ int occupancy_forward32_long() {
 
 int occupancy_forward32_long_pipe(int kind) {
     int b = 0;
-    if (kind == 2)
+    if (kind == 3)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_forward_serial<32, 3>, kSerialThreads, 0);
+    else if (kind == 2)
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_forward_pipe<24, kCtaWarps>, kCtaWarps * 32, 0);
     else
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_forward_pipe<32, kCtaWarpsPipe>, kCtaWarpsPipe * 32, 0);

@@ -187,6 +187,9 @@ struct BatchHeader {
     uint64_t n_bnd_words;
     unsigned long long *rbnd;   // rescue / single-launch scratch: 2 boundaries per CTA
     uint64_t rbnd_words_per_cta;
+    float4 *sbnd;            // serial multi-warp pairs: 2 strip boundaries of sbnd_rows rows
+    uint32_t sbnd_rows;      // per resident warp of k_forward_serial (not cleared)
+    uint32_t sbnd_warps;     // warps the scratch holds (the kernel's grid x warps per CTA)
     uint32_t l_max;          // longest read of the batch
     // outputs
     double *out;             // n_pairs log10 L

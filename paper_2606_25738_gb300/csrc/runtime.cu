@@ -96,6 +96,7 @@ struct Plan {
     uint64_t bnd_words = 0;   // strip boundary buffer (tagged words)
     uint32_t n_extra = 0;     // extra partial slots (strips 1.. of wide pairs)
     int long_kind = 0;        // FP32 multi-warp kernel (launch.h: kLongN / kLongCW)
+    uint32_t serial_rows = 0; // long kind 3: longest read among the serial pairs
 };
 
 // Cost model constants (issue slots): per lane and cell of a row, and per lane and row
@@ -183,7 +184,7 @@ static void pack_teams(std::vector<Team>& run_teams, std::vector<uint32_t>& run_
 // CTA, packed best-fit into CTAs of CW warps (wider pairs: strips of CW warps).  Items
 // are ordered longest first.
 void make_plan(const uint32_t* l, const uint32_t* k, const uint32_t* pr, uint32_t n, int Ns, int NP,
-               int Nl, Plan& P, int kw = 4, int CW = kCtaWarps) {
+               int Nl, Plan& P, int kw = 4, int CW = kCtaWarps, bool serial = false) {
     P = Plan();
     P.N = Ns;
     P.NP = NP;
@@ -255,6 +256,27 @@ void make_plan(const uint32_t* l, const uint32_t* k, const uint32_t* pr, uint32_
         cp.bnd_out = kNoBnd;
         return cp;
     };
+    if (serial) {
+        // one item per pair, largest first: a warp runs its W strips of 32 Nl columns in
+        // order (strip s >= 1 leaves its partial at extra_base + s - 1)
+        for (uint32_t p : lo) {
+            const uint32_t Wt = W_of(p);
+            CtaPair cp = cpair(p, 0, 1);
+            cp.nstrip = Wt;
+            if (Wt > 1) {
+                cp.extra_base = n + P.n_extra;
+                P.n_extra += Wt - 1;
+            }
+            CtaItem it;
+            it.first = (uint32_t)P.cpairs.size();
+            it.n = 1;
+            P.cpairs.push_back(cp);
+            P.citems.push_back(it);
+            P.serial_rows = std::max(P.serial_rows, l[p]);
+            P.cost += (double)l[p] * Wt * 32.0 * (Nl * kCellCost + kRowCost);
+        }
+        return;
+    }
     // Units: a pair that fits one CTA, or one strip of a wider pair (S = ceil(W / CW)
     // strips of near-equal width, the wider ones first).  Units are best-fit packed into
     // CTAs of CW warps, in runs of similar read length (the CTA waits for its longest
@@ -419,6 +441,8 @@ struct Slot {
     DevBuf small;  // counters[8], status[1], dropgrow[4]
     DevBuf bnd;    // strip boundaries of the batch
     DevBuf rbnd;   // rescue / launch-per-pair boundary scratch
+    DevBuf sbnd;   // serial multi-warp pairs: two boundaries per resident warp
+    uint32_t sbnd_warps = 0, sbnd_rows = 0;  // what sbnd holds for the current plan
     DevBuf hdr;
     HostBuf h_out, h_oflags, h_small, h_roff, h_hoff, h_pr, h_ph;
     BatchHeader hh;
@@ -461,7 +485,7 @@ struct phmm_ctx {
     DevBuf scan_row;                        // scan test: one PowRow<float> (global memory)
     DevBuf pow32[5];                        // N = 12, 16, 20, 24 (packed short), 32 (long)
     DevBuf pow64;
-    int occ_packed[kNumPacked] = {}, occ_scalar[kNumScalar] = {}, occ_longk[kNumLong] = {1, 1, 1}, occ64 = 1;
+    int occ_packed[kNumPacked] = {}, occ_scalar[kNumScalar] = {}, occ_longk[kNumLong] = {1, 1, 1, 1}, occ64 = 1;
     std::map<uint64_t, std::array<int, 3>> tuned;  // batch signature -> (scalar id, packed id, long kind)
     uint64_t inflight_foot = 0;             // sum of pending slots' footprints
     bool dead = false;
@@ -489,7 +513,7 @@ int pow_index(int N) { return N == 12 ? 0 : N == 16 ? 1 : N == 20 ? 2 : N == 24 
 DevBuf* arena_bufs(Slot& S, int i) {
     DevBuf* d[] = {&S.in_bases, &S.in_bq, &S.in_iq, &S.in_dq, &S.in_gq, &S.in_hap, &S.in_roff, &S.in_hoff,
                    &S.in_pr, &S.in_ph, &S.desc, &S.rec32, &S.rec32j, &S.rec64, &S.teams, &S.witems, &S.witems2,
-                   &S.cpairs, &S.citems, &S.parts, &S.out, &S.oflags, &S.rescue, &S.bnd, &S.rbnd};
+                   &S.cpairs, &S.citems, &S.parts, &S.out, &S.oflags, &S.rescue, &S.bnd, &S.rbnd, &S.sbnd};
     return i < (int)(sizeof(d) / sizeof(d[0])) ? d[i] : nullptr;
 }
 
@@ -503,6 +527,26 @@ uint64_t slot_capacity(Slot& S) {
 void release_arenas(Slot& S) {
     for (int i = 0; DevBuf* b = arena_bufs(S, i); ++i) release(*b);
     S.plan_valid = false;
+}
+
+// Serial multi-warp pairs (long kind 3): two strip boundaries of serial_rows float4 rows
+// for every warp of k_forward_serial's grid.
+uint64_t serial_bytes(const phmm_ctx* ctx, const Plan& P) {
+    if (P.long_kind != 3 || P.citems.empty()) return 0;
+    const uint64_t warps = (uint64_t)ctx->sms * ctx->occ_longk[3] * (kSerialThreads / 32);
+    return warps * 2 * P.serial_rows * sizeof(float4);
+}
+cudaError_t ensure_serial(const phmm_ctx* ctx, Slot& S, const Plan& P) {
+    const uint64_t b = serial_bytes(ctx, P);
+    if (b == 0) {
+        S.sbnd_warps = S.sbnd_rows = 0;
+        return cudaSuccess;
+    }
+    const cudaError_t e = ensure(S.sbnd, b);
+    if (e != cudaSuccess) return e;
+    S.sbnd_warps = (uint32_t)ctx->sms * ctx->occ_longk[3] * (kSerialThreads / 32);
+    S.sbnd_rows = P.serial_rows;
+    return cudaSuccess;
 }
 
 int launch_sequence(phmm_ctx* ctx, Slot& S, int scal_id, int pack_id, int long_kind, bool record_events) {
@@ -597,6 +641,9 @@ void plan_header(const Slot& S, const Plan& P, BatchHeader& hh) {
     hh.n_partials = hh.n_pairs + P.n_extra;
     hh.bnd = (unsigned long long*)S.bnd.p;
     hh.n_bnd_words = P.bnd_words;
+    hh.sbnd = (float4*)S.sbnd.p;
+    hh.sbnd_rows = S.sbnd_rows;
+    hh.sbnd_warps = S.sbnd_warps;
     // the Rec32 layout is read by the lean and packed short kernels and the lean
     // multi-warp kernel only; without them prep skips it
     const bool need32 = P.pack_id >= 0 || !kShortScalarPipe[P.scal_id] || (P.long_kind == 0 && !P.citems.empty());
@@ -626,7 +673,7 @@ std::vector<std::pair<int, int>> fp32_candidates(const phmm_config& cfg) {
 void make_plan_id(const uint32_t* l, const uint32_t* k, const uint32_t* pr, uint32_t n, int scal_id,
                   int pack_id, int long_kind, Plan& P) {
     make_plan(l, k, pr, n, kShortScalarN[scal_id], pack_id >= 0 ? kShortPackedN[pack_id] : 0,
-              kLongN[long_kind], P, 4, kLongCW[long_kind]);
+              kLongN[long_kind], P, 4, kLongCW[long_kind], long_kind == 3);
     P.scal_id = scal_id;
     P.pack_id = pack_id;
     P.long_kind = long_kind;
@@ -641,8 +688,9 @@ std::vector<int> long_kinds_of(const phmm_config& cfg) {
     if (cfg.flags & PHMM_F_LONG_LEAN) return {0};
     if (cfg.flags & PHMM_F_LONG_PIPE32) return {1};
     if (cfg.flags & PHMM_F_LONG_PIPE24) return {2};
+    if (cfg.flags & PHMM_F_LONG_SERIAL) return {3};
     if (cfg.kernel_variant == 3) return {0};
-    return {0, 1};  // kind 2 only when forced: measured slower than kind 1 everywhere
+    return {0, 1, 3};  // kind 2 only when forced: measured slower than kind 1 everywhere
 }
 int default_long_kind(const phmm_config& cfg) {
     const std::vector<int> k = long_kinds_of(cfg);
@@ -696,7 +744,8 @@ int phmm_create(const phmm_config* cfg, phmm_ctx** out) {
     if (cfg->precision < 0 || cfg->precision > 2) return PHMM_EINVAL;
     if (cfg->kernel_variant < 0 || cfg->kernel_variant > 5) return PHMM_EINVAL;
     {
-        const unsigned lk = cfg->flags & (PHMM_F_LONG_LEAN | PHMM_F_LONG_PIPE32 | PHMM_F_LONG_PIPE24);
+        const unsigned lk =
+            cfg->flags & (PHMM_F_LONG_LEAN | PHMM_F_LONG_PIPE32 | PHMM_F_LONG_PIPE24 | PHMM_F_LONG_SERIAL);
         if (lk & (lk - 1)) return PHMM_EINVAL;  // more than one forced multi-warp kernel
     }
     {
@@ -750,10 +799,11 @@ int phmm_create(const phmm_config* cfg, phmm_ctx** out) {
     ctx->occ_longk[0] = occupancy_forward32_long();
     ctx->occ_longk[1] = occupancy_forward32_long_pipe(1);
     ctx->occ_longk[2] = occupancy_forward32_long_pipe(2);
+    ctx->occ_longk[3] = occupancy_forward32_long_pipe(3);
     if (getenv("PHMM_DEBUG")) {
-        fprintf(stderr, "phmm: sms %d occupancy packed %d %d long %d %d %d fp64 %d scalar", ctx->sms,
+        fprintf(stderr, "phmm: sms %d occupancy packed %d %d long %d %d %d %d fp64 %d scalar", ctx->sms,
                 ctx->occ_packed[0], ctx->occ_packed[1], ctx->occ_longk[0], ctx->occ_longk[1],
-                ctx->occ_longk[2], ctx->occ64);
+                ctx->occ_longk[2], ctx->occ_longk[3], ctx->occ64);
         for (int q = 0; q < kNumScalar; ++q) fprintf(stderr, " %d", ctx->occ_scalar[q]);
         fprintf(stderr, "\n");
     }
@@ -796,9 +846,9 @@ void phmm_destroy(phmm_ctx* ctx) {
     }
     for (auto& S : ctx->slots) {
         DevBuf* d[] = {&S.in_bases, &S.in_bq, &S.in_iq, &S.in_dq, &S.in_gq, &S.in_hap, &S.in_roff,
-                       &S.in_hoff, &S.in_pr, &S.in_ph, &S.desc, &S.rec32, &S.rec64, &S.teams,
+                       &S.in_hoff, &S.in_pr, &S.in_ph, &S.desc, &S.rec32, &S.rec32j, &S.rec64, &S.teams,
                        &S.witems, &S.witems2, &S.cpairs, &S.citems, &S.parts, &S.out, &S.oflags, &S.rescue,
-                       &S.small, &S.hdr, &S.bnd, &S.rbnd};
+                       &S.small, &S.hdr, &S.bnd, &S.rbnd, &S.sbnd};
         for (auto* b : d) release(*b);
         HostBuf* h[] = {&S.h_out, &S.h_oflags, &S.h_small, &S.h_roff, &S.h_hoff, &S.h_pr, &S.h_ph};
         for (auto* b : h) release(*b);
@@ -956,7 +1006,7 @@ int phmm_submit_batch(phmm_ctx* ctx, const phmm_batch* b, uint64_t* ticket) {
                           (need64 ? nbases * sizeof(Rec64) : 0) +
                           P.teams.size() * sizeof(Team) + (P.witems.size() + P.witems2.size()) * sizeof(WarpItem) +
                           P.cpairs.size() * sizeof(CtaPair) + P.citems.size() * sizeof(CtaItem) +
-                          P.bnd_words * 8ull + P.n_extra * sizeof(Partial);
+                          P.bnd_words * 8ull + P.n_extra * sizeof(Partial) + serial_bytes(ctx, P);
     if (foot > ctx->budget) return PHMM_ENOMEM;
     if (foot + ctx->inflight_foot > ctx->budget) return PHMM_EBUSY;  // admissible once others retire
     {
@@ -1006,6 +1056,7 @@ int phmm_submit_batch(phmm_ctx* ctx, const phmm_batch* b, uint64_t* ticket) {
     if (need64) CK(ensure(S->rec64, nbases * sizeof(Rec64)));
     CK(ensure(S->parts, (np + P.n_extra) * sizeof(Partial)));
     CK(ensure(S->bnd, P.bnd_words * 8ull));
+    CK(ensure_serial(ctx, *S, P));
     if (ctx->cfg.precision != PHMM_PREC_FP32_ONLY) CK(ensure(S->rbnd, rb_bytes));
     CK(ensure(S->out, np * 8ull));
     CK(ensure(S->oflags, np * 1ull));
@@ -1059,8 +1110,13 @@ int phmm_submit_batch(phmm_ctx* ctx, const phmm_batch* b, uint64_t* ticket) {
         if (tune_short)
             for (auto& cd : tune_cand) runs.push_back({cd.first, cd.second, bl});
         const size_t n_short = runs.size();
-        if (tune_long)
-            for (int lk : long_kinds_of(ctx->cfg)) runs.push_back({-1, -1, lk});
+        if (tune_long) {
+            // the serial kind needs several multi-warp pairs per resident warp: with fewer
+            // it leaves most of the GPU idle, so it is not worth a (long) trial run
+            const uint64_t swarps = (uint64_t)ctx->sms * ctx->occ_longk[3] * (kSerialThreads / 32);
+            for (int lk : long_kinds_of(ctx->cfg))
+                if (lk != 3 || (uint64_t)P.n_long >= 2 * swarps) runs.push_back({-1, -1, lk});
+        }
         for (size_t ri = 0; ri < runs.size(); ++ri) {
             if (ri == n_short) best_ms = 1e30;  // second stage: the short choice is fixed
             std::array<int, 3> cd = runs[ri];
@@ -1074,6 +1130,7 @@ int phmm_submit_batch(phmm_ctx* ctx, const phmm_batch* b, uint64_t* ticket) {
             CK(upload_plan(*S, c, cs));
             CK(ensure(S->parts, (np + c.n_extra) * sizeof(Partial)));
             CK(ensure(S->bnd, c.bnd_words * 8ull));
+            CK(ensure_serial(ctx, *S, c));
             hh.parts = (Partial*)S->parts.p;
             plan_header(*S, c, hh);
             CK(cudaMemcpyAsync(S->hdr.p, &hh, sizeof(hh), cudaMemcpyHostToDevice, cs));
@@ -1105,6 +1162,7 @@ int phmm_submit_batch(phmm_ctx* ctx, const phmm_batch* b, uint64_t* ticket) {
         CK(upload_plan(*S, P, cs));
         CK(ensure(S->parts, (np + P.n_extra) * sizeof(Partial)));
         CK(ensure(S->bnd, P.bnd_words * 8ull));
+        CK(ensure_serial(ctx, *S, P));
         hh.parts = (Partial*)S->parts.p;
         plan_header(*S, P, hh);
         CK(cudaMemcpyAsync(S->hdr.p, &hh, sizeof(hh), cudaMemcpyHostToDevice, cs));
@@ -1369,6 +1427,8 @@ int phmm_plan_check(const uint32_t* l, const uint32_t* k, const uint32_t* pair_r
         std::vector<uint64_t> bin, bout;
     };
     std::map<uint32_t, StripSeen> strips;
+    std::vector<std::pair<uint64_t, uint64_t>> bnd_ranges, extra_ranges;
+    const bool serial = precision != PHMM_PREC_FP64 && long_kind == 3;
     for (size_t it = 0; it < P.citems.size(); ++it) {
         const CtaItem& ci = P.citems[it];
         uint32_t used = 0;
@@ -1381,6 +1441,22 @@ int phmm_plan_check(const uint32_t* l, const uint32_t* k, const uint32_t* pair_r
             used |= bits;
             if (cp.pair >= n) return fail(13);
             const uint64_t Wt = (k[cp.pair] + seg - 1) / seg;
+            if (serial) {
+                // one pair per item, all its strips on one warp; strips 1.. leave their
+                // partials at extra_base + s - 1
+                if (ci.n != 1 || cp.W != 1 || cp.w0 != 0 || cp.col0 != 0 || cp.bnd_in != kNoBnd ||
+                    cp.bnd_out != kNoBnd)
+                    return fail(16);
+                if (cp.nstrip != Wt) return fail(17);
+                if (l[cp.pair] > P.serial_rows) return fail(18);
+                if (cp.nstrip > 1) {
+                    if (cp.extra_base < n || cp.extra_base + cp.nstrip - 1 > n + P.n_extra) return fail(27);
+                    extra_ranges.push_back({cp.extra_base, cp.extra_base + cp.nstrip - 1});
+                    stats[5]++;
+                }
+                seen[cp.pair]++;
+                continue;
+            }
             if (cp.nstrip <= 1) {
                 if (cp.W != Wt || cp.col0 != 0 || cp.bnd_in != kNoBnd || cp.bnd_out != kNoBnd) return fail(14);
                 seen[cp.pair]++;
@@ -1407,7 +1483,6 @@ int phmm_plan_check(const uint32_t* l, const uint32_t* k, const uint32_t* pair_r
             sv.count++;
         }
     }
-    std::vector<std::pair<uint64_t, uint64_t>> bnd_ranges, extra_ranges;
     for (auto& kv : strips) {
         const uint32_t p = kv.first;
         StripSeen& sv = kv.second;

@@ -67,6 +67,8 @@ def test_create_rejects_bad_config(lib):
     assert so.phmm_create(ctypes.byref(cfg), ctypes.byref(h)) == lib.PHMM_EINVAL
     cfg = lib.Config(0, 0, 0, 0, lib.F_LONG_LEAN | lib.F_LONG_PIPE24, None, 0, 0)  # two forced kernels
     assert so.phmm_create(ctypes.byref(cfg), ctypes.byref(h)) == lib.PHMM_EINVAL
+    cfg = lib.Config(0, 0, 0, 0, lib.F_LONG_SERIAL | lib.F_LONG_PIPE32, None, 0, 0)
+    assert so.phmm_create(ctypes.byref(cfg), ctypes.byref(h)) == lib.PHMM_EINVAL
     assert so.phmm_create(None, ctypes.byref(h)) == lib.PHMM_EINVAL
 
 

@@ -40,7 +40,8 @@ SHAPES = _shapes()
 
 
 @pytest.mark.parametrize("shape", sorted(SHAPES))
-@pytest.mark.parametrize("scal,pack,kind", [(0, -1, 0), (4, -1, 1), (5, 1, 1), (7, 0, 0), (3, -1, 2), (8, 1, 2)])
+@pytest.mark.parametrize("scal,pack,kind", [(0, -1, 0), (4, -1, 1), (5, 1, 1), (7, 0, 0), (3, -1, 2), (8, 1, 2),
+                                            (7, -1, 3), (5, 1, 3)])
 def test_fp32_plans_valid(P, shape, scal, pack, kind):
     l, k, pr = SHAPES[shape]
     rc, st = P.plan_check(l, k, pr, "fp32", scal, pack, kind)
@@ -70,3 +71,13 @@ def test_plan_check_rejects_bad_ids(P):
     assert P.plan_check(l, k, pr, "fp32", 99, -1, 1)[0] == P.PHMM_EINVAL
     assert P.plan_check(l, k, pr, "fp32", 4, 7, 1)[0] == P.PHMM_EINVAL
     assert P.plan_check(l, k, pr, "fp32", 4, -1, 5)[0] == P.PHMM_EINVAL
+
+
+def test_serial_plan_one_item_per_long_pair(P):
+    """Long kind 3: every multi-warp pair is one item (one warp runs all its strips)."""
+    l, k, pr = SHAPES["uneven"]
+    rc, st = P.plan_check(l, k, pr, "fp32", 7, -1, 3)
+    assert rc == P.PHMM_OK
+    n_long = int(np.sum(k > 1024))
+    assert st["cta_items"] == n_long and st["cta_pairs"] == n_long
+    assert st["striped_pairs"] == int(np.sum(k > 1024))  # all of them span two or more strips
