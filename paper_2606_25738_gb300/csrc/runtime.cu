@@ -692,9 +692,14 @@ std::vector<int> long_kinds_of(const phmm_config& cfg) {
     if (cfg.kernel_variant == 3) return {0};
     return {0, 1, 3};  // kind 2 only when forced: measured slower than kind 1 everywhere
 }
-int default_long_kind(const phmm_config& cfg) {
+// Without measurement: the serial kind when multi-warp pairs outnumber the resident
+// warps of k_forward_serial four times over (each warp then has several pairs to run),
+// else the pipelined 12-warp kernel.
+int default_long_kind(const phmm_config& cfg, uint64_t n_long = 0, uint64_t serial_warps = 0) {
     const std::vector<int> k = long_kinds_of(cfg);
-    return k.size() == 1 ? k[0] : 1;
+    if (k.size() == 1) return k[0];
+    const bool serial_ok = std::find(k.begin(), k.end(), 3) != k.end();
+    return serial_ok && serial_warps > 0 && n_long >= 4 * serial_warps ? 3 : 1;
 }
 
 // Coarse shape of a batch for the tuner cache: pair count, mean read and haplotype
@@ -963,11 +968,15 @@ int phmm_submit_batch(phmm_ctx* ctx, const phmm_batch* b, uint64_t* ticket) {
                 make_plan_id(L.data(), K.data(), pr, np, hit->second[0], hit->second[1], hit->second[2], P);
             } else {
                 // cost-model choice first; measured tuning (below) may replace it
+                uint64_t n_wide = 0;  // pairs wider than one warp of 32 columns per lane
+                for (uint32_t p = 0; p < np; ++p) n_wide += K[p] > 1024u;
+                const int dlk = default_long_kind(ctx->cfg, n_wide,
+                                                  (uint64_t)ctx->sms * ctx->occ_longk[3] * (kSerialThreads / 32));
                 Plan best;
                 bool have = false;
                 for (auto& cd : cand) {
                     Plan c;
-                    make_plan_id(L.data(), K.data(), pr, np, cd.first, cd.second, default_long_kind(ctx->cfg), c);
+                    make_plan_id(L.data(), K.data(), pr, np, cd.first, cd.second, dlk, c);
                     const double cost = c.cost + (double)c.n_too_long * 1e18;
                     if (!have || cost < best.cost + (double)best.n_too_long * 1e18) {
                         best = std::move(c);
