@@ -351,3 +351,39 @@ def test_bounded_wait_times_out_and_context_survives(phmm):
         out, flags, rc, st = ctx.run(b)
     assert rc == 0
     _check(out, flags, oracle.batch(b))
+
+
+def _strip_edge_batch():
+    """Wide pairs at the serial kind's strip edges: one column in the last strip, exact
+    multiples of 1024, one-row reads, reads longer than the haplotype."""
+    rng = np.random.default_rng(41)
+    rs = lambda n: "".join(rng.choice(list("ACGT"), size=n))
+    hap = rs(5 * 1024 + 1)
+    pairs = [
+        (rs(120), hap[:1025], 30, 45, 45, 10),           # last strip: one column
+        (rs(120), hap[:2048], 30, 45, 45, 10),           # exactly two strips
+        (hap[100:400], hap[:4096], 30, 45, 45, 10),      # exactly four strips
+        ("A", hap[:3000], 30, 45, 45, 10),               # one row
+        (hap[:70], hap[:5121], 30, 45, 45, 10),          # five strips and one column
+        (rs(1500), hap[:1100], 30, 45, 45, 10),          # more rows than columns
+        (hap[:2000], hap[:2100], 30, 40, 40, np.arange(2000) % 20 + 5),  # per-row gcp
+    ]
+    return W.from_strings(pairs)
+
+
+@pytest.mark.parametrize("prec,flag", [("fp32_only", "serial"), ("fp32", "serial"), ("fp32", "rescue")])
+def test_serial_strip_edges(phmm, prec, flag):
+    """The serial multi-warp kind at its strip boundaries; with forced rescue the FP64
+    pass recomputes the same pairs."""
+    b = _strip_edge_batch()
+    f = phmm.F_LONG_SERIAL | (phmm.F_FORCE_RESCUE if flag == "rescue" else 0)
+    with phmm.Context(precision=prec, flags=f) as ctx:
+        out, flags, rc, st = ctx.run(b)
+    assert st["long_kernel"] == 3
+    ref = oracle.batch(b)
+    if flag == "rescue":
+        assert np.all(flags & phmm.PAIR_RESCUED)
+        assert np.max(np.abs(out - ref)) <= TOL64
+    else:
+        assert np.all((flags & 0x78) == 0)
+        assert np.max(np.abs(out - ref)) <= TOL32
