@@ -1031,11 +1031,17 @@ __device__ __forceinline__ float2 fmul2_sel(float2 a, float2 b) {
     else return make_float2(a.x * b.x, a.y * b.y);
 }
 
-template <int N, bool PACKED>
+// LINK: the team is a whole warp running one 32 N-column strip of a wider pair whose
+// strips run one after another on this warp (the serial multi-warp kind).  As in
+// seg_link_pipe<N, true>: the finished left strip's boundary (float4 per row: M, J, D-hat,
+// E of its last column; `sin`) enters lane 0 and, as a carry g^(N t - 1), every lane's
+// D-hat; checkpoints keep E >= E_left; lane 31 stores this strip's boundary (`sout`).
+template <int N, bool PACKED, bool LINK = false>
 __device__ SegOut team_run_pipe2(const Rec32J* __restrict__ rec, int l, int lmax,
                                  const uint8_t* __restrict__ hap, int k, int col0, int lt,
                                  int tlast, int nsteps, const PowRow<float>* __restrict__ pow_tab,
-                                 const PipeRange& rng) {
+                                 const PipeRange& rng, const float4* sin = nullptr, float4* sout = nullptr,
+                                 bool has_left = false, bool has_right = false) {
     using NT = Num<float>;
     static_assert(N <= 32 && N % 2 == 0, "match masks hold 32 columns; two halves");
     constexpr int H = N / 2;
@@ -1060,6 +1066,8 @@ __device__ SegOut team_run_pipe2(const Rec32J* __restrict__ rec, int l, int lmax
     float2 dt2 = make_float2(0.f, 0.f), ml2 = make_float2(0.f, 0.f);
     float gprev = 0.f;
     float sp1[5], sp2[5], last1 = 0.f, last2 = 0.f, hh1 = 0.f, hh2 = 0.f, hm1 = 0.f, hm2 = 0.f;
+    float qa1 = 0.f, qa2 = 0.f, qb1 = 0.f, qb2 = 0.f;  // LINK: g^(N lt - 1), g^(N (lt + 1) - 1)
+    float4 bnd4 = make_float4(0.f, 0.f, 0.f, 0.f);      // LINK: this lane's row of the left boundary
     int gcp = -1;
     SegOut out;
     out.S = 0.0;
@@ -1088,6 +1096,12 @@ __device__ SegOut team_run_pipe2(const Rec32J* __restrict__ rec, int l, int lmax
             hh2 = __ldg(&pr->hh2);
             hm1 = __ldg(&pr->hm1);
             hm2 = __ldg(&pr->hm2);
+            if constexpr (LINK) {
+                qa1 = __ldg(&pr->lq1[lt]);
+                qa2 = __ldg(&pr->lq2[lt]);
+                qb1 = __ldg(&pr->lq1[lt + 1]);
+                qb2 = __ldg(&pr->lq2[lt + 1]);
+            }
             gcp = gq;
         }
         const int code = (int)(meta & META_CODE_MASK);
@@ -1145,7 +1159,9 @@ __device__ SegOut team_run_pipe2(const Rec32J* __restrict__ rec, int l, int lmax
         // lane aggregates of the local (zero-carry) D-hat chain: one past the lane's last
         // column (scan input) and at its last column (the right neighbour's carry)
         const float zl = fmaf(y2.x * hh1, hh2, y2.y);
-        const float ypl = fmaf(y2.x * hm1, hm2, yp2.y);
+        float ypl = fmaf(y2.x * hm1, hm2, yp2.y);
+        float jl = 0.f;
+        if constexpr (LINK) jl = J2[H - 1].y;  // this lane's last J of row i (sent right)
         float yA = yp2.x;  // first half, at its last column
         float nm = __shfl_up_sync(kFull, M2[H - 1].y, 1);
         float nj = __shfl_up_sync(kFull, J2[H - 1].y, 1);
@@ -1174,6 +1190,97 @@ __device__ SegOut team_run_pipe2(const Rec32J* __restrict__ rec, int l, int lmax
         }
         float zz = __shfl_up_sync(kFull, Z, 2);
         if (lt < 2) zz = 0.f;
+        if constexpr (LINK) {
+            float Wd = __shfl_up_sync(kFull, Z, 1);
+            if (lt == 0) Wd = 0.f;
+            float lM = 0.f, lJ = 0.f, lD = 0.f;
+            int Eleft = INT_MIN;
+            if (has_left) {
+                if (((i - 1) & 31) == 0) {  // next 32 rows of the finished left strip (L2 loads)
+                    const int r = i + lt;
+                    bnd4 = r <= l ? __ldcg(sin + (r - 1)) : make_float4(0.f, 0.f, 0.f, __int_as_float(INT_MIN));
+                }
+                const int src = (i - 1) & 31;
+                lM = __shfl_sync(kFull, bnd4.x, src);
+                lJ = __shfl_sync(kFull, bnd4.y, src);
+                lD = __shfl_sync(kFull, bnd4.z, src);
+                Eleft = __float_as_int(__shfl_sync(kFull, bnd4.w, src));
+            }
+            // checkpoint (same rows in every strip of the pair): E >= E_left, so that left
+            // values only ever scale down
+            int Enew = E;
+            if (until == 0) {
+                until = rng.R;
+                float2 m2 = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int q = 0; q < H; ++q) {
+                    m2.x = fmaxf(m2.x, fmaxf(fabsf(M2[q].x), fabsf(J2[q].x)));
+                    m2.y = fmaxf(m2.y, fmaxf(fabsf(M2[q].y), fabsf(J2[q].y)));
+                }
+                const float m = team_max<float>(fmaxf(m2.x, m2.y), lt, tlast, nsteps);
+                const int e = NT::expo(m);
+                int desired = E;
+                if (e == INT_MAX) {
+                    flags |= PF_NONFINITE;
+                } else if (e == INT_MIN) {
+                    if (has_left) desired = INT_MIN;  // nothing representable: follow the left
+                } else if (e > rng.hi || e <= NT::kLo) {
+                    desired = E + (e - rng.target);
+                }
+                Enew = desired;
+                bool forced = false;
+                if (has_left && Eleft > Enew) {
+                    Enew = Eleft;
+                    forced = true;
+                }
+                if (Enew == INT_MIN) Enew = E;
+                if (!forced && e != INT_MIN && e != INT_MAX && e <= rng.danger) flags |= PF_DANGER;
+            }
+            --until;
+            if (Enew != E) {
+                const int sdn = E - Enew;
+#pragma unroll
+                for (int q = 0; q < H; ++q) {
+                    M2[q] = make_float2(scale2(M2[q].x, sdn), scale2(M2[q].y, sdn));
+                    J2[q] = make_float2(scale2(J2[q].x, sdn), scale2(J2[q].y, sdn));
+                    U2[q] = make_float2(scale2(U2[q].x, sdn), scale2(U2[q].y, sdn));
+                }
+                nm = scale2(nm, sdn);
+                zz = scale2(zz, sdn);
+                yp = scale2(yp, sdn);
+                yA = scale2(yA, sdn);
+                Wd = scale2(Wd, sdn);
+                ypl = scale2(ypl, sdn);
+                jl = scale2(jl, sdn);
+                flags |= PF_RESCALED;
+                E = Enew;
+            }
+            // left values into this strip's scale (no left: zeros stay zero)
+            const int dsh = has_left ? Eleft - E : 0;
+            lM = scale2(lM, dsh);
+            lJ = scale2(lJ, dsh);
+            lD = scale2(lD, dsh);
+            const float Wseg = fmaf(rg, lD, lM);  // D-hat at the strip's first column
+            float ndA = fmaf(zz * last1, last2, yp);
+            ndA = fmaf(Wseg * qa1, qa2, ndA);
+            if (lt == 0) {
+                ndA = lD;
+                nm = lM;
+                U2[0].x = fmaf(nxt.a, lM, lJ);
+            }
+            if (has_right && lt == 31) {
+                // D-hat at the strip's last column
+                const float dl = fmaf(Wseg * qb1, qb2, fmaf(Wd * last1, last2, ypl));
+                __stcg(sout + (i - 1), make_float4(M2[H - 1].y, jl, dl, __int_as_float(E)));
+            }
+            const float wl = fmaf(rg, ndA, nm);         // D-hat at the lane's first column
+            const float ndB = fmaf(wl * hm1, hm2, yA);  // D-hat at the first half's last column
+            dt2 = make_float2(ndA, ndB);
+            ml2 = make_float2(nm, M2[H - 1].x);
+            gprev = rg;
+            cur = nxt;
+            continue;
+        }
         if (until == 0) {
             until = rng.R;
             float2 m2 = make_float2(0.f, 0.f);
@@ -1233,18 +1340,11 @@ __device__ SegOut team_run_pipe2(const Rec32J* __restrict__ rec, int l, int lmax
 // boundary of the previous strip), the checkpoint keeps E >= E_left, the left values are
 // brought into this segment's scale, and lane 31 hands this segment's last column on.
 // The segment carry enters lane t's previous column with the power g^(N t - 1).
-//
-// SER: the strips of a pair run one after another on the same warp.  The left strip is
-// complete before this one starts, so its boundary (one float4 per row: M, J, D-hat and
-// the exponent E of its last column) is read without waiting: every 32 rows each lane
-// loads one row of it, and row i comes from lane (i - 1) mod 32 by shuffle.  Lane 31
-// stores this strip's boundary row by row for the next strip.
 // ------------------------------------------------------------------------------------
-template <int N, bool SER = false>
+template <int N>
 __device__ SegOut seg_link_pipe(const Rec32J* __restrict__ rec, int l, const uint8_t* __restrict__ hap,
                                 int k, int col0, int lane, const PowRow<float>* __restrict__ pow_tab,
-                                const PipeRange& rng, const SmemLink& link, uint32_t* __restrict__ status,
-                                const float4* sin = nullptr, float4* sout = nullptr) {
+                                const PipeRange& rng, const SmemLink& link, uint32_t* __restrict__ status) {
     using NT = Num<float>;
     static_assert(N <= 32, "match masks hold 32 columns");
     uint32_t bmA = 0, bmC = 0, bmG = 0, bmT = 0, flags = rng.ok ? 0u : PF_DEGEN, mflags = 0;
@@ -1275,7 +1375,6 @@ __device__ SegOut seg_link_pipe(const Rec32J* __restrict__ rec, int l, const uin
     const int l1 = max(l, 1) - 1;
     Rec32J cur = load_recj(rec);
     int until = 0;
-    float4 bnd4 = make_float4(0.f, 0.f, 0.f, 0.f);  // SER: this lane's row of the left boundary
     for (int i = 1; i <= l; ++i) {
         Rec32J nxt = cur;
         if (i < l) nxt = load_recj(rec + min(i, l1));
@@ -1371,36 +1470,20 @@ __device__ SegOut seg_link_pipe(const Rec32J* __restrict__ rec, int l, const uin
         // the left segment's last column of row i: lane 0 waits for it, then the whole
         // (converged) warp takes it
         float lM = 0.f, lJ = 0.f, lD = 0.f;
-        int Eleft = INT_MIN;
-        if constexpr (SER) {
-            if (has_left) {
-                if (((i - 1) & 31) == 0) {  // next 32 rows of the finished left strip
-                    const int r = i + lane;
-                    // L2 load (.cg): written earlier in this launch by this warp's lane 31
-                    bnd4 = r <= l ? __ldcg(sin + (r - 1)) : make_float4(0.f, 0.f, 0.f, __int_as_float(INT_MIN));
-                }
-                const int src = (i - 1) & 31;
-                lM = __shfl_sync(kFull, bnd4.x, src);
-                lJ = __shfl_sync(kFull, bnd4.y, src);
-                lD = __shfl_sync(kFull, bnd4.z, src);
-                Eleft = __float_as_int(__shfl_sync(kFull, bnd4.w, src));
+        int e_in = INT_MIN;
+        if (has_left && lane == 0) {
+            const bool ok = link.in_g ? link_recv_g<float>(link.in_g, i, lM, lJ, lD, e_in)
+                                      : link_recv<float>(link, i, lM, lJ, lD, e_in);
+            if (!ok) {
+                flags |= PF_TIMEOUT;
+                atomicOr(status, ST_TIMEOUT);
             }
-        } else {
-            int e_in = INT_MIN;
-            if (has_left && lane == 0) {
-                const bool ok = link.in_g ? link_recv_g<float>(link.in_g, i, lM, lJ, lD, e_in)
-                                          : link_recv<float>(link, i, lM, lJ, lD, e_in);
-                if (!ok) {
-                    flags |= PF_TIMEOUT;
-                    atomicOr(status, ST_TIMEOUT);
-                }
-            }
-            __syncwarp();
-            lM = __shfl_sync(kFull, lM, 0);
-            lJ = __shfl_sync(kFull, lJ, 0);
-            lD = __shfl_sync(kFull, lD, 0);
-            Eleft = __shfl_sync(kFull, e_in, 0);
         }
+        __syncwarp();
+        lM = __shfl_sync(kFull, lM, 0);
+        lJ = __shfl_sync(kFull, lJ, 0);
+        lD = __shfl_sync(kFull, lD, 0);
+        const int Eleft = __shfl_sync(kFull, e_in, 0);
         // checkpoint (same rows in every segment of the pair): power-of-two rescaling,
         // with E >= E_left so that left values only ever scale down
         int Enew = E;
@@ -1464,9 +1547,7 @@ __device__ SegOut seg_link_pipe(const Rec32J* __restrict__ rec, int l, const uin
         if (has_right && lane == 31) {
             // D-hat at the segment's last column
             const float dl = fmaf(Wseg * qb1, qb2, fmaf(Wd * last1, last2, yprev));
-            if constexpr (SER) {
-                __stcg(sout + (i - 1), make_float4(M[N - 1], jl, dl, __int_as_float(E)));
-            } else if (link.out_g) {
+            if (link.out_g) {
                 link_send_g<float>(link.out_g, i, M[N - 1], jl, dl, E);
             } else if (!link_send<float>(link, i, M[N - 1], jl, dl, E)) {
                 flags |= PF_TIMEOUT;

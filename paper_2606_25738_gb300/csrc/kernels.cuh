@@ -541,7 +541,7 @@ k_forward_pipe(const BatchHeader* __restrict__ H, const PowRow<float>* __restric
 }
 
 // Multi-warp pairs one warp at a time (long kind 3): each warp takes a whole pair and
-// runs its strips of 32 N columns one after another (seg_link_pipe<N, true>), strip s
+// runs its strips of 32 N columns one after another (team_run_pipe2 in LINK mode), strip s
 // reading the boundary strip s - 1 left in this warp's scratch.  No warp ever waits on
 // another; the pair's S strips leave S partials, combined by the finalize kernel as for
 // CTA strips.
@@ -555,10 +555,6 @@ k_forward_serial(const BatchHeader* __restrict__ H, const PowRow<float>* __restr
     if (gw >= H->sbnd_warps) return;  // no scratch for this warp (grid larger than planned)
     float4* buf0 = H->sbnd + (size_t)gw * 2 * H->sbnd_rows;
     float4* buf1 = buf0 + H->sbnd_rows;
-    SmemLink L;
-    L.in_ring = L.out_ring = nullptr;
-    L.my_cons = L.next_cons = nullptr;
-    L.in_g = L.out_g = nullptr;
     for (;;) {
         uint32_t wi = 0;
         if (lane == 0) wi = atomicAdd(&H->counters[0], 1u);
@@ -568,13 +564,12 @@ k_forward_serial(const BatchHeader* __restrict__ H, const PowRow<float>* __restr
         const PairDesc d = H->desc[cp.pair];
         const uint32_t S = cp.nstrip;
         for (uint32_t s = 0; s < S; ++s) {
-            L.has_left = s > 0;
-            L.has_right = s + 1 < S;
             const float4* in = (s & 1u) ? buf0 : buf1;  // what strip s - 1 wrote
             float4* outb = (s & 1u) ? buf1 : buf0;
             const int c0 = (int)(s * 32u * N) + lane * N;
-            const SegOut o = seg_link_pipe<N, true>(H->rec32j + d.roff, (int)d.l, H->hap_bases + d.hoff,
-                                                    (int)d.k, c0, lane, pow, rng, L, H->status, in, outb);
+            const SegOut o = team_run_pipe2<N, true, true>(H->rec32j + d.roff, (int)d.l, (int)d.l,
+                                                           H->hap_bases + d.hoff, (int)d.k, c0, lane, 31, 5,
+                                                           pow, rng, in, outb, s > 0, s + 1 < S);
             __syncwarp();  // this strip's boundary stores before the next strip's loads
             if (lane == 0) {
                 Partial p;

@@ -15,11 +15,13 @@ void launch_prep32(const BatchHeader* H, const PhredTables* T, int grid, cudaStr
 void launch_prep32_first(const BatchHeader* H, const PhredTables* T, int grid, cudaStream_t s);
 void launch_forward32_long(const BatchHeader* H, const void* pow, int grid, cudaStream_t s);
 // FP32 multi-warp kernels: kind 0 = lean engine (N 32, 16-warp CTAs), 1 = pipelined
-// (N 32, 12-warp CTAs), 2 = pipelined (N 24, 16-warp CTAs), 3 = pipelined, one warp per
-// pair running its 1024-column strips one after another (k_forward_serial, 4-warp CTAs).
+// (N 32, 12-warp CTAs), 2 = pipelined (N 24, 16-warp CTAs), 3 = pipelined with packed
+// column halves, one warp per pair running its 1024-column strips one after another
+// (k_forward_serial, 4-warp CTAs).
 constexpr int kNumLong = 4;
 constexpr int kLongN[kNumLong] = {32, 32, 24, 32};
 constexpr int kLongCW[kNumLong] = {16, 12, 16, 1};
+constexpr bool kLongSerial[kNumLong] = {false, false, false, true};
 constexpr int kSerialThreads = 128;
 void launch_forward32_long_pipe(int kind, const BatchHeader* H, const void* pow, int grid, cudaStream_t s);
 // Short-pair kernels by variant id (see kShortScalar / kShortPacked).

@@ -532,8 +532,8 @@ void release_arenas(Slot& S) {
 // Serial multi-warp pairs (long kind 3): two strip boundaries of serial_rows float4 rows
 // for every warp of k_forward_serial's grid.
 uint64_t serial_bytes(const phmm_ctx* ctx, const Plan& P) {
-    if (P.long_kind != 3 || P.citems.empty()) return 0;
-    const uint64_t warps = (uint64_t)ctx->sms * ctx->occ_longk[3] * (kSerialThreads / 32);
+    if (!kLongSerial[P.long_kind] || P.citems.empty()) return 0;
+    const uint64_t warps = (uint64_t)ctx->sms * ctx->occ_longk[P.long_kind] * (kSerialThreads / 32);
     return warps * 2 * P.serial_rows * sizeof(float4);
 }
 cudaError_t ensure_serial(const phmm_ctx* ctx, Slot& S, const Plan& P) {
@@ -544,7 +544,7 @@ cudaError_t ensure_serial(const phmm_ctx* ctx, Slot& S, const Plan& P) {
     }
     const cudaError_t e = ensure(S.sbnd, b);
     if (e != cudaSuccess) return e;
-    S.sbnd_warps = (uint32_t)ctx->sms * ctx->occ_longk[3] * (kSerialThreads / 32);
+    S.sbnd_warps = (uint32_t)ctx->sms * ctx->occ_longk[P.long_kind] * (kSerialThreads / 32);
     S.sbnd_rows = P.serial_rows;
     return cudaSuccess;
 }
@@ -673,7 +673,7 @@ std::vector<std::pair<int, int>> fp32_candidates(const phmm_config& cfg) {
 void make_plan_id(const uint32_t* l, const uint32_t* k, const uint32_t* pr, uint32_t n, int scal_id,
                   int pack_id, int long_kind, Plan& P) {
     make_plan(l, k, pr, n, kShortScalarN[scal_id], pack_id >= 0 ? kShortPackedN[pack_id] : 0,
-              kLongN[long_kind], P, 4, kLongCW[long_kind], long_kind == 3);
+              kLongN[long_kind], P, 4, kLongCW[long_kind], kLongSerial[long_kind]);
     P.scal_id = scal_id;
     P.pack_id = pack_id;
     P.long_kind = long_kind;
@@ -1124,7 +1124,7 @@ int phmm_submit_batch(phmm_ctx* ctx, const phmm_batch* b, uint64_t* ticket) {
             // it leaves most of the GPU idle, so it is not worth a (long) trial run
             const uint64_t swarps = (uint64_t)ctx->sms * ctx->occ_longk[3] * (kSerialThreads / 32);
             for (int lk : long_kinds_of(ctx->cfg))
-                if (lk != 3 || (uint64_t)P.n_long >= 2 * swarps) runs.push_back({-1, -1, lk});
+                if (!kLongSerial[lk] || (uint64_t)P.n_long >= 2 * swarps) runs.push_back({-1, -1, lk});
         }
         for (size_t ri = 0; ri < runs.size(); ++ri) {
             if (ri == n_short) best_ms = 1e30;  // second stage: the short choice is fixed
@@ -1437,7 +1437,7 @@ int phmm_plan_check(const uint32_t* l, const uint32_t* k, const uint32_t* pair_r
     };
     std::map<uint32_t, StripSeen> strips;
     std::vector<std::pair<uint64_t, uint64_t>> bnd_ranges, extra_ranges;
-    const bool serial = precision != PHMM_PREC_FP64 && long_kind == 3;
+    const bool serial = precision != PHMM_PREC_FP64 && kLongSerial[long_kind];
     for (size_t it = 0; it < P.citems.size(); ++it) {
         const CtaItem& ci = P.citems[it];
         uint32_t used = 0;
