@@ -79,6 +79,9 @@ typedef enum {
 /* ... or one warp per multi-warp pair, running its 1024-column strips one after
  * another (no warp waits on another; for batches with many long pairs). */
 #define PHMM_F_LONG_SERIAL 0x100u
+/* ... or the pipelined engine in 4-warp CTAs (strips of 4096 columns: a few very wide
+ * pairs spread over many SMs). */
+#define PHMM_F_LONG_PIPE4 0x200u
 /* No measured tuning: the built-in cost model and defaults choose the kernels.  For
  * serving, where nearly every batch (epoch) has a new shape and tuning would re-run it. */
 #define PHMM_F_NO_TUNE 0x80u
@@ -163,8 +166,8 @@ typedef struct {
      * short_kernel = scalar-team variant 0..8 (k_short_scalar<32,4>, <24,4>, <24,5>,
      * <16,6>, k_short_pipe<32,3>, <24,4>, <16,4>, k_short_pipe2<32,3>, <24,4>);
      * packed_kernel = packed-team variant 0..1 (k_short_packed<12,4>, <16,3>);
-     * long_kernel = multi-warp kind 0..3 (lean k_forward<32>, k_forward_pipe<32,12>,
-     * k_forward_pipe<24,16>, k_forward_serial<32,3>). */
+     * long_kernel = multi-warp kind 0..4 (lean k_forward<32>, k_forward_pipe<32,12>,
+     * k_forward_pipe<24,16>, k_forward_serial<32,3>, k_forward_pipe<32,4>). */
     int32_t short_kernel;
     int32_t packed_kernel;
     int32_t long_kernel;

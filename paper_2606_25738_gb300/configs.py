@@ -90,11 +90,11 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--units", type=int, default=0,
                     help="pairs (plain, long, uneven) or regions (short) instead of the default")
-    ap.add_argument("--long-kind", default="auto", choices=["auto", "lean", "pipe32", "pipe24", "serial"],
+    ap.add_argument("--long-kind", default="auto", choices=["auto", "lean", "pipe32", "pipe24", "serial", "pipe4"],
                     help="force one multi-warp kernel")
     a = ap.parse_args(argv)
     flags = {"auto": 0, "lean": phmm.F_LONG_LEAN, "pipe32": phmm.F_LONG_PIPE32,
-             "pipe24": phmm.F_LONG_PIPE24, "serial": phmm.F_LONG_SERIAL}[a.long_kind]
+             "pipe24": phmm.F_LONG_PIPE24, "serial": phmm.F_LONG_SERIAL, "pipe4": phmm.F_LONG_PIPE4}[a.long_kind]
     t = time.perf_counter()
     b = MAKERS[a.config](a.units) if a.units > 0 else MAKERS[a.config]()
     gen_s = time.perf_counter() - t

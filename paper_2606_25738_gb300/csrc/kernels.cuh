@@ -505,9 +505,11 @@ __device__ __forceinline__ void cta_strip_run_pipe(const BatchHeader* __restrict
 
 constexpr int kCtaThreadsPipe = kCtaWarpsPipe * 32;
 
-// CW warps per CTA: 12 at N = 32 (168 registers), 16 at N = 24 (128 registers).
+// CW warps per CTA: 12 at N = 32 (168 registers), 16 at N = 24 (128 registers), or 4 at
+// N = 32 with three CTAs per SM: a very wide pair then spreads over many SMs, one warp per
+// scheduler, instead of filling a few.
 template <int N, int CW>
-__global__ void __launch_bounds__(CW * 32, 1)
+__global__ void __launch_bounds__(CW * 32, CW <= 4 ? 3 : 1)
 k_forward_pipe(const BatchHeader* __restrict__ H, const PowRow<float>* __restrict__ pow) {
     __shared__ CtaShared<float> sh;
     const PipeRange rng = pipe_range(H->dropgrow);

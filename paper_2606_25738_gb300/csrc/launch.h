@@ -17,11 +17,12 @@ void launch_forward32_long(const BatchHeader* H, const void* pow, int grid, cuda
 // FP32 multi-warp kernels: kind 0 = lean engine (N 32, 16-warp CTAs), 1 = pipelined
 // (N 32, 12-warp CTAs), 2 = pipelined (N 24, 16-warp CTAs), 3 = pipelined with packed
 // column halves, one warp per pair running its 1024-column strips one after another
-// (k_forward_serial, 4-warp CTAs).
-constexpr int kNumLong = 4;
-constexpr int kLongN[kNumLong] = {32, 32, 24, 32};
-constexpr int kLongCW[kNumLong] = {16, 12, 16, 1};
-constexpr bool kLongSerial[kNumLong] = {false, false, false, true};
+// (k_forward_serial, 4-warp CTAs), 4 = pipelined in 4-warp CTAs (3 per SM): strips of
+// 4096 columns, so that a few very wide pairs spread over many SMs.
+constexpr int kNumLong = 5;
+constexpr int kLongN[kNumLong] = {32, 32, 24, 32, 32};
+constexpr int kLongCW[kNumLong] = {16, 12, 16, 1, 4};
+constexpr bool kLongSerial[kNumLong] = {false, false, false, true, false};
 constexpr int kSerialThreads = 128;
 void launch_forward32_long_pipe(int kind, const BatchHeader* H, const void* pow, int grid, cudaStream_t s);
 // Short-pair kernels by variant id (see kShortScalar / kShortPacked).

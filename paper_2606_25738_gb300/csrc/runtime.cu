@@ -485,7 +485,7 @@ struct phmm_ctx {
     DevBuf scan_row;                        // scan test: one PowRow<float> (global memory)
     DevBuf pow32[5];                        // N = 12, 16, 20, 24 (packed short), 32 (long)
     DevBuf pow64;
-    int occ_packed[kNumPacked] = {}, occ_scalar[kNumScalar] = {}, occ_longk[kNumLong] = {1, 1, 1, 1}, occ64 = 1;
+    int occ_packed[kNumPacked] = {}, occ_scalar[kNumScalar] = {}, occ_longk[kNumLong] = {1, 1, 1, 1, 1}, occ64 = 1;
     std::map<uint64_t, std::array<int, 3>> tuned;  // batch signature -> (scalar id, packed id, long kind)
     uint64_t inflight_foot = 0;             // sum of pending slots' footprints
     bool dead = false;
@@ -689,8 +689,9 @@ std::vector<int> long_kinds_of(const phmm_config& cfg) {
     if (cfg.flags & PHMM_F_LONG_PIPE32) return {1};
     if (cfg.flags & PHMM_F_LONG_PIPE24) return {2};
     if (cfg.flags & PHMM_F_LONG_SERIAL) return {3};
+    if (cfg.flags & PHMM_F_LONG_PIPE4) return {4};
     if (cfg.kernel_variant == 3) return {0};
-    return {0, 1, 3};  // kind 2 only when forced: measured slower than kind 1 everywhere
+    return {0, 1, 3, 4};  // kind 2 only when forced: measured slower than kind 1 everywhere
 }
 // Without measurement: the serial kind when multi-warp pairs outnumber the resident
 // warps of k_forward_serial four times over (each warp then has several pairs to run),
@@ -750,7 +751,8 @@ int phmm_create(const phmm_config* cfg, phmm_ctx** out) {
     if (cfg->kernel_variant < 0 || cfg->kernel_variant > 5) return PHMM_EINVAL;
     {
         const unsigned lk =
-            cfg->flags & (PHMM_F_LONG_LEAN | PHMM_F_LONG_PIPE32 | PHMM_F_LONG_PIPE24 | PHMM_F_LONG_SERIAL);
+            cfg->flags & (PHMM_F_LONG_LEAN | PHMM_F_LONG_PIPE32 | PHMM_F_LONG_PIPE24 | PHMM_F_LONG_SERIAL |
+                          PHMM_F_LONG_PIPE4);
         if (lk & (lk - 1)) return PHMM_EINVAL;  // more than one forced multi-warp kernel
     }
     {
@@ -805,10 +807,11 @@ int phmm_create(const phmm_config* cfg, phmm_ctx** out) {
     ctx->occ_longk[1] = occupancy_forward32_long_pipe(1);
     ctx->occ_longk[2] = occupancy_forward32_long_pipe(2);
     ctx->occ_longk[3] = occupancy_forward32_long_pipe(3);
+    ctx->occ_longk[4] = occupancy_forward32_long_pipe(4);
     if (getenv("PHMM_DEBUG")) {
-        fprintf(stderr, "phmm: sms %d occupancy packed %d %d long %d %d %d %d fp64 %d scalar", ctx->sms,
+        fprintf(stderr, "phmm: sms %d occupancy packed %d %d long %d %d %d %d %d fp64 %d scalar", ctx->sms,
                 ctx->occ_packed[0], ctx->occ_packed[1], ctx->occ_longk[0], ctx->occ_longk[1],
-                ctx->occ_longk[2], ctx->occ_longk[3], ctx->occ64);
+                ctx->occ_longk[2], ctx->occ_longk[3], ctx->occ_longk[4], ctx->occ64);
         for (int q = 0; q < kNumScalar; ++q) fprintf(stderr, " %d", ctx->occ_scalar[q]);
         fprintf(stderr, "\n");
     }
@@ -1123,8 +1126,13 @@ int phmm_submit_batch(phmm_ctx* ctx, const phmm_batch* b, uint64_t* ticket) {
             // the serial kind needs several multi-warp pairs per resident warp: with fewer
             // it leaves most of the GPU idle, so it is not worth a (long) trial run
             const uint64_t swarps = (uint64_t)ctx->sms * ctx->occ_longk[3] * (kSerialThreads / 32);
-            for (int lk : long_kinds_of(ctx->cfg))
-                if (!kLongSerial[lk] || (uint64_t)P.n_long >= 2 * swarps) runs.push_back({-1, -1, lk});
+            // the 4-warp-CTA kind pays off only for a few very wide pairs (it spreads them over
+            // more SMs); with many wide pairs it is not worth a trial run either
+            for (int lk : long_kinds_of(ctx->cfg)) {
+                if (kLongSerial[lk] && (uint64_t)P.n_long < 2 * swarps) continue;
+                if (lk == 4 && (uint64_t)P.n_long >= swarps) continue;
+                runs.push_back({-1, -1, lk});
+            }
         }
         for (size_t ri = 0; ri < runs.size(); ++ri) {
             if (ri == n_short) best_ms = 1e30;  // second stage: the short choice is fixed
@@ -1299,13 +1307,16 @@ int phmm_batch_footprint(phmm_ctx* ctx, const phmm_batch* b, uint64_t* bytes) {
         const uint64_t k = hoff[b->pair_hap[p] + 1] - hoff[b->pair_hap[p]];
         lmax = std::max(lmax, l);
         const uint64_t Wt = (k + seg - 1) / seg;
-        const uint64_t cw = prec == PHMM_PREC_FP64 ? (uint64_t)kCtaWarps : (uint64_t)kCtaWarpsPipe;
+        // the narrowest CTA strips of any FP32 multi-warp kind bound the boundary words
+        const uint64_t cw = prec == PHMM_PREC_FP64 ? (uint64_t)kCtaWarps : (uint64_t)kLongCW[4];
         if (Wt > cw) {  // strips of a very wide pair
             const uint64_t S = (Wt + cw - 1) / cw;
             f += (S - 1) * (l * (prec == PHMM_PREC_FP64 ? 8 : 4) * 8 + sizeof(Partial) + sizeof(CtaPair) + sizeof(CtaItem));
         }
     }
     if (need64) f += (uint64_t)ctx->sms * ctx->occ64 * 2 * lmax * 8 * 8 + 16;
+    if (prec != PHMM_PREC_FP64)  // serial multi-warp kind: two boundaries per resident warp
+        f += (uint64_t)ctx->sms * ctx->occ_longk[3] * (kSerialThreads / 32) * 2 * lmax * sizeof(float4);
     *bytes = f;
     return PHMM_OK;
 }

@@ -93,12 +93,12 @@ def test_columns_per_lane(phmm, variant, N):
     _check(out, flags, oracle.batch(b))
 
 
-LONG_KINDS = ["lean", "pipe32", "pipe24", "serial"]
+LONG_KINDS = ["lean", "pipe32", "pipe24", "serial", "pipe4"]
 
 
 def _long_flag(phmm, kind):
     return {"lean": phmm.F_LONG_LEAN, "pipe32": phmm.F_LONG_PIPE32, "pipe24": phmm.F_LONG_PIPE24,
-            "serial": phmm.F_LONG_SERIAL}[kind]
+            "serial": phmm.F_LONG_SERIAL, "pipe4": phmm.F_LONG_PIPE4}[kind]
 
 
 @pytest.mark.parametrize("variant,N", VARIANTS)
