@@ -193,6 +193,23 @@ def _serve_leg(dev, args):
     return r
 
 
+def _cpu_rowwise(b, pick, ref, cores):
+    """The library's row-wise CPU path (libphmm_cpu.so, FP64, all host cores) on the pairs
+    the cpu_baseline leg sampled, checked against the oracle's values for them."""
+    from paper_2606_25738_gb300 import cpu
+    from paper_2606_25738_gb300 import workloads as W
+    sb = W.subset(b, pick)
+    cells = float(W.cells(sb))
+    cpu.forward(W.subset(b, pick[: min(len(pick), 256)]), cores)  # warm the library and caches
+    t = time.perf_counter()
+    out, _ = cpu.forward(sb, cores)
+    dt = time.perf_counter() - t
+    return {"value": cells / dt / 1e9, "unit": "GCUPS", "cores": cores, "seconds": dt,
+            "max_abs_dlog10_vs_oracle": float(np.max(np.abs(out - ref))),
+            "what": "row-wise CPU path (FP64, vectorised loops, blocked deletion chain) on the "
+                    "cpu_baseline sample"}
+
+
 def _fp64_comparators(b, d, dev, args):
     """The all-FP64 GPU comparators on the same workload (outside the timed region):
     the batched FP64 path of this library over the whole batch, and a plain FP64
@@ -346,6 +363,7 @@ def run_ours(args):
     cpu_v, cores, sdesc, _, pick, ref = _oracle_sample(b, seconds=12.0)
     fp64 = (flg[pick] & 0x5) != 0
     err = float(np.max(np.abs(res[pick] - ref)[~fp64])) if (~fp64).any() else 0.0
+    comparators["cpu_rowwise"] = _cpu_rowwise(b, pick, ref, cores)
     clocks = clk.summary()
     # the dominant kernel is the short-team kernel the plan ran; its DRAM bytes per launch
     # come from an ncu capture of that same kernel (null for any other kernel)

@@ -1,6 +1,7 @@
 """Builds the CUDA library libphmm.so in-tree (paper_2606_25738_gb300/_lib/) with nvcc
 for sm_103a: the translation units compiled in parallel, then linked as a shared
-library exporting the C ABI of include/phmm.h."""
+library exporting the C ABI of include/phmm.h.  build_cpu() builds the separate host
+comparator libphmm_cpu.so (include/phmm_cpu.h) with the C compiler."""
 from __future__ import annotations
 
 import os
@@ -14,6 +15,8 @@ CSRC = os.path.join(HERE, "csrc")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libphmm.so")
 SOURCES = ["kernels_f32.cu", "kernels_f64.cu", "runtime.cu", "noalloc.cu", "serve.cpp"]
+CPU_SOURCE = "cpu_rowwise.c"
+CPU_LIB = os.path.join(LIBDIR, "libphmm_cpu.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "-diag-suppress", "177", "-I" + os.path.join(ROOT, "include"), "-I" + CSRC]
@@ -30,8 +33,8 @@ def _stale() -> bool:
     if not os.path.exists(LIB):
         return True
     t = os.path.getmtime(LIB)
-    deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(ROOT, "include", "phmm.h"),
-                                                                  os.path.abspath(__file__)]
+    deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f != CPU_SOURCE] + [
+        os.path.join(ROOT, "include", "phmm.h"), os.path.abspath(__file__)]
     return any(os.path.getmtime(d) > t for d in deps)
 
 
@@ -65,5 +68,26 @@ def build(force: bool = False, verbose: bool = False) -> str:
     return LIB
 
 
+def build_cpu(force: bool = False) -> str:
+    """Compile (if its sources changed) and return the path of libphmm_cpu.so.  Portable
+    flags only (-O3; no -march): the compiler vectorises for the host's baseline SIMD."""
+    src = os.path.join(CSRC, CPU_SOURCE)
+    deps = [src, os.path.join(ROOT, "include", "phmm_cpu.h"), os.path.join(ROOT, "include", "phmm.h")]
+    if not force and os.path.exists(CPU_LIB) and all(os.path.getmtime(d) <= os.path.getmtime(CPU_LIB) for d in deps):
+        return CPU_LIB
+    os.makedirs(LIBDIR, exist_ok=True)
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        raise RuntimeError("no C compiler for libphmm_cpu.so")
+    tmp = CPU_LIB + "." + str(os.getpid())
+    r = subprocess.run([cc, "-O3", "-std=c11", "-fPIC", "-shared", "-pthread", "-I" + os.path.join(ROOT, "include"),
+                        src, "-o", tmp, "-lm"], capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError("cc failed for %s:\n%s" % (CPU_SOURCE, r.stderr[-4000:]))
+    os.replace(tmp, CPU_LIB)
+    return CPU_LIB
+
+
 if __name__ == "__main__":
     print(build(force=True, verbose=True))
+    print(build_cpu(force=True))

@@ -118,3 +118,21 @@ def test_ctypes_structs_match_header(lib, tmp_path):
         want.append(ctypes.sizeof(cls))
         want += [getattr(cls, f).offset for f, _ in cls._fields_]
     assert got == want
+
+
+def test_cpu_library_exports_its_header():
+    """libphmm_cpu.so (the row-wise CPU comparator) exports what include/phmm_cpu.h declares,
+    and the GPU library does not contain it (no CPU path behind the GPU ABI)."""
+    import ctypes
+    from paper_2606_25738_gb300 import build
+    build.build()
+    path = build.build_cpu()
+    src = open(os.path.join(ROOT, "include", "phmm_cpu.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = sorted(set(re.findall(r"\b(phmm_[a-z_0-9]+)\s*\(", src)))
+    assert names == ["phmm_cpu_forward"]
+    so = ctypes.CDLL(path)
+    for n in names:
+        assert hasattr(so, n), n
+    gpu = ctypes.CDLL(build.LIB)
+    assert not hasattr(gpu, "phmm_cpu_forward")
