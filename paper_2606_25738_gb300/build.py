@@ -70,9 +70,11 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
 def build_cpu(force: bool = False) -> str:
     """Compile (if its sources changed) and return the path of libphmm_cpu.so.  Portable
-    flags only (-O3; no -march): the compiler vectorises for the host's baseline SIMD."""
+    flags only (-O3, no -march: the compiler vectorises for the host's baseline SIMD) and no
+    FMA contraction, so that every host rounds the same way."""
     src = os.path.join(CSRC, CPU_SOURCE)
-    deps = [src, os.path.join(ROOT, "include", "phmm_cpu.h"), os.path.join(ROOT, "include", "phmm.h")]
+    deps = [src, os.path.join(ROOT, "include", "phmm_cpu.h"), os.path.join(ROOT, "include", "phmm.h"),
+            os.path.abspath(__file__)]
     if not force and os.path.exists(CPU_LIB) and all(os.path.getmtime(d) <= os.path.getmtime(CPU_LIB) for d in deps):
         return CPU_LIB
     os.makedirs(LIBDIR, exist_ok=True)
@@ -80,7 +82,8 @@ def build_cpu(force: bool = False) -> str:
     if cc is None:
         raise RuntimeError("no C compiler for libphmm_cpu.so")
     tmp = CPU_LIB + "." + str(os.getpid())
-    r = subprocess.run([cc, "-O3", "-std=c11", "-fPIC", "-shared", "-pthread", "-I" + os.path.join(ROOT, "include"),
+    r = subprocess.run([cc, "-O3", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared", "-pthread",
+                        "-I" + os.path.join(ROOT, "include"),
                         src, "-o", tmp, "-lm"], capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("cc failed for %s:\n%s" % (CPU_SOURCE, r.stderr[-4000:]))
