@@ -387,3 +387,22 @@ def test_serial_strip_edges(phmm, prec, flag):
     else:
         assert np.all((flags & 0x78) == 0)
         assert np.max(np.abs(out - ref)) <= TOL32
+
+
+def test_stats_name_the_kernels_and_no_tune(phmm):
+    """Per-ticket stats report the kernels a plan ran; PHMM_F_NO_TUNE (cost model only)
+    gives oracle-equal results too."""
+    b = W.plain_pairs(40, seed=17, k_range=(100, 6000), l_range=(50, 300))
+    ref = oracle.batch(b)
+    with phmm.Context(precision="fp32", variant="pipe2", cols_per_lane=32, flags=phmm.F_LONG_SERIAL) as ctx:
+        out, flags, rc, st = ctx.run(b)
+    assert phmm.SHORT_KERNELS[st["short_kernel"]].startswith("k_short_pipe2<32")
+    assert phmm.LONG_KERNELS[st["long_kernel"]] == "k_forward_serial<32, 3>"
+    assert st["packed_kernel"] == -1
+    _check(out, flags, ref)
+    with phmm.Context(precision="fp32", flags=phmm.F_NO_TUNE) as ctx:
+        out2, flags2, rc2, st2 = ctx.run(b)
+    _check(out2, flags2, ref)
+    with phmm.Context(precision="fp64") as ctx:
+        out3, flags3, rc3, st3 = ctx.run(b)
+    assert st3["short_kernel"] == -1 and st3["long_kernel"] == -1
