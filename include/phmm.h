@@ -241,11 +241,13 @@ int phmm_wait_test(phmm_ctx *ctx);
  * Test entry (host only, no device needed): builds the work plan the runtime would use
  * for a batch with read lengths l[p], haplotype lengths k[p] and read index pair_read[p]
  * (n pairs), for precision (PHMM_PREC_*) and, in FP32, the short-pair kernel ids (scalar
- * 0..8, packed -1..1) and the multi-warp kernel kind (0..2), and checks it: every pair
- * scheduled exactly once; teams inside their warp, disjoint and wide enough, packed pairs
- * sharing a read; CTA warp ranges inside the CTA and disjoint; a wide pair's strips tiling
- * its columns in order, never placed in an earlier work item than the strip to their left,
- * with matching and disjoint boundary buffers and partial slots.  stats[8] receives:
+ * 0..8, packed -1..1) and the multi-warp kernel kind (0..4, as phmm_stats.long_kernel),
+ * and checks it: every pair scheduled exactly once; teams inside their warp, disjoint and
+ * wide enough, packed pairs sharing a read; CTA warp ranges inside the CTA and disjoint; a
+ * wide pair's strips tiling its columns in order, never placed in an earlier work item
+ * than the strip to their left, with matching and disjoint boundary buffers and partial
+ * slots; in the serial kind one item per wide pair, its strips' partial slots disjoint and
+ * its rows within the serial scratch.  stats[8] receives:
  * teams, warp items, packed warp items, CTA items, CTA pairs, striped pairs, pairs too
  * long, and the number of the failed check (0 = none).  PHMM_OK or PHMM_EINVAL.
  */
