@@ -86,3 +86,9 @@ def test_malformed_batch_is_rejected(cpu):
     with pytest.raises(phmm.PhmmError) as e:
         cpu.forward(b, 1)
     assert e.value.status == phmm.PHMM_EINVAL
+
+
+def test_empty_batch(cpu):
+    b = W.subset(W.plain_pairs(3, seed=1), [])
+    out, fl = cpu.forward(b, 2)
+    assert len(out) == 0 and len(fl) == 0

@@ -406,3 +406,12 @@ def test_stats_name_the_kernels_and_no_tune(phmm):
     with phmm.Context(precision="fp64") as ctx:
         out3, flags3, rc3, st3 = ctx.run(b)
     assert st3["short_kernel"] == -1 and st3["long_kernel"] == -1
+
+
+def test_empty_batch(phmm):
+    """A batch with reads and haplotypes but no pairs completes with empty outputs."""
+    b = W.subset(W.plain_pairs(3, seed=1), [])
+    with phmm.Context() as ctx:
+        out, flags, rc, st = ctx.run(b)
+    assert rc == phmm.PHMM_OK and len(out) == 0 and len(flags) == 0
+    assert st["n_pairs"] == 0 and st["cells"] == 0
