@@ -6,7 +6,7 @@
 
 namespace phmm {
 
-__device__ Rec32 g_dummy32;
+__device__ __align__(16) Rec32 g_dummy32;  // read as two float4
 
 template <>
 __device__ const Rec32* dummy_rec<float>() { return &g_dummy32; }
