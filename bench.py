@@ -22,7 +22,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-METRIC = "GCUPS (FP32+FP64-rescue vs plain FP64, |dlog10|<=1e-3); serve p50/p99 ms"
+METRIC = "GCUPS (FP32+FP64-rescue vs plain FP64, |\u0394log10|\u22641e-3); serve p50/p99 ms"
 WORKLOAD = "short-read batch: 2000 regions x 50 reads (150 bp) x 1-8 haplotypes (250-600 bp)"
 
 
