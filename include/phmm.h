@@ -37,7 +37,7 @@
 extern "C" {
 #endif
 
-#define PHMM_ABI_VERSION 2
+#define PHMM_ABI_VERSION 3
 
 /* Opaque context: device arenas, stream, captured graphs, pending tickets. */
 typedef struct phmm_ctx phmm_ctx;
@@ -171,6 +171,13 @@ typedef struct {
     int32_t short_kernel;
     int32_t packed_kernel;
     int32_t long_kernel;
+    /* The FP32 forward pass runs three branches concurrently, each a persistent kernel on
+     * its own stream: [0] scalar short teams, [1] packed short teams, [2] multi-warp pairs.
+     * cells_branch = sum of l * k over the pairs each branch scored; ms_branch = device time
+     * of each branch's kernel (CUDA events on its stream).  FP64: [0] holds the whole
+     * forward pass. */
+    uint64_t cells_branch[3];
+    float ms_branch[3];
 } phmm_stats;
 
 /* Create a context on cfg->device.  *out receives the handle.  PHMM_EINVAL on a bad
@@ -323,11 +330,17 @@ void phmm_server_destroy(phmm_server *srv);
  *            its own work to finish before returning.
  *   batch    as for phmm_submit_batch, with inputs_on_device = outputs_on_device = 1 (all
  *            pointers are device pointers) and out_flags required.
+ * Offsets are checked on the device before they are used: a pair whose read or
+ * haplotype is empty, runs backwards or ends past the last offset gets NaN and
+ * PHMM_PAIR_ERROR, and the call returns PHMM_EINVAL (as phmm_submit_batch would).
  * Limits: at most 2^20 read bases in the batch (PHMM_ENOMEM beyond) and haplotypes of at
  * most 1024 bases (such pairs get NaN and PHMM_PAIR_ERROR; the call returns PHMM_EINVAL).
- * FP32 only (no FP64 rescue pass): out_flags reports PHMM_PAIR_DANGER / NONFINITE /
- * DEGENERATE where the regular API would rescue.  All calls share the scratch, so calls
- * that overlap on the GPU (other streams or threads) race and must be serialised.
+ * FP32 only (no FP64 rescue pass): out_flags sets PHMM_PAIR_DANGER / NONFINITE /
+ * SMALL_SUM / DEGENERATE by the same tests the regular API uses to pick pairs for its FP64
+ * pass, and the call still returns PHMM_OK for such pairs.  The per-row coefficients are
+ * rounded with the regular API's default seed, so they equal a default context's.  All
+ * calls share the scratch, so calls that overlap on the GPU (other streams or threads)
+ * race and must be serialised.
  */
 int phmm_forward_noalloc(int device, void *stream, const phmm_batch *batch);
 

@@ -26,6 +26,9 @@ constexpr uint64_t kNaMaxBases = 1ull << 20;  // records scratch: 32 MiB
 constexpr int kNaN = 32;                      // columns per lane
 constexpr uint32_t kNaMaxCols = 32u * kNaN;   // one warp per pair
 constexpr uint32_t kNaScratchFull = 1u << 8;  // status bit: more read bases than the scratch holds
+// Seed of the stochastic rounding of the per-row coefficients: the same value a context
+// uses by default, so the records (and hence the results) equal the regular path's.
+constexpr uint32_t kNaRoundingSeed = 0x5eed1234u;
 
 // Scratch (every GPU that loads the library holds these until the process exits).
 static __device__ __align__(256) Rec32 na_rec[kNaMaxBases];
@@ -113,7 +116,7 @@ __global__ void __launch_bounds__(256) k_na_prep(const uint8_t* __restrict__ rb,
             x.del = min(x.del, kMaxPhred);
             x.gcp = min(x.gcp, kMaxPhred);
             x.delp = min(x.delp, kMaxPhred);
-            const Rec32 r = make_rec32(x, tq, tom, tq3, tinv, 0x5eed1234u, b);
+            const Rec32 r = make_rec32(x, tq, tom, tq3, tinv, kNaRoundingSeed, b);
             float4* dst = reinterpret_cast<float4*>(rec + b);
             dst[0] = make_float4(r.pm, r.px, r.a, r.b);
             dst[1] = make_float4(r.mi, r.g, r.gm, __uint_as_float(r.meta));
@@ -142,18 +145,27 @@ __global__ void __launch_bounds__(128) k_na_forward(const uint8_t* __restrict__ 
     const int lane = threadIdx.x & 31;
     const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
     const int R = checkpoint_interval<float>(words + 1);
-    const bool scratch_ok = read_off[n_reads] <= kNaMaxBases;
+    const uint64_t read_end = read_off[n_reads], hap_end = hap_off[n_haps];
+    const bool scratch_ok = read_end <= kNaMaxBases;
     for (uint32_t p = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; p < n_pairs; p += warps) {
         const uint32_t r = pair_read[p], h = pair_hap[p];
         bool ok = scratch_ok && r < n_reads && h < n_haps;
         int l = 0, k = 0;
         uint64_t roff = 0, hoff = 0;
         if (ok) {
-            roff = read_off[r];
-            hoff = hap_off[h];
-            l = (int)(read_off[r + 1] - roff);
-            k = (int)(hap_off[h + 1] - hoff);
-            ok = l >= 1 && k >= 1 && (uint32_t)k <= kNaMaxCols;
+            // Offsets are checked here, before any access through them: each read and
+            // haplotype must be a non-empty range inside [0, last offset] (the records
+            // scratch holds exactly the bases below read_off[n_reads]).  Lengths stay
+            // 64-bit until they are known to be small.
+            const uint64_t r0 = read_off[r], r1 = read_off[r + 1];
+            const uint64_t h0 = hap_off[h], h1 = hap_off[h + 1];
+            ok = r0 < r1 && r1 <= read_end && h0 < h1 && h1 <= hap_end && h1 - h0 <= kNaMaxCols;
+            if (ok) {
+                roff = r0;
+                hoff = h0;
+                l = (int)(r1 - r0);  // <= kNaMaxBases
+                k = (int)(h1 - h0);  // <= kNaMaxCols
+            }
         }
         if (!ok) {
             if (lane == 0) {
@@ -173,11 +185,16 @@ __global__ void __launch_bounds__(128) k_na_forward(const uint8_t* __restrict__ 
                 f = 0x80u;
                 atomicOr(words, ST_BAD_INPUT);
             } else {
-                v = o.S > 0.0 && isfinite(o.S) ? log10(o.S) + (double)(o.E - 120) * 0.30102999566398119521
-                                               : (o.S == 0.0 ? -INFINITY : NAN);
+                v = o.S > 0.0 && isfinite(o.S)
+                        ? log10(o.S) + (double)(o.E - Num<float>::kLog2C) * 0.30102999566398119521
+                        : (o.S == 0.0 ? -INFINITY : NAN);
+                // The regular path's selection for its FP64 pass: the engine's flags plus
+                // the underflow test on the FP32 sum in stored units (1e4 * 3 l k FLT_MIN).
+                const double tau = 3.0e4 * (double)l * (double)k * 1.1754943508222875e-38;
                 if (o.flags & PF_RESCALED) f |= 0x2u;
                 if (o.flags & PF_DANGER) f |= 0x8u;
-                if (o.flags & PF_NONFINITE) f |= 0x10u;
+                if ((o.flags & PF_NONFINITE) || !isfinite(o.S)) f |= 0x10u;
+                if (!(o.S > tau)) f |= 0x20u;
                 if (o.flags & PF_DEGEN) f |= 0x40u;
             }
             out[p] = v;

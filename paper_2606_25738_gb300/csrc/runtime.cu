@@ -97,6 +97,7 @@ struct Plan {
     uint32_t n_extra = 0;     // extra partial slots (strips 1.. of wide pairs)
     int long_kind = 0;        // FP32 multi-warp kernel (launch.h: kLongN / kLongCW)
     uint32_t serial_rows = 0; // long kind 3: longest read among the serial pairs
+    uint64_t cells_br[3] = {0, 0, 0};  // cells of the scalar, packed and multi-warp branches
 };
 
 // Cost model constants (issue slots): per lane and cell of a row, and per lane and row
@@ -233,6 +234,10 @@ void make_plan(const uint32_t* l, const uint32_t* k, const uint32_t* pr, uint32_
             }
         }
     }
+    for (const Team& t : st) P.cells_br[0] += (uint64_t)l[t.pair] * k[t.pair];
+    for (const Team& t : pt)
+        P.cells_br[1] += (uint64_t)l[t.pair] * k[t.pair] + (uint64_t)l[t.pair2] * k[t.pair2];
+    for (uint32_t p : lo) P.cells_br[2] += (uint64_t)l[p] * k[p];
     pack_teams(st, sl, P.teams, P.witems, (double)Ns, P.cost);
     pack_teams(pt, pl, P.teams, P.witems2, 2.0 * NP * 1.2, P.cost);
     // long pairs
@@ -452,6 +457,10 @@ struct Slot {
     // sm carries the pipeline, sb2/sb3 the multi-warp and packed branches of the forward pass.
     cudaStream_t sm = nullptr, sb2 = nullptr, sb3 = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_join3 = nullptr, ev_user = nullptr;
+    // FP32 forward branches, each timed on its own stream: [0, 1] scalar short teams (sm),
+    // [2, 3] packed teams (sb3), [4, 5] multi-warp pairs (sb2)
+    cudaEvent_t ev_br[6] = {};
+    bool br_timed = false;
     uint64_t foot = 0;  // admitted device footprint while pending
     cudaGraphExec_t gexec = nullptr;
     int g_key = -1;
@@ -555,10 +564,11 @@ int launch_sequence(phmm_ctx* ctx, Slot& S, int scal_id, int pack_id, int long_k
     const PhredTables* T = static_cast<const PhredTables*>(ctx->tables.p);
     const int prec = ctx->cfg.precision;
     const int grid_pre = ctx->sms * 4;
-    auto rec = [&](cudaEvent_t ev) {
-        if (record_events) return cudaEventRecordWithFlags(ev, s, cudaEventRecordExternal);
-        return cudaEventRecord(ev, s);
+    auto rec_on = [&](cudaEvent_t ev, cudaStream_t st) {
+        if (record_events) return cudaEventRecordWithFlags(ev, st, cudaEventRecordExternal);
+        return cudaEventRecord(ev, st);
     };
+    auto rec = [&](cudaEvent_t ev) { return rec_on(ev, s); };
     launch_reset(H, ctx->sms * 4, s);
     if (prec == PHMM_PREC_FP64) {
         launch_prep64_all(H, T, grid_pre, s);
@@ -577,17 +587,24 @@ int launch_sequence(phmm_ctx* ctx, Slot& S, int scal_id, int pack_id, int long_k
         CK(cudaStreamWaitEvent(S.sb2, S.ev_fork, 0));
         CK(cudaStreamWaitEvent(S.sb3, S.ev_fork, 0));
         const void* lpow = ctx->pow32[pow_index(kLongN[long_kind])].p;
+        CK(rec_on(S.ev_br[4], S.sb2));
         if (long_kind > 0)
             launch_forward32_long_pipe(long_kind, H, lpow, ctx->sms * ctx->occ_longk[long_kind], S.sb2);
         else
             launch_forward32_long(H, lpow, ctx->sms * ctx->occ_longk[0], S.sb2);
+        CK(rec_on(S.ev_br[5], S.sb2));
         CK(cudaEventRecord(S.ev_join, S.sb2));
+        CK(rec_on(S.ev_br[2], S.sb3));
         if (pack_id >= 0)
             launch_short_packed(pack_id, H, ctx->pow32[pow_index(kShortPackedN[pack_id])].p,
                                 ctx->sms * ctx->occ_packed[pack_id], S.sb3);
+        CK(rec_on(S.ev_br[3], S.sb3));
         CK(cudaEventRecord(S.ev_join3, S.sb3));
+        CK(rec(S.ev_br[0]));
         launch_short_scalar(scal_id, H, ctx->pow32[pow_index(kShortScalarN[scal_id])].p,
                             ctx->sms * ctx->occ_scalar[scal_id], s);
+        CK(rec(S.ev_br[1]));
+        S.br_timed = true;
         CK(cudaStreamWaitEvent(s, S.ev_join, 0));
         CK(cudaStreamWaitEvent(s, S.ev_join3, 0));
         CK(rec(S.ev_fwd1));
@@ -824,7 +841,8 @@ int phmm_create(const phmm_config* cfg, phmm_ctx** out) {
     }
     ctx->slots.resize(ctx->cfg.max_inflight);
     for (auto& S : ctx->slots) {
-        cudaEvent_t* evs[] = {&S.ev_copy, &S.ev_start, &S.ev_fwd0, &S.ev_fwd1, &S.ev_res0, &S.ev_res1, &S.ev_end};
+        cudaEvent_t* evs[] = {&S.ev_copy, &S.ev_start, &S.ev_fwd0, &S.ev_fwd1, &S.ev_res0, &S.ev_res1, &S.ev_end,
+                              &S.ev_br[0], &S.ev_br[1], &S.ev_br[2], &S.ev_br[3], &S.ev_br[4], &S.ev_br[5]};
         for (auto* e : evs)
             if (cudaEventCreate(e) != cudaSuccess) return fail(PHMM_ECUDA);
         cudaEvent_t* evn[] = {&S.ev_fork, &S.ev_join, &S.ev_join3, &S.ev_user};
@@ -860,7 +878,8 @@ void phmm_destroy(phmm_ctx* ctx) {
         for (auto* b : d) release(*b);
         HostBuf* h[] = {&S.h_out, &S.h_oflags, &S.h_small, &S.h_roff, &S.h_hoff, &S.h_pr, &S.h_ph};
         for (auto* b : h) release(*b);
-        cudaEvent_t evs[] = {S.ev_copy, S.ev_start, S.ev_fwd0, S.ev_fwd1, S.ev_res0, S.ev_res1, S.ev_end};
+        cudaEvent_t evs[] = {S.ev_copy, S.ev_start, S.ev_fwd0, S.ev_fwd1, S.ev_res0, S.ev_res1, S.ev_end,
+                             S.ev_br[0], S.ev_br[1], S.ev_br[2], S.ev_br[3], S.ev_br[4], S.ev_br[5]};
         for (auto e : evs)
             if (e) cudaEventDestroy(e);
         cudaEvent_t evn[] = {S.ev_fork, S.ev_join, S.ev_join3, S.ev_user};
@@ -1270,6 +1289,7 @@ int phmm_submit_batch(phmm_ctx* ctx, const phmm_batch* b, uint64_t* ticket) {
         S->st.short_kernel = f32 && !P.witems.empty() ? P.scal_id : -1;
         S->st.packed_kernel = f32 && !P.witems2.empty() ? P.pack_id : -1;
         S->st.long_kernel = f32 && !P.citems.empty() ? P.long_kind : -1;
+        for (int q = 0; q < 3; ++q) S->st.cells_branch[q] = f32 ? P.cells_br[q] : (q == 0 ? cells : 0);
     }
     S->host_status = P.n_too_long ? PHMM_EINVAL : PHMM_OK;
     S->plan_valid = true;
@@ -1363,6 +1383,12 @@ int phmm_poll(phmm_ctx* ctx, uint64_t ticket, int timeout_ms) {
     ms = 0.f;
     cudaEventElapsedTime(&ms, S->ev_res0, S->ev_res1);
     S->st.ms_rescue = ms;
+    for (int q = 0; q < 3; ++q) {
+        ms = 0.f;
+        if (S->br_timed) cudaEventElapsedTime(&ms, S->ev_br[2 * q], S->ev_br[2 * q + 1]);
+        S->st.ms_branch[q] = ms;
+    }
+    if (!S->br_timed) S->st.ms_branch[0] = S->st.ms_forward;  // FP64: one forward kernel
     ctx->last_stats = S->st;
     ctx->last_retired = S->ticket;
     ctx->inflight_foot -= S->foot;

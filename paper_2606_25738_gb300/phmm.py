@@ -59,7 +59,7 @@ class Batch(ctypes.Structure):
                 ("inputs_on_device", ctypes.c_int), ("outputs_on_device", ctypes.c_int)]
 
 
-ABI_VERSION = 2  # PHMM_ABI_VERSION of include/phmm.h
+ABI_VERSION = 3  # PHMM_ABI_VERSION of include/phmm.h
 
 # Kernel names behind phmm_stats.short_kernel / packed_kernel / long_kernel.
 SHORT_KERNELS = ["k_short_scalar<32, 4>", "k_short_scalar<24, 4>", "k_short_scalar<24, 5>",
@@ -78,10 +78,12 @@ class Stats(ctypes.Structure):
                 ("ms_h2d", ctypes.c_float), ("kernel_launches", ctypes.c_uint32),
                 ("status_bits", ctypes.c_uint32), ("ms_host", ctypes.c_float),
                 ("short_kernel", ctypes.c_int32), ("packed_kernel", ctypes.c_int32),
-                ("long_kernel", ctypes.c_int32)]
+                ("long_kernel", ctypes.c_int32), ("cells_branch", ctypes.c_uint64 * 3),
+                ("ms_branch", ctypes.c_float * 3)]
 
     def as_dict(self) -> dict:
-        return {name: getattr(self, name) for name, _ in self._fields_}
+        return {name: (list(v) if isinstance(v, ctypes.Array) else v)
+                for name, v in ((n, getattr(self, n)) for n, _ in self._fields_)}
 
 
 class ServerConfig(ctypes.Structure):

@@ -218,15 +218,27 @@ def long_pairs(n_pairs: int = 64, seed: int = 0, k_range=(1000, 100000), read_fr
     return _pack(reads, quals, haps, idx, idx)
 
 
+def _unpack_bases(raw: np.ndarray, n: int) -> np.ndarray:
+    """n uniform ACGT bases from random bytes (four 2-bit codes per byte)."""
+    codes = np.empty(4 * len(raw), np.uint8)
+    for s in range(4):
+        codes[s::4] = (raw >> (2 * s)) & 3
+    return ACGT[codes[:n]]
+
+
 def uneven_pairs(n_pairs: int = 1_000_000, seed: int = 0, len_range=(50, 20000),
-                 chunk: int = 65536) -> dict:
+                 chunk: int = 16384, threads: int | None = None) -> dict:
     """Uneven-length batch: read and haplotype lengths each log-uniform in
     ``len_range``, drawn independently and swapped so that haplotype >= read; the read
     is copied from a random haplotype offset with the short-read error and quality model
     (substitutions at a per-read rate U[0.5%, 2%], 1% N, quals 85% U{30..41} / 15%
-    U{2..29}, ins/del U{40..45}, gcp 10).  Vectorised over chunks of pairs, so the full
-    million pairs (about 1.1e9 read and 5.6e9 haplotype bases) take memory in proportion
-    to the output only."""
+    U{2..29}, ins/del U{40..45}, gcp 10).  The million pairs hold about 1.1e9 read and
+    5.6e9 haplotype bases: the lengths come from one stream, then every chunk of
+    ``chunk`` pairs draws its bases and qualities from a stream of its own, so chunks run
+    on ``threads`` threads (default: all cores) and the bytes do not depend on the thread
+    count."""
+    from concurrent.futures import ThreadPoolExecutor
+    import os
     rng = _rng(seed, 4)
     lo, hi = np.log(len_range[0]), np.log(len_range[1])
     a = np.rint(np.exp(rng.uniform(lo, hi, size=n_pairs))).astype(np.int64)
@@ -237,35 +249,61 @@ def uneven_pairs(n_pairs: int = 1_000_000, seed: int = 0, len_range=(50, 20000),
     roff[1:] = np.cumsum(ls)
     hoff[1:] = np.cumsum(ks)
     nb, nh = int(roff[-1]), int(hoff[-1])
-    hap = ACGT[rng.integers(0, 4, size=nh, dtype=np.uint8)]
+    off = (rng.random(n_pairs) * (ks - ls + 1)).astype(np.int64)
+    rate = rng.uniform(0.005, 0.02, size=n_pairs)
+    hap = np.empty(nh, np.uint8)
     read = np.empty(nb, np.uint8)
     bq = np.empty(nb, np.uint8)
     iq = np.empty(nb, np.uint8)
     dq = np.empty(nb, np.uint8)
-    off = (rng.random(n_pairs) * (ks - ls + 1)).astype(np.int64)
-    rate = rng.uniform(0.005, 0.02, size=n_pairs)
-    for p0 in range(0, n_pairs, chunk):
+
+    def fill(ci: int) -> None:
+        p0 = ci * chunk
         p1 = min(n_pairs, p0 + chunk)
+        g = np.random.Generator(np.random.PCG64(np.random.SeedSequence([seed, 4, ci + 1])))
+        h0, h1 = int(hoff[p0]), int(hoff[p1])
+        hap[h0:h1] = _unpack_bases(np.frombuffer(g.bytes((h1 - h0 + 3) // 4), np.uint8), h1 - h0)
         L = ls[p0:p1]
         b0, b1 = int(roff[p0]), int(roff[p1])
         n = b1 - b0
         first = np.repeat(hoff[p0:p1].astype(np.int64) + off[p0:p1], L)
         within = np.arange(n, dtype=np.int64) - np.repeat(roff[p0:p1].astype(np.int64) - b0, L)
         r = hap[first + within]
-        m = rng.random(n) < np.repeat(rate[p0:p1], L)
+        m = g.random(n) < np.repeat(rate[p0:p1], L)
         if m.any():
             codes = np.searchsorted(ACGT, r[m])
-            r[m] = ACGT[(codes + rng.integers(1, 4, size=int(m.sum()))) % 4]
-        r[rng.random(n) < 0.01] = ord("N")
+            r[m] = ACGT[(codes + g.integers(1, 4, size=int(m.sum()))) % 4]
+        r[g.random(n) < 0.01] = ord("N")
         read[b0:b1] = r
-        hq = rng.random(n) < 0.85
-        bq[b0:b1] = np.where(hq, rng.integers(30, 42, size=n), rng.integers(2, 30, size=n))
-        iq[b0:b1] = rng.integers(40, 46, size=n)
-        dq[b0:b1] = rng.integers(40, 46, size=n)
+        hq = g.random(n) < 0.85
+        bq[b0:b1] = np.where(hq, g.integers(30, 42, size=n, dtype=np.uint8), g.integers(2, 30, size=n, dtype=np.uint8))
+        iq[b0:b1] = g.integers(40, 46, size=n, dtype=np.uint8)
+        dq[b0:b1] = g.integers(40, 46, size=n, dtype=np.uint8)
+
+    n_chunks = (n_pairs + chunk - 1) // chunk
+    with ThreadPoolExecutor(max_workers=threads or os.cpu_count() or 1) as ex:
+        list(ex.map(fill, range(n_chunks)))
     idx = np.arange(n_pairs, dtype=np.uint32)
     return {"read_bases": read, "read_off": roff, "hap_bases": hap, "hap_off": hoff,
             "pair_read": idx, "pair_hap": idx.copy(), "base_q": bq, "ins_q": iq, "del_q": dq,
             "gcp_q": np.full(nb, 10, np.uint8)}
+
+
+def stratified_sample(b: dict, per_decile: int, seed: int = 0, max_cells: float = 4e10) -> np.ndarray:
+    """Pair indices for a parity check: up to ``per_decile`` random pairs from each decile
+    of the per-pair cell count l*k, keeping the sample's total cells under ``max_cells``
+    (largest pairs thinned first)."""
+    rl, hl = pair_lengths(b)
+    c = rl * hl
+    order = np.argsort(c, kind="stable")
+    rng = np.random.default_rng(seed)
+    picks = [rng.choice(dec, min(per_decile, len(dec)), replace=False)
+             for dec in np.array_split(order, 10) if len(dec)]
+    pick = np.unique(np.concatenate(picks)) if picks else np.zeros(0, np.int64)
+    while c[pick].sum() > max_cells and len(pick) > 10:
+        big = np.argsort(c[pick])[::-1]
+        pick = np.delete(pick, big[: max(1, len(pick) // 20)])
+    return pick
 
 
 def _short_read_quals(rng, n: int):

@@ -56,7 +56,6 @@ def test_long_pairs_fp64_full(phmm, long_batch):
 def test_uneven_million_pairs_sampled(phmm):
     import torch
 
-    from paper_2606_25738_gb300 import configs
     b = W.uneven_pairs(1_000_000, seed=0)
     n = len(b["pair_read"])
     d = phmm.to_device(b)
@@ -67,7 +66,7 @@ def test_uneven_million_pairs_sampled(phmm):
         assert ctx.poll(t, -1) == 0
     res, flags = out.cpu().numpy(), fl.cpu().numpy()
     assert np.all(np.isfinite(res))
-    pick = configs.stratified_sample(b, 200, max_cells=2e10)
+    pick = W.stratified_sample(b, 200, max_cells=2e10)
     resc = np.flatnonzero(flags & phmm.PAIR_RESCUED)[:200]
     pick = np.unique(np.concatenate([pick, resc]))
     ref = oracle.batch(b, pairs=pick)
@@ -83,7 +82,6 @@ def test_short_read_batch_full_sampled(phmm):
     pair match the oracle; a second replay gives the same bits."""
     import torch
 
-    from paper_2606_25738_gb300 import configs
     b = W.short_read_regions(2000, seed=0)
     n = len(b["pair_read"])
     d = phmm.to_device(b)
@@ -99,7 +97,7 @@ def test_short_read_batch_full_sampled(phmm):
     res, flags = out.cpu().numpy(), fl.cpu().numpy()
     assert np.array_equal(res, res1)
     assert st["n_pairs"] == n and np.all(np.isfinite(res))
-    pick = configs.stratified_sample(b, 300)
+    pick = W.stratified_sample(b, 300)
     resc = np.flatnonzero(flags & phmm.PAIR_RESCUED)[:200]
     pick = np.unique(np.concatenate([pick, resc]))
     ref = oracle.batch(b, pairs=pick)
