@@ -108,6 +108,10 @@ typedef struct {
                                  only (the next row's scan-independent work overlaps the
                                  deletion scan); 5 = pipelined engine with each lane's two
                                  column halves in packed FP32 pairs */
+    double fp32_tolerance;    /* largest |error of log10 L| accepted from the FP32 pass
+                                 (0 = 1e-3): with PHMM_PREC_FP32_RESCUE a pair whose
+                                 a-priori FP32 rounding bound exceeds it is recomputed in
+                                 FP64 (flag PHMM_PAIR_DANGER) */
 } phmm_config;
 
 /*
@@ -142,7 +146,9 @@ typedef struct {
 #define PHMM_PAIR_RESCALED 0x2u /* power-of-two rescaling was applied */
 #define PHMM_PAIR_FP64 0x4u     /* final value computed in FP64 */
 /* why the FP32 pass selected a pair for the FP64 rescue (kept when it was rescued) */
-#define PHMM_PAIR_DANGER 0x8u     /* a checkpoint row maximum fell below the danger level */
+#define PHMM_PAIR_DANGER 0x8u     /* FP32 accuracy not assured: a checkpoint row maximum
+                                     fell below the danger level, or the pair's a-priori
+                                     FP32 rounding bound exceeds the FP32 tolerance */
 #define PHMM_PAIR_NONFINITE 0x10u /* an inf / nan appeared */
 #define PHMM_PAIR_SMALL_SUM 0x20u /* the FP32 last-row sum failed the underflow test */
 #define PHMM_PAIR_DEGENERATE 0x40u /* gcp Phred 0 (T_DD = 1): factored FP32 form unusable */

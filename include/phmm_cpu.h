@@ -2,15 +2,15 @@
  * phmm_cpu -- the row-wise PairHMM forward pass on the host CPU (a comparator for the GPU
  * library; a separate shared library, libphmm_cpu.so, that libphmm.so never calls).
  *
- * It evaluates the same recurrences as the GPU path (Section 2, Eq. 1-4) in the paper's
- * row-wise CPU form (Section 3.1, Eq. 5-7): per row, every column's Match and Insertion
- * value from the previous row in vectorisable loops, then the deletion chain
- * D_ij = T_MD M_i,j-1 + g_i D_i,j-1 as a first-order linear recurrence, split into blocks
- * that run as independent chains and are then joined by their carries g^m.  Arithmetic is
- * FP64 with power-of-two rescaling every 16 rows, so no pair needs a second pass.
+ * It evaluates the same recurrences as the GPU path (Section 2, Eq. 1-4) with the paper's
+ * CPU mapping (Section 3.5): one (read, haplotype) pair per SIMD lane, pairs of similar
+ * length packed side by side (on AArch64 8 pairs per FP32 pack, 4 per FP64 pack), every
+ * instruction updating one cell of each pair of a pack.  Per lane, rows are computed in
+ * order and the deletion chain D_ij = T_MD M_i,j-1 + g_i D_i,j-1 left to right, so no scan
+ * is needed.  Power-of-two rescaling per lane keeps long reads in range.
  *
  * Inputs use the phmm_batch layout of phmm.h; every pointer must be a host pointer
- * (inputs_on_device and outputs_on_device are ignored and must be 0).
+ * (inputs_on_device and outputs_on_device must be 0).
  */
 #ifndef PHMM_CPU_H
 #define PHMM_CPU_H
@@ -21,14 +21,23 @@
 extern "C" {
 #endif
 
-/* log10 L for every pair of b into b->out_log10 (caller-owned, n_pairs doubles); when
- * b->out_flags is not NULL, each pair's flags get PHMM_PAIR_FP64, or PHMM_PAIR_ERROR for an
- * invalid pair (its result is NaN).  n_threads POSIX threads take pairs from a shared
- * counter (n_threads <= 0: one per online core).  Returns PHMM_OK, or PHMM_EINVAL for a
- * malformed batch (NULL arrays, offsets out of order or out of range) -- per-pair problems
- * (a base other than ACGTN, a quality above 93, an empty read or haplotype) mark only
- * that pair.  PHMM_ENOMEM if scratch memory cannot be allocated. */
-int phmm_cpu_forward(const phmm_batch *b, int n_threads);
+/* log10 L for every pair of b into b->out_log10 (caller-owned, n_pairs doubles).
+ *   n_threads       POSIX threads taking packs from a shared counter (<= 0: one per
+ *                   online core); results do not depend on it.
+ *   precision       PHMM_PREC_FP32_RESCUE: FP32, then FP64 for every pair the FP32 pass
+ *                   flags (a non-finite value, a checkpoint maximum below the danger
+ *                   level, the last-row sum below 1e4 * 3 l k FLT_MIN, or an a-priori
+ *                   rounding bound above fp32_tolerance); PHMM_PREC_FP64: every pair in
+ *                   FP64; PHMM_PREC_FP32_ONLY: FP32, flagged pairs keep their FP32 value.
+ *   fp32_tolerance  largest |error of log10 L| accepted from the FP32 pass (0: 1e-3).
+ * b->out_flags (optional) gets the PHMM_PAIR_* bits of phmm.h per pair: RESCALED, FP64,
+ * RESCUED, the reason bits (DANGER also covers the rounding bound), or ERROR for an
+ * invalid pair (its result is NaN).  Returns PHMM_OK, or PHMM_EINVAL for a malformed
+ * batch (NULL arrays, offsets out of order or out of range, a bad precision or
+ * tolerance) -- per-pair problems (a base other than ACGTN, a quality above 93, an empty
+ * read or haplotype) mark only that pair.  PHMM_ENOMEM if scratch memory cannot be
+ * allocated. */
+int phmm_cpu_forward(const phmm_batch *b, int n_threads, int precision, double fp32_tolerance);
 
 #ifdef __cplusplus
 }

@@ -16,6 +16,7 @@ LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libphmm.so")
 SOURCES = ["kernels_f32.cu", "kernels_f64.cu", "runtime.cu", "noalloc.cu", "serve.cpp"]
 CPU_SOURCE = "cpu_rowwise.c"
+CPU_DEPS = ["cpu_rowwise.c", "cpu_engine.inc"]
 CPU_LIB = os.path.join(LIBDIR, "libphmm_cpu.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
@@ -33,7 +34,7 @@ def _stale() -> bool:
     if not os.path.exists(LIB):
         return True
     t = os.path.getmtime(LIB)
-    deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f != CPU_SOURCE] + [
+    deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f not in CPU_DEPS] + [
         os.path.join(ROOT, "include", "phmm.h"), os.path.abspath(__file__)]
     return any(os.path.getmtime(d) > t for d in deps)
 
@@ -70,11 +71,12 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
 def build_cpu(force: bool = False) -> str:
     """Compile (if its sources changed) and return the path of libphmm_cpu.so.  Portable
-    flags only (-O3, no -march: the compiler vectorises for the host's baseline SIMD) and no
-    FMA contraction, so that every host rounds the same way."""
+    flags only (-O3, no -march: the generic vector types map to the host's baseline SIMD,
+    NEON on Arm and SSE2 on x86); FMA contraction is allowed where the host has FMA."""
     src = os.path.join(CSRC, CPU_SOURCE)
-    deps = [src, os.path.join(ROOT, "include", "phmm_cpu.h"), os.path.join(ROOT, "include", "phmm.h"),
-            os.path.abspath(__file__)]
+    deps = [os.path.join(CSRC, f) for f in CPU_DEPS] + [
+        os.path.join(ROOT, "include", "phmm_cpu.h"), os.path.join(ROOT, "include", "phmm.h"),
+        os.path.abspath(__file__)]
     if not force and os.path.exists(CPU_LIB) and all(os.path.getmtime(d) <= os.path.getmtime(CPU_LIB) for d in deps):
         return CPU_LIB
     os.makedirs(LIBDIR, exist_ok=True)
@@ -82,7 +84,7 @@ def build_cpu(force: bool = False) -> str:
     if cc is None:
         raise RuntimeError("no C compiler for libphmm_cpu.so")
     tmp = CPU_LIB + "." + str(os.getpid())
-    r = subprocess.run([cc, "-O3", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared", "-pthread",
+    r = subprocess.run([cc, "-O3", "-std=gnu11", "-ffp-contract=fast", "-fPIC", "-shared", "-pthread",
                         "-I" + os.path.join(ROOT, "include"),
                         src, "-o", tmp, "-lm"], capture_output=True, text=True)
     if r.returncode != 0:

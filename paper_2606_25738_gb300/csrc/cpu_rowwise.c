@@ -1,8 +1,7 @@
 /*
  * Row-wise PairHMM forward pass on the host CPU (include/phmm_cpu.h).
  *
- * Per pair, rows i = 1..l over columns j = 1..k (Section 2, Eq. 1-4; row-wise form of
- * Section 3.1, Eq. 5-7):
+ * Per pair, rows i = 1..l over columns j = 1..k (Section 2, Eq. 1-4):
  *   M_ij = P_ij (T_MM_i M_i-1,j-1 + T_IM_i I_i-1,j-1 + T_DM_i D_i-1,j-1)
  *   I_ij = T_MI_i M_i-1,j + g_i I_i-1,j
  *   D_ij = T_MD_i M_i,j-1 + g_i D_i,j-1
@@ -11,15 +10,22 @@
  * T_IM = T_DM = 1 - g; P = 1 - q(base) on a match (an N on either side matches), else
  * q(base) / 3; q(x) = 10^(-x / 10).
  *
- * The M and I loops of a row read only the previous row: they vectorise.  The deletion
- * chain is the first-order recurrence d_j = a_j + g d_j-1 (a_j = T_MD M_i,j-1); it is
- * evaluated in NB blocks of the row at once (NB independent dependency chains, each from
- * a zero carry), then each block's true carry enters as carry * g^(m + 1) at its m-th
- * column (a vectorisable fix-up).  FP64 throughout; every 16 rows the row is multiplied by
- * a power of two that brings its maximum to 2^500 (exact), and the exponents are summed.
+ * CPU mapping (the paper's Section 3.5): one pair per SIMD lane.  Pairs are sorted by
+ * length (read-length class, then haplotype length) and taken in packs of equal-ish
+ * shape; a pack's lanes step through their rows and columns together, so every
+ * instruction updates one cell of every pair of the pack (cpu_engine.inc).  The vectors
+ * are the compiler's generic vector types: the same source builds for NEON on Arm and
+ * SSE2 on x86, with no intrinsics and no target flags.
  *
- * Portable C: no intrinsics, no target flags; the compiler vectorises the loops for the
- * host's SIMD unit (NEON / SVE on Arm, SSE on x86).
+ * Range: power-of-two rescaling per lane at checkpoints every R rows (R from the pack's
+ * worst per-row drop and growth), folded into the next row's coefficients.
+ * Precision (phmm_precision): FP32 with FP64 rescue of flagged pairs, FP64 for every
+ * pair, or FP32 alone.  The FP32 pass flags a pair for the FP64 pass on the same tests
+ * as the GPU library: a non-finite value, a checkpoint maximum below the danger level,
+ * the last-row sum below tau(l, k) = 1e4 * 3 l k 2^-106 (this path flushes cells below
+ * 2^-106 to zero; the GPU's test uses FLT_MIN), or an a-priori rounding bound
+ * above the FP32 tolerance.  FP32 per-row coefficients are stochastically rounded from
+ * double, so their rounding errors average out over long reads instead of drifting.
  */
 #include "phmm_cpu.h"
 
@@ -30,8 +36,21 @@
 #include <string.h>
 #include <unistd.h>
 
-#define NB 8             /* deletion-chain blocks per row */
-#define RESCALE_ROWS 16  /* rows between power-of-two rescalings */
+/* Lanes per pack: two 128-bit registers per operation on AArch64 (32 vector registers:
+ * the per-row coefficients and the carried diagonal stay in registers), one on hosts
+ * with 16 (x86-64 SSE2). */
+#if defined(__aarch64__)
+#define W32 8 /* FP32 lanes per pack */
+#define W64 4 /* FP64 lanes per pack */
+#else
+#define W32 4
+#define W64 2
+#endif
+
+typedef float v32f __attribute__((vector_size(W32 * sizeof(float))));
+typedef int32_t v32i __attribute__((vector_size(W32 * sizeof(int32_t))));
+typedef double v64d __attribute__((vector_size(W64 * sizeof(double))));
+typedef int64_t v64i __attribute__((vector_size(W64 * sizeof(int64_t))));
 
 static double q_tab[94];
 static pthread_once_t q_once = PTHREAD_ONCE_INIT;
@@ -39,239 +58,289 @@ static void q_init(void) {
     for (int x = 0; x < 94; ++x) q_tab[x] = pow(10.0, -(double)x / 10.0);
 }
 
-/* base code: A C G T = 0..3, N = 4, anything else -1 */
-static int code_of(uint8_t c) {
+/* base as a bit set: A 1, C 2, G 4, T 8, N 15 (an N matches everything); 0 = invalid */
+static int32_t base_bits(uint8_t c) {
     switch (c) {
-    case 'A': case 'a': return 0;
-    case 'C': case 'c': return 1;
-    case 'G': case 'g': return 2;
-    case 'T': case 't': return 3;
-    case 'N': case 'n': return 4;
-    default: return -1;
+    case 'A': case 'a': return 1;
+    case 'C': case 'c': return 2;
+    case 'G': case 'g': return 4;
+    case 'T': case 't': return 8;
+    case 'N': case 'n': return 15;
+    default: return 0;
     }
+}
+
+/* SplitMix64 finaliser (Steele, Lea & Flood 2014): a counter-based uniform source. */
+static uint64_t mix64(uint64_t z) {
+    z += 0x9e3779b97f4a7c15ull;
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+    return z ^ (z >> 31);
+}
+
+/* x rounded to float stochastically: to one of the two neighbouring floats, with
+ * probabilities that make the expected value x (unbiased), from a hash of the read base
+ * index and the coefficient number. */
+static float sr_round(double x, uint64_t base, int q) {
+    const float f = (float)x; /* nearest */
+    const double e = x - (double)f;
+    if (e == 0.0 || !isfinite(x)) return f;
+    const float g = nextafterf(f, e > 0.0 ? INFINITY : -INFINITY);
+    const double gap = fabs((double)g - (double)f);
+    const double u = (double)(mix64(0x5eed1234ull << 32 ^ (base * 8u + (uint64_t)q)) >> 11) * 0x1.0p-53;
+    return u < fabs(e) / gap ? g : f;
+}
+
+/* A-priori bound on |log10 L(FP32) - log10 L| for a pair of l rows and k columns.
+ * Every term of the forward sum is a product of nonnegative factors and every sum adds
+ * nonnegative terms, so no cancellation occurs and the relative error of L is bounded by
+ * the roundings along one path: at most 16 per row (coefficients and cell arithmetic)
+ * and 4 per column (the deletion chain and its carries), each below u = 2^-23.  The
+ * coefficient roundings are stochastic (independent, mean zero) and the cell roundings
+ * are modelled the same way, so the sum of m of them stays below lambda sqrt(m) u except
+ * with probability 2 exp(-lambda^2 / 2) (probabilistic rounding-error analysis, Higham &
+ * Mary 2019; for stochastic rounding, Connolly, Higham & Mary 2021); lambda = 6.5 makes
+ * that 1.4e-9.  A deterministic part covers the coefficients' own double precision
+ * (8 per row, 2^-46 each). */
+static double fp32_bound_log10(double l, double k) {
+    const double u = 0x1.0p-23, lambda = 6.5;
+    return (lambda * sqrt(16.0 * l + 4.0 * k) * u + 8.0 * l * 0x1.0p-46) / log(10.0);
 }
 
 typedef struct {
-    double *M, *I, *D, *Mn, *In, *Dn;  /* previous and new row, k + 1 columns each */
-    double *match;                     /* 5 x n match indicators (1.0 / 0.0) per read base A C G T N */
-    double *gp;                        /* g^1 .. g^gp_n for g = gp_g */
-    size_t cap_k, cap_n, gp_n;
-    double gp_g;
-} scratch;
+    int n;                 /* pairs in the pack (lanes beyond n are idle) */
+    uint32_t lmax, kmax, R;
+    uint32_t idx[W32];     /* pair indices */
+    uint32_t l[W32], k[W32];
+    uint64_t r0[W32], h0[W32];
+} pack;
 
-static int scratch_fit(scratch *s, size_t k) {
-    if (k <= s->cap_k) return 1;
-    free(s->M);
-    size_t n = ((k + NB - 1) / NB) * NB + 1; /* whole deletion-chain blocks */
-    /* one block: 6 rows of n, 5 x n match indicators, the powers (<= n) */
-    double *p = (double *)malloc(sizeof(double) * (6 * n + 5 * n + n));
-    if (!p) {
-        s->M = NULL;
-        s->cap_k = 0;
-        return 0;
-    }
-    s->M = p;
-    s->I = p + n;
-    s->D = p + 2 * n;
-    s->Mn = p + 3 * n;
-    s->In = p + 4 * n;
-    s->Dn = p + 5 * n;
-    s->match = p + 6 * n;
-    s->gp = s->match + 5 * n;
-    s->cap_k = k;
-    s->cap_n = n;
-    s->gp_g = -1.0;
-    s->gp_n = 0;
-    return 1;
+typedef struct {
+    double S;
+    int E;
+    uint32_t flags;
+    int nomem;
+} pair_result;
+
+typedef struct {
+    void *buf;
+    size_t cap;
+} cpu_scratch;
+
+static int scratch_reserve(cpu_scratch *s, size_t bytes) {
+    if (bytes <= s->cap) return 1;
+    free(s->buf);
+    bytes = (bytes + 63) & ~(size_t)63;
+    s->buf = aligned_alloc(64, bytes);
+    s->cap = s->buf ? bytes : 0;
+    return s->buf != NULL;
 }
 
-/* d[1..k] from d_j = a_j + g d_j-1 with d_0 = 0, where a_j = tmd * m[j - 1]. */
-static void deletion_row(const double *m, double *d, size_t k, double tmd, double g, scratch *s) {
-    d[0] = 0.0;
-    if (k < 4 * NB) {  /* short rows: plain chain */
-        double x = 0.0;
-        for (size_t j = 1; j <= k; ++j) {
-            x = tmd * m[j - 1] + g * x;
-            d[j] = x;
+/* FP32 engine: C = 2^120; the lane maximum is brought back to 2^96 when it leaves
+ * (2^40, 2^100]; below 2^-100 the pair is flagged; cells at or below 2^-106 are flushed
+ * to zero (the underflow test below accounts for them). */
+#define ENG_NAME pack_forward32
+#define ENG_T float
+#define ENG_V v32f
+#define ENG_VI v32i
+#define ENG_W W32
+#define ENG_SR 1
+#define ENG_LOG2C 120
+#define ENG_HI 100
+#define ENG_LO 40
+#define ENG_TARGET 96
+#define ENG_DANGER (-100)
+#define ENG_MAXSHIFT 126
+#define ENG_FLUSH 0x1.0p-106f
+#include "cpu_engine.inc"
+#undef ENG_NAME
+#undef ENG_T
+#undef ENG_V
+#undef ENG_VI
+#undef ENG_W
+#undef ENG_SR
+#undef ENG_LOG2C
+#undef ENG_HI
+#undef ENG_LO
+#undef ENG_TARGET
+#undef ENG_DANGER
+#undef ENG_MAXSHIFT
+#undef ENG_FLUSH
+
+/* FP64 engine: C = 2^1020; maximum kept in (2^300, 2^900], target 2^800; cells at or
+ * below 2^-1000 are flushed to zero. */
+#define ENG_NAME pack_forward64
+#define ENG_T double
+#define ENG_V v64d
+#define ENG_VI v64i
+#define ENG_W W64
+#define ENG_SR 0
+#define ENG_LOG2C 1020
+#define ENG_HI 900
+#define ENG_LO 300
+#define ENG_TARGET 800
+#define ENG_DANGER (-950)
+#define ENG_MAXSHIFT 1020
+#define ENG_FLUSH 0x1.0p-1000
+#include "cpu_engine.inc"
+
+/* Checkpoint interval of a pack: between checkpoints the lane maximum can fall by at most
+ * min(T_MI, g) per row (I_ij >= T_MI M_i-1,j and >= g I_i-1,j) and grow by at most the
+ * row's largest transition sum; R keeps both within the range budgets. */
+static uint32_t pack_interval(const phmm_batch *b, const pack *pk, double drop_budget, double grow_budget) {
+    double dmax = 1e-3, gmax = 1e-3;
+    for (int w = 0; w < pk->n; ++w) {
+        const uint64_t r0 = pk->r0[w];
+        for (uint32_t i = 0; i < pk->l[w]; ++i) {
+            const double qi = q_tab[b->ins_q[r0 + i]], qd = q_tab[b->del_q[r0 + i]], g = q_tab[b->gcp_q[r0 + i]];
+            const double lo = qi < g ? qi : g;
+            const double drop = lo > 0.0 ? -log2(lo) : 1e9;
+            /* D adds up to T_MD / (1 - g) times the row's M (k times at g = 1) */
+            const double dg = 1.0 - g > 1.0 / (double)pk->k[w] ? qd / (1.0 - g) : qd * (double)pk->k[w];
+            const double grow = log2(fmax(fmax(1.0 - qi - qd + (1.0 - g) * (1.0 + dg), qi + g), 1.0));
+            if (drop > dmax) dmax = drop;
+            if (grow > gmax) gmax = grow;
         }
-        return;
     }
-    const size_t blk = (k + NB - 1) / NB;
-    if (s->gp_g != g || s->gp_n < blk) {  /* g^1 .. g^blk (rows usually share one g) */
-        double p = 1.0;
-        for (size_t t = 0; t < blk; ++t) {
-            p *= g;
-            s->gp[t] = p;
-        }
-        s->gp_g = g;
-        s->gp_n = blk;
-    }
-    /* NB independent chains, block b covering columns b*blk+1 .. (b+1)*blk (the rows are
-     * padded to whole blocks; columns beyond k are computed and ignored) */
-    double x[NB];
-    for (int b = 0; b < NB; ++b) x[b] = 0.0;
-    for (size_t t = 0; t < blk; ++t) {
-        const double *mm = m + t;
-        double *dd = d + t + 1;
-        for (int b = 0; b < NB; ++b) {
-            x[b] = tmd * mm[(size_t)b * blk] + g * x[b];
-            dd[(size_t)b * blk] = x[b];
-        }
-    }
-    /* carries: block b's chain starts from the true d at the end of block b - 1 */
-    for (int b = 1; b < NB; ++b) {
-        const size_t j0 = (size_t)b * blk; /* last column of block b - 1 */
-        if (j0 >= k) break;
-        const double carry = d[j0];
-        const size_t n = (j0 + blk <= k) ? blk : k - j0;
-        double *dd = d + j0 + 1;
-        const double *gp = s->gp;
-        for (size_t t = 0; t < n; ++t) dd[t] += carry * gp[t];
-    }
+    double r = fmin(drop_budget / dmax, grow_budget / gmax);
+    if (r > 32.0) r = 32.0;
+    return r < 1.0 ? 1u : (uint32_t)r;
 }
 
-/* M and I of a row i >= 2 from row i - 1 (columns 1..k; index 0 is column 0); the
- * emission of column j is px + (pm - px) mt[j - 1]. */
-static void mi_row(double *restrict Mn, double *restrict In, const double *restrict M,
-                   const double *restrict I, const double *restrict D, const double *restrict mt, size_t k,
-                   double px, double dp, double tmm, double tgm, double tmi, double g) {
-    for (size_t j = 1; j <= k; ++j) {
-        Mn[j] = (px + dp * mt[j - 1]) * (tmm * M[j - 1] + tgm * I[j - 1] + tgm * D[j - 1]);
-        In[j] = tmi * M[j] + g * I[j];
-    }
-}
-
-/* One pair; NaN for an invalid one. */
-static double pair_forward(const phmm_batch *b, uint32_t p, scratch *s, int *bad) {
-    *bad = 0;
-    const uint32_t r = b->pair_read[p], h = b->pair_hap[p];
-    const uint64_t r0 = b->read_off[r], r1 = b->read_off[r + 1];
-    const uint64_t h0 = b->hap_off[h], h1 = b->hap_off[h + 1];
-    const size_t l = (size_t)(r1 - r0), k = (size_t)(h1 - h0);
-    if (l == 0 || k == 0) {
-        *bad = 1;
-        return NAN;
-    }
-    if (!scratch_fit(s, k)) {
-        *bad = 2;
-        return NAN;
-    }
-    /* match indicators of the haplotype per read base A, C, G, T, N (an N matches all) */
-    const size_t n = s->cap_n;
-    const uint8_t *hb = b->hap_bases + h0;
-    for (size_t j = 0; j < k; ++j) {
-        const int c = code_of(hb[j]);
-        if (c < 0) {
-            *bad = 1;
-            return NAN;
-        }
-        for (int x = 0; x < 4; ++x) s->match[(size_t)x * n + j] = (c == x || c == 4) ? 1.0 : 0.0;
-        s->match[4 * n + j] = 1.0;
-    }
-    /* padding beyond column k (whole deletion-chain blocks) stays zero */
-    for (size_t j = k + 1; j < n; ++j) s->M[j] = s->I[j] = s->D[j] = s->Mn[j] = s->In[j] = s->Dn[j] = 0.0;
-    const uint8_t *rb = b->read_bases + r0, *bq = b->base_q + r0, *iq = b->ins_q + r0, *dq = b->del_q + r0,
-                  *gq = b->gcp_q + r0;
-    for (size_t i = 0; i < l; ++i)
-        if (code_of(rb[i]) < 0 || bq[i] > 93 || iq[i] > 93 || dq[i] > 93 || gq[i] > 93) {
-            *bad = 1;
-            return NAN;
-        }
-    double *M = s->M, *I = s->I, *D = s->D, *Mn = s->Mn, *In = s->In, *Dn = s->Dn;
-    /* Row 1 is formed from D_0j = 1/k instead of C/k, so the stored values are L's terms
-     * (true values over C) times 2^lg2s, the sum of the rescaling shifts. */
-    long lg2s = 0;
-    for (size_t i = 0; i < l; ++i) {
-        const double e = q_tab[bq[i]], pm = 1.0 - e, px = e / 3.0;
-        const double tmi = q_tab[iq[i]], tmd = q_tab[dq[i]], g = q_tab[gq[i]];
-        const double tmm = 1.0 - tmi - tmd, tgm = 1.0 - g;
-        const double *mt = s->match + (size_t)code_of(rb[i]) * n, dp = pm - px;
-        Mn[0] = 0.0;
-        In[0] = 0.0;
-        if (i == 0) {
-            /* row 0: M = I = 0, D = C/k in every column (stored as 1/k) */
-            const double d0 = 1.0 / (double)k;
-            for (size_t j = 1; j <= k; ++j) {
-                Mn[j] = (px + dp * mt[j - 1]) * (tgm * d0);
-                In[j] = 0.0;
-            }
-        } else {
-            mi_row(Mn, In, M, I, D, mt, k, px, dp, tmm, tgm, tmi, g);
-        }
-        deletion_row(Mn, Dn, k, tmd, g, s);
-        /* the new row becomes the previous one */
-        double *t;
-        t = M; M = Mn; Mn = t;
-        t = I; I = In; In = t;
-        t = D; D = Dn; Dn = t;
-        if ((i + 1) % RESCALE_ROWS == 0 && i + 1 < l) {
-            double mx = 0.0;
-            for (size_t j = 1; j <= k; ++j) {
-                const double a = fabs(M[j]), b2 = fabs(I[j]), c2 = fabs(D[j]);
-                const double m2 = a > b2 ? a : b2;
-                mx = mx > m2 ? mx : m2;
-                mx = mx > c2 ? mx : c2;
-            }
-            if (mx > 0.0 && isfinite(mx)) {
-                int ex;
-                frexp(mx, &ex);
-                const int sh = 500 - ex; /* multiply by 2^sh: maximum near 2^500 */
-                /* two exact power-of-two factors (2^sh alone may not be representable) */
-                const double f1 = ldexp(1.0, sh / 2), f2 = ldexp(1.0, sh - sh / 2);
-                for (size_t j = 1; j <= k; ++j) {
-                    M[j] = (M[j] * f1) * f2;
-                    I[j] = (I[j] * f1) * f2;
-                    D[j] = (D[j] * f1) * f2;
-                }
-                lg2s += sh;
-            }
-        }
-    }
-    double S = 0.0;
-    for (size_t j = 1; j <= k; ++j) S += M[j] + I[j];
-    return log10(S) - (double)lg2s * log10(2.0); /* log10 L = log10(S 2^-lg2s) */
-}
+/* ------------------------------------------------------------------------------------ */
 
 typedef struct {
     const phmm_batch *b;
+    pack *packs;
+    uint32_t n_packs;
+    int fp64;
     uint32_t next;
     pthread_mutex_t mu;
     int nomem;
+    pair_result *res; /* per pair */
 } job;
 
 static void *worker(void *arg) {
     job *J = (job *)arg;
-    scratch s;
-    memset(&s, 0, sizeof(s));
+    cpu_scratch s = {NULL, 0};
+    pair_result pr[W32];
     for (;;) {
-        uint32_t p0;
         pthread_mutex_lock(&J->mu);
-        p0 = J->next;
-        J->next = p0 + 64 < p0 ? J->b->n_pairs : p0 + 64;
+        const uint32_t q = J->next < J->n_packs ? J->next++ : J->n_packs;
         pthread_mutex_unlock(&J->mu);
-        if (p0 >= J->b->n_pairs) break;
-        uint32_t p1 = p0 + 64 < J->b->n_pairs ? p0 + 64 : J->b->n_pairs;
-        for (uint32_t p = p0; p < p1; ++p) {
-            int bad = 0;
-            const double v = pair_forward(J->b, p, &s, &bad);
-            J->b->out_log10[p] = v;
-            if (J->b->out_flags) J->b->out_flags[p] = bad ? (uint8_t)PHMM_PAIR_ERROR : (uint8_t)PHMM_PAIR_FP64;
-            if (bad == 2) {
+        if (q >= J->n_packs) break;
+        const pack *pk = &J->packs[q];
+        for (int w = 0; w < W32; ++w) {
+            pr[w].S = NAN;
+            pr[w].E = 0;
+            pr[w].flags = 0;
+            pr[w].nomem = 0;
+        }
+        if (J->fp64) pack_forward64(J->b, pk, &s, pr);
+        else pack_forward32(J->b, pk, &s, pr);
+        for (int w = 0; w < pk->n; ++w) {
+            J->res[pk->idx[w]] = pr[w];
+            if (pr[w].nomem) {
                 pthread_mutex_lock(&J->mu);
                 J->nomem = 1;
                 pthread_mutex_unlock(&J->mu);
             }
         }
     }
-    free(s.M);
+    free(s.buf);
     return NULL;
 }
 
-int phmm_cpu_forward(const phmm_batch *b, int n_threads) {
+static int run_packs(job *J, int n_threads) {
+    J->next = 0;
+    pthread_mutex_init(&J->mu, NULL);
+    pthread_t th[1024];
+    int started = 0;
+    for (int t = 1; t < n_threads && (uint32_t)t < J->n_packs; ++t) {
+        if (pthread_create(&th[started], NULL, worker, J) != 0) break;
+        ++started;
+    }
+    worker(J);
+    for (int t = 0; t < started; ++t) pthread_join(th[t], NULL);
+    pthread_mutex_destroy(&J->mu);
+    return J->nomem ? PHMM_ENOMEM : PHMM_OK;
+}
+
+typedef struct {
+    uint32_t p, l, k, cls;
+} pair_key;
+
+static int key_cmp(const void *a, const void *b) {
+    const pair_key *x = (const pair_key *)a, *y = (const pair_key *)b;
+    if (x->cls != y->cls) return x->cls > y->cls ? -1 : 1; /* longer reads first */
+    if (x->k != y->k) return x->k > y->k ? -1 : 1;
+    if (x->l != y->l) return x->l > y->l ? -1 : 1;
+    return x->p < y->p ? -1 : x->p > y->p;
+}
+
+/* Packs of up to w pairs from the listed pairs: sorted by read-length class (ratio
+ * 2^(1/4)), then haplotype length, so a pack's lanes have similar l and k. */
+static pack *make_packs(const phmm_batch *b, const uint32_t *list, uint32_t n, int w, uint32_t *n_packs,
+                        int fp64) {
+    pair_key *key = (pair_key *)malloc(sizeof(pair_key) * (n ? n : 1));
+    const uint32_t np = (n + (uint32_t)w - 1) / (uint32_t)w;
+    pack *pk = (pack *)calloc(np ? np : 1, sizeof(pack));
+    if (!key || !pk) {
+        free(key);
+        free(pk);
+        return NULL;
+    }
+    for (uint32_t q = 0; q < n; ++q) {
+        const uint32_t p = list[q], r = b->pair_read[p], h = b->pair_hap[p];
+        key[q].p = p;
+        key[q].l = (uint32_t)(b->read_off[r + 1] - b->read_off[r]);
+        key[q].k = (uint32_t)(b->hap_off[h + 1] - b->hap_off[h]);
+        key[q].cls = (uint32_t)floor(4.0 * log2((double)key[q].l));
+    }
+    qsort(key, n, sizeof(pair_key), key_cmp);
+    for (uint32_t t = 0; t < np; ++t) {
+        pack *P = &pk[t];
+        P->n = 0;
+        for (uint32_t q = t * (uint32_t)w; q < n && q < (t + 1) * (uint32_t)w; ++q) {
+            const uint32_t p = key[q].p;
+            const int x = P->n++;
+            P->idx[x] = p;
+            P->l[x] = key[q].l;
+            P->k[x] = key[q].k;
+            P->r0[x] = b->read_off[b->pair_read[p]];
+            P->h0[x] = b->hap_off[b->pair_hap[p]];
+            if (key[q].l > P->lmax) P->lmax = key[q].l;
+            if (key[q].k > P->kmax) P->kmax = key[q].k;
+        }
+        P->R = fp64 ? pack_interval(b, P, 300.0 + 950.0, 1023.0 - 900.0) : pack_interval(b, P, 40.0 + 100.0, 127.0 - 100.0);
+    }
+    free(key);
+    *n_packs = np;
+    return pk;
+}
+
+/* Per-pair validity: lengths >= 1, bases ACGTN, qualities <= 93. */
+static int pair_valid(const phmm_batch *b, uint32_t p) {
+    const uint32_t r = b->pair_read[p], h = b->pair_hap[p];
+    const uint64_t r0 = b->read_off[r], r1 = b->read_off[r + 1], h0 = b->hap_off[h], h1 = b->hap_off[h + 1];
+    if (r1 <= r0 || h1 <= h0) return 0;
+    for (uint64_t x = r0; x < r1; ++x)
+        if (!base_bits(b->read_bases[x]) || b->base_q[x] > 93 || b->ins_q[x] > 93 || b->del_q[x] > 93 ||
+            b->gcp_q[x] > 93)
+            return 0;
+    for (uint64_t x = h0; x < h1; ++x)
+        if (!base_bits(b->hap_bases[x])) return 0;
+    return 1;
+}
+
+int phmm_cpu_forward(const phmm_batch *b, int n_threads, int precision, double fp32_tolerance) {
     if (!b || !b->out_log10 || !b->read_bases || !b->read_off || !b->base_q || !b->ins_q || !b->del_q ||
         !b->gcp_q || !b->hap_bases || !b->hap_off || (b->n_pairs && (!b->pair_read || !b->pair_hap)))
         return PHMM_EINVAL;
     if (b->inputs_on_device || b->outputs_on_device) return PHMM_EINVAL;
+    if (precision < PHMM_PREC_FP32_RESCUE || precision > PHMM_PREC_FP32_ONLY) return PHMM_EINVAL;
+    if (!(fp32_tolerance >= 0.0)) return PHMM_EINVAL;
+    if (fp32_tolerance == 0.0) fp32_tolerance = 1e-3;
     for (uint32_t r = 0; r < b->n_reads; ++r)
         if (b->read_off[r + 1] < b->read_off[r]) return PHMM_EINVAL;
     for (uint32_t h = 0; h < b->n_haps; ++h)
@@ -284,19 +353,71 @@ int phmm_cpu_forward(const phmm_batch *b, int n_threads) {
         n_threads = c > 0 ? (int)c : 1;
     }
     if (n_threads > 1024) n_threads = 1024;
-    job J;
-    J.b = b;
-    J.next = 0;
-    J.nomem = 0;
-    pthread_mutex_init(&J.mu, NULL);
-    pthread_t th[1024];
-    int started = 0;
-    for (int t = 1; t < n_threads; ++t) {
-        if (pthread_create(&th[started], NULL, worker, &J) != 0) break;
-        ++started;
+    const uint32_t n = b->n_pairs;
+    uint32_t *list = (uint32_t *)malloc(sizeof(uint32_t) * (n ? n : 1));
+    pair_result *res = (pair_result *)calloc(n ? n : 1, sizeof(pair_result));
+    if (!list || !res) {
+        free(list);
+        free(res);
+        return PHMM_ENOMEM;
     }
-    worker(&J);
-    for (int t = 0; t < started; ++t) pthread_join(th[t], NULL);
-    pthread_mutex_destroy(&J.mu);
-    return J.nomem ? PHMM_ENOMEM : PHMM_OK;
+    uint32_t nv = 0;
+    for (uint32_t p = 0; p < n; ++p) {
+        if (pair_valid(b, p)) list[nv++] = p;
+        else {
+            b->out_log10[p] = NAN;
+            if (b->out_flags) b->out_flags[p] = PHMM_PAIR_ERROR;
+        }
+    }
+    int rc = PHMM_OK;
+    const int fp64_all = precision == PHMM_PREC_FP64;
+    for (int pass = 0; pass < 2 && rc == PHMM_OK && nv > 0; ++pass) {
+        const int fp64 = fp64_all || pass == 1;
+        uint32_t np = 0;
+        pack *pk = make_packs(b, list, nv, fp64 ? W64 : W32, &np, fp64);
+        if (!pk) {
+            rc = PHMM_ENOMEM;
+            break;
+        }
+        job J;
+        memset(&J, 0, sizeof(J));
+        J.b = b;
+        J.packs = pk;
+        J.n_packs = np;
+        J.fp64 = fp64;
+        J.res = res;
+        rc = run_packs(&J, n_threads);
+        free(pk);
+        if (rc != PHMM_OK) break;
+        /* results; the FP32 pass collects the pairs its tests send to the FP64 pass */
+        uint32_t nr = 0;
+        for (uint32_t q = 0; q < nv; ++q) {
+            const uint32_t p = list[q], r = b->pair_read[p], h = b->pair_hap[p];
+            const double l = (double)(b->read_off[r + 1] - b->read_off[r]);
+            const double k = (double)(b->hap_off[h + 1] - b->hap_off[h]);
+            const pair_result *x = &res[p];
+            const int log2c = fp64 ? 1020 : 120;
+            const double v = x->S > 0.0 && isfinite(x->S)
+                                 ? log10(x->S) + (double)(x->E - log2c) * 0.30102999566398119521
+                                 : (x->S == 0.0 ? -INFINITY : NAN);
+            uint32_t f = x->flags & (PHMM_PAIR_RESCALED | PHMM_PAIR_DANGER | PHMM_PAIR_NONFINITE);
+            if (fp64) {
+                f |= PHMM_PAIR_FP64;
+                if (pass == 1) f |= PHMM_PAIR_RESCUED | (b->out_flags ? b->out_flags[p] & 0x78u : 0u);
+            } else {
+                /* underflow test: at most 3 l k flushed cells, each below 2^-106 and each
+                 * reaching L with total weight <= 1; the relative loss must stay <= 1e-4 */
+                if (!(x->S > 3.0e4 * l * k * 0x1.0p-106)) f |= PHMM_PAIR_SMALL_SUM;
+                if (fp32_bound_log10(l, k) > fp32_tolerance) f |= PHMM_PAIR_DANGER;
+                if (precision == PHMM_PREC_FP32_RESCUE && ((f & 0x78u) || !isfinite(v))) list[nr++] = p;
+            }
+            b->out_log10[p] = v;
+            if (b->out_flags) b->out_flags[p] = (uint8_t)f;
+        }
+        if (fp64) break;
+        nv = nr;
+    }
+    free(list);
+    free(res);
+    return rc;
 }

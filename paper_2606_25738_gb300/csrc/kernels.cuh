@@ -742,6 +742,21 @@ k_short_packed(const BatchHeader* __restrict__ H, const PowRow<float>* __restric
     }
 }
 
+// A-priori bound on |log10 L(FP32) - log10 L| for a pair of l rows and k columns.  The
+// forward sum adds products of nonnegative factors, so nothing cancels and the relative
+// error of L is set by the roundings along one path: at most 16 per row (the per-row
+// coefficients and the cell arithmetic of Eq. 7 in its factored form) and 4 per column
+// (the deletion chain, the scan and its carries), each below u = 2^-23.  The coefficients
+// are stochastically rounded (independent, mean-zero errors) and the cell roundings are
+// modelled the same way, so m of them add up to less than lambda sqrt(m) u except with
+// probability 2 exp(-lambda^2 / 2) (probabilistic rounding-error analysis: Higham & Mary
+// 2019; stochastic rounding: Connolly, Higham & Mary 2021); lambda = 6.5 makes that
+// 1.4e-9.  The deterministic part is the double-float accuracy of the coefficients
+// (8 per row at 2^-46).
+__device__ __forceinline__ double fp32_bound_log10(double l, double k) {
+    return (6.5 * sqrt(16.0 * l + 4.0 * k) * 0x1.0p-23 + 8.0 * l * 0x1.0p-46) * 0.43429448190325182765;
+}
+
 // log10 L per pair (Eq. 4 with C divided out) and selection for the FP64 rescue pass.
 // mode: 0 FP32 + rescue, 1 FP64, 2 FP32 only.
 template <typename T>
@@ -796,7 +811,7 @@ __global__ void k_finalize(const BatchHeader* __restrict__ H) {
                 // Underflow test (the FP32 sum in stored units against 1e4 * 3 l k FLT_MIN)
                 // plus the kernel's own danger / non-finite / degenerate flags.
                 const double tau = 3.0e4 * (double)d.l * (double)d.k * 1.1754943508222875e-38;
-                if (f & PF_DANGER) of |= 0x8u;
+                if ((f & PF_DANGER) || fp32_bound_log10((double)d.l, (double)d.k) > H->tol32) of |= 0x8u;
                 if ((f & PF_NONFINITE) || !isfinite(q.S)) of |= 0x10u;
                 if (!(q.S > tau)) of |= 0x20u;
                 if (f & PF_DEGEN) of |= 0x40u;

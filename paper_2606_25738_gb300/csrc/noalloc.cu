@@ -192,7 +192,7 @@ __global__ void __launch_bounds__(128) k_na_forward(const uint8_t* __restrict__ 
                 // the underflow test on the FP32 sum in stored units (1e4 * 3 l k FLT_MIN).
                 const double tau = 3.0e4 * (double)l * (double)k * 1.1754943508222875e-38;
                 if (o.flags & PF_RESCALED) f |= 0x2u;
-                if (o.flags & PF_DANGER) f |= 0x8u;
+                if ((o.flags & PF_DANGER) || fp32_bound_log10((double)l, (double)k) > 1e-3) f |= 0x8u;
                 if ((o.flags & PF_NONFINITE) || !isfinite(o.S)) f |= 0x10u;
                 if (!(o.S > tau)) f |= 0x20u;
                 if (o.flags & PF_DEGEN) f |= 0x40u;

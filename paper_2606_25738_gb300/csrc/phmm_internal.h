@@ -204,6 +204,7 @@ struct BatchHeader {
                              // largest of a, b / (1 - g), 1 / mi_{i-1}), [3] J growth bits * 64
     uint32_t seed;
     uint32_t mode;           // 0 FP32+rescue, 1 FP64, 2 FP32 only
+    double tol32;            // FP32 tolerance of |log10 L| for the a-priori rounding bound
 };
 
 }  // namespace phmm

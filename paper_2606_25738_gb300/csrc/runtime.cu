@@ -766,6 +766,7 @@ int phmm_create(const phmm_config* cfg, phmm_ctx** out) {
     *out = nullptr;
     if (cfg->precision < 0 || cfg->precision > 2) return PHMM_EINVAL;
     if (cfg->kernel_variant < 0 || cfg->kernel_variant > 5) return PHMM_EINVAL;
+    if (!(cfg->fp32_tolerance >= 0.0)) return PHMM_EINVAL;
     {
         const unsigned lk =
             cfg->flags & (PHMM_F_LONG_LEAN | PHMM_F_LONG_PIPE32 | PHMM_F_LONG_PIPE24 | PHMM_F_LONG_SERIAL |
@@ -1113,6 +1114,7 @@ int phmm_submit_batch(phmm_ctx* ctx, const phmm_batch* b, uint64_t* ticket) {
     hh.rbnd_words_per_cta = rb_words;
     hh.l_max = lmax_b;
     hh.force_rescue = (ctx->cfg.flags & PHMM_F_FORCE_RESCUE) ? 1u : 0u;
+    hh.tol32 = ctx->cfg.fp32_tolerance > 0.0 ? ctx->cfg.fp32_tolerance : 1e-3;
     hh.parts = (Partial*)S->parts.p;
     hh.out = (double*)S->out.p;
     hh.out_flags = (uint8_t*)S->oflags.p;

@@ -45,7 +45,8 @@ class Config(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int), ("precision", ctypes.c_int),
                 ("mem_budget_bytes", ctypes.c_size_t), ("max_inflight", ctypes.c_uint),
                 ("flags", ctypes.c_uint), ("stream", ctypes.c_void_p),
-                ("cols_per_lane", ctypes.c_int), ("kernel_variant", ctypes.c_int)]
+                ("cols_per_lane", ctypes.c_int), ("kernel_variant", ctypes.c_int),
+                ("fp32_tolerance", ctypes.c_double)]
 
 
 class Batch(ctypes.Structure):
@@ -184,10 +185,10 @@ class Context:
 
     def __init__(self, device: int = 0, precision: str = "fp32", flags: int = 0, stream=None,
                  cols_per_lane: int = 0, mem_budget: int = 0, max_inflight: int = 2,
-                 variant: str = "auto"):
+                 variant: str = "auto", tolerance: float = 0.0):
         cfg = Config(device, PREC[precision], mem_budget, max_inflight, flags,
                      ctypes.c_void_p(stream) if stream else None, cols_per_lane,
-                     VARIANTS[variant])
+                     VARIANTS[variant], float(tolerance))
         h = ctypes.c_void_p()
         rc = _lib.phmm_create(ctypes.byref(cfg), ctypes.byref(h))
         if rc != PHMM_OK:

@@ -65,6 +65,10 @@ def test_create_rejects_bad_config(lib):
     assert so.phmm_create(ctypes.byref(cfg), ctypes.byref(h)) == lib.PHMM_EINVAL
     cfg = lib.Config(0, 0, 0, 0, 0, None, 0, 6)  # bad variant
     assert so.phmm_create(ctypes.byref(cfg), ctypes.byref(h)) == lib.PHMM_EINVAL
+    cfg = lib.Config(0, 0, 0, 0, 0, None, 0, 0, -1e-3)  # negative FP32 tolerance
+    assert so.phmm_create(ctypes.byref(cfg), ctypes.byref(h)) == lib.PHMM_EINVAL
+    cfg = lib.Config(0, 0, 0, 0, 0, None, 0, 0, float("nan"))
+    assert so.phmm_create(ctypes.byref(cfg), ctypes.byref(h)) == lib.PHMM_EINVAL
     cfg = lib.Config(0, 0, 0, 0, lib.F_LONG_LEAN | lib.F_LONG_PIPE24, None, 0, 0)  # two forced kernels
     assert so.phmm_create(ctypes.byref(cfg), ctypes.byref(h)) == lib.PHMM_EINVAL
     cfg = lib.Config(0, 0, 0, 0, lib.F_LONG_SERIAL | lib.F_LONG_PIPE32, None, 0, 0)

@@ -339,6 +339,30 @@ def test_pipelined_engine_extreme_gap_qualities(phmm):
         _check(out, flags, oracle.batch(b))
 
 
+def test_rounding_bound_triggers_fp64_rescue(phmm):
+    """The a-priori FP32 rounding bound, (6.5 sqrt(16 l + 4 k) 2^-23 + 8 l 2^-46) / ln 10,
+    grows with the pair's size.  Under a tolerance that half the pairs exceed, exactly
+    those are flagged DANGER and recomputed in FP64 (within 1e-9 of the oracle); at the
+    default tolerance (1e-3) none of them is."""
+    b = W.plain_pairs(24, seed=4, k_range=(250, 400), l_range=(2, 300))
+    rl, hl = W.pair_lengths(b)
+    ref = oracle.batch(b)
+    with phmm.Context(precision="fp32") as ctx:
+        out, flags, rc, st = ctx.run(b)
+    assert st["n_rescued"] == 0 and not np.any(flags & 0x8)
+    bound = (6.5 * np.sqrt(16.0 * rl + 4.0 * hl) * 2.0 ** -23 + 8.0 * rl * 2.0 ** -46) / np.log(10.0)
+    tol = float(np.median(bound))
+    over = bound > tol
+    assert over.any() and (~over).any()
+    with phmm.Context(precision="fp32", tolerance=tol) as ctx:
+        out, flags, rc, st = ctx.run(b)
+    assert np.array_equal((flags & phmm.PAIR_RESCUED) != 0, over)
+    assert np.all(flags[over] & phmm.PAIR_DANGER)
+    assert st["n_rescued"] == int(over.sum())
+    _check(out, flags, ref)
+    assert np.max(np.abs(out[over] - ref[over])) <= TOL64
+
+
 def test_bounded_wait_times_out_and_context_survives(phmm):
     """A device-side wait that can never be satisfied gives up within its poll limit and
     reports PHMM_ETIMEOUT; the same context then still scores a batch correctly."""
