@@ -46,7 +46,7 @@ WORKLOADS = {
                           "of the haplotype, 5%% substitutions, 3%% 1-3 bp indels, quals Phred 5-30"),
     "plain": (64, "pairs", "plain pairs: %d pairs, haplotypes 200-400 bp, reads 100-150 bp, 1%% "
                            "substitutions, 0.1%% indels"),
-    "sweep": (0, "lengths", "equal-length sweep: read = haplotype length %s, ~2e10 cells per length"),
+    "sweep": (0, "lengths", "equal-length sweep: read = haplotype length %s, %s per length"),
 }
 
 
@@ -80,9 +80,10 @@ def make_workload(name: str, units: int):
     raise ValueError(name)
 
 
-def sweep_batch(L: int, target_cells: float = 2e10, max_pairs: int = 1 << 20):
+def sweep_batch(L: int, target_cells: float = 2e10, max_pairs: int = 1 << 20, pairs: int = 0):
+    """Equal-length pairs of length L: ``pairs`` of them, or (0) about target_cells cells."""
     from paper_2606_25738_gb300 import workloads as W
-    n = int(min(max_pairs, max(1, round(target_cells / (L * L)))))
+    n = pairs if pairs > 0 else int(min(max_pairs, max(1, round(target_cells / (L * L)))))
     return W.equal_length(n, L, seed=0)
 
 
@@ -91,7 +92,9 @@ def config_dict(name: str, units: int, b, world: int, args) -> dict:
     from paper_2606_25738_gb300 import workloads as W
     if name == "sweep":
         lens = sweep_lengths(args)
-        desc = WORKLOADS[name][2] % ("%d-%d bp" % (lens[0], lens[-1]))
+        sp = getattr(args, "sweep_pairs", 0)
+        desc = WORKLOADS[name][2] % ("%d-%d bp" % (lens[0], lens[-1]),
+                                     "%d pairs" % sp if sp > 0 else "about 2e10 cells")
         return {"workload": desc, "lengths": lens, "l2": L2_NOTE,
                 "parallelism": "replicas" if world > 1 else "single GPU"}
     desc = WORKLOADS[name][2] % units
@@ -264,7 +267,7 @@ def run_reference(args):
     if name == "sweep":
         units = 0
         lens = sweep_lengths(args)
-        batches = [sweep_batch(L) for L in lens]
+        batches = [sweep_batch(L, pairs=getattr(args, "sweep_pairs", 0)) for L in lens]
         cfg = config_dict(name, 0, None, world, args)
     else:
         units = getattr(args, "units", 0) or WORKLOADS[name][0]
@@ -299,7 +302,8 @@ def run_reference(args):
 
 def _flag_bits(args, phmm):
     return {"auto": 0, "lean": phmm.F_LONG_LEAN, "pipe32": phmm.F_LONG_PIPE32, "pipe24": phmm.F_LONG_PIPE24,
-            "serial": phmm.F_LONG_SERIAL, "pipe4": phmm.F_LONG_PIPE4}[args.long_kind]
+            "serial": phmm.F_LONG_SERIAL, "pipe4": phmm.F_LONG_PIPE4,
+            "cluster": phmm.F_LONG_CLUSTER}[args.long_kind]
 
 
 def kernel_names(st: dict, phmm) -> list:
@@ -494,15 +498,20 @@ def serve_leg(dev, rate, seconds, pool_n):
 
 
 def run_sweep(args, dev, world):
-    """Equal-length sweep: one batch per length (about 2e10 cells, at least one pair),
-    kernel-only and whole-step GCUPS per length, sampled parity where the oracle is cheap."""
+    """Equal-length sweep: one batch per length (about 2e10 cells, at least one pair, or
+    --sweep-pairs pairs), kernel-only and whole-step GCUPS per length, the forward time per
+    row step, sampled parity where the oracle is cheap."""
     import oracle
+
+    from paper_2606_25738_gb300 import phmm
     rows = []
     tot_cells, tot_ms = 0.0, 0.0
     for L in sweep_lengths(args):
-        b = sweep_batch(L)
+        b = sweep_batch(L, pairs=args.sweep_pairs)
         row = gpu_leg("sweep", b, dev, args, steps=max(1, args.steps), warmup=max(1, min(args.warmup, 2)),
-                      parity="none")
+                      parity="none", flags=_flag_bits(args, phmm))
+        row["us_per_row"] = row["ms_forward"] * 1e3 / L  # one row step along the pair's chain
+        row["long_kernel"] = row["kernels"][-1] if row["kernels"] else None
         n = row["pairs"]
         m = int(max(1, min(n, 4e8 // (L * L)))) if L * L <= 4e8 else 0
         row["L"] = L
@@ -512,7 +521,7 @@ def run_sweep(args, dev, world):
             from paper_2606_25738_gb300 import workloads as W
             pick = np.sort(np.random.default_rng(L).choice(n, m, replace=False))
             sb = W.subset(b, pick)
-            with phmm.Context(device=dev, precision="fp32") as ctx:
+            with phmm.Context(device=dev, precision="fp32", flags=_flag_bits(args, phmm)) as ctx:
                 o, f, rc, _ = ctx.run(sb)
             row["parity"] = parity_block(sb, o, f, np.arange(m), oracle.batch(sb))
         tot_cells += row["cells"]
@@ -677,10 +686,13 @@ def main():
     ap.add_argument("--regions", type=int, default=0, help="same as --units for --config short")
     ap.add_argument("--min-len", type=int, default=32, help="sweep: shortest length")
     ap.add_argument("--max-len", type=int, default=16384, help="sweep: longest length")
+    ap.add_argument("--sweep-pairs", type=int, default=0,
+                    help="sweep: pairs per length (0: about 2e10 cells per length)")
     ap.add_argument("--variant", default="auto", choices=["auto", "packed", "scalar", "lean", "pipe", "pipe2"],
                     help="short-pair kernel family (default: the built-in tuner decides)")
     ap.add_argument("--cols", type=int, default=0, help="columns per lane (0: tuner)")
-    ap.add_argument("--long-kind", default="auto", choices=["auto", "lean", "pipe32", "pipe24", "serial", "pipe4"],
+    ap.add_argument("--long-kind", default="auto",
+                    choices=["auto", "lean", "pipe32", "pipe24", "serial", "pipe4", "cluster"],
                     help="force one multi-warp kernel (default: the tuner decides)")
     ap.add_argument("--extras", default="all", choices=["all", "core", "none"],
                     help="all: cpu_baseline, parity, comparators, extra legs, serving; core: without the "

@@ -82,6 +82,9 @@ typedef enum {
 /* ... or the pipelined engine in 4-warp CTAs (strips of 4096 columns: a few very wide
  * pairs spread over many SMs). */
 #define PHMM_F_LONG_PIPE4 0x200u
+/* ... or the same 4-warp strips run by thread-block clusters of eight CTAs, neighbouring
+ * strips exchanging their boundary rows through distributed shared memory. */
+#define PHMM_F_LONG_CLUSTER 0x400u
 /* No measured tuning: the built-in cost model and defaults choose the kernels.  For
  * serving, where nearly every batch (epoch) has a new shape and tuning would re-run it. */
 #define PHMM_F_NO_TUNE 0x80u
@@ -172,8 +175,9 @@ typedef struct {
      * short_kernel = scalar-team variant 0..8 (k_short_scalar<32,4>, <24,4>, <24,5>,
      * <16,6>, k_short_pipe<32,3>, <24,4>, <16,4>, k_short_pipe2<32,3>, <24,4>);
      * packed_kernel = packed-team variant 0..1 (k_short_packed<12,4>, <16,3>);
-     * long_kernel = multi-warp kind 0..4 (lean k_forward<32>, k_forward_pipe<32,12>,
-     * k_forward_pipe<24,16>, k_forward_serial<32,3>, k_forward_pipe<32,4>). */
+     * long_kernel = multi-warp kind 0..5 (lean k_forward<32>, k_forward_pipe<32,12>,
+     * k_forward_pipe<24,16>, k_forward_serial<32,3>, k_forward_pipe<32,4>,
+     * k_forward_cluster<32,4,8>). */
     int32_t short_kernel;
     int32_t packed_kernel;
     int32_t long_kernel;
@@ -270,14 +274,19 @@ int phmm_plan_check(const uint32_t *l, const uint32_t *k, const uint32_t *pair_r
 /*
  * Serving: continuous batching of independent requests (an active region: R reads x H
  * haplotypes, scored as one phmm_batch).  The paper has no serving layer; this loop is
- * built on phmm_submit_batch / phmm_poll of one context.  A scheduler thread keeps a FIFO
- * of waiting requests.  Whenever an epoch slot is free it admits waiting requests, in
- * arrival order, while their summed footprint (phmm_batch_footprint) fits in the budget
- * left by epochs still on the device and the epoch stays under max_epoch_pairs, joins
- * them into one batch and submits it.  Up to max_inflight_epochs epochs run concurrently,
- * so requests that arrive while others are on the GPU start as soon as a slot and memory
- * free up.  When an epoch finishes, each request's results are copied to its own output
- * buffers and the request completes.
+ * built on phmm_submit_batch / phmm_poll of one context.  A scheduler thread keeps the
+ * waiting requests in arrival order.  Whenever an epoch slot is free it forms an epoch
+ * (one batch) whose summed footprint (phmm_batch_footprint) fits in the budget left by
+ * epochs still on the device, and submits it.  Up to max_inflight_epochs epochs run
+ * concurrently, so requests that arrive while others are on the GPU start as soon as a
+ * slot and memory free up.  Size classes keep small requests from waiting behind large
+ * ones: requests of at most small_cells cells (sum of l * k) form epochs of their own and
+ * go first; larger requests follow in arrival order, split into chunks of consecutive
+ * pairs of at most epoch_cells cells, each chunk an epoch (so no epoch holds the device
+ * for long); large epochs use at most max_inflight_epochs - 1 slots; a large request that
+ * has waited longer than max_wait_ms goes ahead of small ones.  When an epoch finishes,
+ * its results are copied to the requests' output buffers; a request completes when all
+ * its pairs are done.
  */
 typedef struct phmm_server phmm_server;
 
@@ -286,6 +295,9 @@ typedef struct {
     uint32_t max_epoch_pairs;      /* pairs per epoch (0: 2^20) */
     uint32_t max_inflight_epochs;  /* concurrent epochs (0: 2); the context needs as many slots */
     uint32_t max_pending;          /* waiting requests before enqueue returns PHMM_EBUSY (0: no limit) */
+    uint32_t max_wait_ms;          /* a large request waiting longer goes ahead of small ones (0: 2000) */
+    uint64_t epoch_cells;          /* cell budget of one epoch; larger requests are split (0: 1e11) */
+    uint64_t small_cells;          /* requests of at most this many cells are small (0: epoch_cells / 20) */
 } phmm_server_config;
 
 typedef struct {

@@ -5,6 +5,7 @@
 #pragma once
 
 #include <cmath>
+#include <cooperative_groups.h>
 #include <cstdint>
 #include <type_traits>
 
@@ -12,6 +13,9 @@
 #include "phmm_internal.h"
 
 namespace phmm {
+
+namespace cg = cooperative_groups;
+
 
 // ------------------------------------------------------------------------------------
 // Double-float helpers for the FP32 prep (Phred tables: see PhredTables).
@@ -539,6 +543,87 @@ k_forward_pipe(const BatchHeader* __restrict__ H, const PowRow<float>* __restric
             }
         }
         __syncthreads();
+    }
+}
+
+// Multi-warp FP32 pairs in thread-block clusters (long kind 5): the plan's CTA items (as
+// for 4-warp CTAs: strips of 4096 columns) are taken CS at a time by a cluster of CS CTAs,
+// CTA rank r running item CS g + r.  Where consecutive strips of a pair sit in
+// neighbouring ranks, the left strip's last warp writes each row's boundary values (M, J,
+// D-hat and exponent of its last column) straight into the right strip's first-warp ring
+// in the other CTA's shared memory (distributed shared memory, the paper's multi-CTA
+// design); other strip boundaries go through global memory as for k_forward_pipe.
+template <int N>
+__device__ __forceinline__ void cta_strip_run_cluster(const BatchHeader* __restrict__ H,
+                                                      const PowRow<float>* __restrict__ pow, const CtaPair& cp,
+                                                      CtaShared<float>& sh, const PipeRange& rng, unsigned rank) {
+    constexpr int KW = Num<float>::kWords;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int s = warp - cp.w0;
+    if (s < 0 || s >= cp.W) return;
+    const PairDesc d = H->desc[cp.pair];
+    const bool din = is_dsmem_bnd(cp.bnd_in), dout = is_dsmem_bnd(cp.bnd_out);
+    SmemLink L;
+    L.in_ring = sh.ring + warp * kRing * KW;
+    L.out_ring = sh.ring + min(warp + 1, kCtaWarps - 1) * kRing * KW;
+    L.my_cons = sh.cons + warp;
+    L.next_cons = sh.cons + warp + 1;
+    if (s == cp.W - 1 && dout) {
+        // the receiving strip's first warp w1 in the next CTA of the cluster
+        const int w1 = (int)(cp.bnd_out & 0xffu);
+        cg::cluster_group cl = cg::this_cluster();
+        L.out_ring = cl.map_shared_rank(sh.ring + w1 * kRing * KW, rank + 1);
+        L.next_cons = cl.map_shared_rank(sh.cons + w1, rank + 1);
+    }
+    L.in_g = (s == 0 && cp.bnd_in != kNoBnd && !din) ? H->bnd + cp.bnd_in : nullptr;
+    L.out_g = (s == cp.W - 1 && cp.bnd_out != kNoBnd && !dout) ? H->bnd + cp.bnd_out : nullptr;
+    L.has_left = s > 0 || cp.bnd_in != kNoBnd;
+    L.has_right = s < cp.W - 1 || cp.bnd_out != kNoBnd;
+    const int c0 = (int)cp.col0 + (s * 32 + lane) * N;
+    const SegOut o = seg_link_pipe<N>(H->rec32j + d.roff, (int)d.l, H->hap_bases + d.hoff, (int)d.k, c0,
+                                      lane, pow, rng, L, H->status);
+    if (lane == 0) sh.out[warp] = o;
+}
+
+template <int N, int CW, int CS>
+__global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(CW * 32, 3)
+k_forward_cluster(const BatchHeader* __restrict__ H, const PowRow<float>* __restrict__ pow) {
+    __shared__ CtaShared<float> sh;
+    cg::cluster_group cl = cg::this_cluster();
+    const unsigned rank = cl.block_rank();
+    const PipeRange rng = pipe_range(H->dropgrow);
+    const uint32_t n_c = H->n_citems;
+    const uint32_t n_g = (n_c + CS - 1) / CS;
+    const int warp = threadIdx.x >> 5;
+    cl.sync();  // every CTA of the cluster runs before any shared memory of another is touched
+    for (;;) {
+        if (rank == 0 && threadIdx.x == 0) {
+            const uint32_t g = atomicAdd(&H->counters[5], 1u);
+            for (unsigned r = 0; r < CS; ++r) *cl.map_shared_rank(&sh.item, r) = g;
+        }
+        cta_clear<float>(sh);
+        cl.sync();  // the group index is everywhere; every ring is clear before a neighbour writes
+        const uint32_t g = sh.item;
+        if (g >= n_g) break;
+        const uint32_t it = g * CS + rank;
+        CtaItem ci;
+        ci.first = 0;
+        ci.n = 0;
+        if (it < n_c) ci = H->citems[it];
+        for (uint32_t q = 0; q < ci.n; ++q) {
+            const CtaPair cp = H->cpairs[ci.first + q];
+            if (warp >= cp.w0 && warp < cp.w0 + cp.W) cta_strip_run_cluster<N>(H, pow, cp, sh, rng, rank);
+        }
+        __syncthreads();
+        if ((threadIdx.x & 31) == 0) {
+            for (uint32_t q = 0; q < ci.n; ++q) {
+                const CtaPair cp = H->cpairs[ci.first + q];
+                if (warp == cp.w0)
+                    write_strip_part(H, cp.pair, cp.strip, cp.nstrip, cp.extra_base,
+                                     cta_combine<float>(sh, cp.w0, cp.W));
+            }
+        }
+        cl.sync();  // no CTA clears its rings for the next group while a neighbour still writes
     }
 }
 

@@ -115,6 +115,7 @@ template __global__ void k_forward_pipe<32, kCtaWarpsPipe>(const BatchHeader*, c
 template __global__ void k_forward_pipe<24, kCtaWarps>(const BatchHeader*, const PowRow<float>*);
 template __global__ void k_forward_serial<32, 3>(const BatchHeader*, const PowRow<float>*);
 template __global__ void k_forward_pipe<32, 4>(const BatchHeader*, const PowRow<float>*);
+template __global__ void k_forward_cluster<32, kClusterWarps, kClusterCtas>(const BatchHeader*, const PowRow<float>*);
 template __global__ void k_short_scalar<32, 4>(const BatchHeader*, const PowRow<float>*);
 template __global__ void k_short_scalar<24, 4>(const BatchHeader*, const PowRow<float>*);
 template __global__ void k_short_scalar<24, 5>(const BatchHeader*, const PowRow<float>*);
@@ -185,7 +186,8 @@ void launch_forward32_long(const BatchHeader* H, const void* pow, int grid, cuda
 
 void launch_forward32_long_pipe(int kind, const BatchHeader* H, const void* pow, int grid, cudaStream_t s) {
     const PowRow<float>* p = static_cast<const PowRow<float>*>(pow);
-    if (kind == 3) k_forward_serial<32, 3><<<grid, kSerialThreads, 0, s>>>(H, p);
+    if (kind == 5) k_forward_cluster<32, kClusterWarps, kClusterCtas><<<grid, kClusterWarps * 32, 0, s>>>(H, p);
+    else if (kind == 3) k_forward_serial<32, 3><<<grid, kSerialThreads, 0, s>>>(H, p);
     else if (kind == 4) k_forward_pipe<32, 4><<<grid, 4 * 32, 0, s>>>(H, p);
     else if (kind == 2) k_forward_pipe<24, kCtaWarps><<<grid, kCtaWarps * 32, 0, s>>>(H, p);
     else k_forward_pipe<32, kCtaWarpsPipe><<<grid, kCtaWarpsPipe * 32, 0, s>>>(H, p);
@@ -253,6 +255,20 @@ int occupancy_forward32_long() {
 
 int occupancy_forward32_long_pipe(int kind) {
     int b = 0;
+    if (kind == 5) {
+        // clusters that fit on the GPU at once (the grid of the persistent cluster kernel)
+        cudaLaunchConfig_t c = {};
+        c.gridDim = dim3(kClusterCtas, 1, 1);
+        c.blockDim = dim3(kClusterWarps * 32, 1, 1);
+        c.dynamicSmemBytes = 0;
+        c.attrs = nullptr;
+        c.numAttrs = 0;
+        if (cudaOccupancyMaxActiveClusters(&b, (const void*)k_forward_cluster<32, kClusterWarps, kClusterCtas>, &c) !=
+            cudaSuccess)
+            b = 0;
+        cudaGetLastError();
+        return b > 0 ? b : 1;
+    }
     if (kind == 3)
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_forward_serial<32, 3>, kSerialThreads, 0);
     else if (kind == 4)

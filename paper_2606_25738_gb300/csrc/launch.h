@@ -18,11 +18,13 @@ void launch_forward32_long(const BatchHeader* H, const void* pow, int grid, cuda
 // (N 32, 12-warp CTAs), 2 = pipelined (N 24, 16-warp CTAs), 3 = pipelined with packed
 // column halves, one warp per pair running its 1024-column strips one after another
 // (k_forward_serial, 4-warp CTAs), 4 = pipelined in 4-warp CTAs (3 per SM): strips of
-// 4096 columns, so that a few very wide pairs spread over many SMs.
-constexpr int kNumLong = 5;
-constexpr int kLongN[kNumLong] = {32, 32, 24, 32, 32};
-constexpr int kLongCW[kNumLong] = {16, 12, 16, 1, 4};
-constexpr bool kLongSerial[kNumLong] = {false, false, false, true, false};
+// 4096 columns, so that a few very wide pairs spread over many SMs, 5 = the same 4-warp
+// strips taken eight at a time by thread-block clusters, neighbouring strips linked
+// through distributed shared memory (k_forward_cluster).
+constexpr int kNumLong = 6;
+constexpr int kLongN[kNumLong] = {32, 32, 24, 32, 32, 32};
+constexpr int kLongCW[kNumLong] = {16, 12, 16, 1, 4, kClusterWarps};
+constexpr bool kLongSerial[kNumLong] = {false, false, false, true, false, false};
 constexpr int kSerialThreads = 128;
 void launch_forward32_long_pipe(int kind, const BatchHeader* H, const void* pow, int grid, cudaStream_t s);
 // Short-pair kernels by variant id (see kShortScalar / kShortPacked).
@@ -30,7 +32,7 @@ void launch_short_scalar(int id, const BatchHeader* H, const void* pow, int grid
 void launch_short_packed(int id, const BatchHeader* H, const void* pow, int grid, cudaStream_t s);
 void launch_finalize32(const BatchHeader* H, int grid, cudaStream_t s);
 int occupancy_forward32_long();          // resident CTAs per SM
-int occupancy_forward32_long_pipe(int kind);
+int occupancy_forward32_long_pipe(int kind);  // kind 5: resident clusters on the GPU
 int occupancy_short_scalar(int id);
 int occupancy_short_packed(int id);
 // pow_row: a device pointer to one PowRow<float>

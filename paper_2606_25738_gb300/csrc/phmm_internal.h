@@ -119,6 +119,16 @@ struct WarpItem {
 // (consecutive CTA items, dequeued in order); strips pass each row's boundary values
 // through the global buffer `bnd` (bnd_in / bnd_out: word offsets, kNoBnd if none).
 constexpr uint64_t kNoBnd = ~0ull;
+// Cluster kind: a strip whose neighbouring strip runs in the next (previous) CTA of the
+// same thread-block cluster passes its boundary rows through that CTA's shared memory
+// (DSMEM) instead of `bnd`.  bnd_out = kDsmemBnd | first warp of the receiving strip;
+// bnd_in = kDsmemBnd.
+constexpr uint64_t kDsmemBnd = 0xFFFFFFFF00000000ull;
+__host__ __device__ inline bool is_dsmem_bnd(uint64_t b) {
+    return b != kNoBnd && (b & 0xFFFFFFFF00000000ull) == kDsmemBnd;
+}
+constexpr int kClusterCtas = 8;   // CTAs per cluster of the cluster kind (portable size)
+constexpr int kClusterWarps = 4;  // warps per CTA of the cluster kind
 struct CtaPair {
     uint32_t pair;
     uint8_t w0;          // first warp

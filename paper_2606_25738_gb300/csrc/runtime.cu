@@ -494,7 +494,8 @@ struct phmm_ctx {
     DevBuf scan_row;                        // scan test: one PowRow<float> (global memory)
     DevBuf pow32[5];                        // N = 12, 16, 20, 24 (packed short), 32 (long)
     DevBuf pow64;
-    int occ_packed[kNumPacked] = {}, occ_scalar[kNumScalar] = {}, occ_longk[kNumLong] = {1, 1, 1, 1, 1}, occ64 = 1;
+    // resident CTAs per SM of each kernel (long kind 5: resident clusters of the GPU)
+    int occ_packed[kNumPacked] = {}, occ_scalar[kNumScalar] = {}, occ_longk[kNumLong] = {1, 1, 1, 1, 1, 1}, occ64 = 1;
     std::map<uint64_t, std::array<int, 3>> tuned;  // batch signature -> (scalar id, packed id, long kind)
     uint64_t inflight_foot = 0;             // sum of pending slots' footprints
     bool dead = false;
@@ -589,7 +590,10 @@ int launch_sequence(phmm_ctx* ctx, Slot& S, int scal_id, int pack_id, int long_k
         const void* lpow = ctx->pow32[pow_index(kLongN[long_kind])].p;
         CK(rec_on(S.ev_br[4], S.sb2));
         if (long_kind > 0)
-            launch_forward32_long_pipe(long_kind, H, lpow, ctx->sms * ctx->occ_longk[long_kind], S.sb2);
+            launch_forward32_long_pipe(long_kind, H, lpow,
+                                       long_kind == 5 ? ctx->occ_longk[5] * kClusterCtas
+                                                      : ctx->sms * ctx->occ_longk[long_kind],
+                                       S.sb2);
         else
             launch_forward32_long(H, lpow, ctx->sms * ctx->occ_longk[0], S.sb2);
         CK(rec_on(S.ev_br[5], S.sb2));
@@ -687,10 +691,34 @@ std::vector<std::pair<int, int>> fp32_candidates(const phmm_config& cfg) {
     return c;
 }
 
+// Cluster kind: CTA items are taken kClusterCtas at a time, item g kClusterCtas + r by CTA
+// rank r of a cluster.  A strip boundary whose two strips sit in neighbouring items of one
+// group goes through distributed shared memory (the receiving strip's first warp in the
+// marker); the others stay in global memory.
+void cluster_links(Plan& P) {
+    const size_t n = P.citems.size();
+    for (size_t a = 0; a + 1 < n; ++a) {
+        if ((a + 1) % kClusterCtas == 0) continue;  // item a + 1 starts the next group
+        const CtaItem A = P.citems[a], B = P.citems[a + 1];
+        for (uint32_t x = 0; x < A.n; ++x) {
+            CtaPair& Lp = P.cpairs[A.first + x];
+            if (Lp.bnd_out == kNoBnd) continue;
+            for (uint32_t y = 0; y < B.n; ++y) {
+                CtaPair& Rp = P.cpairs[B.first + y];
+                if (Rp.pair == Lp.pair && Rp.strip == Lp.strip + 1) {
+                    Lp.bnd_out = kDsmemBnd | Rp.w0;
+                    Rp.bnd_in = kDsmemBnd;
+                }
+            }
+        }
+    }
+}
+
 void make_plan_id(const uint32_t* l, const uint32_t* k, const uint32_t* pr, uint32_t n, int scal_id,
                   int pack_id, int long_kind, Plan& P) {
     make_plan(l, k, pr, n, kShortScalarN[scal_id], pack_id >= 0 ? kShortPackedN[pack_id] : 0,
               kLongN[long_kind], P, 4, kLongCW[long_kind], kLongSerial[long_kind]);
+    if (long_kind == 5) cluster_links(P);
     P.scal_id = scal_id;
     P.pack_id = pack_id;
     P.long_kind = long_kind;
@@ -707,8 +735,9 @@ std::vector<int> long_kinds_of(const phmm_config& cfg) {
     if (cfg.flags & PHMM_F_LONG_PIPE24) return {2};
     if (cfg.flags & PHMM_F_LONG_SERIAL) return {3};
     if (cfg.flags & PHMM_F_LONG_PIPE4) return {4};
+    if (cfg.flags & PHMM_F_LONG_CLUSTER) return {5};
     if (cfg.kernel_variant == 3) return {0};
-    return {0, 1, 3, 4};  // kind 2 only when forced: measured slower than kind 1 everywhere
+    return {0, 1, 3, 4, 5};  // kind 2 only when forced: measured slower than kind 1 everywhere
 }
 // Without measurement: the serial kind when multi-warp pairs outnumber the resident
 // warps of k_forward_serial four times over (each warp then has several pairs to run),
@@ -770,7 +799,7 @@ int phmm_create(const phmm_config* cfg, phmm_ctx** out) {
     {
         const unsigned lk =
             cfg->flags & (PHMM_F_LONG_LEAN | PHMM_F_LONG_PIPE32 | PHMM_F_LONG_PIPE24 | PHMM_F_LONG_SERIAL |
-                          PHMM_F_LONG_PIPE4);
+                          PHMM_F_LONG_PIPE4 | PHMM_F_LONG_CLUSTER);
         if (lk & (lk - 1)) return PHMM_EINVAL;  // more than one forced multi-warp kernel
     }
     {
@@ -826,6 +855,7 @@ int phmm_create(const phmm_config* cfg, phmm_ctx** out) {
     ctx->occ_longk[2] = occupancy_forward32_long_pipe(2);
     ctx->occ_longk[3] = occupancy_forward32_long_pipe(3);
     ctx->occ_longk[4] = occupancy_forward32_long_pipe(4);
+    ctx->occ_longk[5] = occupancy_forward32_long_pipe(5);
     if (getenv("PHMM_DEBUG")) {
         fprintf(stderr, "phmm: sms %d occupancy packed %d %d long %d %d %d %d %d fp64 %d scalar", ctx->sms,
                 ctx->occ_packed[0], ctx->occ_packed[1], ctx->occ_longk[0], ctx->occ_longk[1],
@@ -1151,7 +1181,7 @@ int phmm_submit_batch(phmm_ctx* ctx, const phmm_batch* b, uint64_t* ticket) {
             // more SMs); with many wide pairs it is not worth a trial run either
             for (int lk : long_kinds_of(ctx->cfg)) {
                 if (kLongSerial[lk] && (uint64_t)P.n_long < 2 * swarps) continue;
-                if (lk == 4 && (uint64_t)P.n_long >= swarps) continue;
+                if ((lk == 4 || lk == 5) && (uint64_t)P.n_long >= swarps) continue;
                 runs.push_back({-1, -1, lk});
             }
         }
@@ -1471,7 +1501,7 @@ int phmm_plan_check(const uint32_t* l, const uint32_t* k, const uint32_t* pair_r
     // CTA items: warp ranges fit and are disjoint; strips tile their pair in item order
     struct StripSeen {
         uint32_t nstrip = 0, count = 0, extra_base = 0;
-        std::vector<int64_t> col0, width, item;
+        std::vector<int64_t> col0, width, item, w0;
         std::vector<uint64_t> bin, bout;
     };
     std::map<uint32_t, StripSeen> strips;
@@ -1517,6 +1547,7 @@ int phmm_plan_check(const uint32_t* l, const uint32_t* k, const uint32_t* pair_r
                 sv.col0.assign(cp.nstrip, -1);
                 sv.width.assign(cp.nstrip, -1);
                 sv.item.assign(cp.nstrip, -1);
+                sv.w0.assign(cp.nstrip, -1);
                 sv.bin.assign(cp.nstrip, 0);
                 sv.bout.assign(cp.nstrip, 0);
             }
@@ -1526,6 +1557,7 @@ int phmm_plan_check(const uint32_t* l, const uint32_t* k, const uint32_t* pair_r
             sv.col0[cp.strip] = cp.col0;
             sv.width[cp.strip] = cp.W;
             sv.item[cp.strip] = (int64_t)it;
+            sv.w0[cp.strip] = cp.w0;
             sv.bin[cp.strip] = cp.bnd_in;
             sv.bout[cp.strip] = cp.bnd_out;
             sv.count++;
@@ -1543,8 +1575,20 @@ int phmm_plan_check(const uint32_t* l, const uint32_t* k, const uint32_t* pair_r
             if (st > 0 && sv.item[st] < sv.item[st - 1]) return fail(22);  // never before its left strip
             if ((st == 0) != (sv.bin[st] == kNoBnd)) return fail(23);
             if ((st + 1 == sv.nstrip) != (sv.bout[st] == kNoBnd)) return fail(23);
-            if (st > 0 && sv.bin[st] != sv.bout[st - 1]) return fail(24);
-            if (st + 1 < sv.nstrip) {
+            if (st > 0) {
+                const bool din = is_dsmem_bnd(sv.bin[st]);
+                if (din != is_dsmem_bnd(sv.bout[st - 1])) return fail(28);
+                if (din) {
+                    // distributed shared memory: neighbouring CTAs of one cluster group, and
+                    // the left strip names the receiving strip's first warp
+                    if (long_kind != 5 || precision == PHMM_PREC_FP64) return fail(28);
+                    if (sv.item[st] != sv.item[st - 1] + 1 || sv.item[st] % kClusterCtas == 0) return fail(29);
+                    if ((int64_t)(sv.bout[st - 1] & 0xffu) != sv.w0[st]) return fail(29);
+                } else if (sv.bin[st] != sv.bout[st - 1]) {
+                    return fail(24);
+                }
+            }
+            if (st + 1 < sv.nstrip && !is_dsmem_bnd(sv.bout[st])) {
                 const uint64_t a = sv.bout[st], b = a + (uint64_t)l[p] * kw;
                 if (b > P.bnd_words) return fail(25);
                 bnd_ranges.push_back({a, b});

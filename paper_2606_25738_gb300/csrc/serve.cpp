@@ -28,19 +28,34 @@ struct Request {
     std::vector<uint8_t> bases, bq, iq, dq, gq, hap;
     std::vector<uint64_t> roff, hoff;
     std::vector<uint32_t> pr, ph;
+    std::vector<uint64_t> pcells;  // l * k of each pair
     double* out = nullptr;
     uint8_t* out_flags = nullptr;
     uint64_t foot = 0, cells = 0;
+    bool small = false;
+    uint32_t next = 0;        // first pair not yet given to an epoch
+    uint32_t done = 0;        // pairs whose epoch has finished
+    bool started = false;     // a first chunk was admitted
+    bool any_error = false;   // a pair came back with PHMM_PAIR_ERROR
+    int fail = PHMM_OK;       // status of a failed epoch, if any
     Clock::time_point t_in, t_done;
+};
+
+// A slice of one request's pairs inside an epoch (the whole request, or one chunk of a
+// request larger than the epoch cell budget).
+struct Segment {
+    Request* r = nullptr;
+    uint32_t p0 = 0, p1 = 0;  // the request's pairs [p0, p1)
+    uint32_t first = 0;       // index of pair p0 in the epoch's batch
 };
 
 struct Epoch {
     uint64_t ticket = 0;
-    std::vector<Request*> reqs;
-    std::vector<uint32_t> first;  // index of each request's first pair in the epoch
+    std::vector<Segment> segs;
     std::vector<double> out;
     std::vector<uint8_t> flags;
     uint64_t foot = 0;
+    bool large = false;
 };
 
 }  // namespace
@@ -51,7 +66,7 @@ struct phmm_server {
     std::mutex mu;
     std::condition_variable cv_work;  // scheduler: new request or stop
     std::condition_variable cv_done;  // pollers: a request finished
-    std::deque<Request*> pending;
+    std::deque<Request*> pending;     // requests with pairs not yet in an epoch, by arrival
     std::unordered_map<uint64_t, Request*> live;  // enqueued, not yet retired by poll
     std::vector<Epoch*> inflight;                  // touched by the scheduler thread only
     uint64_t next_id = 0;
@@ -59,6 +74,9 @@ struct phmm_server {
     bool single = false;  // after an ENOMEM epoch: admit one request at a time once
     phmm_server_stats st{};
     std::thread th;
+
+    uint64_t epoch_cells() const { return cfg.epoch_cells ? cfg.epoch_cells : 100000000000ull; }
+    uint64_t small_cells() const { return cfg.small_cells ? cfg.small_cells : epoch_cells() / 20; }
 
     void finish(Request* r, int status) {  // with mu held
         r->status = status;
@@ -72,45 +90,50 @@ struct phmm_server {
         st.inflight--;
     }
 
-    // Copy an epoch's results to its requests and complete them.
+    // Copy an epoch's results to its requests; complete the requests whose last pairs
+    // these were.
     void retire(Epoch* e, int rc) {
         std::lock_guard<std::mutex> lk(mu);
-        for (size_t q = 0; q < e->reqs.size(); ++q) {
-            Request* r = e->reqs[q];
-            int s = rc;
+        for (const Segment& g : e->segs) {
+            Request* r = g.r;
+            const uint32_t n = g.p1 - g.p0;
             if (rc == PHMM_OK || rc == PHMM_EINVAL) {
-                const double* src = e->out.data() + e->first[q];
-                const uint8_t* fl = e->flags.data() + e->first[q];
-                memcpy(r->out, src, r->np * sizeof(double));
-                if (r->out_flags) memcpy(r->out_flags, fl, r->np);
-                s = PHMM_OK;
-                for (uint32_t p = 0; p < r->np; ++p)
-                    if (fl[p] & PHMM_PAIR_ERROR) s = PHMM_EINVAL;
+                const double* src = e->out.data() + g.first;
+                const uint8_t* fl = e->flags.data() + g.first;
+                memcpy(r->out + g.p0, src, n * sizeof(double));
+                if (r->out_flags) memcpy(r->out_flags + g.p0, fl, n);
+                for (uint32_t p = 0; p < n; ++p)
+                    if (fl[p] & PHMM_PAIR_ERROR) r->any_error = true;
+            } else if (r->fail == PHMM_OK) {
+                r->fail = rc;
             }
-            finish(r, s);
+            r->done += n;
+            if (r->done == r->np)
+                finish(r, r->fail != PHMM_OK ? r->fail : (r->any_error ? PHMM_EINVAL : PHMM_OK));
         }
         st.bytes_inflight -= e->foot;
         cv_done.notify_all();
     }
 
-    // Join requests into one host batch and submit it.  Returns the submit status.
+    // Join the segments' requests into one host batch (every read and haplotype of each
+    // request, the segment's pairs) and submit it.  Returns the submit status.
     int submit(Epoch* e) {
         uint64_t nb = 0, nhb = 0;
         uint32_t nr = 0, nh = 0, np = 0;
-        for (Request* r : e->reqs) {
-            nb += r->roff[r->nr];
-            nhb += r->hoff[r->nh];
-            nr += r->nr;
-            nh += r->nh;
-            np += r->np;
+        for (const Segment& g : e->segs) {
+            nb += g.r->roff[g.r->nr];
+            nhb += g.r->hoff[g.r->nh];
+            nr += g.r->nr;
+            nh += g.r->nh;
+            np += g.p1 - g.p0;
         }
         std::vector<uint8_t> bases(nb), bq(nb), iq(nb), dq(nb), gq(nb), hap(nhb);
         std::vector<uint64_t> roff(nr + 1), hoff(nh + 1);
         std::vector<uint32_t> pr(np), ph(np);
         uint64_t ob = 0, oh = 0;
         uint32_t orr = 0, ohh = 0, op = 0;
-        e->first.clear();
-        for (Request* r : e->reqs) {
+        for (Segment& g : e->segs) {
+            const Request* r = g.r;
             const uint64_t rb = r->roff[r->nr], hb = r->hoff[r->nh];
             memcpy(&bases[ob], r->bases.data(), rb);
             memcpy(&bq[ob], r->bq.data(), rb);
@@ -120,16 +143,15 @@ struct phmm_server {
             memcpy(&hap[oh], r->hap.data(), hb);
             for (uint32_t i = 0; i < r->nr; ++i) roff[orr + i] = ob + r->roff[i];
             for (uint32_t i = 0; i < r->nh; ++i) hoff[ohh + i] = oh + r->hoff[i];
-            e->first.push_back(op);
-            for (uint32_t p = 0; p < r->np; ++p) {
-                pr[op + p] = orr + r->pr[p];
-                ph[op + p] = ohh + r->ph[p];
+            g.first = op;
+            for (uint32_t p = g.p0; p < g.p1; ++p, ++op) {
+                pr[op] = orr + r->pr[p];
+                ph[op] = ohh + r->ph[p];
             }
             ob += rb;
             oh += hb;
             orr += r->nr;
             ohh += r->nh;
-            op += r->np;
         }
         roff[nr] = nb;
         hoff[nh] = nhb;
@@ -155,6 +177,93 @@ struct phmm_server {
         return phmm_submit_batch(ctx, &b, &e->ticket);
     }
 
+    // Gives the epoch the next pairs of r: all of them, or for a request larger than
+    // the cell budget the pairs up to that budget (at least one).  With mu held.
+    void take(Epoch* e, Request* r, uint64_t& cells, uint32_t& pairs, uint32_t max_pairs) {
+        Segment g;
+        g.r = r;
+        g.p0 = r->next;
+        uint64_t c = 0;
+        uint32_t p = r->next;
+        const uint64_t cap = epoch_cells() > cells ? epoch_cells() - cells : 0;
+        while (p < r->np && (p == r->next || (c + r->pcells[p] <= cap && pairs + (p - r->next) < max_pairs)))
+            c += r->pcells[p++];
+        g.p1 = p;
+        r->next = p;
+        if (!r->started) {
+            r->started = true;
+            st.admitted++;
+            st.inflight++;
+        }
+        e->segs.push_back(g);
+        e->foot += r->foot;
+        cells += c;
+        pairs += g.p1 - g.p0;
+    }
+
+    // Forms the next epoch (with mu held).  Small requests (at most small_cells) go first,
+    // in arrival order, into epochs of their own; then larger requests in arrival order,
+    // split into chunks of at most epoch_cells, so no epoch holds the device for long and
+    // small requests that arrive meanwhile start within about one epoch.  A large request
+    // that has waited longer than max_wait_ms goes ahead of small ones.  Large epochs use
+    // at most max_inflight_epochs - 1 slots, leaving one for small requests.
+    Epoch* form(uint32_t max_pairs, uint32_t max_ep, uint64_t budget, size_t large_inflight) {
+        const auto now = Clock::now();
+        const double max_wait = cfg.max_wait_ms ? (double)cfg.max_wait_ms : 2000.0;
+        bool have_small = false, aged = false;
+        for (Request* r : pending) {
+            if (r->small) have_small = true;
+            else if (std::chrono::duration<double, std::milli>(now - r->t_in).count() > max_wait) aged = true;
+        }
+        const bool large_slot = max_ep < 2 || large_inflight + 1 < max_ep;
+        const bool want_large = large_slot && (aged || !have_small);
+        Epoch* e = new Epoch();
+        e->large = want_large;
+        uint64_t cells = 0;
+        uint32_t pairs = 0;
+        for (auto it = pending.begin(); it != pending.end();) {
+            Request* r = *it;
+            if (r->small == want_large) {
+                ++it;
+                continue;
+            }
+            if (st.bytes_inflight + e->foot + r->foot > budget) break;  // wait for memory
+            if (!e->segs.empty() && (single || pairs + (r->np - r->next) > max_pairs || cells >= epoch_cells()))
+                break;
+            take(e, r, cells, pairs, max_pairs);
+            if (r->next == r->np) {
+                it = pending.erase(it);
+                st.pending--;
+            } else {
+                break;  // a chunk of a large request fills the epoch
+            }
+        }
+        if (e->segs.empty()) {
+            delete e;
+            return nullptr;
+        }
+        return e;
+    }
+
+    // Puts an epoch that could not be submitted back: its requests' cursors move back and
+    // requests that had left the queue return to its front.  With mu held.
+    void unform(Epoch* e) {
+        for (auto it = e->segs.rbegin(); it != e->segs.rend(); ++it) {
+            Request* r = it->r;
+            const bool was_out = r->next == r->np;
+            r->next = it->p0;
+            if (r->next == 0 && r->done == 0 && r->started) {
+                r->started = false;
+                st.admitted--;
+                st.inflight--;
+            }
+            if (was_out) {
+                pending.push_front(r);
+                st.pending++;
+            }
+        }
+    }
+
     void run() {
         const uint32_t max_pairs = cfg.max_epoch_pairs ? cfg.max_epoch_pairs : (1u << 20);
         const uint32_t max_ep = cfg.max_inflight_epochs ? cfg.max_inflight_epochs : 2;
@@ -175,30 +284,14 @@ struct phmm_server {
             // admit waiting requests into new epochs while a slot and memory are free
             bool blocked = false;
             while (!blocked && inflight.size() < max_ep) {
-                Epoch* e = new Epoch();
+                Epoch* e = nullptr;
                 {
                     std::lock_guard<std::mutex> lk(mu);
-                    if (stop || pending.empty()) {
-                        delete e;
-                        break;
-                    }
-                    uint64_t pairs = 0;
-                    while (!pending.empty()) {
-                        Request* r = pending.front();
-                        if (st.bytes_inflight + e->foot + r->foot > budget) break;
-                        if (!e->reqs.empty() && (pairs + r->np > max_pairs || single)) break;
-                        e->reqs.push_back(r);
-                        e->foot += r->foot;
-                        pairs += r->np;
-                        pending.pop_front();
-                    }
-                    if (e->reqs.empty()) {  // the head waits for memory held by running epochs
-                        delete e;
-                        break;
-                    }
-                    st.pending -= e->reqs.size();
-                    st.admitted += e->reqs.size();
-                    st.inflight += e->reqs.size();
+                    if (stop || pending.empty()) break;
+                    size_t large = 0;
+                    for (Epoch* x : inflight) large += x->large ? 1 : 0;
+                    e = form(max_pairs, max_ep, budget, large);
+                    if (!e) break;  // the head waits for memory or a slot held by running epochs
                     st.bytes_inflight += e->foot;
                 }
                 const int rc = submit(e);
@@ -210,19 +303,20 @@ struct phmm_server {
                     continue;
                 }
                 std::lock_guard<std::mutex> lk(mu);
-                if ((rc == PHMM_EBUSY || rc == PHMM_ENOMEM) && (rc == PHMM_EBUSY || e->reqs.size() > 1)) {
-                    // put the requests back in order; retry after a retirement (EBUSY) or
-                    // one request at a time (ENOMEM of a joined epoch)
-                    for (auto it = e->reqs.rbegin(); it != e->reqs.rend(); ++it) pending.push_front(*it);
-                    st.pending += e->reqs.size();
-                    st.admitted -= e->reqs.size();
-                    st.inflight -= e->reqs.size();
-                    st.bytes_inflight -= e->foot;
+                st.bytes_inflight -= e->foot;
+                if ((rc == PHMM_EBUSY || rc == PHMM_ENOMEM) && (rc == PHMM_EBUSY || e->segs.size() > 1)) {
+                    // retry after a retirement (EBUSY) or one request at a time (ENOMEM of
+                    // a joined epoch)
+                    unform(e);
                     if (rc == PHMM_ENOMEM) single = true;
                     blocked = rc == PHMM_EBUSY;
                 } else {
-                    for (Request* r : e->reqs) finish(r, rc);
-                    st.bytes_inflight -= e->foot;
+                    for (const Segment& g : e->segs) {
+                        Request* r = g.r;
+                        if (r->fail == PHMM_OK) r->fail = rc;
+                        r->done += g.p1 - g.p0;
+                        if (r->done == r->np) finish(r, r->fail);
+                    }
                     cv_done.notify_all();
                 }
                 delete e;
@@ -231,8 +325,11 @@ struct phmm_server {
                     Request* r = pending.front();
                     pending.pop_front();
                     st.pending--;
-                    st.inflight++;
-                    finish(r, PHMM_ENOMEM);
+                    if (!r->started) st.inflight++;
+                    r->fail = PHMM_ENOMEM;
+                    r->done += r->np - r->next;
+                    r->next = r->np;
+                    if (r->done == r->np) finish(r, PHMM_ENOMEM);
                     cv_done.notify_all();
                     blocked = false;
                 }
@@ -244,14 +341,17 @@ struct phmm_server {
             else
                 cv_work.wait_for(lk, std::chrono::microseconds(100));
         }
-        // cancel what was never admitted
+        // cancel what was never admitted (or not completely)
         std::lock_guard<std::mutex> lk(mu);
         while (!pending.empty()) {
             Request* r = pending.front();
             pending.pop_front();
             st.pending--;
-            st.inflight++;
-            finish(r, PHMM_ECANCELED);
+            if (!r->started) st.inflight++;
+            r->done += r->np - r->next;
+            r->next = r->np;
+            if (r->fail == PHMM_OK) r->fail = PHMM_ECANCELED;
+            if (r->done == r->np) finish(r, r->fail);
         }
         cv_done.notify_all();
     }
@@ -295,8 +395,12 @@ int phmm_server_enqueue(phmm_server* s, const phmm_batch* b, uint64_t* req_id) {
     r->hoff.assign(b->hap_off, b->hap_off + r->nh + 1);
     r->pr.assign(b->pair_read, b->pair_read + r->np);
     r->ph.assign(b->pair_hap, b->pair_hap + r->np);
-    for (uint32_t p = 0; p < r->np; ++p)
-        r->cells += (r->roff[r->pr[p] + 1] - r->roff[r->pr[p]]) * (r->hoff[r->ph[p] + 1] - r->hoff[r->ph[p]]);
+    r->pcells.resize(r->np);
+    for (uint32_t p = 0; p < r->np; ++p) {
+        r->pcells[p] = (r->roff[r->pr[p] + 1] - r->roff[r->pr[p]]) * (r->hoff[r->ph[p] + 1] - r->hoff[r->ph[p]]);
+        r->cells += r->pcells[p];
+    }
+    r->small = r->cells <= s->small_cells();
     r->out = b->out_log10;
     r->out_flags = b->out_flags;
     r->foot = foot;

@@ -22,7 +22,7 @@ PREC = {"fp32": 0, "fp64": 1, "fp32_only": 2}
 VARIANTS = {"auto": 0, "packed": 1, "scalar": 2, "lean": 3, "pipe": 4, "pipe2": 5}
 F_NO_GRAPH, F_LAUNCH_PER_PAIR, F_FORCE_RESCUE = 0x1, 0x2, 0x4
 F_LONG_LEAN, F_LONG_PIPE32, F_LONG_PIPE24, F_NO_TUNE, F_LONG_SERIAL = 0x10, 0x20, 0x40, 0x80, 0x100
-F_LONG_PIPE4 = 0x200
+F_LONG_PIPE4, F_LONG_CLUSTER = 0x200, 0x400
 PAIR_RESCUED, PAIR_RESCALED, PAIR_FP64, PAIR_ERROR = 0x1, 0x2, 0x4, 0x80
 PAIR_DANGER, PAIR_NONFINITE, PAIR_SMALL_SUM, PAIR_DEGENERATE = 0x8, 0x10, 0x20, 0x40
 
@@ -68,7 +68,7 @@ SHORT_KERNELS = ["k_short_scalar<32, 4>", "k_short_scalar<24, 4>", "k_short_scal
                  "k_short_pipe<16, 4>", "k_short_pipe2<32, 3, 1>", "k_short_pipe2<24, 4, 1>"]
 PACKED_KERNELS = ["k_short_packed<12, 4>", "k_short_packed<16, 3>"]
 LONG_KERNELS = ["k_forward<float, 32, 0>", "k_forward_pipe<32, 12>", "k_forward_pipe<24, 16>",
-                "k_forward_serial<32, 3>", "k_forward_pipe<32, 4>"]
+                "k_forward_serial<32, 3>", "k_forward_pipe<32, 4>", "k_forward_cluster<32, 4, 8>"]
 
 
 class Stats(ctypes.Structure):
@@ -89,7 +89,9 @@ class Stats(ctypes.Structure):
 
 class ServerConfig(ctypes.Structure):
     _fields_ = [("mem_budget_bytes", ctypes.c_uint64), ("max_epoch_pairs", ctypes.c_uint32),
-                ("max_inflight_epochs", ctypes.c_uint32), ("max_pending", ctypes.c_uint32)]
+                ("max_inflight_epochs", ctypes.c_uint32), ("max_pending", ctypes.c_uint32),
+                ("max_wait_ms", ctypes.c_uint32), ("epoch_cells", ctypes.c_uint64),
+                ("small_cells", ctypes.c_uint64)]
 
 
 class ServerStats(ctypes.Structure):
@@ -338,9 +340,11 @@ class Server:
     takes over while it runs.  Requests are host batches; results land in numpy arrays."""
 
     def __init__(self, ctx: Context, mem_budget: int = 40 << 30, max_epoch_pairs: int = 0,
-                 max_inflight_epochs: int = 2, max_pending: int = 0):
+                 max_inflight_epochs: int = 2, max_pending: int = 0, max_wait_ms: int = 0,
+                 epoch_cells: int = 0, small_cells: int = 0):
         self.ctx = ctx
-        cfg = ServerConfig(mem_budget, max_epoch_pairs, max_inflight_epochs, max_pending)
+        cfg = ServerConfig(mem_budget, max_epoch_pairs, max_inflight_epochs, max_pending, max_wait_ms,
+                           epoch_cells, small_cells)
         h = ctypes.c_void_p()
         rc = _lib.phmm_server_create(ctx._h, ctypes.byref(cfg), ctypes.byref(h))
         if rc != PHMM_OK:

@@ -29,8 +29,10 @@ def make_pool(n: int = 64, seed: int = 0, **kw) -> list:
 
 def run(ctx: "phmm.Context", pool: list, rate: float, duration: float, seed: int = 1,
         drain_s: float = 60.0, mem_budget: int = 40 << 30, max_epoch_pairs: int = 0,
-        max_inflight_epochs: int = 2) -> dict:
-    """Drive one open-loop run; returns latency percentiles, throughput and counts."""
+        max_inflight_epochs: int = 2, epoch_cells: int = 0, small_cells: int = 0,
+        max_wait_ms: int = 0) -> dict:
+    """Drive one open-loop run; returns latency percentiles (all requests, and the
+    server's small and large size classes), throughput and counts."""
     rng = np.random.default_rng(seed)
     gaps = rng.exponential(1.0 / rate, size=int(rate * duration * 1.5) + 16)
     arr = np.cumsum(gaps)
@@ -42,7 +44,8 @@ def run(ctx: "phmm.Context", pool: list, rate: float, duration: float, seed: int
     stop_collect = threading.Event()
 
     with phmm.Server(ctx, mem_budget=mem_budget, max_epoch_pairs=max_epoch_pairs,
-                     max_inflight_epochs=max_inflight_epochs) as srv:
+                     max_inflight_epochs=max_inflight_epochs, epoch_cells=epoch_cells,
+                     small_cells=small_cells, max_wait_ms=max_wait_ms) as srv:
         t0 = time.perf_counter()
 
         def submitter():
@@ -96,7 +99,17 @@ def run(ctx: "phmm.Context", pool: list, rate: float, duration: float, seed: int
     lat = np.array([done[rid][1] - recs[rid][1] for rid in ok]) * 1e3
     cells_done = float(sum(pool[recs[rid][0]][1] for rid in ok))
     lag = np.array([recs[rid][2] - recs[rid][1] for rid in recs]) * 1e3 if recs else np.zeros(1)
+    small_max = small_cells or (epoch_cells or 100_000_000_000) // 20
+    by_class = {}
+    for name, pick in (("small", lambda c: c <= small_max), ("large", lambda c: c > small_max)):
+        ids = [rid for rid in ok if pick(pool[recs[rid][0]][1])]
+        lc = np.array([done[rid][1] - recs[rid][1] for rid in ids]) * 1e3
+        by_class[name] = {"completed": len(ids),
+                          "p50_ms": float(np.percentile(lc, 50)) if len(lc) else None,
+                          "p99_ms": float(np.percentile(lc, 99)) if len(lc) else None}
+    by_class["small_max_cells"] = int(small_max)
     return {
+        "by_class": by_class,
         "offered_rate": rate, "duration_s": duration, "arrivals": int(len(arr)),
         "enqueued": len(recs), "rejected": rejected[0], "completed": len(ok),
         "not_completed": len(recs) - len(ok),

@@ -93,12 +93,12 @@ def test_columns_per_lane(phmm, variant, N):
     _check(out, flags, oracle.batch(b))
 
 
-LONG_KINDS = ["lean", "pipe32", "pipe24", "serial", "pipe4"]
+LONG_KINDS = ["lean", "pipe32", "pipe24", "serial", "pipe4", "cluster"]
 
 
 def _long_flag(phmm, kind):
     return {"lean": phmm.F_LONG_LEAN, "pipe32": phmm.F_LONG_PIPE32, "pipe24": phmm.F_LONG_PIPE24,
-            "serial": phmm.F_LONG_SERIAL, "pipe4": phmm.F_LONG_PIPE4}[kind]
+            "serial": phmm.F_LONG_SERIAL, "pipe4": phmm.F_LONG_PIPE4, "cluster": phmm.F_LONG_CLUSTER}[kind]
 
 
 @pytest.mark.parametrize("variant,N", VARIANTS)
@@ -260,6 +260,22 @@ def test_wide_pairs_fp32_strips(phmm, kind):
     assert st["n_long"] == 5
     assert np.all((flags & 0x78) == 0)
     assert np.max(np.abs(out - oracle.batch(b))) <= TOL32
+
+
+def test_cluster_kind_single_very_wide_pair(phmm):
+    """One pair of 131072 columns on the cluster kind: 32 strips of 4096 columns in four
+    groups of eight CTAs, neighbours inside a group linked through distributed shared
+    memory, groups through global memory; the read is short enough for the oracle."""
+    rng = np.random.default_rng(44)
+    k = 131072
+    hap = "".join(rng.choice(list("ACGT"), size=k))
+    off = 70000
+    read = hap[off:off + 180]
+    b = W.from_strings([(read, hap, 30, 45, 45, 10), (read[:90], hap[:20000], 25, 45, 45, 10)])
+    with phmm.Context(precision="fp32", flags=phmm.F_LONG_CLUSTER) as ctx:
+        out, flags, rc, st = ctx.run(b)
+    assert st["long_kernel"] == 5 and st["n_long"] == 2
+    _check(out, flags, oracle.batch(b))
 
 
 def test_wide_pairs_fp64_strips(phmm):

@@ -68,6 +68,34 @@ def test_server_alone_vs_mix(phmm):
         assert np.all(np.abs(out - ref) <= tol)
 
 
+def test_server_chunks_large_requests_and_runs_small_first(phmm):
+    """A request larger than the epoch cell budget is split into chunks of consecutive
+    pairs across epochs and still gets the same results as alone; small requests queued
+    behind it complete before it (they go ahead between its chunks)."""
+    import time
+    big = W.long_pairs(24, seed=31, k_range=(1500, 3000))
+    smalls = [W.plain_pairs(3, seed=40 + q) for q in range(6)]
+    big_cells = W.cells(big)
+    with phmm.Context(max_inflight=2, variant="scalar", cols_per_lane=32) as ctx:
+        alone = ctx.run(big)[0]
+        with phmm.Server(ctx, max_inflight_epochs=2, epoch_cells=big_cells // 8,
+                         small_cells=big_cells // 100) as srv:
+            ib = srv.enqueue(big)
+            time.sleep(0.001)
+            ids = [srv.enqueue(r) for r in smalls]
+            res = [srv.poll(i, -1) for i in ids]
+            rb = srv.poll(ib, -1)
+            st = srv.stats()
+    assert rb[0] == 0 and np.max(np.abs(rb[2] - alone)) <= TOL32
+    assert st["epochs"] >= 8 + 1  # the large request alone needs at least 8 chunks
+    assert st["completed"] == 1 + len(smalls) and st["failed"] == 0 and st["pending"] == 0
+    big_lat = rb[1]
+    for q, (rc, lat, out, fl) in enumerate(res):
+        assert rc == 0
+        assert lat < big_lat
+        assert np.max(np.abs(out - oracle.batch(smalls[q]))) <= TOL32
+
+
 def test_server_error_isolated_to_its_request(phmm):
     good = W.plain_pairs(6, seed=21)
     bad = W.from_strings([("ACGT", "ACGT", 30, 45, 45, 10), ("AXGT", "ACGT", 30, 45, 45, 10)])
@@ -108,3 +136,4 @@ def test_open_loop_run(phmm):
         r = serving.run(ctx, pool, rate=40.0, duration=1.5, drain_s=60.0)
     assert r["enqueued"] == r["arrivals"] and r["completed"] == r["enqueued"]
     assert r["p50_ms"] > 0 and r["p99_ms"] >= r["p50_ms"] and r["gcups"] > 0
+    assert r["by_class"]["small"]["completed"] + r["by_class"]["large"]["completed"] == r["completed"]
