@@ -22,8 +22,8 @@
  * Precision (phmm_precision): FP32 with FP64 rescue of flagged pairs, FP64 for every
  * pair, or FP32 alone.  The FP32 pass flags a pair for the FP64 pass on the same tests
  * as the GPU library: a non-finite value, a checkpoint maximum below the danger level,
- * the last-row sum below tau(l, k) = 1e4 * 3 l k 2^-106 (this path flushes cells below
- * 2^-106 to zero; the GPU's test uses FLT_MIN), or an a-priori rounding bound
+ * the last-row sum below tau(l, k) = 1e4 * 3 l k FLT_MIN (on x86 hosts, which flush
+ * cells below 2^-106 to zero, 2^-106 instead of FLT_MIN), or an a-priori rounding bound
  * above the FP32 tolerance.  FP32 per-row coefficients are stochastically rounded from
  * double, so their rounding errors average out over long reads instead of drifting.
  */
@@ -36,17 +36,22 @@
 #include <string.h>
 #include <unistd.h>
 
-/* Lanes per pack: two 128-bit registers per operation on AArch64 (32 vector registers:
- * the per-row coefficients and the carried diagonal stay in registers), one on hosts
- * with 16 (x86-64 SSE2). */
-#if defined(__aarch64__)
-#define W32 8 /* FP32 lanes per pack */
-#define W64 4 /* FP64 lanes per pack */
-#else
-#define W32 4
-#define W64 2
-#endif
+/* Lanes per pack: one 128-bit register per operation (wider generic vectors measured
+ * slower on Neoverse-V2: the per-row coefficients no longer fit the register file). */
+#define W32 4 /* FP32 lanes per pack */
+#define W64 2 /* FP64 lanes per pack */
 
+/* Cells at or below FLUSH are stored as zero.  x86 cores compute with subnormal values
+ * far slower, so there they are flushed (2^-106 FP32, 2^-1000 FP64); AArch64 cores
+ * handle them at full speed (measured on Neoverse-V2: flushing cost more than it saved),
+ * so there nothing is flushed beyond what the format itself does. */
+#if defined(__aarch64__)
+#define FLUSH32 0.0f
+#define FLUSH64 0.0
+#else
+#define FLUSH32 0x1.0p-106f
+#define FLUSH64 0x1.0p-1000
+#endif
 typedef float v32f __attribute__((vector_size(W32 * sizeof(float))));
 typedef int32_t v32i __attribute__((vector_size(W32 * sizeof(int32_t))));
 typedef double v64d __attribute__((vector_size(W64 * sizeof(double))));
@@ -79,16 +84,25 @@ static uint64_t mix64(uint64_t z) {
 }
 
 /* x rounded to float stochastically: to one of the two neighbouring floats, with
- * probabilities that make the expected value x (unbiased), from a hash of the read base
- * index and the coefficient number. */
-static float sr_round(double x, uint64_t base, int q) {
+ * probabilities that make the expected value x (unbiased up to 2^-16 of a unit in the last
+ * place), from a 16-bit uniform u16 (a quarter of one hash of the read base index). */
+static float sr_round(double x, uint32_t u16) {
     const float f = (float)x; /* nearest */
     const double e = x - (double)f;
-    if (e == 0.0 || !isfinite(x)) return f;
-    const float g = nextafterf(f, e > 0.0 ? INFINITY : -INFINITY);
+    if (e == 0.0 || !(fabs(x) < 3.0e38)) return f;
+    float g;
+    if (f != 0.0f) {
+        /* the neighbour on the side of x: one step of the bit pattern away from or
+         * towards zero */
+        uint32_t fb;
+        memcpy(&fb, &f, 4);
+        fb += ((e > 0.0) == (f > 0.0f)) ? 1u : (uint32_t)-1;
+        memcpy(&g, &fb, 4);
+    } else {
+        g = nextafterf(f, e > 0.0 ? INFINITY : -INFINITY);
+    }
     const double gap = fabs((double)g - (double)f);
-    const double u = (double)(mix64(0x5eed1234ull << 32 ^ (base * 8u + (uint64_t)q)) >> 11) * 0x1.0p-53;
-    return u < fabs(e) / gap ? g : f;
+    return ((double)u16 + 0.5) * 0x1.0p-16 * gap < fabs(e) ? g : f;
 }
 
 /* A-priori bound on |log10 L(FP32) - log10 L| for a pair of l rows and k columns.
@@ -151,7 +165,7 @@ static int scratch_reserve(cpu_scratch *s, size_t bytes) {
 #define ENG_TARGET 96
 #define ENG_DANGER (-100)
 #define ENG_MAXSHIFT 126
-#define ENG_FLUSH 0x1.0p-106f
+#define ENG_FLUSH FLUSH32
 #include "cpu_engine.inc"
 #undef ENG_NAME
 #undef ENG_T
@@ -181,7 +195,7 @@ static int scratch_reserve(cpu_scratch *s, size_t bytes) {
 #define ENG_TARGET 800
 #define ENG_DANGER (-950)
 #define ENG_MAXSHIFT 1020
-#define ENG_FLUSH 0x1.0p-1000
+#define ENG_FLUSH FLUSH64
 #include "cpu_engine.inc"
 
 /* Checkpoint interval of a pack: between checkpoints the lane maximum can fall by at most
@@ -405,9 +419,11 @@ int phmm_cpu_forward(const phmm_batch *b, int n_threads, int precision, double f
                 f |= PHMM_PAIR_FP64;
                 if (pass == 1) f |= PHMM_PAIR_RESCUED | (b->out_flags ? b->out_flags[p] & 0x78u : 0u);
             } else {
-                /* underflow test: at most 3 l k flushed cells, each below 2^-106 and each
-                 * reaching L with total weight <= 1; the relative loss must stay <= 1e-4 */
-                if (!(x->S > 3.0e4 * l * k * 0x1.0p-106)) f |= PHMM_PAIR_SMALL_SUM;
+                /* underflow test: at most 3 l k cells lost to the flush (or to the format's
+                 * own underflow), each below max(FLUSH32, FLT_MIN) and each reaching L with
+                 * total weight <= 1; the relative loss must stay <= 1e-4 */
+                const double lost = FLUSH32 > 1.1754943508222875e-38 ? (double)FLUSH32 : 1.1754943508222875e-38;
+                if (!(x->S > 3.0e4 * l * k * lost)) f |= PHMM_PAIR_SMALL_SUM;
                 if (fp32_bound_log10(l, k) > fp32_tolerance) f |= PHMM_PAIR_DANGER;
                 if (precision == PHMM_PREC_FP32_RESCUE && ((f & 0x78u) || !isfinite(v))) list[nr++] = p;
             }

@@ -1018,6 +1018,17 @@ __device__ SegOut team_run_pipe(const Rec32J* __restrict__ rec, int l, int lmax,
 // formed after the scan.  The lane's scan aggregate joins the two half chains with
 // g^(N/2).  Same results as team_run_pipe up to rounding order.
 // ------------------------------------------------------------------------------------
+// Asynchronous 16-byte copy global -> shared through L2 only (cp.async.cg: the source was
+// written by this warp's previous strip with L2-only stores, so L1 may hold stale lines),
+// and the group bookkeeping around it.
+__device__ __forceinline__ void cp_async16_cg(void* smem_dst, const void* gmem_src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_0() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
 // float2 FMA / multiply as one packed instruction (PACKED) or as two scalar ones (two
 // independent dependency chains for the scheduler to interleave).
 template <bool PACKED>
@@ -1036,12 +1047,15 @@ __device__ __forceinline__ float2 fmul2_sel(float2 a, float2 b) {
 // seg_link_pipe<N, true>: the finished left strip's boundary (float4 per row: M, J, D-hat,
 // E of its last column; `sin`) enters lane 0 and, as a carry g^(N t - 1), every lane's
 // D-hat; checkpoints keep E >= E_left; lane 31 stores this strip's boundary (`sout`).
+// The left boundary is staged in shared memory (`stg`: two blocks of 32 rows for this
+// warp), each block copied asynchronously (cp.async, one row per lane) while the warp
+// computes the 32 rows before it; every row then reads its float4 as one broadcast.
 template <int N, bool PACKED, bool LINK = false>
 __device__ SegOut team_run_pipe2(const Rec32J* __restrict__ rec, int l, int lmax,
                                  const uint8_t* __restrict__ hap, int k, int col0, int lt,
                                  int tlast, int nsteps, const PowRow<float>* __restrict__ pow_tab,
                                  const PipeRange& rng, const float4* sin = nullptr, float4* sout = nullptr,
-                                 bool has_left = false, bool has_right = false) {
+                                 bool has_left = false, bool has_right = false, float4* stg = nullptr) {
     using NT = Num<float>;
     static_assert(N <= 32 && N % 2 == 0, "match masks hold 32 columns; two halves");
     constexpr int H = N / 2;
@@ -1066,9 +1080,13 @@ __device__ SegOut team_run_pipe2(const Rec32J* __restrict__ rec, int l, int lmax
     float2 dt2 = make_float2(0.f, 0.f), ml2 = make_float2(0.f, 0.f);
     float gprev = 0.f;
     float sp1[5], sp2[5], last1 = 0.f, last2 = 0.f, hh1 = 0.f, hh2 = 0.f, hm1 = 0.f, hm2 = 0.f;
-    float qa1 = 0.f, qa2 = 0.f, qb1 = 0.f, qb2 = 0.f;  // LINK: g^(N lt - 1), g^(N (lt + 1) - 1)
-    float4 bnd4 = make_float4(0.f, 0.f, 0.f, 0.f);      // LINK: this lane's row of the left boundary
     int gcp = -1;
+    if constexpr (LINK) {
+        if (has_left) {  // rows 1..32 of the left boundary into stage block 0
+            if (lt + 1 <= l) cp_async16_cg(stg + lt, sin + lt);
+            cp_async_commit();
+        }
+    }
     SegOut out;
     out.S = 0.0;
     out.E = 0;
@@ -1096,12 +1114,6 @@ __device__ SegOut team_run_pipe2(const Rec32J* __restrict__ rec, int l, int lmax
             hh2 = __ldg(&pr->hh2);
             hm1 = __ldg(&pr->hm1);
             hm2 = __ldg(&pr->hm2);
-            if constexpr (LINK) {
-                qa1 = __ldg(&pr->lq1[lt]);
-                qa2 = __ldg(&pr->lq2[lt]);
-                qb1 = __ldg(&pr->lq1[lt + 1]);
-                qb2 = __ldg(&pr->lq2[lt + 1]);
-            }
             gcp = gq;
         }
         const int code = (int)(meta & META_CODE_MASK);
@@ -1196,15 +1208,23 @@ __device__ SegOut team_run_pipe2(const Rec32J* __restrict__ rec, int l, int lmax
             float lM = 0.f, lJ = 0.f, lD = 0.f;
             int Eleft = INT_MIN;
             if (has_left) {
-                if (((i - 1) & 31) == 0) {  // next 32 rows of the finished left strip (L2 loads)
-                    const int r = i + lt;
-                    bnd4 = r <= l ? __ldcg(sin + (r - 1)) : make_float4(0.f, 0.f, 0.f, __int_as_float(INT_MIN));
+                const int blk = (i - 1) >> 5;
+                if (((i - 1) & 31) == 0) {
+                    // start copying the next 32 rows into the other stage block (every lane
+                    // has read the rows it held), then wait for this block (copied while
+                    // the previous 32 rows were computed)
+                    __syncwarp();
+                    const int r = i + 32 + lt;
+                    if (r <= l) cp_async16_cg(stg + ((blk + 1) & 1) * 32 + lt, sin + (r - 1));
+                    cp_async_commit();
+                    cp_async_wait_1();
+                    __syncwarp();
                 }
-                const int src = (i - 1) & 31;
-                lM = __shfl_sync(kFull, bnd4.x, src);
-                lJ = __shfl_sync(kFull, bnd4.y, src);
-                lD = __shfl_sync(kFull, bnd4.z, src);
-                Eleft = __float_as_int(__shfl_sync(kFull, bnd4.w, src));
+                const float4 v = stg[(blk & 1) * 32 + ((i - 1) & 31)];  // one broadcast read
+                lM = v.x;
+                lJ = v.y;
+                lD = v.z;
+                Eleft = __float_as_int(v.w);
             }
             // checkpoint (same rows in every strip of the pair): E >= E_left, so that left
             // values only ever scale down
@@ -1257,20 +1277,27 @@ __device__ SegOut team_run_pipe2(const Rec32J* __restrict__ rec, int l, int lmax
             }
             // left values into this strip's scale (no left: zeros stay zero)
             const int dsh = has_left ? Eleft - E : 0;
-            lM = scale2(lM, dsh);
-            lJ = scale2(lJ, dsh);
-            lD = scale2(lD, dsh);
+            if (dsh != 0) {  // warp-uniform; the scales differ only after a checkpoint
+                lM = scale2(lM, dsh);
+                lJ = scale2(lJ, dsh);
+                lD = scale2(lD, dsh);
+            }
             const float Wseg = fmaf(rg, lD, lM);  // D-hat at the strip's first column
             float ndA = fmaf(zz * last1, last2, yp);
-            ndA = fmaf(Wseg * qa1, qa2, ndA);
+            {
+                // carry g^(N lt - 1) from the row's table (L1; not kept in registers)
+                const PowRow<float>* pr = pow_tab + min(gcp, kMaxPhred);
+                ndA = fmaf(Wseg * __ldg(&pr->lq1[lt]), __ldg(&pr->lq2[lt]), ndA);
+            }
             if (lt == 0) {
                 ndA = lD;
                 nm = lM;
                 U2[0].x = fmaf(nxt.a, lM, lJ);
             }
             if (has_right && lt == 31) {
-                // D-hat at the strip's last column
-                const float dl = fmaf(Wseg * qb1, qb2, fmaf(Wd * last1, last2, ypl));
+                // D-hat at the strip's last column (carry g^(32 N - 1) from the row's table)
+                const PowRow<float>* pr = pow_tab + min(gcp, kMaxPhred);
+                const float dl = fmaf(Wseg * __ldg(&pr->lq1[32]), __ldg(&pr->lq2[32]), fmaf(Wd * last1, last2, ypl));
                 __stcg(sout + (i - 1), make_float4(M2[H - 1].y, jl, dl, __int_as_float(E)));
             }
             const float wl = fmaf(rg, ndA, nm);         // D-hat at the lane's first column
@@ -1328,6 +1355,9 @@ __device__ SegOut team_run_pipe2(const Rec32J* __restrict__ rec, int l, int lmax
         ml2 = make_float2(nm, M2[H - 1].x);
         gprev = rg;
         cur = nxt;
+    }
+    if constexpr (LINK) {
+        if (has_left) cp_async_wait_0();  // nothing may land in the stage after this strip
     }
     return out;
 }
@@ -1532,9 +1562,11 @@ __device__ SegOut seg_link_pipe(const Rec32J* __restrict__ rec, int l, const uin
         }
         // left values into this segment's scale (E >= E_left here; no left: zeros stay zero)
         const int dsh = has_left ? Eleft - E : 0;
-        lM = scale2(lM, dsh);
-        lJ = scale2(lJ, dsh);
-        lD = scale2(lD, dsh);
+        if (dsh != 0) {  // warp-uniform; the scales differ only after a checkpoint
+            lM = scale2(lM, dsh);
+            lJ = scale2(lJ, dsh);
+            lD = scale2(lD, dsh);
+        }
         const float Wseg = fmaf(rg, lD, lM);  // D-hat at the segment's first column
         // D-hat at the column before this lane: the left lanes' part plus the carry
         float nd = fmaf(zz * last1, last2, yp);

@@ -635,6 +635,7 @@ k_forward_cluster(const BatchHeader* __restrict__ H, const PowRow<float>* __rest
 template <int N, int MINB>
 __global__ void __launch_bounds__(128, MINB)
 k_forward_serial(const BatchHeader* __restrict__ H, const PowRow<float>* __restrict__ pow) {
+    __shared__ float4 stage[4][64];  // per warp: two blocks of 32 left-boundary rows
     const PipeRange rng = pipe_range(H->dropgrow);
     const uint32_t n_c = H->n_citems;
     const int lane = threadIdx.x & 31;
@@ -656,7 +657,8 @@ k_forward_serial(const BatchHeader* __restrict__ H, const PowRow<float>* __restr
             const int c0 = (int)(s * 32u * N) + lane * N;
             const SegOut o = team_run_pipe2<N, true, true>(H->rec32j + d.roff, (int)d.l, (int)d.l,
                                                            H->hap_bases + d.hoff, (int)d.k, c0, lane, 31, 5,
-                                                           pow, rng, in, outb, s > 0, s + 1 < S);
+                                                           pow, rng, in, outb, s > 0, s + 1 < S,
+                                                           stage[threadIdx.x >> 5]);
             __syncwarp();  // this strip's boundary stores before the next strip's loads
             if (lane == 0) {
                 Partial p;
