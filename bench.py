@@ -67,10 +67,10 @@ def sweep_lengths(args):
     return out
 
 
-def make_workload(name: str, units: int):
+def make_workload(name: str, units: int, uneven_max: int = 20000):
     from paper_2606_25738_gb300 import workloads as W
     if name == "uneven":
-        return W.uneven_pairs(units, seed=0)
+        return W.uneven_pairs(units, seed=0, len_range=(50, uneven_max))
     if name == "short":
         return W.short_read_regions(units, seed=0)
     if name == "long":
@@ -98,6 +98,8 @@ def config_dict(name: str, units: int, b, world: int, args) -> dict:
         return {"workload": desc, "lengths": lens, "l2": L2_NOTE,
                 "parallelism": "replicas" if world > 1 else "single GPU"}
     desc = WORKLOADS[name][2] % units
+    if name == "uneven" and getattr(args, "uneven_max", 20000) != 20000:
+        desc = desc.replace("50-20k bp", "50-%d bp" % args.uneven_max)
     return {"workload": desc, "pairs": int(len(b["pair_read"])), "reads": int(len(b["read_off"]) - 1),
             "haplotypes": int(len(b["hap_off"]) - 1), "cells": int(W.cells(b)), "l2": L2_NOTE,
             "parallelism": "replicas" if world > 1 else "single GPU"}
@@ -273,7 +275,7 @@ def run_reference(args):
         units = getattr(args, "units", 0) or WORKLOADS[name][0]
         if getattr(args, "regions", None) and name == "short":
             units = args.regions
-        batches = [make_workload(name, units)]
+        batches = [make_workload(name, units, getattr(args, "uneven_max", 20000))]
         cfg = config_dict(name, units, batches[0], world, args)
     vals = []
     # each step is a bounded random sample of the workload, sized so that the whole run
@@ -562,7 +564,7 @@ def run_ours(args):
     t = time.perf_counter()
     # Replicas: every rank scores its own copy of the workload (pairs are independent;
     # there is no exchange step), so per-GPU work is fixed as N grows.
-    b = make_workload(name, units)
+    b = make_workload(name, units, args.uneven_max)
     gen_s = time.perf_counter() - t
     n = len(b["pair_read"])
     cells = W.cells(b)
@@ -571,7 +573,7 @@ def run_ours(args):
     out = torch.empty(n, dtype=torch.float64, device="cuda")
     fl = torch.zeros(n, dtype=torch.uint8, device="cuda")
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # > L2 (129 MB)
-    ctx = phmm.Context(device=dev, precision="fp32", stream=stream.cuda_stream, max_inflight=1,
+    ctx = phmm.Context(device=dev, precision=args.precision, stream=stream.cuda_stream, max_inflight=1,
                        variant=args.variant, cols_per_lane=args.cols, flags=_flag_bits(args, phmm))
     info = ctx.device_info()
     t = time.perf_counter()
@@ -626,7 +628,9 @@ def run_ours(args):
     line = {
         "metric": METRIC, "value": value, "unit": "GCUPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32 (f64 rescue + reduction)",
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": {"fp32": "f32 (f64 rescue + reduction)", "fp64": "f64",
+                  "fp32_only": "f32 (f64 reduction)"}[args.precision],
         "data": "synthetic (seeded, shaped like the paper's workloads)",
         "config": config_dict(name, units, b, world, args),
         "roofline": roofline(dom, info, name),
@@ -697,6 +701,11 @@ def main():
     ap.add_argument("--extras", default="all", choices=["all", "core", "none"],
                     help="all: cpu_baseline, parity, comparators, extra legs, serving; core: without the "
                          "extra workload legs; none: the timed headline only (profiling)")
+    ap.add_argument("--uneven-max", type=int, default=20000,
+                    help="uneven: longest read / haplotype (20000 = the benchmark; smaller only for "
+                         "profiling captures)")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "fp32_only"],
+                    help="precision of the timed run (fp32 = FP32 with FP64 rescue, the benchmark)")
     ap.add_argument("--e2e-steps", type=int, default=3, help="end-to-end steps (host buffers)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="cpu_baseline sample size in seconds")
     ap.add_argument("--lpp-pairs", type=int, default=4000,
