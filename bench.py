@@ -424,7 +424,8 @@ def gpu_leg(name: str, b, dev: int, args, steps: int = 5, warmup: int = 3, preci
     row = {"workload": name, "precision": precision, "pairs": n, "cells": cells,
            "gcups_step": cells / tot / 1e6, "gcups_forward": cells / fwd / 1e6, "ms_per_step": tot,
            "ms_forward": fwd, "rescued_pairs": int(sts[-1]["n_rescued"]), "first_submit_s": first_s,
-           "kernels": [k for k in kernel_names(sts[-1], phmm) if k] if precision != "fp64" else ["k_forward<double, 8, 1>"]}
+           "kernels": ([k for k in kernel_names(sts[-1], phmm) if k] if precision != "fp64"
+                       else [phmm.FP64_KERNELS[sts[-1]["short_kernel"]]])}
     if precision != "fp64":
         dom = dominant_branch(sts, phmm)
         row["roofline"] = roofline(dom, info, name)

@@ -102,7 +102,9 @@ typedef struct {
     int cols_per_lane;        /* haplotype columns per thread (the paper's N) for FP32 short
                                  pairs: 12 or 16 fixes the packed-team width, 24 or 32 the
                                  scalar-team width, 0 = chosen by the built-in tuner.
-                                 Multi-warp pairs use 32 (FP32); FP64 kernels use 8. */
+                                 Multi-warp pairs use 32 (FP32).  With PHMM_PREC_FP64: 8
+                                 or 16 fixes the FP64 kernel variant (8 columns per lane in
+                                 16-warp CTAs, 16 in 8-warp CTAs), 0 = tuner. */
     int kernel_variant;       /* FP32 short-pair kernels the tuner may use: 0 = any; 1 =
                                  pairs of the same read share packed teams (two haplotypes
                                  per thread in float2 halves), the rest run in scalar
@@ -171,7 +173,9 @@ typedef struct {
     uint32_t kernel_launches; /* kernels launched for the ticket */
     uint32_t status_bits;     /* device status word (0 = clean) */
     float ms_host;            /* host time of phmm_submit_batch's planning and enqueue */
-    /* FP32 kernels the plan ran (-1: that branch had no work or the precision is FP64):
+    /* Kernels the plan ran (-1: that branch had no work).  FP64 precision: short_kernel =
+     * the FP64 forward variant (0: 8 columns per lane in 16-warp CTAs, 1: 16 columns per
+     * lane in 8-warp CTAs), the other two -1.  FP32:
      * short_kernel = scalar-team variant 0..8 (k_short_scalar<32,4>, <24,4>, <24,5>,
      * <16,6>, k_short_pipe<32,3>, <24,4>, <16,4>, k_short_pipe2<32,3>, <24,4>);
      * packed_kernel = packed-team variant 0..1 (k_short_packed<12,4>, <16,3>);

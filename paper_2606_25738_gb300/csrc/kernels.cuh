@@ -434,8 +434,8 @@ __device__ __forceinline__ void write_part(const BatchHeader* __restrict__ H, ui
 // Persistent forward kernel for multi-warp pairs: CTA items (longest first) taken from
 // an atomic counter; with WARP_ITEMS it then also takes warp items (the FP64 engine, which
 // has no packed short kernel).
-template <typename T, int N, bool WARP_ITEMS>
-__global__ void __launch_bounds__(kCtaThreads, 1)
+template <typename T, int N, bool WARP_ITEMS, int CW = kCtaWarps>
+__global__ void __launch_bounds__(CW * 32, 1)
 k_forward(const BatchHeader* __restrict__ H, const PowRow<T>* __restrict__ pow) {
     __shared__ CtaShared<T> sh;
     const int R = checkpoint_interval<T>(H->dropgrow);

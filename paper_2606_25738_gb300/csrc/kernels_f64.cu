@@ -49,6 +49,7 @@ __global__ void __launch_bounds__(256) k_prep64_list(const BatchHeader* __restri
 }
 
 template __global__ void k_forward<double, kN64, true>(const BatchHeader*, const PowRow<double>*);
+template __global__ void k_forward<double, kF64N[1], true, kF64CW[1]>(const BatchHeader*, const PowRow<double>*);
 template __global__ void k_finalize<double>(const BatchHeader*);
 
 __device__ __forceinline__ double log10_of(const Partial& q) {
@@ -101,8 +102,10 @@ void launch_prep64_all(const BatchHeader* H, const PhredTables* T, int grid, cud
 void launch_prep64_list(const BatchHeader* H, const PhredTables* T, int grid, cudaStream_t s) {
     k_prep64_list<<<grid, 256, 0, s>>>(H, T);
 }
-void launch_forward64(const BatchHeader* H, const void* pow, int grid, cudaStream_t s) {
-    k_forward<double, kN64, true><<<grid, kCtaThreads, 0, s>>>(H, static_cast<const PowRow<double>*>(pow));
+void launch_forward64(int id, const BatchHeader* H, const void* pow, int grid, cudaStream_t s) {
+    const PowRow<double>* p = static_cast<const PowRow<double>*>(pow);
+    if (id == 1) k_forward<double, kF64N[1], true, kF64CW[1]><<<grid, kF64CW[1] * 32, 0, s>>>(H, p);
+    else k_forward<double, kN64, true><<<grid, kCtaThreads, 0, s>>>(H, p);
 }
 void launch_finalize64(const BatchHeader* H, int grid, cudaStream_t s) {
     k_finalize<double><<<grid, 256, 0, s>>>(H);
@@ -113,9 +116,13 @@ void launch_rescue64(const BatchHeader* H, const void* pow, int grid, cudaStream
 void launch_single64(const BatchHeader* H, const void* pow, uint32_t pair, cudaStream_t s) {
     k_single<<<1, kCtaThreads, 0, s>>>(H, static_cast<const PowRow<double>*>(pow), pair);
 }
-int occupancy_forward64() {
+int occupancy_forward64(int id) {
     int b = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_forward<double, kN64, true>, kCtaThreads, 0);
+    if (id == 1)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_forward<double, kF64N[1], true, kF64CW[1]>,
+                                                      kF64CW[1] * 32, 0);
+    else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_forward<double, kN64, true>, kCtaThreads, 0);
     return b > 0 ? b : 1;
 }
 

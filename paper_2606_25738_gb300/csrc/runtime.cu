@@ -493,7 +493,9 @@ struct phmm_ctx {
     DevBuf tables;                          // PhredTables
     DevBuf scan_row;                        // scan test: one PowRow<float> (global memory)
     DevBuf pow32[5];                        // N = 12, 16, 20, 24 (packed short), 32 (long)
-    DevBuf pow64;
+    DevBuf pow64;                           // FP64 powers, N = 8 (variant 0, rescue, comparator)
+    DevBuf pow64w;                          // FP64 powers, N = 16 (variant 1)
+    int occ64v[kNumF64] = {1, 1};           // resident CTAs per SM of the FP64 forward variants
     // resident CTAs per SM of each kernel (long kind 5: resident clusters of the GPU)
     int occ_packed[kNumPacked] = {}, occ_scalar[kNumScalar] = {}, occ_longk[kNumLong] = {1, 1, 1, 1, 1, 1}, occ64 = 1;
     std::map<uint64_t, std::array<int, 3>> tuned;  // batch signature -> (scalar id, packed id, long kind)
@@ -574,7 +576,8 @@ int launch_sequence(phmm_ctx* ctx, Slot& S, int scal_id, int pack_id, int long_k
     if (prec == PHMM_PREC_FP64) {
         launch_prep64_all(H, T, grid_pre, s);
         CK(rec(S.ev_fwd0));
-        launch_forward64(H, ctx->pow64.p, ctx->sms * ctx->occ64, s);
+        // scal_id carries the FP64 variant (see make_plan64)
+        launch_forward64(scal_id, H, scal_id == 1 ? ctx->pow64w.p : ctx->pow64.p, ctx->sms * ctx->occ64v[scal_id], s);
         CK(rec(S.ev_fwd1));
         launch_finalize64(H, grid_pre, s);
         CK(rec(S.ev_res0));
@@ -689,6 +692,15 @@ std::vector<std::pair<int, int>> fp32_candidates(const phmm_config& cfg) {
             c.push_back({si, pi});
         }
     return c;
+}
+
+// FP64 plan of variant id (launch.h: kF64N columns per lane, kF64CW-warp CTAs); the
+// variant travels in scal_id.
+void make_plan64(const uint32_t* l, const uint32_t* k, const uint32_t* pr, uint32_t n, int id, Plan& P) {
+    make_plan(l, k, pr, n, kF64N[id], 0, kF64N[id], P, 8, kF64CW[id]);
+    P.scal_id = id;
+    P.pack_id = -1;
+    P.long_kind = 0;
 }
 
 // Cluster kind: CTA items are taken kClusterCtas at a time, item g kClusterCtas + r by CTA
@@ -806,7 +818,11 @@ int phmm_create(const phmm_config* cfg, phmm_ctx** out) {
         const int n = cfg->cols_per_lane;
         const bool okp = n == 12 || n == 16;  // packed widths
         const bool oks = n == 16 || n == 24 || n == 32;  // scalar widths
-        if (n != 0 && !(cfg->kernel_variant >= 2 ? oks : (okp || oks))) return PHMM_EINVAL;
+        if (cfg->precision == PHMM_PREC_FP64) {
+            if (n != 0 && n != kF64N[0] && n != kF64N[1]) return PHMM_EINVAL;  // the FP64 variants
+        } else if (n != 0 && !(cfg->kernel_variant >= 2 ? oks : (okp || oks))) {
+            return PHMM_EINVAL;
+        }
     }
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || cfg->device < 0 || cfg->device >= ndev)
@@ -868,7 +884,11 @@ int phmm_create(const phmm_config* cfg, phmm_ctx** out) {
         build_pow_table<double>(kN64, v);
         if (ensure(ctx->pow64, v.size() * sizeof(v[0])) != cudaSuccess) return fail(PHMM_ECUDA);
         cudaMemcpy(ctx->pow64.p, v.data(), v.size() * sizeof(v[0]), cudaMemcpyHostToDevice);
-        ctx->occ64 = occupancy_forward64();
+        build_pow_table<double>(kF64N[1], v);
+        if (ensure(ctx->pow64w, v.size() * sizeof(v[0])) != cudaSuccess) return fail(PHMM_ECUDA);
+        cudaMemcpy(ctx->pow64w.p, v.data(), v.size() * sizeof(v[0]), cudaMemcpyHostToDevice);
+        for (int q = 0; q < kNumF64; ++q) ctx->occ64v[q] = occupancy_forward64(q);
+        ctx->occ64 = ctx->occ64v[0];
     }
     ctx->slots.resize(ctx->cfg.max_inflight);
     for (auto& S : ctx->slots) {
@@ -925,6 +945,7 @@ void phmm_destroy(phmm_ctx* ctx) {
     release(ctx->scan_row);
     for (auto& b : ctx->pow32) release(b);
     release(ctx->pow64);
+    release(ctx->pow64w);
     if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
     if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
@@ -1006,13 +1027,30 @@ int phmm_submit_batch(phmm_ctx* ctx, const phmm_batch* b, uint64_t* ticket) {
     hsh ^= np;
     Plan& P = S->plan;
     int N = kN64;
-    bool tune_short = false, tune_long = false;
+    bool tune_short = false, tune_long = false, tune64 = false;
     uint64_t tune_sig = 0;
     std::vector<std::pair<int, int>> tune_cand;
     const bool reuse = S->plan_valid && S->plan_hash == hsh && S->plan_np == np;
     if (!reuse) {
         if (ctx->cfg.precision == PHMM_PREC_FP64) {
-            make_plan(L.data(), K.data(), pr, np, kN64, 0, kN64, P, 8);
+            // FP64 variant: cached choice for this batch shape, else the cost model's (the
+            // smaller plan cost), measured below for large batches
+            const uint64_t sig = batch_signature(L.data(), K.data(), pr, np, ctx->cfg);
+            auto hit = ctx->tuned.find(sig);
+            const int forced = ctx->cfg.cols_per_lane == kF64N[0] ? 0 : ctx->cfg.cols_per_lane == kF64N[1] ? 1 : -1;
+            if (forced >= 0) {
+                make_plan64(L.data(), K.data(), pr, np, forced, P);
+            } else if (hit != ctx->tuned.end()) {
+                make_plan64(L.data(), K.data(), pr, np, hit->second[0], P);
+            } else {
+                Plan c1;
+                make_plan64(L.data(), K.data(), pr, np, 0, P);
+                make_plan64(L.data(), K.data(), pr, np, 1, c1);
+                if (c1.cost < P.cost) P = std::move(c1);
+                tune64 = !(ctx->cfg.flags & PHMM_F_NO_TUNE) && !(ctx->cfg.flags & PHMM_F_LAUNCH_PER_PAIR) &&
+                         cells >= kTuneMinCells;
+                tune_sig = sig;
+            }
         } else {
             const std::vector<std::pair<int, int>> cand = fp32_candidates(ctx->cfg);
             const uint64_t sig = batch_signature(L.data(), K.data(), pr, np, ctx->cfg);
@@ -1162,6 +1200,51 @@ int phmm_submit_batch(phmm_ctx* ctx, const phmm_batch* b, uint64_t* ticket) {
     CK(cudaEventRecord(S->ev_user, ctx->stream));
     CK(cudaStreamWaitEvent(S->sm, S->ev_user, 0));
     CK(cudaStreamWaitEvent(S->sm, S->ev_copy, 0));
+    if (tune64) {
+        // Measured choice of the FP64 variant: the forward pass of each, twice (the first
+        // launch after a plan change runs cold), the faster kept for this batch shape.
+        float best_ms = 1e30f;
+        int best = P.scal_id;
+        for (int id = 0; id < kNumF64; ++id) {
+            Plan c;
+            make_plan64(L.data(), K.data(), pr, np, id, c);
+            if (c.n_too_long) continue;
+            CK(upload_plan(*S, c, cs));
+            CK(ensure(S->parts, (np + c.n_extra) * sizeof(Partial)));
+            CK(ensure(S->bnd, c.bnd_words * 8ull));
+            hh.parts = (Partial*)S->parts.p;
+            plan_header(*S, c, hh);
+            CK(cudaMemcpyAsync(S->hdr.p, &hh, sizeof(hh), cudaMemcpyHostToDevice, cs));
+            CK(cudaStreamSynchronize(cs));
+            float ms = 1e30f;
+            for (int rep = 0; rep < 2; ++rep) {
+                const int rc = launch_sequence(ctx, *S, id, -1, 0, false);
+                if (rc != PHMM_OK) return rc;
+                CK(cudaStreamSynchronize(S->sm));
+                float m1 = 0.f;
+                CK(cudaEventElapsedTime(&m1, S->ev_fwd0, S->ev_fwd1));
+                ms = std::min(ms, m1);
+                if (m1 > 100.f) break;
+            }
+            if (getenv("PHMM_DEBUG"))
+                fprintf(stderr, "phmm tuner: fp64 variant %d (N %d, %d-warp CTAs): forward %.3f ms\n", id, kF64N[id],
+                        kF64CW[id], ms);
+            if (ms < best_ms) {
+                best_ms = ms;
+                best = id;
+            }
+        }
+        ctx->tuned[tune_sig] = {best, -1, 0};
+        make_plan64(L.data(), K.data(), pr, np, best, P);
+        CK(upload_plan(*S, P, cs));
+        CK(ensure(S->parts, (np + P.n_extra) * sizeof(Partial)));
+        CK(ensure(S->bnd, P.bnd_words * 8ull));
+        hh.parts = (Partial*)S->parts.p;
+        plan_header(*S, P, hh);
+        CK(cudaMemcpyAsync(S->hdr.p, &hh, sizeof(hh), cudaMemcpyHostToDevice, cs));
+        CK(cudaMemsetAsync(S->parts.p, 0, (np + P.n_extra) * sizeof(Partial), cs));
+        CK(cudaStreamSynchronize(cs));
+    }
     if (tune_short || tune_long) {
         // Measured tuning: run the FP32 pipeline once per candidate on this batch (events
         // around the forward kernels), keep the fastest for this shape: first the short-
@@ -1323,7 +1406,8 @@ int phmm_submit_batch(phmm_ctx* ctx, const phmm_batch* b, uint64_t* ticket) {
     S->st.kernel_launches = launches;
     {
         const bool f32 = ctx->cfg.precision != PHMM_PREC_FP64;
-        S->st.short_kernel = f32 && !P.witems.empty() ? P.scal_id : -1;
+        // FP64: the forward variant (0: N 8 in 16-warp CTAs, 1: N 16 in 8-warp CTAs)
+        S->st.short_kernel = f32 ? (!P.witems.empty() ? P.scal_id : -1) : P.scal_id;
         S->st.packed_kernel = f32 && !P.witems2.empty() ? P.pack_id : -1;
         S->st.long_kernel = f32 && !P.citems.empty() ? P.long_kind : -1;
         for (int q = 0; q < 3; ++q) S->st.cells_branch[q] = f32 ? P.cells_br[q] : (q == 0 ? cells : 0);
@@ -1460,7 +1544,10 @@ int phmm_plan_check(const uint32_t* l, const uint32_t* k, const uint32_t* pair_r
     Plan P;
     int CW = kCtaWarps, Nl = kN64, kw = 8;
     if (precision == PHMM_PREC_FP64) {
-        make_plan(l, k, pair_read, n, kN64, 0, kN64, P, 8);
+        if (scal_id < 0 || scal_id >= kNumF64) return PHMM_EINVAL;  // the FP64 variant
+        make_plan64(l, k, pair_read, n, scal_id, P);
+        CW = kF64CW[scal_id];
+        Nl = kF64N[scal_id];
     } else {
         if (scal_id < 0 || scal_id >= kNumScalar || pack_id < -1 || pack_id >= kNumPacked || long_kind < 0 ||
             long_kind >= kNumLong)

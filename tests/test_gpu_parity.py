@@ -48,11 +48,16 @@ def test_plain_64_pairs_fp32(phmm):
     assert st["kernel_launches"] >= 4
 
 
-def test_plain_64_pairs_fp64(phmm):
-    b = W.plain_pairs(64, seed=0)
-    with phmm.Context(precision="fp64") as ctx:
+@pytest.mark.parametrize("N", [0, 8, 16])
+def test_plain_64_pairs_fp64(phmm, N):
+    """FP64 mode, both forward variants (8 columns per lane in 16-warp CTAs, 16 in 8-warp
+    CTAs) and the tuner's choice; pairs up to 1200 columns (teams and linked warps)."""
+    b = W.plain_pairs(64, seed=0, k_range=(200, 1200))
+    with phmm.Context(precision="fp64", cols_per_lane=N) as ctx:
         out, flags, rc, st = ctx.run(b)
     assert np.all(flags & phmm.PAIR_FP64)
+    if N:
+        assert st["short_kernel"] == (0 if N == 8 else 1)
     ref = oracle.batch(b)
     assert np.max(np.abs(out - ref)) <= TOL64
 
@@ -278,10 +283,11 @@ def test_cluster_kind_single_very_wide_pair(phmm):
     _check(out, flags, oracle.batch(b))
 
 
-def test_wide_pairs_fp64_strips(phmm):
-    """Concurrent strips in the batched FP64 engine (4096 columns per CTA)."""
+@pytest.mark.parametrize("N", [8, 16])
+def test_wide_pairs_fp64_strips(phmm, N):
+    """Concurrent strips in the batched FP64 engine (4096 columns per CTA), both variants."""
     b = _wide_batch(seed=31)
-    with phmm.Context(precision="fp64") as ctx:
+    with phmm.Context(precision="fp64", cols_per_lane=N) as ctx:
         out, flags, rc, st = ctx.run(b)
     assert np.max(np.abs(out - oracle.batch(b))) <= TOL64
 
