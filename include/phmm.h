@@ -300,7 +300,7 @@ typedef struct {
     uint32_t max_inflight_epochs;  /* concurrent epochs (0: 2); the context needs as many slots */
     uint32_t max_pending;          /* waiting requests before enqueue returns PHMM_EBUSY (0: no limit) */
     uint32_t max_wait_ms;          /* a large request waiting longer goes ahead of small ones (0: 2000) */
-    uint64_t epoch_cells;          /* cell budget of one epoch; larger requests are split (0: 1e11) */
+    uint64_t epoch_cells;          /* cell budget of one epoch; larger requests are split (0: 2e10) */
     uint64_t small_cells;          /* requests of at most this many cells are small (0: epoch_cells / 20) */
 } phmm_server_config;
 

@@ -127,7 +127,14 @@ typedef struct {
     uint32_t idx[W32];     /* pair indices */
     uint32_t l[W32], k[W32];
     uint64_t r0[W32], h0[W32];
+    uint64_t c0[W32];      /* the lane's read in the coefficient table (records) */
 } pack;
+
+/* Per-row coefficients of every read base the pass uses, computed once per read (a read
+ * is shared by all its pairs) and in parallel, as NC values per base: 1 - e, e / 3,
+ * T_MM, T_DM = 1 - g, T_MI, g, (1 - g) T_MD of the previous row (1 on a read's first row),
+ * and the read base's bit set.  FP32 tables hold the values stochastically rounded. */
+#define NC 8
 
 typedef struct {
     double S;
@@ -232,6 +239,7 @@ typedef struct {
     pthread_mutex_t mu;
     int nomem;
     pair_result *res; /* per pair */
+    const void *coef; /* coefficient table of the pass (float or double records) */
 } job;
 
 static void *worker(void *arg) {
@@ -250,8 +258,8 @@ static void *worker(void *arg) {
             pr[w].flags = 0;
             pr[w].nomem = 0;
         }
-        if (J->fp64) pack_forward64(J->b, pk, &s, pr);
-        else pack_forward32(J->b, pk, &s, pr);
+        if (J->fp64) pack_forward64(J->b, pk, (const double *)J->coef, &s, pr);
+        else pack_forward32(J->b, pk, (const float *)J->coef, &s, pr);
         for (int w = 0; w < pk->n; ++w) {
             J->res[pk->idx[w]] = pr[w];
             if (pr[w].nomem) {
@@ -295,7 +303,7 @@ static int key_cmp(const void *a, const void *b) {
 /* Packs of up to w pairs from the listed pairs: sorted by read-length class (ratio
  * 2^(1/4)), then haplotype length, so a pack's lanes have similar l and k. */
 static pack *make_packs(const phmm_batch *b, const uint32_t *list, uint32_t n, int w, uint32_t *n_packs,
-                        int fp64) {
+                        int fp64, const uint64_t *coff) {
     pair_key *key = (pair_key *)malloc(sizeof(pair_key) * (n ? n : 1));
     const uint32_t np = (n + (uint32_t)w - 1) / (uint32_t)w;
     pack *pk = (pack *)calloc(np ? np : 1, sizeof(pack));
@@ -323,6 +331,7 @@ static pack *make_packs(const phmm_batch *b, const uint32_t *list, uint32_t n, i
             P->k[x] = key[q].k;
             P->r0[x] = b->read_off[b->pair_read[p]];
             P->h0[x] = b->hap_off[b->pair_hap[p]];
+            P->c0[x] = coff[b->pair_read[p]];
             if (key[q].l > P->lmax) P->lmax = key[q].l;
             if (key[q].k > P->kmax) P->kmax = key[q].k;
         }
@@ -331,6 +340,104 @@ static pack *make_packs(const phmm_batch *b, const uint32_t *list, uint32_t n, i
     free(key);
     *n_packs = np;
     return pk;
+}
+
+/* The coefficient table: reads used by the listed pairs get consecutive records
+ * (coff[r] = first record of read r), filled by n_threads threads over the reads. */
+typedef struct {
+    const phmm_batch *b;
+    const uint32_t *reads; /* used reads */
+    uint32_t n_reads, next;
+    const uint64_t *coff;
+    void *tab;
+    int fp64;
+    pthread_mutex_t mu;
+} coef_job;
+
+static void coef_read(const phmm_batch *b, uint32_t r, uint64_t c0, void *tab, int fp64) {
+    const uint64_t r0 = b->read_off[r], l = b->read_off[r + 1] - r0;
+    for (uint64_t i = 0; i < l; ++i) {
+        const uint64_t bi = r0 + i;
+        const double e = q_tab[b->base_q[bi]], qi = q_tab[b->ins_q[bi]], qd = q_tab[b->del_q[bi]],
+                     g = q_tab[b->gcp_q[bi]];
+        const double qdp = i > 0 ? q_tab[b->del_q[bi - 1]] : 1.0;
+        const double c[NC - 1] = {1.0 - e, e / 3.0, 1.0 - qi - qd, 1.0 - g, qi, g, (1.0 - g) * qdp};
+        const int32_t bits = base_bits(b->read_bases[bi]);
+        if (fp64) {
+            double *d = (double *)tab + (c0 + i) * NC;
+            for (int q = 0; q < NC - 1; ++q) d[q] = c[q];
+            const int64_t b64 = bits;
+            memcpy(&d[NC - 1], &b64, 8);
+        } else {
+            /* two hashes of the read base give the eight 16-bit uniforms */
+            const uint64_t h0 = mix64(0x5eed1234ull << 32 ^ (bi * 2u)), h1 = mix64(0x5eed1234ull << 32 ^ (bi * 2u + 1u));
+            float *f = (float *)tab + (c0 + i) * NC;
+            for (int q = 0; q < NC - 1; ++q)
+                f[q] = sr_round(c[q], (uint32_t)(((q < 4 ? h0 : h1) >> (16 * (q & 3))) & 0xffffu));
+            memcpy(&f[NC - 1], &bits, 4);
+        }
+    }
+}
+
+static void *coef_worker(void *arg) {
+    coef_job *J = (coef_job *)arg;
+    for (;;) {
+        pthread_mutex_lock(&J->mu);
+        const uint32_t q0 = J->next;
+        J->next = q0 + 64 < J->n_reads ? q0 + 64 : J->n_reads;
+        pthread_mutex_unlock(&J->mu);
+        if (q0 >= J->n_reads) break;
+        const uint32_t q1 = q0 + 64 < J->n_reads ? q0 + 64 : J->n_reads;
+        for (uint32_t q = q0; q < q1; ++q) coef_read(J->b, J->reads[q], J->coff[J->reads[q]], J->tab, J->fp64);
+    }
+    return NULL;
+}
+
+/* Returns the table (caller frees) and fills coff (n_reads entries); NULL if out of memory. */
+static void *build_coef(const phmm_batch *b, const uint32_t *list, uint32_t n, int fp64, uint64_t *coff,
+                        int n_threads) {
+    uint8_t *used = (uint8_t *)calloc(b->n_reads ? b->n_reads : 1, 1);
+    uint32_t *reads = (uint32_t *)malloc(sizeof(uint32_t) * (b->n_reads ? b->n_reads : 1));
+    if (!used || !reads) {
+        free(used);
+        free(reads);
+        return NULL;
+    }
+    for (uint32_t q = 0; q < n; ++q) used[b->pair_read[list[q]]] = 1;
+    uint64_t total = 0;
+    uint32_t nr = 0;
+    for (uint32_t r = 0; r < b->n_reads; ++r)
+        if (used[r]) {
+            coff[r] = total;
+            total += b->read_off[r + 1] - b->read_off[r];
+            reads[nr++] = r;
+        }
+    free(used);
+    void *tab = malloc((size_t)(total ? total : 1) * NC * (fp64 ? sizeof(double) : sizeof(float)));
+    if (!tab) {
+        free(reads);
+        return NULL;
+    }
+    coef_job J;
+    J.b = b;
+    J.reads = reads;
+    J.n_reads = nr;
+    J.next = 0;
+    J.coff = coff;
+    J.tab = tab;
+    J.fp64 = fp64;
+    pthread_mutex_init(&J.mu, NULL);
+    pthread_t th[1024];
+    int started = 0;
+    for (int t = 1; t < n_threads && (uint32_t)t * 64 < nr; ++t) {
+        if (pthread_create(&th[started], NULL, coef_worker, &J) != 0) break;
+        ++started;
+    }
+    coef_worker(&J);
+    for (int t = 0; t < started; ++t) pthread_join(th[t], NULL);
+    pthread_mutex_destroy(&J.mu);
+    free(reads);
+    return tab;
 }
 
 /* Per-pair validity: lengths >= 1, bases ACGTN, qualities <= 93. */
@@ -370,9 +477,11 @@ int phmm_cpu_forward(const phmm_batch *b, int n_threads, int precision, double f
     const uint32_t n = b->n_pairs;
     uint32_t *list = (uint32_t *)malloc(sizeof(uint32_t) * (n ? n : 1));
     pair_result *res = (pair_result *)calloc(n ? n : 1, sizeof(pair_result));
-    if (!list || !res) {
+    uint64_t *coff = (uint64_t *)malloc(sizeof(uint64_t) * (b->n_reads ? b->n_reads : 1));
+    if (!list || !res || !coff) {
         free(list);
         free(res);
+        free(coff);
         return PHMM_ENOMEM;
     }
     uint32_t nv = 0;
@@ -388,8 +497,10 @@ int phmm_cpu_forward(const phmm_batch *b, int n_threads, int precision, double f
     for (int pass = 0; pass < 2 && rc == PHMM_OK && nv > 0; ++pass) {
         const int fp64 = fp64_all || pass == 1;
         uint32_t np = 0;
-        pack *pk = make_packs(b, list, nv, fp64 ? W64 : W32, &np, fp64);
+        void *coef = build_coef(b, list, nv, fp64, coff, n_threads);
+        pack *pk = coef ? make_packs(b, list, nv, fp64 ? W64 : W32, &np, fp64, coff) : NULL;
         if (!pk) {
+            free(coef);
             rc = PHMM_ENOMEM;
             break;
         }
@@ -400,8 +511,10 @@ int phmm_cpu_forward(const phmm_batch *b, int n_threads, int precision, double f
         J.n_packs = np;
         J.fp64 = fp64;
         J.res = res;
+        J.coef = coef;
         rc = run_packs(&J, n_threads);
         free(pk);
+        free(coef);
         if (rc != PHMM_OK) break;
         /* results; the FP32 pass collects the pairs its tests send to the FP64 pass */
         uint32_t nr = 0;
@@ -435,5 +548,6 @@ int phmm_cpu_forward(const phmm_batch *b, int n_threads, int precision, double f
     }
     free(list);
     free(res);
+    free(coff);
     return rc;
 }

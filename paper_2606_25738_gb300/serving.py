@@ -99,7 +99,7 @@ def run(ctx: "phmm.Context", pool: list, rate: float, duration: float, seed: int
     lat = np.array([done[rid][1] - recs[rid][1] for rid in ok]) * 1e3
     cells_done = float(sum(pool[recs[rid][0]][1] for rid in ok))
     lag = np.array([recs[rid][2] - recs[rid][1] for rid in recs]) * 1e3 if recs else np.zeros(1)
-    small_max = small_cells or (epoch_cells or 100_000_000_000) // 20
+    small_max = small_cells or (epoch_cells or 20_000_000_000) // 20
     by_class = {}
     for name, pick in (("small", lambda c: c <= small_max), ("large", lambda c: c > small_max)):
         ids = [rid for rid in ok if pick(pool[recs[rid][0]][1])]
