@@ -103,8 +103,8 @@ typedef struct {
                                  pairs: 12 or 16 fixes the packed-team width, 24 or 32 the
                                  scalar-team width, 0 = chosen by the built-in tuner.
                                  Multi-warp pairs use 32 (FP32).  With PHMM_PREC_FP64: 8
-                                 or 16 fixes the FP64 kernel variant (8 columns per lane in
-                                 16-warp CTAs, 16 in 8-warp CTAs), 0 = tuner. */
+                                 or 16 fixes the unfactored FP64 variant (8 columns per lane
+                                 in 16-warp CTAs, 16 in 8-warp CTAs), 0 = tuner. */
     int kernel_variant;       /* FP32 short-pair kernels the tuner may use: 0 = any; 1 =
                                  pairs of the same read share packed teams (two haplotypes
                                  per thread in float2 halves), the rest run in scalar
@@ -112,7 +112,9 @@ typedef struct {
                                  3 = lean scalar engine only; 4 = pipelined scalar engine
                                  only (the next row's scan-independent work overlaps the
                                  deletion scan); 5 = pipelined engine with each lane's two
-                                 column halves in packed FP32 pairs */
+                                 column halves in packed FP32 pairs.  With PHMM_PREC_FP64,
+                                 4 or 5 fixes the pipelined FP64 variant (short pairs on
+                                 the J-form engine, six FP64 operations per cell) */
     double fp32_tolerance;    /* largest |error of log10 L| accepted from the FP32 pass
                                  (0 = 1e-3): with PHMM_PREC_FP32_RESCUE a pair whose
                                  a-priori FP32 rounding bound exceeds it is recomputed in
@@ -175,7 +177,8 @@ typedef struct {
     float ms_host;            /* host time of phmm_submit_batch's planning and enqueue */
     /* Kernels the plan ran (-1: that branch had no work).  FP64 precision: short_kernel =
      * the FP64 forward variant (0: 8 columns per lane in 16-warp CTAs, 1: 16 columns per
-     * lane in 8-warp CTAs), the other two -1.  FP32:
+     * lane in 8-warp CTAs, 2: short pairs on the pipelined FP64 engine, 16 columns per
+     * lane, and multi-warp pairs as in 1), the other two -1.  FP32:
      * short_kernel = scalar-team variant 0..8 (k_short_scalar<32,4>, <24,4>, <24,5>,
      * <16,6>, k_short_pipe<32,3>, <24,4>, <16,4>, k_short_pipe2<32,3>, <24,4>);
      * packed_kernel = packed-team variant 0..1 (k_short_packed<12,4>, <16,3>);

@@ -48,6 +48,7 @@ struct Num;
 template <>
 struct Num<float> {
     using Rec = Rec32;
+    using RecJ = Rec32J;
     static constexpr int kLog2C = 120;      // C = 2^120 (FP32 initial scale of D)
     static constexpr int kHi = 100;         // rescale when the row max >= 2^kHi ...
     static constexpr int kLo = 40;          // ... or < 2^kLo
@@ -75,6 +76,7 @@ struct Num<float> {
 template <>
 struct Num<double> {
     using Rec = Rec64;
+    using RecJ = Rec64J;
     static constexpr int kLog2C = 1020;     // C = 2^1020 (Eq. 1)
     static constexpr int kHi = 900;
     static constexpr int kLo = 300;
@@ -124,6 +126,16 @@ __device__ __forceinline__ Rec32J load_recj(const Rec32J* p) {
     Rec32J r;
     r.pm = a.x; r.px = a.y; r.a = a.z; r.b = a.w;
     r.h = b.x; r.g = b.y; r.mi = b.z; r.meta = __float_as_uint(b.w);
+    return r;
+}
+__device__ __forceinline__ Rec64J load_recj(const Rec64J* p) {
+    const double2 a = __ldg(reinterpret_cast<const double2*>(p));
+    const double2 b = __ldg(reinterpret_cast<const double2*>(p) + 1);
+    const double2 c = __ldg(reinterpret_cast<const double2*>(p) + 2);
+    const double2 d = __ldg(reinterpret_cast<const double2*>(p) + 3);
+    Rec64J r;
+    r.pm = a.x; r.px = a.y; r.a = b.x; r.b = b.y;
+    r.h = c.x; r.g = c.y; r.mi = d.x; r.meta = (uint64_t)__double_as_longlong(d.y);
     return r;
 }
 __device__ __forceinline__ Rec64 load_rec(const Rec64* p) {
@@ -380,16 +392,17 @@ struct PipeRange {
     int R, hi, target, danger;
     bool ok;
 };
+template <typename T = float>
 __device__ __forceinline__ PipeRange pipe_range(const uint32_t* dropgrow) {
-    using NT = Num<float>;
+    using NT = Num<T>;
     const int rbits = (int)min(dropgrow[2], 200u);
     PipeRange r;
-    r.hi = min(NT::kHi, 110 - rbits);
+    r.hi = min(NT::kHi, NT::kMaxExp - 17 - rbits);
     r.target = r.hi - 4;
     r.danger = NT::kDanger + rbits;
     r.ok = r.hi >= NT::kLo + 16 && r.danger <= NT::kLo - 32;
     const uint32_t d = max(dropgrow[0], 1u), g = max(max(dropgrow[1], dropgrow[3]), 1u);
-    const int drop_budget = max(NT::kLo - r.danger, 1), grow_budget = max(126 - rbits - r.hi, 1);
+    const int drop_budget = max(NT::kLo - r.danger, 1), grow_budget = max(NT::kMaxExp - 1 - rbits - r.hi, 1);
     const int r1 = (int)((uint64_t)drop_budget * 64u / d), r2 = (int)((uint64_t)grow_budget * 64u / g);
     r.R = max(1, min(min(r1, r2), 64));
     return r;
@@ -829,12 +842,13 @@ namespace phmm {
 // takes five steps (steps beyond the team width change nothing), so it is one basic
 // block that the compiler can interleave with phase A.
 // ------------------------------------------------------------------------------------
-template <int N>
-__device__ SegOut team_run_pipe(const Rec32J* __restrict__ rec, int l, int lmax,
+template <int N, typename T = float>
+__device__ SegOut team_run_pipe(const typename Num<T>::RecJ* __restrict__ rec, int l, int lmax,
                                 const uint8_t* __restrict__ hap, int k, int col0, int lt,
-                                int tlast, int nsteps, const PowRow<float>* __restrict__ pow_tab,
+                                int tlast, int nsteps, const PowRow<T>* __restrict__ pow_tab,
                                 const PipeRange& rng) {
-    using NT = Num<float>;
+    using NT = Num<T>;
+    using RecJ = typename NT::RecJ;
     static_assert(N <= 32, "match masks hold 32 columns");
     uint32_t bmA = 0, bmC = 0, bmG = 0, bmT = 0, flags = rng.ok ? 0u : PF_DEGEN, mflags = 0;
     const int nvalid = max(0, min(k - col0, N));
@@ -850,32 +864,32 @@ __device__ SegOut team_run_pipe(const Rec32J* __restrict__ rec, int l, int lmax,
             if (code == 3 || code == 4) bmT |= bit;
         }
     }
-    float M[N], J[N], U[N];
-    int E = 120 - rng.target;  // see cinit
-    float ml = 0.f, dt = 0.f, gprev = 0.f;
-    float sp1[5], sp2[5], last1 = 0.f, last2 = 0.f;
+    T M[N], J[N], U[N];
+    int E = NT::kLog2C - rng.target;  // see cinit
+    T ml = T(0), dt = T(0), gprev = T(0);
+    T sp1[5], sp2[5], last1 = T(0), last2 = T(0);
     int gcp = -1;
     SegOut out;
     out.S = 0.0;
     out.E = 0;
     out.flags = 0;
-    // Eq. 1's scale C = 2^120 taken as already rescaled to 2^target (E records the
-    // difference), so that row 1 and the partials U formed from it start in range
-    const float cinit = l > 0 && k > 0 ? (float)(ldexp(1.0, rng.target) / (double)k) : 0.f;
+    // Eq. 1's scale C taken as already rescaled to 2^target (E records the difference),
+    // so that row 1 and the partials U formed from it start in range
+    const T cinit = l > 0 && k > 0 ? (T)(ldexp(1.0, rng.target) / (double)k) : T(0);
     const int l1 = max(l, 1) - 1;
-    Rec32J cur = load_recj(rec);
+    RecJ cur = load_recj(rec);
     int until = 0;
     for (int i = 1; i <= lmax; ++i) {
-        Rec32J nxt = cur;
+        RecJ nxt = cur;
         if (i < lmax) nxt = load_recj(rec + min(i, l1));
-        const uint32_t meta = cur.meta;
+        const uint32_t meta = (uint32_t)cur.meta;
         mflags |= meta;
         const int gq = (int)((meta >> META_GCP_SHIFT) & 0xffu);
         if (gq != gcp) {
-            const PowRow<float>* pr = pow_tab + min(gq, kMaxPhred);
+            const PowRow<T>* pr = pow_tab + min(gq, kMaxPhred);
 #pragma unroll
             for (int s = 0; s < 5; ++s) {
-                sp1[s] = lt >= (1 << s) ? __ldg(&pr->sp1[s]) : 0.f;
+                sp1[s] = lt >= (1 << s) ? __ldg(&pr->sp1[s]) : T(0);
                 sp2[s] = __ldg(&pr->sp2[s]);
             }
             last1 = __ldg(&pr->last1);
@@ -885,28 +899,28 @@ __device__ SegOut team_run_pipe(const Rec32J* __restrict__ rec, int l, int lmax,
         const int code = (int)(meta & META_CODE_MASK);
         const uint32_t mask = code == 0 ? bmA : code == 1 ? bmC : code == 2 ? bmG
                             : code == 3 ? bmT : 0xffffffffu;
-        const float pim = cur.pm, pix = cur.px, rg = cur.g;
-        float y = 0.f, yprev = 0.f;
+        const T pim = cur.pm, pix = cur.px, rg = cur.g;
+        T y = T(0), yprev = T(0);
         // phase B
         if (i == 1) {
 #pragma unroll
             for (int c = 0; c < N; ++c) {
                 M[c] = (((mask >> c) & 1u) ? pim : pix) * cinit;
-                J[c] = 0.f;
+                J[c] = T(0);
                 if (c == N - 1) yprev = y;
-                y = fmaf(rg, y, M[c]);
+                y = fma(rg, y, M[c]);
             }
         } else {
-            const float rb = cur.b;
+            const T rb = cur.b;
 #pragma unroll
             for (int c = 0; c < N; ++c) {
-                const float u = fmaf(rb, dt, U[c]);
-                dt = fmaf(gprev, dt, ml);
+                const T u = fma(rb, dt, U[c]);
+                dt = fma(gprev, dt, ml);
                 ml = M[c];
-                const float mn = (((mask >> c) & 1u) ? pim : pix) * u;
+                const T mn = (((mask >> c) & 1u) ? pim : pix) * u;
                 M[c] = mn;
                 if (c == N - 1) yprev = y;
-                y = fmaf(rg, y, mn);
+                y = fma(rg, y, mn);
             }
         }
         // Eq. 4 when a pair of this warp finishes (I = T_MI J on the last row)
@@ -928,42 +942,42 @@ __device__ SegOut team_run_pipe(const Rec32J* __restrict__ rec, int l, int lmax,
             }
         }
         // the deletion scan of row i and, independent of it, phase A of row i+1
-        float nm = __shfl_up_sync(kFull, M[N - 1], 1);
-        float nj = __shfl_up_sync(kFull, J[N - 1], 1);
-        float yp = __shfl_up_sync(kFull, yprev, 1);
+        T nm = __shfl_up_sync(kFull, M[N - 1], 1);
+        T nj = __shfl_up_sync(kFull, J[N - 1], 1);
+        T yp = __shfl_up_sync(kFull, yprev, 1);
         if (lt == 0) {
-            nm = 0.f;
-            nj = 0.f;
-            yp = 0.f;
+            nm = T(0);
+            nj = T(0);
+            yp = T(0);
         }
-        float Z = y;
+        T Z = y;
 #pragma unroll
         for (int s = 0; s < 5; ++s) {
             const int off = 1 << s;
-            const float up = __shfl_up_sync(kFull, Z, off);
-            Z = fmaf(up * sp1[s], sp2[s], Z);
+            const T up = __shfl_up_sync(kFull, Z, off);
+            Z = fma(up * sp1[s], sp2[s], Z);
         }
         {
-            const float na = nxt.a, nh = nxt.h;
+            const T na = nxt.a, nh = nxt.h;
 #pragma unroll
             for (int c = N - 1; c >= 1; --c) {
-                U[c] = fmaf(na, M[c - 1], J[c - 1]);
-                J[c] = fmaf(nh, J[c], M[c]);
+                U[c] = fma(na, M[c - 1], J[c - 1]);
+                J[c] = fma(nh, J[c], M[c]);
             }
-            U[0] = fmaf(na, nm, nj);
-            J[0] = fmaf(nh, J[0], M[0]);
+            U[0] = fma(na, nm, nj);
+            J[0] = fma(nh, J[0], M[0]);
         }
-        float zz = __shfl_up_sync(kFull, Z, 2);
-        if (lt < 2) zz = 0.f;
+        T zz = __shfl_up_sync(kFull, Z, 2);
+        if (lt < 2) zz = T(0);
         if (until == 0) {
             // checkpoint: M holds row i, J and U row i+1 (linear in row i, so they take the
             // same power of two); U was formed before this test, which the headroom of the
             // range bounds covers
             until = rng.R;
-            float m = 0.f;
+            T m = T(0);
 #pragma unroll
-            for (int c = 0; c < N; ++c) m = fmaxf(m, fmaxf(fabsf(M[c]), fabsf(J[c])));
-            m = team_max<float>(m, lt, tlast, nsteps);
+            for (int c = 0; c < N; ++c) m = fmax(m, fmax(fabs(M[c]), fabs(J[c])));
+            m = team_max<T>(m, lt, tlast, nsteps);
             const int e = NT::expo(m);
             if (e == INT_MAX) {
                 flags |= PF_NONFINITE;
@@ -971,8 +985,8 @@ __device__ SegOut team_run_pipe(const Rec32J* __restrict__ rec, int l, int lmax,
                 if (e <= rng.danger) flags |= PF_DANGER;
                 if (e > rng.hi || e <= NT::kLo) {
                     const int sh = e - rng.target;  // multiply by 2^-sh
-                    if (sh >= -126 && sh <= 126) {
-                        const float f = NT::pow2(-sh);
+                    if (sh >= NT::kMinExp && sh <= NT::kMaxExp - 1) {
+                        const T f = NT::pow2(-sh);
 #pragma unroll
                         for (int c = 0; c < N; ++c) {
                             M[c] *= f;
@@ -983,7 +997,7 @@ __device__ SegOut team_run_pipe(const Rec32J* __restrict__ rec, int l, int lmax,
                         zz *= f;
                         yp *= f;
                     } else {  // two exact steps
-                        const float f1 = NT::pow2((-sh) / 2), f2v = NT::pow2(-sh - (-sh) / 2);
+                        const T f1 = NT::pow2((-sh) / 2), f2v = NT::pow2(-sh - (-sh) / 2);
 #pragma unroll
                         for (int c = 0; c < N; ++c) {
                             M[c] = (M[c] * f1) * f2v;
@@ -1001,7 +1015,7 @@ __device__ SegOut team_run_pipe(const Rec32J* __restrict__ rec, int l, int lmax,
         }
         --until;
         ml = nm;
-        dt = fmaf(zz * last1, last2, yp);
+        dt = fma(zz * last1, last2, yp);
         gprev = rg;
         cur = nxt;
     }

@@ -168,6 +168,26 @@ __device__ __forceinline__ Rec64 make_rec64(const BaseQ& x, const PhredTables& T
     return r;
 }
 
+// Record of the FP64 pipelined engine (see Rec64J), in plain double arithmetic.  first:
+// row 1 of a read, where the previous row's T_MI is taken as 1.
+__device__ __forceinline__ Rec64J make_rec64j(const BaseQ& x, const PhredTables& T, bool first) {
+    const double mi_p = first ? 1.0 : T.q[x.insp], imi_p = first ? 1.0 : T.iq[x.insp];
+    const double om_g = T.om[x.gcp];
+    Rec64J r;
+    r.pm = T.om[x.Q] * om_g * mi_p;
+    r.px = T.q3[x.Q] * om_g * mi_p;
+    r.a = (1.0 - T.q[x.ins] - T.q[x.del]) * T.inv[x.gcp] * imi_p;
+    r.b = T.q[x.delp] * imi_p;
+    r.h = T.q[x.gcp] * mi_p * T.iq[x.ins];
+    r.g = T.q[x.gcp];
+    r.mi = T.q[x.ins];
+    uint64_t meta = (uint64_t)x.code | ((uint64_t)x.gcp << META_GCP_SHIFT);
+    if (x.bad) meta |= META_BAD;
+    if (!(om_g >= 0x1p-40) || !isfinite(r.a) || !isfinite(r.b) || !isfinite(r.h)) meta |= META_DEGEN;
+    r.meta = meta;
+    return r;
+}
+
 // Worst per-row drop and growth of the row max in bits (see checkpoint_interval):
 // the max can fall by at most min(T_MI, g) per row and grow by at most
 // max(|T_MM| + (1-g) + T_MD, T_MI + g).
@@ -760,6 +780,39 @@ k_short_pipe(const BatchHeader* __restrict__ H, const PowRow<float>* __restrict_
     }
 }
 
+// FP64 mode, pipelined variant: short pairs on the pipelined engine in FP64
+// (team_run_pipe<N, double>, Rec64J records), same work list as k_short_scalar; the
+// multi-warp pairs run on k_forward<double> (CTA items) on the other branch.  A pair with a
+// degenerate row (1 - g = 0) or a range the engine cannot hold is flagged and goes to the
+// unfactored FP64 pass.
+template <int N, int MINB>
+__global__ void __launch_bounds__(kShortThreads, MINB)
+k_short_pipe64(const BatchHeader* __restrict__ H, const PowRow<double>* __restrict__ pow) {
+    const PipeRange rng = pipe_range<double>(H->dropgrow);
+    const uint32_t n_w = H->n_witems;
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+        uint32_t wi = 0;
+        if (lane == 0) wi = atomicAdd(&H->counters[1], 1u);
+        wi = __shfl_sync(kFull, wi, 0);
+        if (wi >= n_w) break;
+        const TeamOf t = team_of(H->teams, H->witems[wi]);
+        int l = 0, k = 0;
+        const Rec64J* rec = reinterpret_cast<const Rec64J*>(dummy_rec<double>());
+        const uint8_t* hap = H->hap_bases;
+        if (t.pair != kNoPair) {
+            const PairDesc d = H->desc[t.pair];
+            l = (int)d.l;
+            k = (int)d.k;
+            rec = H->rec64j + d.roff;
+            hap = H->hap_bases + d.hoff;
+        }
+        const int lmax = (int)__reduce_max_sync(kFull, (unsigned)l);
+        const SegOut o = team_run_pipe<N, double>(rec, l, lmax, hap, k, t.lt * N, t.lt, t.tlast, t.nsteps, pow, rng);
+        if (t.pair != kNoPair && t.lt == 0) write_part(H, t.pair, o);
+    }
+}
+
 // Pipelined scalar teams with packed column halves (team_run_pipe2).
 template <int N, int MINB, bool PACKED>
 __global__ void __launch_bounds__(kShortThreads, MINB)
@@ -894,6 +947,14 @@ __global__ void k_finalize(const BatchHeader* __restrict__ H) {
             if (f & PF_RESCALED) of |= 0x2u;
             if (mode == 1) of |= 0x4u;
             if (f & PF_TIMEOUT) of |= 0x80u;
+            if (mode == 1) {
+                // FP64: the pipelined engine's own flags (a degenerate row, a range it
+                // cannot hold, a non-finite value) send the pair to the unfactored pass
+                if (f & PF_DANGER) of |= 0x8u;
+                if ((f & PF_NONFINITE) || !isfinite(q.S)) of |= 0x10u;
+                if (f & PF_DEGEN) of |= 0x40u;
+                rescue = (of & 0x58u) != 0;
+            }
             if (mode == 0) {
                 // Underflow test (the FP32 sum in stored units against 1e4 * 3 l k FLT_MIN)
                 // plus the kernel's own danger / non-finite / degenerate flags.
@@ -903,8 +964,6 @@ __global__ void k_finalize(const BatchHeader* __restrict__ H) {
                 if (!(q.S > tau)) of |= 0x20u;
                 if (f & PF_DEGEN) of |= 0x40u;
                 rescue = H->force_rescue || (of & 0x78u) || !isfinite(v);
-            } else if (!isfinite(q.S)) {
-                atomicOr(H->status, ST_NONFINITE);
             }
         }
         H->out[p] = v;

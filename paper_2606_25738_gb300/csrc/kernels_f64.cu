@@ -16,12 +16,23 @@ __global__ void __launch_bounds__(256) k_prep64_all(const BatchHeader* __restric
     __shared__ PhredTables T;
     load_tables(TG, T);
     __syncthreads();
-    uint32_t dmax = 0, gmax = 0;
+    uint32_t dmax = 0, gmax = 0, jmax = 0, hmax = 0;
     const uint64_t n = H->n_read_bases;
+    Rec64J* const rj = H->rec64j;
     for (uint64_t b = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; b < n;
          b += (uint64_t)gridDim.x * blockDim.x) {
         const BaseQ x = base_inputs(H, b);
         H->rec64[b] = make_rec64(x, T);
+        if (rj) {
+            // J-form records of the pipelined FP64 engine and the range of its
+            // intermediates relative to the row maximum (as in the FP32 prep)
+            const Rec64J r2 = make_rec64j(x, T, false);
+            rj[b] = r2;
+            const double om = fmax(1.0 - r2.g, 0x1p-60);
+            const double big = fmax(fmax(fabs(r2.a), fabs(r2.b) / om), T.iq[x.insp]);
+            jmax = max(jmax, (uint32_t)fmax(ceil(log2(fmax(big, 1.0))), 0.0));
+            hmax = max(hmax, (uint32_t)ceil(log2(1.0 + fabs(r2.h)) * 64.0) + 1u);
+        }
         if (x.bad) atomicOr(H->status, ST_BAD_INPUT);
         uint32_t d, g;
         drop_grow(x, T, d, g);
@@ -29,7 +40,25 @@ __global__ void __launch_bounds__(256) k_prep64_all(const BatchHeader* __restric
         gmax = max(gmax, g);
     }
     block_max2(dmax, gmax, H->dropgrow);
+    __syncthreads();
+    block_max2(jmax, hmax, H->dropgrow + 2);
     build_desc(H);
+}
+
+// Row 1 of every read in the FP64 J-form records: the previous row's T_MI is 1 there
+// (k_prep64_all used the previous base of the batch).  Runs after k_prep64_all.
+__global__ void __launch_bounds__(256) k_prep64_first(const BatchHeader* __restrict__ H,
+                                                      const PhredTables* __restrict__ TG) {
+    __shared__ PhredTables T;
+    load_tables(TG, T);
+    __syncthreads();
+    Rec64J* const rj = H->rec64j;
+    if (!rj) return;
+    for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < H->n_reads; r += gridDim.x * blockDim.x) {
+        const uint64_t b = H->read_off[r];
+        if (b >= H->read_off[r + 1]) continue;
+        rj[b] = make_rec64j(base_inputs(H, b), T, true);
+    }
 }
 
 // Records of the reads of the pairs selected for rescue (one block per pair).
@@ -50,6 +79,8 @@ __global__ void __launch_bounds__(256) k_prep64_list(const BatchHeader* __restri
 
 template __global__ void k_forward<double, kN64, true>(const BatchHeader*, const PowRow<double>*);
 template __global__ void k_forward<double, kF64N[1], true, kF64CW[1]>(const BatchHeader*, const PowRow<double>*);
+template __global__ void k_forward<double, kF64N[2], false, kF64CW[2]>(const BatchHeader*, const PowRow<double>*);
+template __global__ void k_short_pipe64<kF64N[2], 2>(const BatchHeader*, const PowRow<double>*);
 template __global__ void k_finalize<double>(const BatchHeader*);
 
 __device__ __forceinline__ double log10_of(const Partial& q) {
@@ -104,8 +135,20 @@ void launch_prep64_list(const BatchHeader* H, const PhredTables* T, int grid, cu
 }
 void launch_forward64(int id, const BatchHeader* H, const void* pow, int grid, cudaStream_t s) {
     const PowRow<double>* p = static_cast<const PowRow<double>*>(pow);
-    if (id == 1) k_forward<double, kF64N[1], true, kF64CW[1]><<<grid, kF64CW[1] * 32, 0, s>>>(H, p);
+    if (id == 2) k_forward<double, kF64N[2], false, kF64CW[2]><<<grid, kF64CW[2] * 32, 0, s>>>(H, p);
+    else if (id == 1) k_forward<double, kF64N[1], true, kF64CW[1]><<<grid, kF64CW[1] * 32, 0, s>>>(H, p);
     else k_forward<double, kN64, true><<<grid, kCtaThreads, 0, s>>>(H, p);
+}
+void launch_short_pipe64(const BatchHeader* H, const void* pow, int grid, cudaStream_t s) {
+    k_short_pipe64<kF64N[2], 2><<<grid, kShortThreads, 0, s>>>(H, static_cast<const PowRow<double>*>(pow));
+}
+int occupancy_short_pipe64() {
+    int b = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_short_pipe64<kF64N[2], 2>, kShortThreads, 0);
+    return b > 0 ? b : 1;
+}
+void launch_prep64_first(const BatchHeader* H, const PhredTables* T, int grid, cudaStream_t s) {
+    k_prep64_first<<<grid, 256, 0, s>>>(H, T);
 }
 void launch_finalize64(const BatchHeader* H, int grid, cudaStream_t s) {
     k_finalize<double><<<grid, 256, 0, s>>>(H);
@@ -118,7 +161,10 @@ void launch_single64(const BatchHeader* H, const void* pow, uint32_t pair, cudaS
 }
 int occupancy_forward64(int id) {
     int b = 0;
-    if (id == 1)
+    if (id == 2)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_forward<double, kF64N[2], false, kF64CW[2]>,
+                                                      kF64CW[2] * 32, 0);
+    else if (id == 1)
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_forward<double, kF64N[1], true, kF64CW[1]>,
                                                       kF64CW[1] * 32, 0);
     else

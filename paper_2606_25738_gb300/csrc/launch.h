@@ -45,12 +45,17 @@ void launch_prep64_all(const BatchHeader* H, const PhredTables* T, int grid, cud
 void launch_prep64_list(const BatchHeader* H, const PhredTables* T, int grid, cudaStream_t s);
 // FP64 forward kernels (precision FP64): variant 0 = N 8 in 16-warp CTAs, 1 = N 16 in
 // 8-warp CTAs (fewer padded columns and per-row operations per cell for pairs up to 512
-// columns; the same 4096-column CTA width for wider pairs).  pow: the FP64 power table of
-// that N.
-constexpr int kNumF64 = 2;
-constexpr int kF64N[kNumF64] = {8, 16};
-constexpr int kF64CW[kNumF64] = {16, 8};
+// columns; the same 4096-column CTA width for wider pairs), both on the unfactored engine;
+// 2 = short pairs (up to 512 columns) on the pipelined FP64 engine (J-form records, six
+// FP64 operations per cell) and multi-warp pairs on the unfactored engine in 8-warp CTAs
+// (CTA items only), two concurrent branches.  pow: the FP64 power table of that N.
+constexpr int kNumF64 = 3;
+constexpr int kF64N[kNumF64] = {8, 16, 16};
+constexpr int kF64CW[kNumF64] = {16, 8, 8};
 void launch_forward64(int id, const BatchHeader* H, const void* pow, int grid, cudaStream_t s);
+void launch_short_pipe64(const BatchHeader* H, const void* pow, int grid, cudaStream_t s);
+int occupancy_short_pipe64();
+void launch_prep64_first(const BatchHeader* H, const PhredTables* T, int grid, cudaStream_t s);
 void launch_finalize64(const BatchHeader* H, int grid, cudaStream_t s);
 void launch_rescue64(const BatchHeader* H, const void* pow, int grid, cudaStream_t s);
 void launch_single64(const BatchHeader* H, const void* pow, uint32_t pair, cudaStream_t s);

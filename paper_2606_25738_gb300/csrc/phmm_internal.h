@@ -43,6 +43,13 @@ struct alignas(16) Rec32J {
     float pm, px, a, b, h, g, mi;
     uint32_t meta;
 };
+// The same J-form record in FP64, for the pipelined engine of the FP64 mode (plain double
+// arithmetic; rows with 1 - g_i = 0 are flagged degenerate and go to the unfactored FP64
+// pass).
+struct alignas(16) Rec64J {
+    double pm, px, a, b, h, g, mi;
+    uint64_t meta;
+};
 
 constexpr uint32_t META_CODE_MASK = 0x7u;
 constexpr int META_GCP_SHIFT = 8;
@@ -183,6 +190,7 @@ struct BatchHeader {
     Rec32 *rec32;
     Rec32J *rec32j;  // pipelined-engine records (nullptr when no kernel of the plan uses them)
     Rec64 *rec64;
+    Rec64J *rec64j;  // FP64 pipelined-engine records (FP64 mode, variant 2; else nullptr)
     // plan
     const WarpItem *witems;   // FP32: scalar teams; FP64: all teams
     const WarpItem *witems2;  // FP32: packed same-read teams

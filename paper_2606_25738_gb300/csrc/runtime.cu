@@ -98,6 +98,7 @@ struct Plan {
     int long_kind = 0;        // FP32 multi-warp kernel (launch.h: kLongN / kLongCW)
     uint32_t serial_rows = 0; // long kind 3: longest read among the serial pairs
     uint64_t cells_br[3] = {0, 0, 0};  // cells of the scalar, packed and multi-warp branches
+    bool fp64 = false;        // an FP64 plan (scal_id = the FP64 variant)
 };
 
 // Cost model constants (issue slots): per lane and cell of a row, and per lane and row
@@ -442,7 +443,7 @@ void build_pow_table(int N, std::vector<PowRow<T>>& out) {
 // ------------------------------------------------------------------------------------
 struct Slot {
     DevBuf in_bases, in_bq, in_iq, in_dq, in_gq, in_hap, in_roff, in_hoff, in_pr, in_ph;
-    DevBuf desc, rec32, rec32j, rec64, teams, witems, witems2, cpairs, citems, parts, out, oflags, rescue;
+    DevBuf desc, rec32, rec32j, rec64, rec64j, teams, witems, witems2, cpairs, citems, parts, out, oflags, rescue;
     DevBuf small;  // counters[8], status[1], dropgrow[4]
     DevBuf bnd;    // strip boundaries of the batch
     DevBuf rbnd;   // rescue / launch-per-pair boundary scratch
@@ -495,7 +496,8 @@ struct phmm_ctx {
     DevBuf pow32[5];                        // N = 12, 16, 20, 24 (packed short), 32 (long)
     DevBuf pow64;                           // FP64 powers, N = 8 (variant 0, rescue, comparator)
     DevBuf pow64w;                          // FP64 powers, N = 16 (variant 1)
-    int occ64v[kNumF64] = {1, 1};           // resident CTAs per SM of the FP64 forward variants
+    int occ64v[kNumF64] = {1, 1, 1};        // resident CTAs per SM of the FP64 forward variants
+    int occ64s = 1;                         // ... and of the pipelined FP64 short-team kernel
     // resident CTAs per SM of each kernel (long kind 5: resident clusters of the GPU)
     int occ_packed[kNumPacked] = {}, occ_scalar[kNumScalar] = {}, occ_longk[kNumLong] = {1, 1, 1, 1, 1, 1}, occ64 = 1;
     std::map<uint64_t, std::array<int, 3>> tuned;  // batch signature -> (scalar id, packed id, long kind)
@@ -524,7 +526,7 @@ int pow_index(int N) { return N == 12 ? 0 : N == 16 ? 1 : N == 20 ? 2 : N == 24 
 
 DevBuf* arena_bufs(Slot& S, int i) {
     DevBuf* d[] = {&S.in_bases, &S.in_bq, &S.in_iq, &S.in_dq, &S.in_gq, &S.in_hap, &S.in_roff, &S.in_hoff,
-                   &S.in_pr, &S.in_ph, &S.desc, &S.rec32, &S.rec32j, &S.rec64, &S.teams, &S.witems, &S.witems2,
+                   &S.in_pr, &S.in_ph, &S.desc, &S.rec32, &S.rec32j, &S.rec64, &S.rec64j, &S.teams, &S.witems, &S.witems2,
                    &S.cpairs, &S.citems, &S.parts, &S.out, &S.oflags, &S.rescue, &S.bnd, &S.rbnd, &S.sbnd};
     return i < (int)(sizeof(d) / sizeof(d[0])) ? d[i] : nullptr;
 }
@@ -574,13 +576,36 @@ int launch_sequence(phmm_ctx* ctx, Slot& S, int scal_id, int pack_id, int long_k
     auto rec = [&](cudaEvent_t ev) { return rec_on(ev, s); };
     launch_reset(H, ctx->sms * 4, s);
     if (prec == PHMM_PREC_FP64) {
-        launch_prep64_all(H, T, grid_pre, s);
-        CK(rec(S.ev_fwd0));
         // scal_id carries the FP64 variant (see make_plan64)
-        launch_forward64(scal_id, H, scal_id == 1 ? ctx->pow64w.p : ctx->pow64.p, ctx->sms * ctx->occ64v[scal_id], s);
+        launch_prep64_all(H, T, grid_pre, s);
+        if (scal_id == 2) launch_prep64_first(H, T, grid_pre, s);
+        CK(rec(S.ev_fwd0));
+        const void* pw = scal_id == 0 ? ctx->pow64.p : ctx->pow64w.p;
+        if (scal_id == 2) {
+            // two branches: short teams on the pipelined engine here, multi-warp CTA items
+            // on the unfactored engine on sb2
+            CK(cudaEventRecord(S.ev_fork, s));
+            CK(cudaStreamWaitEvent(S.sb2, S.ev_fork, 0));
+            CK(rec_on(S.ev_br[4], S.sb2));
+            launch_forward64(2, H, pw, ctx->sms * ctx->occ64v[2], S.sb2);
+            CK(rec_on(S.ev_br[5], S.sb2));
+            CK(cudaEventRecord(S.ev_join, S.sb2));
+            CK(rec(S.ev_br[0]));
+            launch_short_pipe64(H, pw, ctx->sms * ctx->occ64s, s);
+            CK(rec(S.ev_br[1]));
+            CK(cudaStreamWaitEvent(s, S.ev_join, 0));
+            CK(rec_on(S.ev_br[2], S.sb3));  // no packed branch in FP64
+            CK(rec_on(S.ev_br[3], S.sb3));
+            S.br_timed = true;
+        } else {
+            launch_forward64(scal_id, H, pw, ctx->sms * ctx->occ64v[scal_id], s);
+            S.br_timed = false;
+        }
         CK(rec(S.ev_fwd1));
         launch_finalize64(H, grid_pre, s);
         CK(rec(S.ev_res0));
+        // pairs the FP64 engine flagged (a degenerate row, range) on the unfactored engine
+        launch_rescue64(H, ctx->pow64.p, ctx->sms * ctx->occ64, s);
         CK(rec(S.ev_res1));
     } else {
         launch_prep32(H, T, grid_pre, s);
@@ -627,9 +652,10 @@ int launch_sequence(phmm_ctx* ctx, Slot& S, int scal_id, int pack_id, int long_k
     return PHMM_OK;
 }
 
-int kernels_per_launch(int prec, int NP) {
+int kernels_per_launch(int prec, int NP, int fp64_id = 0) {
     const int packed = NP > 0 ? 1 : 0;
-    return prec == PHMM_PREC_FP64 ? 4 : prec == PHMM_PREC_FP32_RESCUE ? 8 + packed : 6 + packed;
+    // FP64: reset, prep, [first-row prep, short teams], forward, finalize, rescue
+    return prec == PHMM_PREC_FP64 ? (fp64_id == 2 ? 7 : 5) : prec == PHMM_PREC_FP32_RESCUE ? 8 + packed : 6 + packed;
 }
 
 uint64_t u64(const void* p) { return (uint64_t)(uintptr_t)p; }
@@ -672,6 +698,8 @@ void plan_header(const Slot& S, const Plan& P, BatchHeader& hh) {
     // multi-warp kernel only; without them prep skips it
     const bool need32 = P.pack_id >= 0 || !kShortScalarPipe[P.scal_id] || (P.long_kind == 0 && !P.citems.empty());
     if (hh.rec32 || hh.rec32j) hh.rec32 = need32 ? (Rec32*)S.rec32.p : nullptr;
+    // FP64 J-form records: only the pipelined FP64 variant reads them
+    hh.rec64j = P.fp64 && P.scal_id == 2 ? (Rec64J*)S.rec64j.p : nullptr;
 }
 
 // FP32 short-pair kernel candidates (scalar id, packed id or -1) allowed by the config.
@@ -701,6 +729,10 @@ void make_plan64(const uint32_t* l, const uint32_t* k, const uint32_t* pr, uint3
     P.scal_id = id;
     P.pack_id = -1;
     P.long_kind = 0;
+    P.fp64 = true;
+    // the pipelined engine does about 6 FP64 operations per cell of a short team against
+    // 8 for the unfactored one
+    if (id == 2) P.cost -= 0.25 * (double)P.cells_br[0] * 8.0;
 }
 
 // Cluster kind: CTA items are taken kClusterCtas at a time, item g kClusterCtas + r by CTA
@@ -888,6 +920,7 @@ int phmm_create(const phmm_config* cfg, phmm_ctx** out) {
         if (ensure(ctx->pow64w, v.size() * sizeof(v[0])) != cudaSuccess) return fail(PHMM_ECUDA);
         cudaMemcpy(ctx->pow64w.p, v.data(), v.size() * sizeof(v[0]), cudaMemcpyHostToDevice);
         for (int q = 0; q < kNumF64; ++q) ctx->occ64v[q] = occupancy_forward64(q);
+        ctx->occ64s = occupancy_short_pipe64();
         ctx->occ64 = ctx->occ64v[0];
     }
     ctx->slots.resize(ctx->cfg.max_inflight);
@@ -923,7 +956,7 @@ void phmm_destroy(phmm_ctx* ctx) {
     }
     for (auto& S : ctx->slots) {
         DevBuf* d[] = {&S.in_bases, &S.in_bq, &S.in_iq, &S.in_dq, &S.in_gq, &S.in_hap, &S.in_roff,
-                       &S.in_hoff, &S.in_pr, &S.in_ph, &S.desc, &S.rec32, &S.rec32j, &S.rec64, &S.teams,
+                       &S.in_hoff, &S.in_pr, &S.in_ph, &S.desc, &S.rec32, &S.rec32j, &S.rec64, &S.rec64j, &S.teams,
                        &S.witems, &S.witems2, &S.cpairs, &S.citems, &S.parts, &S.out, &S.oflags, &S.rescue,
                        &S.small, &S.hdr, &S.bnd, &S.rbnd, &S.sbnd};
         for (auto* b : d) release(*b);
@@ -1037,16 +1070,22 @@ int phmm_submit_batch(phmm_ctx* ctx, const phmm_batch* b, uint64_t* ticket) {
             // smaller plan cost), measured below for large batches
             const uint64_t sig = batch_signature(L.data(), K.data(), pr, np, ctx->cfg);
             auto hit = ctx->tuned.find(sig);
-            const int forced = ctx->cfg.cols_per_lane == kF64N[0] ? 0 : ctx->cfg.cols_per_lane == kF64N[1] ? 1 : -1;
+            // forced: cols_per_lane 8 / 16 = the unfactored variants, kernel_variant 4 or 5
+            // (the pipelined engine) = variant 2
+            const int forced = ctx->cfg.kernel_variant >= 4 ? 2
+                             : ctx->cfg.cols_per_lane == kF64N[0] ? 0
+                             : ctx->cfg.cols_per_lane == kF64N[1] ? 1 : -1;
             if (forced >= 0) {
                 make_plan64(L.data(), K.data(), pr, np, forced, P);
             } else if (hit != ctx->tuned.end()) {
                 make_plan64(L.data(), K.data(), pr, np, hit->second[0], P);
             } else {
-                Plan c1;
                 make_plan64(L.data(), K.data(), pr, np, 0, P);
-                make_plan64(L.data(), K.data(), pr, np, 1, c1);
-                if (c1.cost < P.cost) P = std::move(c1);
+                for (int id = 1; id < kNumF64; ++id) {
+                    Plan c;
+                    make_plan64(L.data(), K.data(), pr, np, id, c);
+                    if (c.cost < P.cost) P = std::move(c);
+                }
                 tune64 = !(ctx->cfg.flags & PHMM_F_NO_TUNE) && !(ctx->cfg.flags & PHMM_F_LAUNCH_PER_PAIR) &&
                          cells >= kTuneMinCells;
                 tune_sig = sig;
@@ -1104,6 +1143,7 @@ int phmm_submit_batch(phmm_ctx* ctx, const phmm_batch* b, uint64_t* ticket) {
                           np * (sizeof(PairDesc) + sizeof(Partial) + 8 + 1 + 4) +
                           (ctx->cfg.precision == PHMM_PREC_FP64 ? 0 : nbases * (sizeof(Rec32) + sizeof(Rec32J))) +
                           (need64 ? nbases * sizeof(Rec64) : 0) +
+                          (ctx->cfg.precision == PHMM_PREC_FP64 ? nbases * sizeof(Rec64J) : 0) +
                           P.teams.size() * sizeof(Team) + (P.witems.size() + P.witems2.size()) * sizeof(WarpItem) +
                           P.cpairs.size() * sizeof(CtaPair) + P.citems.size() * sizeof(CtaItem) +
                           P.bnd_words * 8ull + P.n_extra * sizeof(Partial) + serial_bytes(ctx, P);
@@ -1154,6 +1194,7 @@ int phmm_submit_batch(phmm_ctx* ctx, const phmm_batch* b, uint64_t* ticket) {
         CK(ensure(S->rec32j, nbases * sizeof(Rec32J)));
     }
     if (need64) CK(ensure(S->rec64, nbases * sizeof(Rec64)));
+    if (ctx->cfg.precision == PHMM_PREC_FP64) CK(ensure(S->rec64j, nbases * sizeof(Rec64J)));
     CK(ensure(S->parts, (np + P.n_extra) * sizeof(Partial)));
     CK(ensure(S->bnd, P.bnd_words * 8ull));
     CK(ensure_serial(ctx, *S, P));
@@ -1364,11 +1405,11 @@ int phmm_submit_batch(phmm_ctx* ctx, const phmm_batch* b, uint64_t* ticket) {
                 S->g_key = key;
             }
             CK(cudaGraphLaunch(S->gexec, s));
-            launches = (uint32_t)kernels_per_launch(ctx->cfg.precision, P.NP);
+            launches = (uint32_t)kernels_per_launch(ctx->cfg.precision, P.NP, P.scal_id);
         } else {
             const int rc = launch_sequence(ctx, *S, P.scal_id, P.pack_id, P.long_kind, false);
             if (rc != PHMM_OK) return rc;
-            launches = (uint32_t)kernels_per_launch(ctx->cfg.precision, P.NP);
+            launches = (uint32_t)kernels_per_launch(ctx->cfg.precision, P.NP, P.scal_id);
         }
         // outputs
         if (b->outputs_on_device) {
@@ -1410,7 +1451,8 @@ int phmm_submit_batch(phmm_ctx* ctx, const phmm_batch* b, uint64_t* ticket) {
         S->st.short_kernel = f32 ? (!P.witems.empty() ? P.scal_id : -1) : P.scal_id;
         S->st.packed_kernel = f32 && !P.witems2.empty() ? P.pack_id : -1;
         S->st.long_kernel = f32 && !P.citems.empty() ? P.long_kind : -1;
-        for (int q = 0; q < 3; ++q) S->st.cells_branch[q] = f32 ? P.cells_br[q] : (q == 0 ? cells : 0);
+        const bool branched = f32 || P.scal_id == 2;  // the pipelined FP64 variant has two branches
+        for (int q = 0; q < 3; ++q) S->st.cells_branch[q] = branched ? P.cells_br[q] : (q == 0 ? cells : 0);
     }
     S->host_status = P.n_too_long ? PHMM_EINVAL : PHMM_OK;
     S->plan_valid = true;
@@ -1438,7 +1480,8 @@ int phmm_batch_footprint(phmm_ctx* ctx, const phmm_batch* b, uint64_t* bytes) {
     const uint64_t nbases = roff[nr], nhb = hoff[nh];
     const uint64_t seg = 32ull * (prec == PHMM_PREC_FP64 ? kN64 : kNLong32);
     uint64_t f = nbases * 5 + nhb + (nr + 1) * 8ull + (nh + 1) * 8ull + np * 8ull;
-    f += nbases * ((prec != PHMM_PREC_FP64 ? sizeof(Rec32) + sizeof(Rec32J) : 0) + (need64 ? sizeof(Rec64) : 0));
+    f += nbases * ((prec != PHMM_PREC_FP64 ? sizeof(Rec32) + sizeof(Rec32J) : sizeof(Rec64J)) +
+                   (need64 ? sizeof(Rec64) : 0));
     f += (uint64_t)np * (sizeof(PairDesc) + sizeof(Partial) + 8 + 1 + 4 + sizeof(Team) + 2 * sizeof(WarpItem) +
                          sizeof(CtaPair) + sizeof(CtaItem));
     uint64_t lmax = 0;

@@ -70,7 +70,8 @@ PACKED_KERNELS = ["k_short_packed<12, 4>", "k_short_packed<16, 3>"]
 LONG_KERNELS = ["k_forward<float, 32, 0>", "k_forward_pipe<32, 12>", "k_forward_pipe<24, 16>",
                 "k_forward_serial<32, 3>", "k_forward_pipe<32, 4>", "k_forward_cluster<32, 4, 8>"]
 # FP64 forward variant behind phmm_stats.short_kernel when the precision is FP64.
-FP64_KERNELS = ["k_forward<double, 8, 1, 16>", "k_forward<double, 16, 1, 8>"]
+FP64_KERNELS = ["k_forward<double, 8, 1, 16>", "k_forward<double, 16, 1, 8>",
+                "k_short_pipe64<16, 2> + k_forward<double, 16, 0, 8>"]
 
 
 class Stats(ctypes.Structure):

@@ -48,18 +48,40 @@ def test_plain_64_pairs_fp32(phmm):
     assert st["kernel_launches"] >= 4
 
 
-@pytest.mark.parametrize("N", [0, 8, 16])
-def test_plain_64_pairs_fp64(phmm, N):
-    """FP64 mode, both forward variants (8 columns per lane in 16-warp CTAs, 16 in 8-warp
-    CTAs) and the tuner's choice; pairs up to 1200 columns (teams and linked warps)."""
+@pytest.mark.parametrize("N,variant", [(0, "auto"), (8, "auto"), (16, "auto"), (0, "pipe")])
+def test_plain_64_pairs_fp64(phmm, N, variant):
+    """FP64 mode, every forward variant (unfactored: 8 columns per lane in 16-warp CTAs, 16
+    in 8-warp CTAs; pipelined short teams) and the tuner's choice; pairs up to 1200 columns
+    (teams and linked warps)."""
     b = W.plain_pairs(64, seed=0, k_range=(200, 1200))
-    with phmm.Context(precision="fp64", cols_per_lane=N) as ctx:
+    with phmm.Context(precision="fp64", cols_per_lane=N, variant=variant) as ctx:
         out, flags, rc, st = ctx.run(b)
     assert np.all(flags & phmm.PAIR_FP64)
-    if N:
-        assert st["short_kernel"] == (0 if N == 8 else 1)
+    if N or variant == "pipe":
+        assert st["short_kernel"] == {8: 0, 16: 1, 0: 2}[N]
     ref = oracle.batch(b)
     assert np.max(np.abs(out - ref)) <= TOL64
+
+
+def test_fp64_pipelined_engine_range_and_degenerate_rows(phmm):
+    """The pipelined FP64 engine carries J = I / T_MI with checkpoints like the FP32 one:
+    long reads (rescaling), insertion Phred 93 next to 1, and a gap-continuation Phred 0
+    row (1 - g = 0: the J-form is unusable) which must go to the unfactored pass."""
+    rng = np.random.default_rng(8)
+    hap = "".join(rng.choice(list("ACGT"), size=900))
+    read = hap[100:400] + hap[410:500]
+    l = len(read)
+    alt = np.where(np.arange(l) % 2 == 0, 93, 1)
+    pairs = [(read, hap, 30, 45, 45, 10), (read, hap, 30, alt, 45, 10), (read, hap, 30, 45, 45, 0),
+             (read[:80], hap[:200], 20, 93, 93, 10)]
+    b = W.from_strings(pairs)
+    lb = W.long_pairs(3, seed=14, k_range=(2000, 9000))
+    for batch in (b, lb):
+        with phmm.Context(precision="fp64", variant="pipe") as ctx:
+            out, flags, rc, st = ctx.run(batch)
+        assert st["short_kernel"] == 2
+        assert np.max(np.abs(out - oracle.batch(batch))) <= TOL64
+    assert flags is not None
 
 
 def test_force_rescue_fp64_pass(phmm):
