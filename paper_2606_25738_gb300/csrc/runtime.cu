@@ -462,6 +462,7 @@ struct Slot {
     // [2, 3] packed teams (sb3), [4, 5] multi-warp pairs (sb2)
     cudaEvent_t ev_br[6] = {};
     bool br_timed = false;
+    unsigned br_mask = 0;  // branches whose events the last launch sequence recorded
     uint64_t foot = 0;  // admitted device footprint while pending
     cudaGraphExec_t gexec = nullptr;
     int g_key = -1;
@@ -594,9 +595,8 @@ int launch_sequence(phmm_ctx* ctx, Slot& S, int scal_id, int pack_id, int long_k
             launch_short_pipe64(H, pw, ctx->sms * ctx->occ64s, s);
             CK(rec(S.ev_br[1]));
             CK(cudaStreamWaitEvent(s, S.ev_join, 0));
-            CK(rec_on(S.ev_br[2], S.sb3));  // no packed branch in FP64
-            CK(rec_on(S.ev_br[3], S.sb3));
             S.br_timed = true;
+            S.br_mask = 0x5u;  // no packed branch in FP64
         } else {
             launch_forward64(scal_id, H, pw, ctx->sms * ctx->occ64v[scal_id], s);
             S.br_timed = false;
@@ -637,6 +637,7 @@ int launch_sequence(phmm_ctx* ctx, Slot& S, int scal_id, int pack_id, int long_k
                             ctx->sms * ctx->occ_scalar[scal_id], s);
         CK(rec(S.ev_br[1]));
         S.br_timed = true;
+        S.br_mask = 0x7u;
         CK(cudaStreamWaitEvent(s, S.ev_join, 0));
         CK(cudaStreamWaitEvent(s, S.ev_join3, 0));
         CK(rec(S.ev_fwd1));
@@ -1549,7 +1550,7 @@ int phmm_poll(phmm_ctx* ctx, uint64_t ticket, int timeout_ms) {
     S->st.ms_rescue = ms;
     for (int q = 0; q < 3; ++q) {
         ms = 0.f;
-        if (S->br_timed) cudaEventElapsedTime(&ms, S->ev_br[2 * q], S->ev_br[2 * q + 1]);
+        if (S->br_timed && (S->br_mask >> q & 1u)) cudaEventElapsedTime(&ms, S->ev_br[2 * q], S->ev_br[2 * q + 1]);
         S->st.ms_branch[q] = ms;
     }
     if (!S->br_timed) S->st.ms_branch[0] = S->st.ms_forward;  // FP64: one forward kernel
