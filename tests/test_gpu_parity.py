@@ -80,8 +80,10 @@ def test_fp64_pipelined_engine_range_and_degenerate_rows(phmm):
         with phmm.Context(precision="fp64", variant="pipe") as ctx:
             out, flags, rc, st = ctx.run(batch)
         assert st["short_kernel"] == 2
-        assert np.max(np.abs(out - oracle.batch(batch))) <= TOL64
-    assert flags is not None
+        ref = oracle.batch(batch)
+        _check(out, flags, ref, tol32=TOL64)
+        if batch is b:
+            assert ref[2] == -np.inf and out[2] == -np.inf
 
 
 def test_force_rescue_fp64_pass(phmm):
@@ -474,7 +476,7 @@ def test_stats_name_the_kernels_and_no_tune(phmm):
     with phmm.Context(precision="fp64") as ctx:
         out3, flags3, rc3, st3 = ctx.run(b)
     # FP64: short_kernel names the FP64 forward variant
-    assert st3["short_kernel"] in (0, 1) and st3["long_kernel"] == -1 and st3["packed_kernel"] == -1
+    assert st3["short_kernel"] in (0, 1, 2) and st3["long_kernel"] == -1 and st3["packed_kernel"] == -1
     _check(out3, flags3, ref)
 
 
