@@ -693,7 +693,7 @@ def main():
     ap.add_argument("--max-len", type=int, default=16384, help="sweep: longest length")
     ap.add_argument("--sweep-pairs", type=int, default=0,
                     help="sweep: pairs per length (0: about 2e10 cells per length)")
-    ap.add_argument("--variant", default="auto", choices=["auto", "packed", "scalar", "lean", "pipe", "pipe2"],
+    ap.add_argument("--variant", default="auto", choices=["auto", "packed", "scalar", "lean", "pipe", "pipe2", "pipe2lean"],
                     help="short-pair kernel family (default: the built-in tuner decides)")
     ap.add_argument("--cols", type=int, default=0, help="columns per lane (0: tuner)")
     ap.add_argument("--long-kind", default="auto",

@@ -112,9 +112,12 @@ typedef struct {
                                  3 = lean scalar engine only; 4 = pipelined scalar engine
                                  only (the next row's scan-independent work overlaps the
                                  deletion scan); 5 = pipelined engine with each lane's two
-                                 column halves in packed FP32 pairs.  With PHMM_PREC_FP64,
-                                 4 or 5 fixes the pipelined FP64 variant (short pairs on
-                                 the J-form engine, six FP64 operations per cell) */
+                                 column halves in packed FP32 pairs; 6 = its lean form
+                                 (the next row's partials formed inside the row, records
+                                 and carry powers read from L1: four CTAs per SM).  With
+                                 PHMM_PREC_FP64, 4, 5 or 6 fixes the pipelined FP64
+                                 variant (short pairs on the J-form engine, six FP64
+                                 operations per cell) */
     double fp32_tolerance;    /* largest |error of log10 L| accepted from the FP32 pass
                                  (0 = 1e-3): with PHMM_PREC_FP32_RESCUE a pair whose
                                  a-priori FP32 rounding bound exceeds it is recomputed in

@@ -1030,7 +1030,11 @@ __device__ SegOut team_run_pipe(const typename Num<T>::RecJ* __restrict__ rec, i
 // of phase B at once, each from its own carry: the first half's comes from the left lane
 // (as in team_run_pipe), the second half's is the first half's D-hat at its last column,
 // formed after the scan.  The lane's scan aggregate joins the two half chains with
-// g^(N/2).  Same results as team_run_pipe up to rounding order.
+// g^(N/2).  Phase A is not a separate pass here: row i's partials U and insertions J are
+// formed column by column inside phase B of row i, from row i - 1's M (the value the D-hat
+// chain reads anyway) and J, so no partials array is kept between rows (32 registers at
+// N = 32); the scan's latency is then left to the other warps.  Same results as
+// team_run_pipe up to rounding order.
 // ------------------------------------------------------------------------------------
 // Asynchronous 16-byte copy global -> shared through L2 only (cp.async.cg: the source was
 // written by this warp's previous strip with L2-only stores, so L1 may hold stale lines),
@@ -1061,19 +1065,22 @@ __device__ __forceinline__ float2 fmul2_sel(float2 a, float2 b) {
 // seg_link_pipe<N, true>: the finished left strip's boundary (float4 per row: M, J, D-hat,
 // E of its last column; `sin`) enters lane 0 and, as a carry g^(N t - 1), every lane's
 // D-hat; checkpoints keep E >= E_left; lane 31 stores this strip's boundary (`sout`).
-// The left boundary is staged in shared memory (`stg`: two blocks of 32 rows for this
-// warp), each block copied asynchronously (cp.async, one row per lane) while the warp
-// computes the 32 rows before it; every row then reads its float4 as one broadcast.
+// The left boundary and the records are staged in shared memory (`stg`, `rstg`: two
+// blocks of 32 rows each for this warp), each block copied asynchronously (cp.async, one
+// row per lane) while the warp computes the 32 rows before it; every row then reads its
+// boundary and record as broadcasts (no record is held in registers across a row).
 // The lane's carry power g^(N lt - 1) stays in registers (reloaded when gcp changes):
 // reading it from L1 every row measured 2% slower on the 1M-pair uneven batch.
-template <int N, bool PACKED, bool LINK = false>
+template <int N, bool PACKED, bool LINK = false, bool FUSE = LINK, bool L1P = false>
 __device__ SegOut team_run_pipe2(const Rec32J* __restrict__ rec, int l, int lmax,
                                  const uint8_t* __restrict__ hap, int k, int col0, int lt,
                                  int tlast, int nsteps, const PowRow<float>* __restrict__ pow_tab,
                                  const PipeRange& rng, const float4* sin = nullptr, float4* sout = nullptr,
-                                 bool has_left = false, bool has_right = false, float4* stg = nullptr) {
+                                 bool has_left = false, bool has_right = false, float4* stg = nullptr,
+                                 float4* rstg = nullptr) {
     using NT = Num<float>;
     static_assert(N <= 32 && N % 2 == 0, "match masks hold 32 columns; two halves");
+    static_assert(FUSE || !(LINK || L1P), "the serial strips and the L1 tables need the fused row");
     constexpr int H = N / 2;
     uint32_t bmA = 0, bmC = 0, bmG = 0, bmT = 0, flags = rng.ok ? 0u : PF_DEGEN, mflags = 0;
     const int nvalid = max(0, min(k - col0, N));
@@ -1091,35 +1098,76 @@ __device__ SegOut team_run_pipe2(const Rec32J* __restrict__ rec, int l, int lmax
             if (code == 3 || code == 4) bmT |= bit;
         }
     }
-    float2 M2[H], J2[H], U2[H];  // .x: column q, .y: column H + q of the lane
+    float2 M2[H], J2[H];  // .x: column q, .y: column H + q of the lane
+    float2 U2[FUSE ? 1 : H];  // unfused: row i + 1's partials, formed after row i's scan
     int E = 120 - rng.target;    // see team_run_pipe's cinit
     float2 dt2 = make_float2(0.f, 0.f), ml2 = make_float2(0.f, 0.f);
+    float nj = 0.f;  // J of row i - 1 at the column before the lane (previous lane's last)
     float gprev = 0.f;
     float sp1[5], sp2[5], last1 = 0.f, last2 = 0.f, hh1 = 0.f, hh2 = 0.f, hm1 = 0.f, hm2 = 0.f;
     int gcp = -1;
     float qa1 = 0.f, qa2 = 0.f;
+    const int l1 = max(l, 1) - 1;
     if constexpr (LINK) {
-        if (has_left) {  // rows 1..32 of the left boundary into stage block 0
-            if (lt + 1 <= l) cp_async16_cg(stg + lt, sin + lt);
-            cp_async_commit();
-        }
+        // block 0 (rows 1..32): records and, with a left strip, its boundary rows
+        const float4* src = reinterpret_cast<const float4*>(rec + min(lt, l1));
+        cp_async16_cg(rstg + 2 * lt, src);
+        cp_async16_cg(rstg + 2 * lt + 1, src + 1);
+        if (has_left && lt + 1 <= l) cp_async16_cg(stg + lt, sin + lt);
+        cp_async_commit();
+        cp_async_wait_0();
+        __syncwarp();
     }
     SegOut out;
     out.S = 0.0;
     out.E = 0;
     out.flags = 0;
     const float cinit = l > 0 && k > 0 ? (float)(ldexp(1.0, rng.target) / (double)k) : 0.f;
-    const int l1 = max(l, 1) - 1;
-    Rec32J cur = load_recj(rec);
+    Rec32J cur;
+    if constexpr (!LINK && !L1P) cur = load_recj(rec);
     int until = 0;
     for (int i = 1; i <= lmax; ++i) {
-        Rec32J nxt = cur;
-        if (i < lmax) nxt = load_recj(rec + min(i, l1));
+        Rec32J nxt;
+        if constexpr (LINK) {
+            // Stage blocks of 32 rows (records and left boundary), two buffers: block b
+            // is copied while block b - 1 is computed and waited for at b - 1's last row.
+            const int blk = (i - 1) >> 5, r0 = (i - 1) & 31;
+            if (r0 == 0) {
+                __syncwarp();  // every lane is done with block b - 1's buffer
+                const int r = i + 32 + lt;
+                const int nb = (blk + 1) & 1;
+                const float4* src = reinterpret_cast<const float4*>(rec + min(r - 1, l1));
+                cp_async16_cg(rstg + nb * 64 + 2 * lt, src);
+                cp_async16_cg(rstg + nb * 64 + 2 * lt + 1, src + 1);
+                if (has_left && r <= l) cp_async16_cg(stg + nb * 32 + lt, sin + (r - 1));
+                cp_async_commit();
+            }
+            const float4 a = rstg[(blk & 1) * 64 + 2 * r0], b = rstg[(blk & 1) * 64 + 2 * r0 + 1];
+            cur.pm = a.x; cur.px = a.y; cur.a = a.z; cur.b = a.w;
+            cur.h = b.x; cur.g = b.y; cur.mi = b.z; cur.meta = __float_as_uint(b.w);
+        } else if constexpr (L1P) {
+            // the row's record from L1 at the row's start; a few rows ahead are prefetched
+            const Rec32J* rp = rec + min(i - 1, l1);
+            cur = load_recj(rp);
+            asm volatile("prefetch.global.L1 [%0];" ::"l"(rec + min(i + 7, l1)));
+        } else {
+            nxt = cur;
+            if (i < lmax) nxt = load_recj(rec + min(i, l1));
+        }
         const uint32_t meta = cur.meta;
         mflags |= meta;
         const int gq = (int)((meta >> META_GCP_SHIFT) & 0xffu);
-        if (gq != gcp) {
-            const PowRow<float>* pr = pow_tab + min(gq, kMaxPhred);
+        const PowRow<float>* pr = pow_tab + min(gq, kMaxPhred);
+        if constexpr (L1P) {
+            // carry powers read from L1 where they are used (no registers across the row)
+            if constexpr (LINK) {
+                if (gq != gcp) {
+                    qa1 = __ldg(&pr->lq1[lt]);
+                    qa2 = __ldg(&pr->lq2[lt]);
+                    gcp = gq;
+                }
+            }
+        } else if (gq != gcp) {
 #pragma unroll
             for (int s = 0; s < 5; ++s) {
                 sp1[s] = lt >= (1 << s) ? __ldg(&pr->sp1[s]) : 0.f;
@@ -1137,6 +1185,15 @@ __device__ SegOut team_run_pipe2(const Rec32J* __restrict__ rec, int l, int lmax
             }
             gcp = gq;
         }
+        // the row's carry powers: registers, or L1 reads at their use
+        const auto P_sp1 = [&](int s) { if constexpr (L1P) return lt >= (1 << s) ? __ldg(&pr->sp1[s]) : 0.f; else return sp1[s]; };
+        const auto P_sp2 = [&](int s) { if constexpr (L1P) return __ldg(&pr->sp2[s]); else return sp2[s]; };
+        const auto P_last1 = [&]() { if constexpr (L1P) return __ldg(&pr->last1); else return last1; };
+        const auto P_last2 = [&]() { if constexpr (L1P) return __ldg(&pr->last2); else return last2; };
+        const auto P_hh1 = [&]() { if constexpr (L1P) return __ldg(&pr->hh1); else return hh1; };
+        const auto P_hh2 = [&]() { if constexpr (L1P) return __ldg(&pr->hh2); else return hh2; };
+        const auto P_hm1 = [&]() { if constexpr (L1P) return __ldg(&pr->hm1); else return hm1; };
+        const auto P_hm2 = [&]() { if constexpr (L1P) return __ldg(&pr->hm2); else return hm2; };
         const int code = (int)(meta & META_CODE_MASK);
         const uint32_t mask = code == 0 ? bmA : code == 1 ? bmC : code == 2 ? bmG
                             : code == 3 ? bmT : 0xffffffffu;
@@ -1154,7 +1211,7 @@ __device__ SegOut team_run_pipe2(const Rec32J* __restrict__ rec, int l, int lmax
                 if (q == H - 1) yp2 = y2;
                 y2 = ffma2_sel<PACKED>(rg2, y2, mn);
             }
-        } else {
+        } else if constexpr (!FUSE) {
             const float2 rb2 = make_float2(cur.b, cur.b), gp2 = make_float2(gprev, gprev);
 #pragma unroll
             for (int q = 0; q < H; ++q) {
@@ -1168,9 +1225,35 @@ __device__ SegOut team_run_pipe2(const Rec32J* __restrict__ rec, int l, int lmax
                 if (q == H - 1) yp2 = y2;
                 y2 = ffma2_sel<PACKED>(rg2, y2, mn);
             }
+        } else {
+            // Row i's partials U = a M' + J' and insertions J = M' + h J' (primes: row
+            // i - 1, from the column before for U, the same column for J) are formed
+            // column by column as phase B reaches them, from the old M (ml2) and J.
+            const float2 rb2 = make_float2(cur.b, cur.b), gp2 = make_float2(gprev, gprev);
+            const float2 na2 = make_float2(cur.a, cur.a), nh2 = make_float2(cur.h, cur.h);
+            const float2 jp0 = make_float2(nj, J2[H - 1].x);
+#pragma unroll
+            for (int q = 0; q < H; ++q) {
+                const float2 uq = ffma2_sel<PACKED>(na2, ml2, q == 0 ? jp0 : J2[q - 1]);
+                if (q > 0) J2[q - 1] = ffma2_sel<PACKED>(nh2, J2[q - 1], ml2);
+                const float2 u2 = ffma2_sel<PACKED>(rb2, dt2, uq);
+                dt2 = ffma2_sel<PACKED>(gp2, dt2, ml2);
+                ml2 = M2[q];
+                const float2 p2 = make_float2(((mask >> (2 * q)) & 1u) ? pim : pix,
+                                              ((mask >> (2 * q + 1)) & 1u) ? pim : pix);
+                const float2 mn = fmul2_sel<PACKED>(p2, u2);
+                M2[q] = mn;
+                if (q == H - 1) yp2 = y2;
+                y2 = ffma2_sel<PACKED>(rg2, y2, mn);
+            }
+            J2[H - 1] = ffma2_sel<PACKED>(nh2, J2[H - 1], ml2);
         }
-        // Eq. 4 when a pair of this warp finishes (I = T_MI J on the last row)
-        if (__any_sync(kFull, i == l)) {
+        // Eq. 4 when a pair of this warp finishes (I = T_MI J on the last row); a strip
+        // of the serial kind is one pair on the whole warp
+        bool ends;
+        if constexpr (LINK) ends = (i == l);
+        else ends = __any_sync(kFull, i == l);
+        if (ends) {
             const double rmi = (double)cur.mi;
             double s = 0.0;
 #pragma unroll
@@ -1191,13 +1274,13 @@ __device__ SegOut team_run_pipe2(const Rec32J* __restrict__ rec, int l, int lmax
         }
         // lane aggregates of the local (zero-carry) D-hat chain: one past the lane's last
         // column (scan input) and at its last column (the right neighbour's carry)
-        const float zl = fmaf(y2.x * hh1, hh2, y2.y);
-        float ypl = fmaf(y2.x * hm1, hm2, yp2.y);
+        const float zl = fmaf(y2.x * P_hh1(), P_hh2(), y2.y);
+        float ypl = fmaf(y2.x * P_hm1(), P_hm2(), yp2.y);
         float jl = 0.f;
         if constexpr (LINK) jl = J2[H - 1].y;  // this lane's last J of row i (sent right)
         float yA = yp2.x;  // first half, at its last column
         float nm = __shfl_up_sync(kFull, M2[H - 1].y, 1);
-        float nj = __shfl_up_sync(kFull, J2[H - 1].y, 1);
+        nj = __shfl_up_sync(kFull, J2[H - 1].y, 1);
         float yp = __shfl_up_sync(kFull, ypl, 1);
         if (lt == 0) {
             nm = 0.f;
@@ -1208,9 +1291,15 @@ __device__ SegOut team_run_pipe2(const Rec32J* __restrict__ rec, int l, int lmax
 #pragma unroll
         for (int s = 0; s < 5; ++s) {
             const float up = __shfl_up_sync(kFull, Z, 1 << s);
-            Z = fmaf(up * sp1[s], sp2[s], Z);
+            Z = fmaf(up * P_sp1(s), P_sp2(s), Z);
         }
-        {
+        if constexpr (LINK) {  // row i + 1's block is complete before it starts
+            if ((i & 31) == 0) {
+                cp_async_wait_0();
+                __syncwarp();
+            }
+        }
+        if constexpr (!FUSE) {  // phase A: row i + 1's partials and insertions
             const float2 na2 = make_float2(nxt.a, nxt.a), nh2 = make_float2(nxt.h, nxt.h);
             const float mal = M2[H - 1].x, jal = J2[H - 1].x;
 #pragma unroll
@@ -1230,17 +1319,6 @@ __device__ SegOut team_run_pipe2(const Rec32J* __restrict__ rec, int l, int lmax
             int Eleft = INT_MIN;
             if (has_left) {
                 const int blk = (i - 1) >> 5;
-                if (((i - 1) & 31) == 0) {
-                    // start copying the next 32 rows into the other stage block (every lane
-                    // has read the rows it held), then wait for this block (copied while
-                    // the previous 32 rows were computed)
-                    __syncwarp();
-                    const int r = i + 32 + lt;
-                    if (r <= l) cp_async16_cg(stg + ((blk + 1) & 1) * 32 + lt, sin + (r - 1));
-                    cp_async_commit();
-                    cp_async_wait_1();
-                    __syncwarp();
-                }
                 const float4 v = stg[(blk & 1) * 32 + ((i - 1) & 31)];  // one broadcast read
                 lM = v.x;
                 lJ = v.y;
@@ -1284,9 +1362,9 @@ __device__ SegOut team_run_pipe2(const Rec32J* __restrict__ rec, int l, int lmax
                 for (int q = 0; q < H; ++q) {
                     M2[q] = make_float2(scale2(M2[q].x, sdn), scale2(M2[q].y, sdn));
                     J2[q] = make_float2(scale2(J2[q].x, sdn), scale2(J2[q].y, sdn));
-                    U2[q] = make_float2(scale2(U2[q].x, sdn), scale2(U2[q].y, sdn));
                 }
                 nm = scale2(nm, sdn);
+                nj = scale2(nj, sdn);
                 zz = scale2(zz, sdn);
                 yp = scale2(yp, sdn);
                 yA = scale2(yA, sdn);
@@ -1304,25 +1382,23 @@ __device__ SegOut team_run_pipe2(const Rec32J* __restrict__ rec, int l, int lmax
                 lD = scale2(lD, dsh);
             }
             const float Wseg = fmaf(rg, lD, lM);  // D-hat at the strip's first column
-            float ndA = fmaf(zz * last1, last2, yp);
+            float ndA = fmaf(zz * P_last1(), P_last2(), yp);
             ndA = fmaf(Wseg * qa1, qa2, ndA);
             if (lt == 0) {
                 ndA = lD;
                 nm = lM;
-                U2[0].x = fmaf(nxt.a, lM, lJ);
+                nj = lJ;
             }
             if (has_right && lt == 31) {
                 // D-hat at the strip's last column (carry g^(32 N - 1) from the row's table)
-                const PowRow<float>* pr = pow_tab + min(gcp, kMaxPhred);
-                const float dl = fmaf(Wseg * __ldg(&pr->lq1[32]), __ldg(&pr->lq2[32]), fmaf(Wd * last1, last2, ypl));
+                const float dl = fmaf(Wseg * __ldg(&pr->lq1[32]), __ldg(&pr->lq2[32]), fmaf(Wd * P_last1(), P_last2(), ypl));
                 __stcg(sout + (i - 1), make_float4(M2[H - 1].y, jl, dl, __int_as_float(E)));
             }
             const float wl = fmaf(rg, ndA, nm);         // D-hat at the lane's first column
-            const float ndB = fmaf(wl * hm1, hm2, yA);  // D-hat at the first half's last column
+            const float ndB = fmaf(wl * P_hm1(), P_hm2(), yA);  // D-hat at the first half's last column
             dt2 = make_float2(ndA, ndB);
             ml2 = make_float2(nm, M2[H - 1].x);
             gprev = rg;
-            cur = nxt;
             continue;
         }
         if (until == 0) {
@@ -1353,9 +1429,10 @@ __device__ SegOut team_run_pipe2(const Rec32J* __restrict__ rec, int l, int lmax
                     for (int q = 0; q < H; ++q) {
                         M2[q] = fmul2_sel<PACKED>(fmul2_sel<PACKED>(M2[q], a2), b2);
                         J2[q] = fmul2_sel<PACKED>(fmul2_sel<PACKED>(J2[q], a2), b2);
-                        U2[q] = fmul2_sel<PACKED>(fmul2_sel<PACKED>(U2[q], a2), b2);
+                        if constexpr (!FUSE) U2[q] = fmul2_sel<PACKED>(fmul2_sel<PACKED>(U2[q], a2), b2);
                     }
                     nm = (nm * f1) * f2v;
+                    nj = (nj * f1) * f2v;
                     zz = (zz * f1) * f2v;
                     yp = (yp * f1) * f2v;
                     yA = (yA * f1) * f2v;
@@ -1365,17 +1442,15 @@ __device__ SegOut team_run_pipe2(const Rec32J* __restrict__ rec, int l, int lmax
             }
         }
         --until;
-        const float ndA = fmaf(zz * last1, last2, yp);  // D-hat at the column before the lane
-        const float wl = fmaf(rg, ndA, nm);              // D-hat at the lane's first column
-        const float ndB = fmaf(wl * hm1, hm2, yA);       // D-hat at the first half's last column
+        const float ndA = fmaf(zz * P_last1(), P_last2(), yp);  // D-hat at the column before the lane
+        const float wl = fmaf(rg, ndA, nm);                      // D-hat at the lane's first column
+        const float ndB = fmaf(wl * P_hm1(), P_hm2(), yA);       // D-hat at the first half's last column
         dt2 = make_float2(ndA, ndB);
         ml2 = make_float2(nm, M2[H - 1].x);
         gprev = rg;
-        cur = nxt;
+        if constexpr (!LINK && !L1P) cur = nxt;
     }
-    if constexpr (LINK) {
-        if (has_left) cp_async_wait_0();  // nothing may land in the stage after this strip
-    }
+    if constexpr (LINK) cp_async_wait_0();  // nothing may land in the stage after this strip
     return out;
 }
 

@@ -652,10 +652,11 @@ k_forward_cluster(const BatchHeader* __restrict__ H, const PowRow<float>* __rest
 // reading the boundary strip s - 1 left in this warp's scratch.  No warp ever waits on
 // another; the pair's S strips leave S partials, combined by the finalize kernel as for
 // CTA strips.
-template <int N, int MINB>
+template <int N, int MINB, bool L1P = false>
 __global__ void __launch_bounds__(128, MINB)
 k_forward_serial(const BatchHeader* __restrict__ H, const PowRow<float>* __restrict__ pow) {
-    __shared__ float4 stage[4][64];  // per warp: two blocks of 32 left-boundary rows
+    __shared__ float4 stage[4][64];    // per warp: two blocks of 32 left-boundary rows
+    __shared__ float4 rstage[4][128];  // per warp: two blocks of 32 records (32 B each)
     const PipeRange rng = pipe_range(H->dropgrow);
     const uint32_t n_c = H->n_citems;
     const int lane = threadIdx.x & 31;
@@ -675,10 +676,10 @@ k_forward_serial(const BatchHeader* __restrict__ H, const PowRow<float>* __restr
             const float4* in = (s & 1u) ? buf0 : buf1;  // what strip s - 1 wrote
             float4* outb = (s & 1u) ? buf1 : buf0;
             const int c0 = (int)(s * 32u * N) + lane * N;
-            const SegOut o = team_run_pipe2<N, true, true>(H->rec32j + d.roff, (int)d.l, (int)d.l,
+            const SegOut o = team_run_pipe2<N, true, true, true, L1P>(H->rec32j + d.roff, (int)d.l, (int)d.l,
                                                            H->hap_bases + d.hoff, (int)d.k, c0, lane, 31, 5,
                                                            pow, rng, in, outb, s > 0, s + 1 < S,
-                                                           stage[threadIdx.x >> 5]);
+                                                           stage[threadIdx.x >> 5], rstage[threadIdx.x >> 5]);
             __syncwarp();  // this strip's boundary stores before the next strip's loads
             if (lane == 0) {
                 Partial p;
@@ -813,8 +814,10 @@ k_short_pipe64(const BatchHeader* __restrict__ H, const PowRow<double>* __restri
     }
 }
 
-// Pipelined scalar teams with packed column halves (team_run_pipe2).
-template <int N, int MINB, bool PACKED>
+// Pipelined scalar teams with packed column halves (team_run_pipe2).  LEAN: the fused row
+// (no partials array) with records and carry powers read from L1 each row, which fits
+// 128 registers and so four CTAs of four warps per SM.
+template <int N, int MINB, bool PACKED, bool LEAN = false>
 __global__ void __launch_bounds__(kShortThreads, MINB)
 k_short_pipe2(const BatchHeader* __restrict__ H, const PowRow<float>* __restrict__ pow) {
     const PipeRange rng = pipe_range(H->dropgrow);
@@ -837,7 +840,7 @@ k_short_pipe2(const BatchHeader* __restrict__ H, const PowRow<float>* __restrict
             hap = H->hap_bases + d.hoff;
         }
         const int lmax = (int)__reduce_max_sync(kFull, (unsigned)l);
-        const SegOut o = team_run_pipe2<N, PACKED>(rec, l, lmax, hap, k, t.lt * N, t.lt, t.tlast, t.nsteps, pow, rng);
+        const SegOut o = team_run_pipe2<N, PACKED, false, LEAN, LEAN>(rec, l, lmax, hap, k, t.lt * N, t.lt, t.tlast, t.nsteps, pow, rng);
         if (t.pair != kNoPair && t.lt == 0) write_part(H, t.pair, o);
     }
 }

@@ -125,6 +125,7 @@ template __global__ void k_short_pipe<24, 4>(const BatchHeader*, const PowRow<fl
 template __global__ void k_short_pipe<16, 4>(const BatchHeader*, const PowRow<float>*);
 template __global__ void k_short_pipe2<32, 3, true>(const BatchHeader*, const PowRow<float>*);
 template __global__ void k_short_pipe2<24, 4, true>(const BatchHeader*, const PowRow<float>*);
+template __global__ void k_short_pipe2<32, 4, true, true>(const BatchHeader*, const PowRow<float>*);
 
 template __global__ void k_short_packed<12, 4>(const BatchHeader*, const PowRow<float>*);
 template __global__ void k_short_packed<16, 3>(const BatchHeader*, const PowRow<float>*);
@@ -196,6 +197,7 @@ void launch_forward32_long_pipe(int kind, const BatchHeader* H, const void* pow,
 // Short-pair kernel variants (ids used by the runtime's tuner):
 //   scalar id 0: N 32, 4 CTAs/SM   1: N 24, 4   2: N 24, 5   3: N 16, 6   (lean)
 //             4: N 32, 3            5: N 24, 4   6: N 16, 4                 (pipelined)
+//             7: N 32, 3 halves     8: N 24, 4 halves   9: N 32, 4 halves, lean (fused row, L1 tables)
 //   packed id 0: N 12, 4 CTAs/SM   1: N 16, 3
 template <typename K>
 static int occ_of(K kern) {
@@ -217,6 +219,7 @@ void launch_short_scalar(int id, const BatchHeader* H, const void* pow, int grid
     case 6: k_short_pipe<16, 4><<<grid, kShortThreads, 0, s>>>(H, p); break;
     case 7: k_short_pipe2<32, 3, true><<<grid, kShortThreads, 0, s>>>(H, p); break;
     case 8: k_short_pipe2<24, 4, true><<<grid, kShortThreads, 0, s>>>(H, p); break;
+    case 9: k_short_pipe2<32, 4, true, true><<<grid, kShortThreads, 0, s>>>(H, p); break;
 
     default: k_short_scalar<32, 4><<<grid, kShortThreads, 0, s>>>(H, p); break;
     }
@@ -238,6 +241,7 @@ int occupancy_short_scalar(int id) {
     case 6: return occ_of(k_short_pipe<16, 4>);
     case 7: return occ_of(k_short_pipe2<32, 3, true>);
     case 8: return occ_of(k_short_pipe2<24, 4, true>);
+    case 9: return occ_of(k_short_pipe2<32, 4, true, true>);
 
     default: return occ_of(k_short_scalar<32, 4>);
     }

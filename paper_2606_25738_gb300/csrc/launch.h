@@ -64,12 +64,15 @@ int occupancy_forward64(int id);
 constexpr int kN64 = 8;       // columns per lane of the FP64 kernels
 constexpr int kNLong32 = 32;  // columns per lane of FP32 multi-warp pairs
 // FP32 short-pair kernel variants: columns per lane of scalar teams / packed teams.
-constexpr int kNumScalar = 9;
-constexpr int kShortScalarN[kNumScalar] = {32, 24, 24, 16, 32, 24, 16, 32, 24};
+constexpr int kNumScalar = 10;
+constexpr int kShortScalarN[kNumScalar] = {32, 24, 24, 16, 32, 24, 16, 32, 24, 32};
 // scalar ids whose kernel is the pipelined engine (Rec32J records)
-constexpr bool kShortScalarPipe[kNumScalar] = {false, false, false, false, true, true, true, true, true};
+constexpr bool kShortScalarPipe[kNumScalar] = {false, false, false, false, true, true, true, true, true, true};
 // scalar ids whose pipelined engine packs the two column halves of a lane (FFMA2)
-constexpr bool kShortScalarHalves[kNumScalar] = {false, false, false, false, false, false, false, true, true};
+constexpr bool kShortScalarHalves[kNumScalar] = {false, false, false, false, false, false, false, true, true, true};
+// scalar ids of the lean halves engine: fused row, records and carry powers from L1, four
+// CTAs per SM
+constexpr bool kShortScalarLean[kNumScalar] = {false, false, false, false, false, false, false, false, false, true};
 constexpr int kNumPacked = 2;
 constexpr int kShortPackedN[kNumPacked] = {12, 16};
 

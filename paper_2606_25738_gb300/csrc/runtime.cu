@@ -715,6 +715,7 @@ std::vector<std::pair<int, int>> fp32_candidates(const phmm_config& cfg) {
             if (v == 3 && kShortScalarPipe[si]) continue;
             if (v == 4 && !kShortScalarPipe[si]) continue;
             if (v == 5 && !kShortScalarHalves[si]) continue;
+            if (v == 6 && !kShortScalarLean[si]) continue;
             if ((n == 24 || n == 32 || n == 16) && scal_only && kShortScalarN[si] != n) continue;
             if ((n == 24 || n == 32) && !scal_only && kShortScalarN[si] != n) continue;
             if ((n == 12 || n == 16) && !scal_only && (pi < 0 || kShortPackedN[pi] != n)) continue;
@@ -839,7 +840,7 @@ int phmm_create(const phmm_config* cfg, phmm_ctx** out) {
     if (!cfg || !out) return PHMM_EINVAL;
     *out = nullptr;
     if (cfg->precision < 0 || cfg->precision > 2) return PHMM_EINVAL;
-    if (cfg->kernel_variant < 0 || cfg->kernel_variant > 5) return PHMM_EINVAL;
+    if (cfg->kernel_variant < 0 || cfg->kernel_variant > 6) return PHMM_EINVAL;
     if (!(cfg->fp32_tolerance >= 0.0)) return PHMM_EINVAL;
     {
         const unsigned lk =

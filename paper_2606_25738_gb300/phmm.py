@@ -19,7 +19,7 @@ PHMM_OK, PHMM_PENDING = 0, 1
 PHMM_EINVAL, PHMM_ENOMEM, PHMM_EBUSY, PHMM_ECUDA = -1, -2, -3, -4
 PHMM_ETIMEOUT, PHMM_ECANCELED, PHMM_ENOTFOUND = -5, -6, -7
 PREC = {"fp32": 0, "fp64": 1, "fp32_only": 2}
-VARIANTS = {"auto": 0, "packed": 1, "scalar": 2, "lean": 3, "pipe": 4, "pipe2": 5}
+VARIANTS = {"auto": 0, "packed": 1, "scalar": 2, "lean": 3, "pipe": 4, "pipe2": 5, "pipe2lean": 6}
 F_NO_GRAPH, F_LAUNCH_PER_PAIR, F_FORCE_RESCUE = 0x1, 0x2, 0x4
 F_LONG_LEAN, F_LONG_PIPE32, F_LONG_PIPE24, F_NO_TUNE, F_LONG_SERIAL = 0x10, 0x20, 0x40, 0x80, 0x100
 F_LONG_PIPE4, F_LONG_CLUSTER = 0x200, 0x400
@@ -65,10 +65,11 @@ ABI_VERSION = 3  # PHMM_ABI_VERSION of include/phmm.h
 # Kernel names behind phmm_stats.short_kernel / packed_kernel / long_kernel.
 SHORT_KERNELS = ["k_short_scalar<32, 4>", "k_short_scalar<24, 4>", "k_short_scalar<24, 5>",
                  "k_short_scalar<16, 6>", "k_short_pipe<32, 3>", "k_short_pipe<24, 4>",
-                 "k_short_pipe<16, 4>", "k_short_pipe2<32, 3, 1>", "k_short_pipe2<24, 4, 1>"]
+                 "k_short_pipe<16, 4>", "k_short_pipe2<32, 3, 1, 0>", "k_short_pipe2<24, 4, 1, 0>",
+                 "k_short_pipe2<32, 4, 1, 1>"]
 PACKED_KERNELS = ["k_short_packed<12, 4>", "k_short_packed<16, 3>"]
 LONG_KERNELS = ["k_forward<float, 32, 0>", "k_forward_pipe<32, 12>", "k_forward_pipe<24, 16>",
-                "k_forward_serial<32, 3>", "k_forward_pipe<32, 4>", "k_forward_cluster<32, 4, 8>"]
+                "k_forward_serial<32, 3, 0>", "k_forward_pipe<32, 4>", "k_forward_cluster<32, 4, 8>"]
 # FP64 forward variant behind phmm_stats.short_kernel when the precision is FP64.
 FP64_KERNELS = ["k_forward<double, 8, 1, 16>", "k_forward<double, 16, 1, 8>",
                 "k_short_pipe64<16, 2> + k_forward<double, 16, 0, 8>"]

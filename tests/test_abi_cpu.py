@@ -63,7 +63,7 @@ def test_create_rejects_bad_config(lib):
     assert so.phmm_create(ctypes.byref(cfg), ctypes.byref(h)) == lib.PHMM_EINVAL
     cfg = lib.Config(0, 0, 0, 0, 0, None, 12, 2)  # 12 is a packed width only
     assert so.phmm_create(ctypes.byref(cfg), ctypes.byref(h)) == lib.PHMM_EINVAL
-    cfg = lib.Config(0, 0, 0, 0, 0, None, 0, 6)  # bad variant
+    cfg = lib.Config(0, 0, 0, 0, 0, None, 0, 7)  # bad variant
     assert so.phmm_create(ctypes.byref(cfg), ctypes.byref(h)) == lib.PHMM_EINVAL
     cfg = lib.Config(0, 0, 0, 0, 0, None, 0, 0, -1e-3)  # negative FP32 tolerance
     assert so.phmm_create(ctypes.byref(cfg), ctypes.byref(h)) == lib.PHMM_EINVAL

@@ -97,7 +97,7 @@ def test_force_rescue_fp64_pass(phmm):
 
 
 VARIANTS = [("packed", 12), ("packed", 16), ("lean", 24), ("lean", 32), ("pipe", 16), ("pipe", 24),
-            ("pipe", 32), ("pipe2", 24), ("pipe2", 32)]
+            ("pipe", 32), ("pipe2", 24), ("pipe2", 32), ("pipe2lean", 32)]
 
 
 @pytest.mark.parametrize("variant,N", [("packed", 12), ("packed", 16)])
@@ -467,7 +467,7 @@ def test_stats_name_the_kernels_and_no_tune(phmm):
     with phmm.Context(precision="fp32", variant="pipe2", cols_per_lane=32, flags=phmm.F_LONG_SERIAL) as ctx:
         out, flags, rc, st = ctx.run(b)
     assert phmm.SHORT_KERNELS[st["short_kernel"]].startswith("k_short_pipe2<32")
-    assert phmm.LONG_KERNELS[st["long_kernel"]] == "k_forward_serial<32, 3>"
+    assert phmm.LONG_KERNELS[st["long_kernel"]] == "k_forward_serial<32, 3, 0>"
     assert st["packed_kernel"] == -1
     _check(out, flags, ref)
     with phmm.Context(precision="fp32", flags=phmm.F_NO_TUNE) as ctx:
