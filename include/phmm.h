@@ -115,9 +115,11 @@ typedef struct {
                                  column halves in packed FP32 pairs; 6 = its lean form
                                  (the next row's partials formed inside the row, records
                                  and carry powers read from L1: four CTAs per SM).  With
-                                 PHMM_PREC_FP64, 4, 5 or 6 fixes the pipelined FP64
-                                 variant (short pairs on the J-form engine, six FP64
-                                 operations per cell) */
+                                 PHMM_PREC_FP64, 4 fixes the pipelined FP64 variant with
+                                 16-column short teams (pairs up to 512 columns on the
+                                 J-form engine, six FP64 operations per cell), 5 or 6 the
+                                 one with 32-column fused teams (pairs up to 1024
+                                 columns) */
     double fp32_tolerance;    /* largest |error of log10 L| accepted from the FP32 pass
                                  (0 = 1e-3): with PHMM_PREC_FP32_RESCUE a pair whose
                                  a-priori FP32 rounding bound exceeds it is recomputed in
@@ -181,9 +183,11 @@ typedef struct {
     /* Kernels the plan ran (-1: that branch had no work).  FP64 precision: short_kernel =
      * the FP64 forward variant (0: 8 columns per lane in 16-warp CTAs, 1: 16 columns per
      * lane in 8-warp CTAs, 2: short pairs on the pipelined FP64 engine, 16 columns per
-     * lane, and multi-warp pairs as in 1), the other two -1.  FP32:
-     * short_kernel = scalar-team variant 0..8 (k_short_scalar<32,4>, <24,4>, <24,5>,
-     * <16,6>, k_short_pipe<32,3>, <24,4>, <16,4>, k_short_pipe2<32,3>, <24,4>);
+     * lane, and multi-warp pairs as in 1, 3: as 2 with 32-column fused short teams), the
+     * other two -1.  FP32:
+     * short_kernel = scalar-team variant 0..9 (k_short_scalar<32,4>, <24,4>, <24,5>,
+     * <16,6>, k_short_pipe<32,3>, <24,4>, <16,4>, k_short_pipe2<32,3>, <24,4>, and the
+     * lean k_short_pipe2<32,4>);
      * packed_kernel = packed-team variant 0..1 (k_short_packed<12,4>, <16,3>);
      * long_kernel = multi-warp kind 0..5 (lean k_forward<32>, k_forward_pipe<32,12>,
      * k_forward_pipe<24,16>, k_forward_serial<32,3>, k_forward_pipe<32,4>,

@@ -842,7 +842,7 @@ namespace phmm {
 // takes five steps (steps beyond the team width change nothing), so it is one basic
 // block that the compiler can interleave with phase A.
 // ------------------------------------------------------------------------------------
-template <int N, typename T = float>
+template <int N, typename T = float, bool FUSE = false>
 __device__ SegOut team_run_pipe(const typename Num<T>::RecJ* __restrict__ rec, int l, int lmax,
                                 const uint8_t* __restrict__ hap, int k, int col0, int lt,
                                 int tlast, int nsteps, const PowRow<T>* __restrict__ pow_tab,
@@ -864,7 +864,9 @@ __device__ SegOut team_run_pipe(const typename Num<T>::RecJ* __restrict__ rec, i
             if (code == 3 || code == 4) bmT |= bit;
         }
     }
-    T M[N], J[N], U[N];
+    T M[N], J[N];
+    T U[FUSE ? 1 : N];  // unfused: row i + 1's partials, formed after row i's scan
+    T nj = T(0);        // fused: row i's J at the column before the lane
     int E = NT::kLog2C - rng.target;  // see cinit
     T ml = T(0), dt = T(0), gprev = T(0);
     T sp1[5], sp2[5], last1 = T(0), last2 = T(0);
@@ -910,6 +912,23 @@ __device__ SegOut team_run_pipe(const typename Num<T>::RecJ* __restrict__ rec, i
                 if (c == N - 1) yprev = y;
                 y = fma(rg, y, M[c]);
             }
+        } else if constexpr (FUSE) {
+            // Row i's partials U = a M' + J' and insertions J = M' + h J' (primes: row i - 1)
+            // formed column by column inside phase B, as in team_run_pipe2's fused row
+            const T rb = cur.b, na = cur.a, nh = cur.h;
+#pragma unroll
+            for (int c = 0; c < N; ++c) {
+                const T uq = fma(na, ml, c == 0 ? nj : J[c - 1]);
+                if (c > 0) J[c - 1] = fma(nh, J[c - 1], ml);
+                const T u = fma(rb, dt, uq);
+                dt = fma(gprev, dt, ml);
+                ml = M[c];
+                const T mn = (((mask >> c) & 1u) ? pim : pix) * u;
+                M[c] = mn;
+                if (c == N - 1) yprev = y;
+                y = fma(rg, y, mn);
+            }
+            J[N - 1] = fma(nh, J[N - 1], ml);
         } else {
             const T rb = cur.b;
 #pragma unroll
@@ -943,7 +962,7 @@ __device__ SegOut team_run_pipe(const typename Num<T>::RecJ* __restrict__ rec, i
         }
         // the deletion scan of row i and, independent of it, phase A of row i+1
         T nm = __shfl_up_sync(kFull, M[N - 1], 1);
-        T nj = __shfl_up_sync(kFull, J[N - 1], 1);
+        nj = __shfl_up_sync(kFull, J[N - 1], 1);
         T yp = __shfl_up_sync(kFull, yprev, 1);
         if (lt == 0) {
             nm = T(0);
@@ -957,7 +976,7 @@ __device__ SegOut team_run_pipe(const typename Num<T>::RecJ* __restrict__ rec, i
             const T up = __shfl_up_sync(kFull, Z, off);
             Z = fma(up * sp1[s], sp2[s], Z);
         }
-        {
+        if constexpr (!FUSE) {
             const T na = nxt.a, nh = nxt.h;
 #pragma unroll
             for (int c = N - 1; c >= 1; --c) {
@@ -970,9 +989,9 @@ __device__ SegOut team_run_pipe(const typename Num<T>::RecJ* __restrict__ rec, i
         T zz = __shfl_up_sync(kFull, Z, 2);
         if (lt < 2) zz = T(0);
         if (until == 0) {
-            // checkpoint: M holds row i, J and U row i+1 (linear in row i, so they take the
-            // same power of two); U was formed before this test, which the headroom of the
-            // range bounds covers
+            // checkpoint: M holds row i, J and U row i+1 when unfused (linear in row i, so
+            // they take the same power of two; U was formed before this test, which the
+            // headroom of the range bounds covers), J row i when fused
             until = rng.R;
             T m = T(0);
 #pragma unroll
@@ -991,9 +1010,10 @@ __device__ SegOut team_run_pipe(const typename Num<T>::RecJ* __restrict__ rec, i
                         for (int c = 0; c < N; ++c) {
                             M[c] *= f;
                             J[c] *= f;
-                            U[c] *= f;
+                            if constexpr (!FUSE) U[c] *= f;
                         }
                         nm *= f;
+                        nj *= f;
                         zz *= f;
                         yp *= f;
                     } else {  // two exact steps
@@ -1002,9 +1022,10 @@ __device__ SegOut team_run_pipe(const typename Num<T>::RecJ* __restrict__ rec, i
                         for (int c = 0; c < N; ++c) {
                             M[c] = (M[c] * f1) * f2v;
                             J[c] = (J[c] * f1) * f2v;
-                            U[c] = (U[c] * f1) * f2v;
+                            if constexpr (!FUSE) U[c] = (U[c] * f1) * f2v;
                         }
                         nm = (nm * f1) * f2v;
+                        nj = (nj * f1) * f2v;
                         zz = (zz * f1) * f2v;
                         yp = (yp * f1) * f2v;
                     }

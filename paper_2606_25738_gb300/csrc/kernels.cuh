@@ -786,7 +786,7 @@ k_short_pipe(const BatchHeader* __restrict__ H, const PowRow<float>* __restrict_
 // multi-warp pairs run on k_forward<double> (CTA items) on the other branch.  A pair with a
 // degenerate row (1 - g = 0) or a range the engine cannot hold is flagged and goes to the
 // unfactored FP64 pass.
-template <int N, int MINB>
+template <int N, int MINB, bool FUSE = false>
 __global__ void __launch_bounds__(kShortThreads, MINB)
 k_short_pipe64(const BatchHeader* __restrict__ H, const PowRow<double>* __restrict__ pow) {
     const PipeRange rng = pipe_range<double>(H->dropgrow);
@@ -809,7 +809,7 @@ k_short_pipe64(const BatchHeader* __restrict__ H, const PowRow<double>* __restri
             hap = H->hap_bases + d.hoff;
         }
         const int lmax = (int)__reduce_max_sync(kFull, (unsigned)l);
-        const SegOut o = team_run_pipe<N, double>(rec, l, lmax, hap, k, t.lt * N, t.lt, t.tlast, t.nsteps, pow, rng);
+        const SegOut o = team_run_pipe<N, double, FUSE>(rec, l, lmax, hap, k, t.lt * N, t.lt, t.tlast, t.nsteps, pow, rng);
         if (t.pair != kNoPair && t.lt == 0) write_part(H, t.pair, o);
     }
 }

@@ -80,7 +80,8 @@ __global__ void __launch_bounds__(256) k_prep64_list(const BatchHeader* __restri
 template __global__ void k_forward<double, kN64, true>(const BatchHeader*, const PowRow<double>*);
 template __global__ void k_forward<double, kF64N[1], true, kF64CW[1]>(const BatchHeader*, const PowRow<double>*);
 template __global__ void k_forward<double, kF64N[2], false, kF64CW[2]>(const BatchHeader*, const PowRow<double>*);
-template __global__ void k_short_pipe64<kF64N[2], 2>(const BatchHeader*, const PowRow<double>*);
+template __global__ void k_short_pipe64<kF64NS[2], 2>(const BatchHeader*, const PowRow<double>*);
+template __global__ void k_short_pipe64<kF64NS[3], 1, true>(const BatchHeader*, const PowRow<double>*);
 template __global__ void k_finalize<double>(const BatchHeader*);
 
 __device__ __forceinline__ double log10_of(const Partial& q) {
@@ -135,16 +136,19 @@ void launch_prep64_list(const BatchHeader* H, const PhredTables* T, int grid, cu
 }
 void launch_forward64(int id, const BatchHeader* H, const void* pow, int grid, cudaStream_t s) {
     const PowRow<double>* p = static_cast<const PowRow<double>*>(pow);
-    if (id == 2) k_forward<double, kF64N[2], false, kF64CW[2]><<<grid, kF64CW[2] * 32, 0, s>>>(H, p);
+    if (f64_pipelined(id)) k_forward<double, kF64N[2], false, kF64CW[2]><<<grid, kF64CW[2] * 32, 0, s>>>(H, p);
     else if (id == 1) k_forward<double, kF64N[1], true, kF64CW[1]><<<grid, kF64CW[1] * 32, 0, s>>>(H, p);
     else k_forward<double, kN64, true><<<grid, kCtaThreads, 0, s>>>(H, p);
 }
-void launch_short_pipe64(const BatchHeader* H, const void* pow, int grid, cudaStream_t s) {
-    k_short_pipe64<kF64N[2], 2><<<grid, kShortThreads, 0, s>>>(H, static_cast<const PowRow<double>*>(pow));
+void launch_short_pipe64(int id, const BatchHeader* H, const void* pow, int grid, cudaStream_t s) {
+    const PowRow<double>* p = static_cast<const PowRow<double>*>(pow);
+    if (id == 3) k_short_pipe64<kF64NS[3], 1, true><<<grid, kShortThreads, 0, s>>>(H, p);
+    else k_short_pipe64<kF64NS[2], 2><<<grid, kShortThreads, 0, s>>>(H, p);
 }
-int occupancy_short_pipe64() {
+int occupancy_short_pipe64(int id) {
     int b = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_short_pipe64<kF64N[2], 2>, kShortThreads, 0);
+    if (id == 3) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_short_pipe64<kF64NS[3], 1, true>, kShortThreads, 0);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_short_pipe64<kF64NS[2], 2>, kShortThreads, 0);
     return b > 0 ? b : 1;
 }
 void launch_prep64_first(const BatchHeader* H, const PhredTables* T, int grid, cudaStream_t s) {
@@ -161,7 +165,7 @@ void launch_single64(const BatchHeader* H, const void* pow, uint32_t pair, cudaS
 }
 int occupancy_forward64(int id) {
     int b = 0;
-    if (id == 2)
+    if (f64_pipelined(id))
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_forward<double, kF64N[2], false, kF64CW[2]>,
                                                       kF64CW[2] * 32, 0);
     else if (id == 1)

@@ -48,13 +48,17 @@ void launch_prep64_list(const BatchHeader* H, const PhredTables* T, int grid, cu
 // columns; the same 4096-column CTA width for wider pairs), both on the unfactored engine;
 // 2 = short pairs (up to 512 columns) on the pipelined FP64 engine (J-form records, six
 // FP64 operations per cell) and multi-warp pairs on the unfactored engine in 8-warp CTAs
-// (CTA items only), two concurrent branches.  pow: the FP64 power table of that N.
-constexpr int kNumF64 = 3;
-constexpr int kF64N[kNumF64] = {8, 16, 16};
-constexpr int kF64CW[kNumF64] = {16, 8, 8};
+// (CTA items only), two concurrent branches; 3 = as 2 with 32-column short teams (pairs
+// up to 1024 columns) on the fused pipelined engine (no partials array).  pow: the FP64
+// power table of that N (kF64N for the multi-warp kernel, kF64NS for the short teams).
+constexpr int kNumF64 = 4;
+constexpr int kF64N[kNumF64] = {8, 16, 16, 16};   // multi-warp (CTA) kernel: columns per lane
+constexpr int kF64NS[kNumF64] = {8, 16, 16, 32};  // short teams: columns per lane
+constexpr int kF64CW[kNumF64] = {16, 8, 8, 8};
+constexpr bool f64_pipelined(int id) { return id >= 2; }
 void launch_forward64(int id, const BatchHeader* H, const void* pow, int grid, cudaStream_t s);
-void launch_short_pipe64(const BatchHeader* H, const void* pow, int grid, cudaStream_t s);
-int occupancy_short_pipe64();
+void launch_short_pipe64(int id, const BatchHeader* H, const void* pow, int grid, cudaStream_t s);
+int occupancy_short_pipe64(int id);
 void launch_prep64_first(const BatchHeader* H, const PhredTables* T, int grid, cudaStream_t s);
 void launch_finalize64(const BatchHeader* H, int grid, cudaStream_t s);
 void launch_rescue64(const BatchHeader* H, const void* pow, int grid, cudaStream_t s);

@@ -496,9 +496,10 @@ struct phmm_ctx {
     DevBuf scan_row;                        // scan test: one PowRow<float> (global memory)
     DevBuf pow32[5];                        // N = 12, 16, 20, 24 (packed short), 32 (long)
     DevBuf pow64;                           // FP64 powers, N = 8 (variant 0, rescue, comparator)
-    DevBuf pow64w;                          // FP64 powers, N = 16 (variant 1)
-    int occ64v[kNumF64] = {1, 1, 1};        // resident CTAs per SM of the FP64 forward variants
-    int occ64s = 1;                         // ... and of the pipelined FP64 short-team kernel
+    DevBuf pow64w;                          // FP64 powers, N = 16 (variants 1-3)
+    DevBuf pow64x;                          // FP64 powers, N = 32 (variant 3's short teams)
+    int occ64v[kNumF64] = {1, 1, 1, 1};     // resident CTAs per SM of the FP64 forward variants
+    int occ64s[kNumF64] = {1, 1, 1, 1};     // ... and of the pipelined FP64 short-team kernels
     // resident CTAs per SM of each kernel (long kind 5: resident clusters of the GPU)
     int occ_packed[kNumPacked] = {}, occ_scalar[kNumScalar] = {}, occ_longk[kNumLong] = {1, 1, 1, 1, 1, 1}, occ64 = 1;
     std::map<uint64_t, std::array<int, 3>> tuned;  // batch signature -> (scalar id, packed id, long kind)
@@ -579,10 +580,10 @@ int launch_sequence(phmm_ctx* ctx, Slot& S, int scal_id, int pack_id, int long_k
     if (prec == PHMM_PREC_FP64) {
         // scal_id carries the FP64 variant (see make_plan64)
         launch_prep64_all(H, T, grid_pre, s);
-        if (scal_id == 2) launch_prep64_first(H, T, grid_pre, s);
+        if (f64_pipelined(scal_id)) launch_prep64_first(H, T, grid_pre, s);
         CK(rec(S.ev_fwd0));
         const void* pw = scal_id == 0 ? ctx->pow64.p : ctx->pow64w.p;
-        if (scal_id == 2) {
+        if (f64_pipelined(scal_id)) {
             // two branches: short teams on the pipelined engine here, multi-warp CTA items
             // on the unfactored engine on sb2
             CK(cudaEventRecord(S.ev_fork, s));
@@ -592,7 +593,7 @@ int launch_sequence(phmm_ctx* ctx, Slot& S, int scal_id, int pack_id, int long_k
             CK(rec_on(S.ev_br[5], S.sb2));
             CK(cudaEventRecord(S.ev_join, S.sb2));
             CK(rec(S.ev_br[0]));
-            launch_short_pipe64(H, pw, ctx->sms * ctx->occ64s, s);
+            launch_short_pipe64(scal_id, H, scal_id == 3 ? ctx->pow64x.p : pw, ctx->sms * ctx->occ64s[scal_id], s);
             CK(rec(S.ev_br[1]));
             CK(cudaStreamWaitEvent(s, S.ev_join, 0));
             S.br_timed = true;
@@ -656,7 +657,7 @@ int launch_sequence(phmm_ctx* ctx, Slot& S, int scal_id, int pack_id, int long_k
 int kernels_per_launch(int prec, int NP, int fp64_id = 0) {
     const int packed = NP > 0 ? 1 : 0;
     // FP64: reset, prep, [first-row prep, short teams], forward, finalize, rescue
-    return prec == PHMM_PREC_FP64 ? (fp64_id == 2 ? 7 : 5) : prec == PHMM_PREC_FP32_RESCUE ? 8 + packed : 6 + packed;
+    return prec == PHMM_PREC_FP64 ? (f64_pipelined(fp64_id) ? 7 : 5) : prec == PHMM_PREC_FP32_RESCUE ? 8 + packed : 6 + packed;
 }
 
 uint64_t u64(const void* p) { return (uint64_t)(uintptr_t)p; }
@@ -700,7 +701,7 @@ void plan_header(const Slot& S, const Plan& P, BatchHeader& hh) {
     const bool need32 = P.pack_id >= 0 || !kShortScalarPipe[P.scal_id] || (P.long_kind == 0 && !P.citems.empty());
     if (hh.rec32 || hh.rec32j) hh.rec32 = need32 ? (Rec32*)S.rec32.p : nullptr;
     // FP64 J-form records: only the pipelined FP64 variant reads them
-    hh.rec64j = P.fp64 && P.scal_id == 2 ? (Rec64J*)S.rec64j.p : nullptr;
+    hh.rec64j = P.fp64 && f64_pipelined(P.scal_id) ? (Rec64J*)S.rec64j.p : nullptr;
 }
 
 // FP32 short-pair kernel candidates (scalar id, packed id or -1) allowed by the config.
@@ -730,14 +731,14 @@ std::vector<std::pair<int, int>> fp32_candidates(const phmm_config& cfg) {
 // FP64 plan of variant id (launch.h: kF64N columns per lane, kF64CW-warp CTAs); the
 // variant travels in scal_id.
 void make_plan64(const uint32_t* l, const uint32_t* k, const uint32_t* pr, uint32_t n, int id, Plan& P) {
-    make_plan(l, k, pr, n, kF64N[id], 0, kF64N[id], P, 8, kF64CW[id]);
+    make_plan(l, k, pr, n, kF64NS[id], 0, kF64N[id], P, 8, kF64CW[id]);
     P.scal_id = id;
     P.pack_id = -1;
     P.long_kind = 0;
     P.fp64 = true;
     // the pipelined engine does about 6 FP64 operations per cell of a short team against
     // 8 for the unfactored one
-    if (id == 2) P.cost -= 0.25 * (double)P.cells_br[0] * 8.0;
+    if (f64_pipelined(id)) P.cost -= 0.25 * (double)P.cells_br[0] * 8.0;
 }
 
 // Cluster kind: CTA items are taken kClusterCtas at a time, item g kClusterCtas + r by CTA
@@ -924,8 +925,11 @@ int phmm_create(const phmm_config* cfg, phmm_ctx** out) {
         build_pow_table<double>(kF64N[1], v);
         if (ensure(ctx->pow64w, v.size() * sizeof(v[0])) != cudaSuccess) return fail(PHMM_ECUDA);
         cudaMemcpy(ctx->pow64w.p, v.data(), v.size() * sizeof(v[0]), cudaMemcpyHostToDevice);
+        build_pow_table<double>(kF64NS[3], v);
+        if (ensure(ctx->pow64x, v.size() * sizeof(v[0])) != cudaSuccess) return fail(PHMM_ECUDA);
+        cudaMemcpy(ctx->pow64x.p, v.data(), v.size() * sizeof(v[0]), cudaMemcpyHostToDevice);
         for (int q = 0; q < kNumF64; ++q) ctx->occ64v[q] = occupancy_forward64(q);
-        ctx->occ64s = occupancy_short_pipe64();
+        for (int q = 2; q < kNumF64; ++q) ctx->occ64s[q] = occupancy_short_pipe64(q);
         ctx->occ64 = ctx->occ64v[0];
     }
     ctx->slots.resize(ctx->cfg.max_inflight);
@@ -984,6 +988,7 @@ void phmm_destroy(phmm_ctx* ctx) {
     for (auto& b : ctx->pow32) release(b);
     release(ctx->pow64);
     release(ctx->pow64w);
+    release(ctx->pow64x);
     if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
     if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
@@ -1075,9 +1080,10 @@ int phmm_submit_batch(phmm_ctx* ctx, const phmm_batch* b, uint64_t* ticket) {
             // smaller plan cost), measured below for large batches
             const uint64_t sig = batch_signature(L.data(), K.data(), pr, np, ctx->cfg);
             auto hit = ctx->tuned.find(sig);
-            // forced: cols_per_lane 8 / 16 = the unfactored variants, kernel_variant 4 or 5
-            // (the pipelined engine) = variant 2
-            const int forced = ctx->cfg.kernel_variant >= 4 ? 2
+            // forced: cols_per_lane 8 / 16 = the unfactored variants, kernel_variant 4 (the
+            // pipelined engine, 16-column teams) = variant 2, 5 or 6 (32-column fused
+            // teams) = variant 3
+            const int forced = ctx->cfg.kernel_variant >= 5 ? 3 : ctx->cfg.kernel_variant == 4 ? 2
                              : ctx->cfg.cols_per_lane == kF64N[0] ? 0
                              : ctx->cfg.cols_per_lane == kF64N[1] ? 1 : -1;
             if (forced >= 0) {
@@ -1273,7 +1279,7 @@ int phmm_submit_batch(phmm_ctx* ctx, const phmm_batch* b, uint64_t* ticket) {
                 if (m1 > 100.f) break;
             }
             if (getenv("PHMM_DEBUG"))
-                fprintf(stderr, "phmm tuner: fp64 variant %d (N %d, %d-warp CTAs): forward %.3f ms\n", id, kF64N[id],
+                fprintf(stderr, "phmm tuner: fp64 variant %d (N %d/%d, %d-warp CTAs): forward %.3f ms\n", id, kF64NS[id], kF64N[id],
                         kF64CW[id], ms);
             if (ms < best_ms) {
                 best_ms = ms;
@@ -1456,7 +1462,7 @@ int phmm_submit_batch(phmm_ctx* ctx, const phmm_batch* b, uint64_t* ticket) {
         S->st.short_kernel = f32 ? (!P.witems.empty() ? P.scal_id : -1) : P.scal_id;
         S->st.packed_kernel = f32 && !P.witems2.empty() ? P.pack_id : -1;
         S->st.long_kernel = f32 && !P.citems.empty() ? P.long_kind : -1;
-        const bool branched = f32 || P.scal_id == 2;  // the pipelined FP64 variant has two branches
+        const bool branched = f32 || f64_pipelined(P.scal_id);  // the pipelined FP64 variants have two branches
         for (int q = 0; q < 3; ++q) S->st.cells_branch[q] = branched ? P.cells_br[q] : (q == 0 ? cells : 0);
     }
     S->host_status = P.n_too_long ? PHMM_EINVAL : PHMM_OK;

@@ -72,7 +72,8 @@ LONG_KERNELS = ["k_forward<float, 32, 0>", "k_forward_pipe<32, 12>", "k_forward_
                 "k_forward_serial<32, 3, 0>", "k_forward_pipe<32, 4>", "k_forward_cluster<32, 4, 8>"]
 # FP64 forward variant behind phmm_stats.short_kernel when the precision is FP64.
 FP64_KERNELS = ["k_forward<double, 8, 1, 16>", "k_forward<double, 16, 1, 8>",
-                "k_short_pipe64<16, 2> + k_forward<double, 16, 0, 8>"]
+                "k_short_pipe64<16, 2, 0> + k_forward<double, 16, 0, 8>",
+                "k_short_pipe64<32, 1, 1> + k_forward<double, 16, 0, 8>"]
 
 
 class Stats(ctypes.Structure):

@@ -48,22 +48,23 @@ def test_plain_64_pairs_fp32(phmm):
     assert st["kernel_launches"] >= 4
 
 
-@pytest.mark.parametrize("N,variant", [(0, "auto"), (8, "auto"), (16, "auto"), (0, "pipe")])
+@pytest.mark.parametrize("N,variant", [(0, "auto"), (8, "auto"), (16, "auto"), (0, "pipe"), (0, "pipe2")])
 def test_plain_64_pairs_fp64(phmm, N, variant):
     """FP64 mode, every forward variant (unfactored: 8 columns per lane in 16-warp CTAs, 16
-    in 8-warp CTAs; pipelined short teams) and the tuner's choice; pairs up to 1200 columns
-    (teams and linked warps)."""
+    in 8-warp CTAs; pipelined short teams of 16 or 32 columns per lane) and the tuner's
+    choice; pairs up to 1200 columns (teams and linked warps)."""
     b = W.plain_pairs(64, seed=0, k_range=(200, 1200))
     with phmm.Context(precision="fp64", cols_per_lane=N, variant=variant) as ctx:
         out, flags, rc, st = ctx.run(b)
     assert np.all(flags & phmm.PAIR_FP64)
-    if N or variant == "pipe":
-        assert st["short_kernel"] == {8: 0, 16: 1, 0: 2}[N]
+    if N or variant != "auto":
+        assert st["short_kernel"] == ({8: 0, 16: 1}[N] if N else {"pipe": 2, "pipe2": 3}[variant])
     ref = oracle.batch(b)
     assert np.max(np.abs(out - ref)) <= TOL64
 
 
-def test_fp64_pipelined_engine_range_and_degenerate_rows(phmm):
+@pytest.mark.parametrize("variant,fid", [("pipe", 2), ("pipe2", 3)])
+def test_fp64_pipelined_engine_range_and_degenerate_rows(phmm, variant, fid):
     """The pipelined FP64 engine carries J = I / T_MI with checkpoints like the FP32 one:
     long reads (rescaling), insertion Phred 93 next to 1, and a gap-continuation Phred 0
     row (1 - g = 0: the J-form is unusable) which must go to the unfactored pass."""
@@ -77,9 +78,9 @@ def test_fp64_pipelined_engine_range_and_degenerate_rows(phmm):
     b = W.from_strings(pairs)
     lb = W.long_pairs(3, seed=14, k_range=(2000, 9000))
     for batch in (b, lb):
-        with phmm.Context(precision="fp64", variant="pipe") as ctx:
+        with phmm.Context(precision="fp64", variant=variant) as ctx:
             out, flags, rc, st = ctx.run(batch)
-        assert st["short_kernel"] == 2
+        assert st["short_kernel"] == fid
         ref = oracle.batch(batch)
         _check(out, flags, ref, tol32=TOL64)
         if batch is b:
@@ -476,7 +477,7 @@ def test_stats_name_the_kernels_and_no_tune(phmm):
     with phmm.Context(precision="fp64") as ctx:
         out3, flags3, rc3, st3 = ctx.run(b)
     # FP64: short_kernel names the FP64 forward variant
-    assert st3["short_kernel"] in (0, 1, 2) and st3["long_kernel"] == -1 and st3["packed_kernel"] == -1
+    assert st3["short_kernel"] in (0, 1, 2, 3) and st3["long_kernel"] == -1 and st3["packed_kernel"] == -1
     _check(out3, flags3, ref)
 
 

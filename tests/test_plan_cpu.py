@@ -51,14 +51,14 @@ def test_fp32_plans_valid(P, shape, scal, pack, kind):
 
 
 @pytest.mark.parametrize("shape", sorted(SHAPES))
-@pytest.mark.parametrize("variant", [0, 1, 2])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3])
 def test_fp64_plans_valid(P, shape, variant):
     """FP64 variants: 8 columns per lane in 16-warp CTAs, 16 in 8-warp CTAs, pipelined
-    short teams of 16 columns per lane with 8-warp CTA items."""
+    short teams of 16 (or 32) columns per lane with 8-warp CTA items."""
     l, k, pr = SHAPES[shape]
     rc, st = P.plan_check(l, k, pr, "fp64", variant)
     assert rc == P.PHMM_OK, st
-    assert P.plan_check(l, k, pr, "fp64", 3)[0] == P.PHMM_EINVAL
+    assert P.plan_check(l, k, pr, "fp64", 4)[0] == P.PHMM_EINVAL
 
 
 def test_wide_pairs_are_striped_and_packed(P):
