@@ -330,7 +330,10 @@ def dominant_branch(sts: list, phmm) -> dict:
             "all": [{"kernel": names[i], "cells": int(cells[i]), "ms": float(ms[i])} for i in range(3)]}
 
 
-def roofline(dom: dict, info: dict, workload_key: str) -> dict:
+def roofline(dom: dict, info: dict) -> dict:
+    """Roofline entry of the dominant kernel.  `traffic` comes from
+    profiles/forward_traffic.json, keyed by kernel name and by the launch's cell count (the
+    exact work of a captured launch, scaled to this one in that file), else null."""
     peaks = _peaks()
     sm_max = float(peaks.get("sm_max_mhz", info["max_clock_mhz"]))
     peak = 2.0 * 128 * info["sms"] * sm_max * 1e6 / 1e12
@@ -339,7 +342,7 @@ def roofline(dom: dict, info: dict, workload_key: str) -> dict:
     tfile = os.path.join(ROOT, "profiles", "forward_traffic.json")
     if os.path.exists(tfile) and dom["kernel"]:
         try:
-            ent = json.load(open(tfile)).get(dom["kernel"], {}).get(workload_key)
+            ent = json.load(open(tfile)).get(dom["kernel"], {}).get(str(dom["cells"]))
             if ent:
                 traffic = ent.get("bytes_per_launch")
         except Exception:
@@ -428,7 +431,7 @@ def gpu_leg(name: str, b, dev: int, args, steps: int = 5, warmup: int = 3, preci
                        else [phmm.FP64_KERNELS[sts[-1]["short_kernel"]]])}
     if precision != "fp64":
         dom = dominant_branch(sts, phmm)
-        row["roofline"] = roofline(dom, info, name)
+        row["roofline"] = roofline(dom, info)
     if parity == "stratified":
         row["parity"] = stratified_parity(b, res, flg, per_decile=100, max_cells=1e10)
     elif parity == "all":
@@ -634,7 +637,7 @@ def run_ours(args):
                   "fp32_only": "f32 (f64 reduction)"}[args.precision],
         "data": "synthetic (seeded, shaped like the paper's workloads)",
         "config": config_dict(name, units, b, world, args),
-        "roofline": roofline(dom, info, name),
+        "roofline": roofline(dom, info),
         "e2e": {"value": e2e_value, "unit": "GCUPS", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "ms_per_step": e2e_ms, "matches_device_run": e2e_ok,
                 "how": "phmm_submit_batch/phmm_poll with pinned host inputs and pinned host outputs, "
