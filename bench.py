@@ -330,13 +330,24 @@ def dominant_branch(sts: list, phmm) -> dict:
             "all": [{"kernel": names[i], "cells": int(cells[i]), "ms": float(ms[i])} for i in range(3)]}
 
 
+def fp64_forward(sts: list, phmm, cells: int) -> dict:
+    """FP64 mode: the forward kernels of the chosen FP64 variant as one unit (the variant's
+    branches both run FP64), their cells and the mean forward time."""
+    ms = float(np.mean([s["ms_forward"] for s in sts]))
+    name = phmm.FP64_KERNELS[sts[-1]["short_kernel"]]
+    return {"branch": "FP64 forward", "kernel": name, "ms": ms, "cells": int(cells), "fp64": True,
+            "all": [{"kernel": name, "cells": int(cells), "ms": ms}]}
+
+
 def roofline(dom: dict, info: dict) -> dict:
     """Roofline entry of the dominant kernel.  `traffic` comes from
     profiles/forward_traffic.json, keyed by kernel name and by the launch's cell count (the
     exact work of a captured launch, scaled to this one in that file), else null."""
     peaks = _peaks()
     sm_max = float(peaks.get("sm_max_mhz", info["max_clock_mhz"]))
-    peak = 2.0 * 128 * info["sms"] * sm_max * 1e6 / 1e12
+    fp64 = bool(dom.get("fp64"))
+    lanes = 2 if fp64 else 128  # FMA lanes per SM per clock: FP64 (nominal) / FP32
+    peak = 2.0 * lanes * info["sms"] * sm_max * 1e6 / 1e12
     achieved = FLOP_PER_CELL * dom["cells"] / (dom["ms"] * 1e-3) / 1e12 if dom["ms"] > 0 else 0.0
     traffic = None
     tfile = os.path.join(ROOT, "profiles", "forward_traffic.json")
@@ -351,8 +362,9 @@ def roofline(dom: dict, info: dict) -> dict:
             "frac": achieved / peak, "traffic": traffic, "kernel": dom["kernel"],
             "branch": dom["branch"], "cells_per_launch": dom["cells"], "ms_per_launch": dom["ms"],
             "flop_per_cell": FLOP_PER_CELL,
-            "peak_note": "2 x 128 FP32 lanes x %d SMs x %.0f MHz (nominal unit count at the max SM clock of "
-                         "MEASURED_PEAKS.json; no measured FP32 peak exists there)" % (info["sms"], sm_max)}
+            "peak_note": "2 x %d %s FMA lanes x %d SMs x %.0f MHz (nominal unit count at the max SM clock of "
+                         "MEASURED_PEAKS.json; no measured %s peak exists there)"
+                         % (lanes, "FP64" if fp64 else "FP32", info["sms"], sm_max, "FP64" if fp64 else "FP32")}
 
 
 def timed_steps(ctx, d, out, fl, steps, warmup, stream, flush, world, clocks: bool = True, dev: int = 0):
@@ -429,9 +441,8 @@ def gpu_leg(name: str, b, dev: int, args, steps: int = 5, warmup: int = 3, preci
            "ms_forward": fwd, "rescued_pairs": int(sts[-1]["n_rescued"]), "first_submit_s": first_s,
            "kernels": ([k for k in kernel_names(sts[-1], phmm) if k] if precision != "fp64"
                        else [phmm.FP64_KERNELS[sts[-1]["short_kernel"]]])}
-    if precision != "fp64":
-        dom = dominant_branch(sts, phmm)
-        row["roofline"] = roofline(dom, info)
+    dom = dominant_branch(sts, phmm) if precision != "fp64" else fp64_forward(sts, phmm, cells)
+    row["roofline"] = roofline(dom, info)
     if parity == "stratified":
         row["parity"] = stratified_parity(b, res, flg, per_decile=100, max_cells=1e10)
     elif parity == "all":
@@ -590,7 +601,7 @@ def run_ours(args):
     value = job_throughput(cells, world, step_ms)
     res = out.cpu().numpy()
     flg = fl.cpu().numpy()
-    dom = dominant_branch(sts, phmm)
+    dom = dominant_branch(sts, phmm) if args.precision != "fp64" else fp64_forward(sts, phmm, cells)
 
     # End to end through the C ABI with host buffers: every step copies its inputs from
     # pinned host memory to the device and its results back, both inside the timed region.
