@@ -131,10 +131,15 @@ typedef struct {
 } pack;
 
 /* Per-row coefficients of every read base the pass uses, computed once per read (a read
- * is shared by all its pairs) and in parallel, as NC values per base: 1 - e, e / 3,
+ * is shared by all its pairs) and in parallel, as NC values per base.  FP64: 1 - e, e / 3,
  * T_MM, T_DM = 1 - g, T_MI, g, (1 - g) T_MD of the previous row (1 on a read's first row),
- * and the read base's bit set.  FP32 tables hold the values stochastically rounded. */
+ * and the read base's bit set.  FP32 takes the factor T_IM = T_DM = 1 - g of Eq. 2 out of
+ * the match update (one multiply less per cell): (1 - e)(1 - g), (e / 3)(1 - g),
+ * T_MM / (1 - g), 1, T_MI, g, T_MD of the previous row, the bit set; a row with
+ * 1 - g < 2^-20 cannot be factored and carries DEGEN_BIT in its bit set instead (its pair
+ * goes to the FP64 pass).  FP32 tables hold the values stochastically rounded. */
 #define NC 8
+#define DEGEN_BIT 0x100
 
 typedef struct {
     double S;
@@ -166,6 +171,7 @@ static int scratch_reserve(cpu_scratch *s, size_t bytes) {
 #define ENG_VI v32i
 #define ENG_W W32
 #define ENG_SR 1
+#define ENG_FACTOR 1
 #define ENG_LOG2C 120
 #define ENG_HI 100
 #define ENG_LO 40
@@ -180,6 +186,7 @@ static int scratch_reserve(cpu_scratch *s, size_t bytes) {
 #undef ENG_VI
 #undef ENG_W
 #undef ENG_SR
+#undef ENG_FACTOR
 #undef ENG_LOG2C
 #undef ENG_HI
 #undef ENG_LO
@@ -196,6 +203,7 @@ static int scratch_reserve(cpu_scratch *s, size_t bytes) {
 #define ENG_VI v64i
 #define ENG_W W64
 #define ENG_SR 0
+#define ENG_FACTOR 0
 #define ENG_LOG2C 1020
 #define ENG_HI 900
 #define ENG_LO 300
@@ -362,7 +370,7 @@ static void coef_read(const phmm_batch *b, uint32_t r, uint64_t c0, void *tab, i
                      g = q_tab[b->gcp_q[bi]];
         const double qdp = i > 0 ? q_tab[b->del_q[bi - 1]] : 1.0;
         const double c[NC - 1] = {1.0 - e, e / 3.0, 1.0 - qi - qd, 1.0 - g, qi, g, (1.0 - g) * qdp};
-        const int32_t bits = base_bits(b->read_bases[bi]);
+        int32_t bits = base_bits(b->read_bases[bi]);
         if (fp64) {
             double *d = (double *)tab + (c0 + i) * NC;
             for (int q = 0; q < NC - 1; ++q) d[q] = c[q];
@@ -371,9 +379,15 @@ static void coef_read(const phmm_batch *b, uint32_t r, uint64_t c0, void *tab, i
         } else {
             /* two hashes of the read base give the eight 16-bit uniforms */
             const uint64_t h0 = mix64(0x5eed1234ull << 32 ^ (bi * 2u)), h1 = mix64(0x5eed1234ull << 32 ^ (bi * 2u + 1u));
+            const double omg = 1.0 - g;
+            double cf[NC - 1] = {c[0] * omg, c[1] * omg, c[2] / omg, 1.0, qi, g, qdp};
+            if (!(omg >= 0x1p-20)) {
+                bits |= DEGEN_BIT;
+                cf[0] = cf[1] = cf[2] = 0.0;
+            }
             float *f = (float *)tab + (c0 + i) * NC;
             for (int q = 0; q < NC - 1; ++q)
-                f[q] = sr_round(c[q], (uint32_t)(((q < 4 ? h0 : h1) >> (16 * (q & 3))) & 0xffffu));
+                f[q] = sr_round(cf[q], (uint32_t)(((q < 4 ? h0 : h1) >> (16 * (q & 3))) & 0xffffu));
             memcpy(&f[NC - 1], &bits, 4);
         }
     }
@@ -527,7 +541,7 @@ int phmm_cpu_forward(const phmm_batch *b, int n_threads, int precision, double f
             const double v = x->S > 0.0 && isfinite(x->S)
                                  ? log10(x->S) + (double)(x->E - log2c) * 0.30102999566398119521
                                  : (x->S == 0.0 ? -INFINITY : NAN);
-            uint32_t f = x->flags & (PHMM_PAIR_RESCALED | PHMM_PAIR_DANGER | PHMM_PAIR_NONFINITE);
+            uint32_t f = x->flags & (PHMM_PAIR_RESCALED | PHMM_PAIR_DANGER | PHMM_PAIR_NONFINITE | PHMM_PAIR_DEGENERATE);
             if (fp64) {
                 f |= PHMM_PAIR_FP64;
                 if (pass == 1) f |= PHMM_PAIR_RESCUED | (b->out_flags ? b->out_flags[p] & 0x78u : 0u);

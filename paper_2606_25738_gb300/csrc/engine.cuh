@@ -414,12 +414,6 @@ struct SegOut {
     uint32_t flags;
 };
 
-// Where a link-mode strip puts its partial (team_run_pipe2<..., LINK>): called by lane 0 on
-// the pair's last row, so no result is held in registers across the rows.
-struct NoSink {
-    __device__ void operator()(const SegOut&) const {}
-};
-
 // ------------------------------------------------------------------------------------
 // One team / segment: rows 1..lmax over the lane's N columns.  Returns the team's
 // final (S, E, flags) in every lane of the team (valid when the team's l <= lmax).
@@ -1098,13 +1092,13 @@ __device__ __forceinline__ float2 fmul2_sel(float2 a, float2 b) {
 // boundary and record as broadcasts (no record is held in registers across a row).
 // The lane's carry power g^(N lt - 1) stays in registers (reloaded when gcp changes):
 // reading it from L1 every row measured 2% slower on the 1M-pair uneven batch.
-template <int N, bool PACKED, bool LINK = false, bool FUSE = LINK, bool L1P = false, typename Sink = NoSink>
+template <int N, bool PACKED, bool LINK = false, bool FUSE = LINK, bool L1P = false>
 __device__ SegOut team_run_pipe2(const Rec32J* __restrict__ rec, int l, int lmax,
                                  const uint8_t* __restrict__ hap, int k, int col0, int lt,
                                  int tlast, int nsteps, const PowRow<float>* __restrict__ pow_tab,
                                  const PipeRange& rng, const float4* sin = nullptr, float4* sout = nullptr,
                                  bool has_left = false, bool has_right = false, float4* stg = nullptr,
-                                 float4* rstg = nullptr, const Sink& sink = Sink()) {
+                                 float4* rstg = nullptr) {
     using NT = Num<float>;
     static_assert(N <= 32 && N % 2 == 0, "match masks hold 32 columns; two halves");
     static_assert(FUSE || !(LINK || L1P), "the serial strips and the L1 tables need the fused row");
@@ -1293,15 +1287,7 @@ __device__ SegOut team_run_pipe2(const Rec32J* __restrict__ rec, int l, int lmax
             if (mflags & META_BAD) f |= PF_BAD;
             if (mflags & META_DEGEN) f |= PF_DEGEN;
             f = team_or(f, lt, tlast, nsteps);
-            if constexpr (LINK) {
-                if (lt == 0) {
-                    SegOut o;
-                    o.S = s;
-                    o.E = E;
-                    o.flags = f;
-                    sink(o);
-                }
-            } else if (i == l) {
+            if (i == l) {
                 out.S = s;
                 out.E = E;
                 out.flags = f;

@@ -676,18 +676,18 @@ k_forward_serial(const BatchHeader* __restrict__ H, const PowRow<float>* __restr
             const float4* in = (s & 1u) ? buf0 : buf1;  // what strip s - 1 wrote
             float4* outb = (s & 1u) ? buf1 : buf0;
             const int c0 = (int)(s * 32u * N) + lane * N;
-            // the strip's partial, written by lane 0 on the pair's last row
-            const auto sink = [=](const SegOut& o) {
+            const SegOut o = team_run_pipe2<N, true, true, true, L1P>(H->rec32j + d.roff, (int)d.l, (int)d.l,
+                                                           H->hap_bases + d.hoff, (int)d.k, c0, lane, 31, 5,
+                                                           pow, rng, in, outb, s > 0, s + 1 < S,
+                                                           stage[threadIdx.x >> 5], rstage[threadIdx.x >> 5]);
+            __syncwarp();  // this strip's boundary stores before the next strip's loads
+            if (lane == 0) {
                 Partial p;
                 p.S = o.S;
                 p.E = o.E;
                 p.flags = o.flags | PF_DONE;
                 write_strip_part(H, cp.pair, s, S, cp.extra_base, p);
-            };
-            team_run_pipe2<N, true, true, true, L1P>(H->rec32j + d.roff, (int)d.l, (int)d.l, H->hap_bases + d.hoff,
-                                                     (int)d.k, c0, lane, 31, 5, pow, rng, in, outb, s > 0, s + 1 < S,
-                                                     stage[threadIdx.x >> 5], rstage[threadIdx.x >> 5], sink);
-            __syncwarp();  // this strip's boundary stores before the next strip's loads
+            }
         }
     }
 }

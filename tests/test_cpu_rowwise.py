@@ -149,3 +149,26 @@ def test_empty_batch(cpu):
     b = W.subset(W.plain_pairs(3, seed=1), [])
     out, fl = cpu.forward(b, 2)
     assert len(out) == 0 and len(fl) == 0
+
+
+def test_degenerate_gap_row_goes_to_fp64(cpu):
+    """FP32 takes T_IM = 1 - g out of the match update; a row with gap-continuation Phred 0
+    (1 - g = 0) cannot be factored, so its pair is flagged DEGENERATE and recomputed in
+    FP64 (to 1e-9), while the FP32-only pass leaves it flagged.  Pairs without such a row
+    stay in FP32."""
+    rng = np.random.default_rng(21)
+    hap = "".join(rng.choice(list("ACGT"), size=600))
+    read = hap[100:250]
+    one_zero = np.full(len(read), 10)
+    one_zero[70] = 0
+    pairs = [(read, hap, 30, 45, 45, 10), (read, hap, 30, 45, 45, one_zero), (read, hap, 30, 45, 45, 1)]
+    b = W.from_strings(pairs)
+    ref = oracle.batch(b)
+    assert np.all(np.isfinite(ref))
+    out, fl = cpu.forward(b, 1, "fp32")
+    assert fl[1] & 0x40 and fl[1] & 0x1 and fl[1] & 0x4
+    assert not (fl[0] & 0x41) and not (fl[2] & 0x41)
+    _check(out, fl, ref)
+    out2, fl2 = cpu.forward(b, 1, "fp32_only")
+    assert fl2[1] & 0x40 and not (fl2[1] & 0x5)
+    assert np.max(np.abs(out2[[0, 2]] - ref[[0, 2]])) <= TOL32
