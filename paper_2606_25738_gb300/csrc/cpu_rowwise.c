@@ -233,7 +233,10 @@ static uint32_t pack_interval(const phmm_batch *b, const pack *pk, double drop_b
     }
     double r = fmin(drop_budget / dmax, grow_budget / gmax);
     if (r > 32.0) r = 32.0;
-    return r < 1.0 ? 1u : (uint32_t)r;
+    /* even when it can be: rows go through the columns two at a time, and a checkpoint
+     * then always follows the second row of a pair (its maximum taken in that pass) */
+    const uint32_t R = r < 1.0 ? 1u : (uint32_t)r;
+    return R >= 2 ? R & ~1u : R;
 }
 
 /* ------------------------------------------------------------------------------------ */
