@@ -1334,8 +1334,6 @@ __device__ SegOut team_run_pipe2(const Rec32J* __restrict__ rec, int l, int lmax
         float zz = __shfl_up_sync(kFull, Z, 2);
         if (lt < 2) zz = 0.f;
         if constexpr (LINK) {
-            float Wd = __shfl_up_sync(kFull, Z, 1);
-            if (lt == 0) Wd = 0.f;
             float lM = 0.f, lJ = 0.f, lD = 0.f;
             int Eleft = INT_MIN;
             if (has_left) {
@@ -1357,7 +1355,9 @@ __device__ SegOut team_run_pipe2(const Rec32J* __restrict__ rec, int l, int lmax
                     m2.x = fmaxf(m2.x, fmaxf(fabsf(M2[q].x), fabsf(J2[q].x)));
                     m2.y = fmaxf(m2.y, fmaxf(fabsf(M2[q].y), fabsf(J2[q].y)));
                 }
-                const float m = team_max<float>(fmaxf(m2.x, m2.y), lt, tlast, nsteps);
+                // the strip is the whole warp: one reduction over the lanes' maxima (values
+                // >= 0, so their bit patterns order like the values)
+                const float m = __uint_as_float(__reduce_max_sync(kFull, __float_as_uint(fmaxf(m2.x, m2.y))));
                 const int e = NT::expo(m);
                 int desired = E;
                 if (e == INT_MAX) {
@@ -1389,7 +1389,6 @@ __device__ SegOut team_run_pipe2(const Rec32J* __restrict__ rec, int l, int lmax
                 zz = scale2(zz, sdn);
                 yp = scale2(yp, sdn);
                 yA = scale2(yA, sdn);
-                Wd = scale2(Wd, sdn);
                 ypl = scale2(ypl, sdn);
                 jl = scale2(jl, sdn);
                 flags |= PF_RESCALED;
@@ -1411,8 +1410,9 @@ __device__ SegOut team_run_pipe2(const Rec32J* __restrict__ rec, int l, int lmax
                 nj = lJ;
             }
             if (has_right && lt == 31) {
-                // D-hat at the strip's last column (carry g^(32 N - 1) from the row's table)
-                const float dl = fmaf(Wseg * __ldg(&pr->lq1[32]), __ldg(&pr->lq2[32]), fmaf(Wd * P_last1(), P_last2(), ypl));
+                // D-hat at the strip's last column: the lane's own chain from ndA (the
+                // column before it, carry included) over its N columns, g^N ndA + ypl
+                const float dl = fmaf((ndA * rg) * P_last1(), P_last2(), ypl);
                 __stcg(sout + (i - 1), make_float4(M2[H - 1].y, jl, dl, __int_as_float(E)));
             }
             const float wl = fmaf(rg, ndA, nm);         // D-hat at the lane's first column
