@@ -209,6 +209,15 @@ __device__ __forceinline__ V team_max(V x, int lt, int last_lane, int nsteps) {
     return __shfl_sync(kFull, x, last_lane);
 }
 
+// Maximum of non-negative FP32 values over a team (lanes last_lane - lt .. last_lane), in
+// every lane of the team: one warp reduction on the bit patterns, which order like the
+// values for x >= 0 (the team's mask keeps other teams apart).  Same result as team_max.
+__device__ __forceinline__ float team_max_pos(float x, int lt, int last_lane) {
+    const int base = (int)(threadIdx.x & 31) - lt, size = last_lane - base + 1;
+    const unsigned mask = size >= 32 ? kFull : ((1u << size) - 1u) << base;
+    return __uint_as_float(__reduce_max_sync(mask, __float_as_uint(x)));
+}
+
 __device__ __forceinline__ uint32_t team_or(uint32_t x, int lt, int last_lane, int nsteps) {
 #pragma unroll
     for (int s = 0; s < 5; ++s) {
@@ -996,7 +1005,8 @@ __device__ SegOut team_run_pipe(const typename Num<T>::RecJ* __restrict__ rec, i
             T m = T(0);
 #pragma unroll
             for (int c = 0; c < N; ++c) m = fmax(m, fmax(fabs(M[c]), fabs(J[c])));
-            m = team_max<T>(m, lt, tlast, nsteps);
+            if constexpr (sizeof(T) == 4) m = team_max_pos(m, lt, tlast);
+            else m = team_max<T>(m, lt, tlast, nsteps);
             const int e = NT::expo(m);
             if (e == INT_MAX) {
                 flags |= PF_NONFINITE;
@@ -1430,7 +1440,7 @@ __device__ SegOut team_run_pipe2(const Rec32J* __restrict__ rec, int l, int lmax
                 m2.x = fmaxf(m2.x, fmaxf(fabsf(M2[q].x), fabsf(J2[q].x)));
                 m2.y = fmaxf(m2.y, fmaxf(fabsf(M2[q].y), fabsf(J2[q].y)));
             }
-            const float m = team_max<float>(fmaxf(m2.x, m2.y), lt, tlast, nsteps);
+            const float m = team_max_pos(fmaxf(m2.x, m2.y), lt, tlast);
             const int e = NT::expo(m);
             if (e == INT_MAX) {
                 flags |= PF_NONFINITE;
@@ -1635,7 +1645,7 @@ __device__ SegOut seg_link_pipe(const Rec32J* __restrict__ rec, int l, const uin
             float m = 0.f;
 #pragma unroll
             for (int c = 0; c < N; ++c) m = fmaxf(m, fmaxf(fabsf(M[c]), fabsf(J[c])));
-            m = team_max<float>(m, lane, 31, 5);
+            m = team_max_pos(m, lane, 31);
             const int e = NT::expo(m);
             int desired = E;
             if (e == INT_MAX) {
