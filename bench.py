@@ -588,7 +588,7 @@ def run_ours(args):
     out = torch.empty(n, dtype=torch.float64, device="cuda")
     fl = torch.zeros(n, dtype=torch.uint8, device="cuda")
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # > L2 (129 MB)
-    ctx = phmm.Context(device=dev, precision=args.precision, stream=stream.cuda_stream, max_inflight=1,
+    ctx = phmm.Context(device=dev, precision=args.precision, stream=stream.cuda_stream, max_inflight=2,
                        variant=args.variant, cols_per_lane=args.cols, flags=_flag_bits(args, phmm))
     info = ctx.device_info()
     t = time.perf_counter()
@@ -605,7 +605,8 @@ def run_ours(args):
 
     # End to end through the C ABI with host buffers: every step copies its inputs from
     # pinned host memory to the device and its results back, both inside the timed region.
-    # Same context (its plan, tuning and graph are reused); one batch in flight.
+    # Same context (its plan, tuning and graph are reused); two batches in flight, as a
+    # streaming caller would keep them: a step's upload overlaps the previous step's kernels.
     del d
     torch.cuda.empty_cache()
     keys = ("read_bases", "base_q", "ins_q", "del_q", "gcp_q", "hap_bases", "read_off", "hap_off",
@@ -615,26 +616,40 @@ def run_ours(args):
         hb[k] = torch.from_numpy(np.ascontiguousarray(b[k])).pin_memory().numpy()
     h2d = int(sum(hb[k].nbytes for k in keys))
     d2h = n * 9
-    ho = torch.empty(n, dtype=torch.float64).pin_memory().numpy()
-    hf = torch.zeros(n, dtype=torch.uint8).pin_memory().numpy()
+    hout = [(torch.empty(n, dtype=torch.float64).pin_memory().numpy(),
+             torch.zeros(n, dtype=torch.uint8).pin_memory().numpy()) for _ in range(2)]
     n_e2e = max(2, min(args.e2e_steps, args.steps))
 
-    def e2e_step():
-        tk = ctx.submit(hb, ho, hf)
-        if ctx.poll(tk, -1) != 0:
-            raise RuntimeError("e2e step failed")
-        return ctx.stats(tk)
+    overlap = [True]
 
-    e2e_step()  # first copy into this slot's input arenas
+    def e2e_run(k):
+        pend = []
+        for q in range(k):
+            while True:
+                try:
+                    pend.append(ctx.submit(hb, *hout[q % 2]))
+                    break
+                except phmm.PhmmError as e:  # two batches do not fit the memory budget
+                    if e.status != phmm.PHMM_EBUSY or not pend:
+                        raise
+                    overlap[0] = False
+                    if ctx.poll(pend.pop(0), -1) != 0:
+                        raise RuntimeError("e2e step failed")
+            if len(pend) == 2 and ctx.poll(pend.pop(0), -1) != 0:
+                raise RuntimeError("e2e step failed")
+        while pend:
+            if ctx.poll(pend.pop(0), -1) != 0:
+                raise RuntimeError("e2e step failed")
+
+    e2e_run(2)  # first copies into both slots' input arenas
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for _ in range(n_e2e):
-        e2e_step()
+    e2e_run(n_e2e)
     e2e_ms = (time.perf_counter() - t0) * 1e3 / n_e2e
     e2e_ms = max_over_ranks([e2e_ms], world)[0]
     e2e_value = job_throughput(cells, world, e2e_ms)
-    e2e_ok = bool(np.array_equal(np.nan_to_num(ho, nan=7.0), np.nan_to_num(res, nan=7.0)) or
-                  np.max(np.abs(ho - res)) <= TOL32)
+    e2e_ok = all(bool(np.array_equal(np.nan_to_num(ho, nan=7.0), np.nan_to_num(res, nan=7.0)) or
+                      np.max(np.abs(ho - res)) <= TOL32) for ho, _ in hout)
     ctx.close()
     del hb
     if rank != 0:
@@ -652,7 +667,9 @@ def run_ours(args):
         "e2e": {"value": e2e_value, "unit": "GCUPS", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "ms_per_step": e2e_ms, "matches_device_run": e2e_ok,
                 "how": "phmm_submit_batch/phmm_poll with pinned host inputs and pinned host outputs, "
-                       "one batch in flight, %d steps, H2D and D2H inside the timed region" % n_e2e},
+                       "%s, %d steps, every step's H2D and D2H inside the timed region"
+                       % ("two batches in flight (a step's upload overlaps the previous step's kernels)"
+                          if overlap[0] else "one batch in flight (two exceed the memory budget)", n_e2e)},
         "gpu_launches": int(sum(s["kernel_launches"] for s in sts)),
         "clocks": clocks,
         "step": {"gcups_forward": cells / float(ms_fwd.mean()) / 1e6, "ms_forward": float(ms_fwd.mean()),

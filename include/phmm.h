@@ -359,7 +359,8 @@ void phmm_server_destroy(phmm_server *srv);
  *            call on a device looks up the scratch addresses (cudaGetSymbolAddress), so
  *            make that first call outside any stream capture.
  *   stream   cudaStream_t to run on (NULL = legacy default stream); the call waits for
- *            its own work to finish before returning.
+ *            its own work to finish before returning (it reads its status word back), so
+ *            it blocks the host and cannot be captured into a CUDA graph.
  *   batch    as for phmm_submit_batch, with inputs_on_device = outputs_on_device = 1 (all
  *            pointers are device pointers) and out_flags required.
  * Offsets are checked on the device before they are used: a pair whose read or

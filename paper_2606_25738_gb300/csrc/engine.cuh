@@ -1162,18 +1162,19 @@ __device__ SegOut team_run_pipe2(const Rec32J* __restrict__ rec, int l, int lmax
         if constexpr (LINK) {
             // Stage blocks of 32 rows (records and left boundary), two buffers: block b
             // is copied while block b - 1 is computed and waited for at b - 1's last row.
-            const int blk = (i - 1) >> 5, r0 = (i - 1) & 31;
-            if (r0 == 0) {
+            // Row i sits in slot (i - 1) mod 64 of the two buffers taken together.
+            const int slot = (i - 1) & 63;
+            if ((slot & 31) == 0) {
                 __syncwarp();  // every lane is done with block b - 1's buffer
                 const int r = i + 32 + lt;
-                const int nb = (blk + 1) & 1;
+                const int ns = (slot + 32 + lt) & 63;  // row r's slot
                 const float4* src = reinterpret_cast<const float4*>(rec + min(r - 1, l1));
-                cp_async16_cg(rstg + nb * 64 + 2 * lt, src);
-                cp_async16_cg(rstg + nb * 64 + 2 * lt + 1, src + 1);
-                if (has_left && r <= l) cp_async16_cg(stg + nb * 32 + lt, sin + (r - 1));
+                cp_async16_cg(rstg + 2 * ns, src);
+                cp_async16_cg(rstg + 2 * ns + 1, src + 1);
+                if (has_left && r <= l) cp_async16_cg(stg + ns, sin + (r - 1));
                 cp_async_commit();
             }
-            const float4 a = rstg[(blk & 1) * 64 + 2 * r0], b = rstg[(blk & 1) * 64 + 2 * r0 + 1];
+            const float4 a = rstg[2 * slot], b = rstg[2 * slot + 1];
             cur.pm = a.x; cur.px = a.y; cur.a = a.z; cur.b = a.w;
             cur.h = b.x; cur.g = b.y; cur.mi = b.z; cur.meta = __float_as_uint(b.w);
         } else if constexpr (L1P) {
@@ -1347,8 +1348,7 @@ __device__ SegOut team_run_pipe2(const Rec32J* __restrict__ rec, int l, int lmax
             float lM = 0.f, lJ = 0.f, lD = 0.f;
             int Eleft = INT_MIN;
             if (has_left) {
-                const int blk = (i - 1) >> 5;
-                const float4 v = stg[(blk & 1) * 32 + ((i - 1) & 31)];  // one broadcast read
+                const float4 v = stg[(i - 1) & 63];  // one broadcast read
                 lM = v.x;
                 lJ = v.y;
                 lD = v.z;
