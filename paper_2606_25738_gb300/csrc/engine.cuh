@@ -1160,12 +1160,14 @@ __device__ SegOut team_run_pipe2(const Rec32J* __restrict__ rec, int l, int lmax
     for (int i = 1; i <= lmax; ++i) {
         Rec32J nxt;
         if constexpr (LINK) {
-            // Stage blocks of 32 rows (records and left boundary), two buffers: block b
-            // is copied while block b - 1 is computed and waited for at b - 1's last row.
-            // Row i sits in slot (i - 1) mod 64 of the two buffers taken together.
+            // Stage blocks of 32 rows (records and left boundary), two buffers: block b + 1
+            // is copied while block b is computed; at block b's first row the warp waits
+            // for block b (issued 32 rows earlier) and then issues block b + 1.  Row i
+            // sits in slot (i - 1) mod 64 of the two buffers taken together.
             const int slot = (i - 1) & 63;
             if ((slot & 31) == 0) {
-                __syncwarp();  // every lane is done with block b - 1's buffer
+                cp_async_wait_0();
+                __syncwarp();  // block b has landed; every lane is done with block b - 1's buffer
                 const int r = i + 32 + lt;
                 const int ns = (slot + 32 + lt) & 63;  // row r's slot
                 const float4* src = reinterpret_cast<const float4*>(rec + min(r - 1, l1));
@@ -1325,12 +1327,6 @@ __device__ SegOut team_run_pipe2(const Rec32J* __restrict__ rec, int l, int lmax
             const float up = __shfl_up_sync(kFull, Z, 1 << s);
             Z = fmaf(up * P_sp1(s), P_sp2(s), Z);
         }
-        if constexpr (LINK) {  // row i + 1's block is complete before it starts
-            if ((i & 31) == 0) {
-                cp_async_wait_0();
-                __syncwarp();
-            }
-        }
         if constexpr (!FUSE) {  // phase A: row i + 1's partials and insertions
             const float2 na2 = make_float2(nxt.a, nxt.a), nh2 = make_float2(nxt.h, nxt.h);
             const float mal = M2[H - 1].x, jal = J2[H - 1].x;
@@ -1385,25 +1381,25 @@ __device__ SegOut team_run_pipe2(const Rec32J* __restrict__ rec, int l, int lmax
                 }
                 if (Enew == INT_MIN) Enew = E;
                 if (!forced && e != INT_MIN && e != INT_MAX && e <= rng.danger) flags |= PF_DANGER;
+                if (Enew != E) {  // only a checkpoint row changes the exponent
+                    const int sdn = E - Enew;
+#pragma unroll
+                    for (int q = 0; q < H; ++q) {
+                        M2[q] = make_float2(scale2(M2[q].x, sdn), scale2(M2[q].y, sdn));
+                        J2[q] = make_float2(scale2(J2[q].x, sdn), scale2(J2[q].y, sdn));
+                    }
+                    nm = scale2(nm, sdn);
+                    nj = scale2(nj, sdn);
+                    zz = scale2(zz, sdn);
+                    yp = scale2(yp, sdn);
+                    yA = scale2(yA, sdn);
+                    ypl = scale2(ypl, sdn);
+                    jl = scale2(jl, sdn);
+                    flags |= PF_RESCALED;
+                    E = Enew;
+                }
             }
             --until;
-            if (Enew != E) {
-                const int sdn = E - Enew;
-#pragma unroll
-                for (int q = 0; q < H; ++q) {
-                    M2[q] = make_float2(scale2(M2[q].x, sdn), scale2(M2[q].y, sdn));
-                    J2[q] = make_float2(scale2(J2[q].x, sdn), scale2(J2[q].y, sdn));
-                }
-                nm = scale2(nm, sdn);
-                nj = scale2(nj, sdn);
-                zz = scale2(zz, sdn);
-                yp = scale2(yp, sdn);
-                yA = scale2(yA, sdn);
-                ypl = scale2(ypl, sdn);
-                jl = scale2(jl, sdn);
-                flags |= PF_RESCALED;
-                E = Enew;
-            }
             // left values into this strip's scale (no left: zeros stay zero)
             const int dsh = has_left ? Eleft - E : 0;
             if (dsh != 0) {  // warp-uniform; the scales differ only after a checkpoint
