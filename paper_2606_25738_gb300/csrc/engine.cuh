@@ -1138,6 +1138,7 @@ __device__ SegOut team_run_pipe2(const Rec32J* __restrict__ rec, int l, int lmax
     float sp1[5], sp2[5], last1 = 0.f, last2 = 0.f, hh1 = 0.f, hh2 = 0.f, hm1 = 0.f, hm2 = 0.f;
     int gcp = -1;
     float qa1 = 0.f, qa2 = 0.f;
+    float lsc = 1.f;  // LINK: 2^(E_left - E), constant between checkpoints
     const int l1 = max(l, 1) - 1;
     if constexpr (LINK) {
         // block 0 (rows 1..32): records and, with a left strip, its boundary rows
@@ -1285,7 +1286,7 @@ __device__ SegOut team_run_pipe2(const Rec32J* __restrict__ rec, int l, int lmax
         // Eq. 4 when a pair of this warp finishes (I = T_MI J on the last row); a strip
         // of the serial kind is one pair on the whole warp
         bool ends;
-        if constexpr (LINK) ends = (i == l);
+        if constexpr (LINK) ends = false;  // one pair on the whole warp: summed after the loop
         else ends = __any_sync(kFull, i == l);
         if (ends) {
             const double rmi = (double)cur.mi;
@@ -1398,15 +1399,17 @@ __device__ SegOut team_run_pipe2(const Rec32J* __restrict__ rec, int l, int lmax
                     flags |= PF_RESCALED;
                     E = Enew;
                 }
+                // both exponents change only on checkpoint rows (the same rows in every
+                // strip of the pair), so the left values' scale 2^(E_left - E) <= 1 is
+                // formed here (exactly, subnormal or zero below 2^-126) and kept
+                const int dsh = has_left ? Eleft - E : 0;
+                lsc = dsh >= -126 ? NT::pow2(dsh) : dsh >= -149 ? __uint_as_float(1u << (dsh + 149)) : 0.f;
             }
             --until;
             // left values into this strip's scale (no left: zeros stay zero)
-            const int dsh = has_left ? Eleft - E : 0;
-            if (dsh != 0) {  // warp-uniform; the scales differ only after a checkpoint
-                lM = scale2(lM, dsh);
-                lJ = scale2(lJ, dsh);
-                lD = scale2(lD, dsh);
-            }
+            lM *= lsc;
+            lJ *= lsc;
+            lD *= lsc;
             const float Wseg = fmaf(rg, lD, lM);  // D-hat at the strip's first column
             float ndA = fmaf(zz * P_last1(), P_last2(), yp);
             ndA = fmaf(Wseg * qa1, qa2, ndA);
@@ -1477,7 +1480,25 @@ __device__ SegOut team_run_pipe2(const Rec32J* __restrict__ rec, int l, int lmax
         gprev = rg;
         if constexpr (!LINK && !L1P) cur = nxt;
     }
-    if constexpr (LINK) cp_async_wait_0();  // nothing may land in the stage after this strip
+    if constexpr (LINK) {
+        cp_async_wait_0();  // nothing may land in the stage after this strip
+        // Eq. 4 on the pair's last row l (= lmax; a checkpoint on it rescaled M, J and E
+        // together, and its flags count)
+        const double rmi = (double)cur.mi;
+        double s = 0.0;
+#pragma unroll
+        for (int q = 0; q < H; ++q) {
+            if (q < nvalid) s += (double)M2[q].x + rmi * (double)J2[q].x;
+            if (q + H < nvalid) s += (double)M2[q].y + rmi * (double)J2[q].y;
+        }
+        s = team_sum<double>(s, lt, tlast, nsteps);
+        uint32_t f = flags;
+        if (mflags & META_BAD) f |= PF_BAD;
+        if (mflags & META_DEGEN) f |= PF_DEGEN;
+        out.S = s;
+        out.E = E;
+        out.flags = team_or(f, lt, tlast, nsteps);
+    }
     return out;
 }
 
