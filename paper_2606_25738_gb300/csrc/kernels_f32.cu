@@ -54,39 +54,98 @@ __device__ __forceinline__ void store_rec32j(Rec32J* dst, const Rec32J& r) {
 
 // One record per read base (both FP32 layouts), plus pair descriptors and the batch's
 // drop / grow maxima.
-__global__ void __launch_bounds__(256) k_prep32(const BatchHeader* __restrict__ H,
-                                                const PhredTables* __restrict__ TG) {
+// Input staging of the prep kernel: a tile of kPrepTile read bases of each byte stream
+// (bases and the four quality strings) and the 16 bytes before it, copied into shared
+// memory with 16-byte loads where the chunk is aligned and inside the array (byte loads
+// at unaligned or ragged edges, zeros outside), so each thread then reads its bases from
+// shared memory and the records it writes stay consecutive across the warp.
+constexpr int kPrepThreads = 256, kPrepTile = kPrepThreads * 16;
+__device__ __forceinline__ void stage_bytes(const uint8_t* __restrict__ src, uint64_t n, uint64_t t0,
+                                            uint4* __restrict__ dst) {
+    const bool al = ((uintptr_t)src & 15u) == 0;
+    for (int c = threadIdx.x; c < kPrepTile / 16 + 1; c += blockDim.x) {
+        const int64_t g = (int64_t)t0 - 16 + 16 * (int64_t)c;  // first byte of chunk c
+        uint4 v;
+        if (al && g >= 0 && g + 16 <= (int64_t)n) {
+            v = __ldg(reinterpret_cast<const uint4*>(src + g));
+        } else {
+            uint32_t w[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {
+                const int64_t bi = g + q;
+                const uint32_t byte = (bi >= 0 && bi < (int64_t)n) ? (uint32_t)src[bi] : 0u;
+                w[q >> 2] |= byte << (8 * (q & 3));
+            }
+            v = make_uint4(w[0], w[1], w[2], w[3]);
+        }
+        dst[c] = v;
+    }
+}
+
+__global__ void __launch_bounds__(kPrepThreads) k_prep32(const BatchHeader* __restrict__ H,
+                                                         const PhredTables* __restrict__ TG) {
     __shared__ Tables32 T;
+    __shared__ uint4 sb[5][kPrepTile / 16 + 1];  // bases, Q, ins, del, gcp; byte 16 = tile start
     stage_tables32(TG, T);
     const float2 *tq = T.tq, *tom = T.tom, *tq3 = T.tq3, *tinv = T.tinv;
     Rec32J* const rj = H->rec32j;
     uint32_t dmax = 0, gmax = 0, jmax = 0, hmax = 0;
     const uint64_t n = H->n_read_bases;
     const uint32_t seed = H->seed;
-    for (uint64_t b = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; b < n;
-         b += (uint64_t)gridDim.x * blockDim.x) {
-        const BaseQ x = base_inputs(H, b);
-        if (H->rec32) {
-            const Rec32 r = make_rec32(x, tq, tom, tq3, tinv, seed, b);
-            float4* dst = reinterpret_cast<float4*>(H->rec32 + b);
-            dst[0] = make_float4(r.pm, r.px, r.a, r.b);
-            dst[1] = make_float4(r.mi, r.g, r.gm, __uint_as_float(r.meta));
+    const uint8_t* const s8[5] = {H->read_bases, H->base_q, H->ins_q, H->del_q, H->gcp_q};
+    for (uint64_t t0 = (uint64_t)blockIdx.x * kPrepTile; t0 < n; t0 += (uint64_t)gridDim.x * kPrepTile) {
+        __syncthreads();  // the previous tile's reads are done
+#pragma unroll
+        for (int q = 0; q < 5; ++q) stage_bytes(s8[q], n, t0, sb[q]);
+        __syncthreads();
+        const uint8_t* const sbase = reinterpret_cast<const uint8_t*>(sb[0]);
+        const uint8_t* const sq = reinterpret_cast<const uint8_t*>(sb[1]);
+        const uint8_t* const si = reinterpret_cast<const uint8_t*>(sb[2]);
+        const uint8_t* const sd = reinterpret_cast<const uint8_t*>(sb[3]);
+        const uint8_t* const sg = reinterpret_cast<const uint8_t*>(sb[4]);
+        for (int m = 0; m < kPrepTile / kPrepThreads; ++m) {
+            const int o = 16 + m * kPrepThreads + (int)threadIdx.x;  // byte of base b in the stage
+            const uint64_t b = t0 + (uint64_t)(o - 16);
+            if (b >= n) break;
+            // the same fields and clamps as base_inputs(), from the staged bytes
+            BaseQ x;
+            x.code = read_code(sbase[o]);
+            x.Q = sq[o];
+            x.ins = si[o];
+            x.del = sd[o];
+            x.gcp = sg[o];
+            x.delp = b > 0 ? sd[o - 1] : 0;
+            x.insp = b > 0 ? si[o - 1] : si[o];
+            x.bad = x.code < 0 || x.Q > kMaxPhred || x.ins > kMaxPhred || x.del > kMaxPhred || x.gcp > kMaxPhred;
+            x.code = x.code < 0 ? 4 : x.code;
+            x.Q = min(x.Q, kMaxPhred);
+            x.ins = min(x.ins, kMaxPhred);
+            x.del = min(x.del, kMaxPhred);
+            x.gcp = min(x.gcp, kMaxPhred);
+            x.delp = min(x.delp, kMaxPhred);
+            x.insp = min(x.insp, kMaxPhred);
+            if (H->rec32) {
+                const Rec32 r = make_rec32(x, tq, tom, tq3, tinv, seed, b);
+                float4* dst = reinterpret_cast<float4*>(H->rec32 + b);
+                dst[0] = make_float4(r.pm, r.px, r.a, r.b);
+                dst[1] = make_float4(r.mi, r.g, r.gm, __uint_as_float(r.meta));
+            }
+            if (rj) {
+                const Rec32J r2 = make_rec32j(x, tq, tom, tq3, tinv, T.tiq, seed, b, false);
+                store_rec32j(rj + b, r2);
+                // range of the pipelined engine's intermediates relative to the row maximum
+                const float om = fmaxf(1.0f - r2.g, 0x1p-60f);
+                const float big = fmaxf(fmaxf(fabsf(r2.a), fabsf(r2.b) / om), T.tiq[x.insp].x);
+                jmax = max(jmax, (uint32_t)fmaxf(ceilf(log2f(fmaxf(big, 1.0f))), 0.0f));
+                hmax = max(hmax, (uint32_t)ceilf(log2f(1.0f + fabsf(r2.h)) * 64.0f) + 1u);
+            }
+            if (x.bad) atomicOr(H->status, ST_BAD_INPUT);
+            const float qi = tq[x.ins].x, qd = tq[x.del].x, qg = tq[x.gcp].x;
+            const float drop = -log2f(fminf(qi, qg));
+            const float grow = log2f(fmaxf(fabsf(1.0f - qi - qd) + (1.0f - qg) + qd, qi + qg));
+            dmax = max(dmax, (uint32_t)ceilf(fmaxf(drop, 0.0f) * 64.0f) + 1u);
+            gmax = max(gmax, (uint32_t)ceilf(fmaxf(grow, 0.0f) * 64.0f) + 1u);
         }
-        if (rj) {
-            const Rec32J r2 = make_rec32j(x, tq, tom, tq3, tinv, T.tiq, seed, b, false);
-            store_rec32j(rj + b, r2);
-            // range of the pipelined engine's intermediates relative to the row maximum
-            const float om = fmaxf(1.0f - r2.g, 0x1p-60f);
-            const float big = fmaxf(fmaxf(fabsf(r2.a), fabsf(r2.b) / om), T.tiq[x.insp].x);
-            jmax = max(jmax, (uint32_t)fmaxf(ceilf(log2f(fmaxf(big, 1.0f))), 0.0f));
-            hmax = max(hmax, (uint32_t)ceilf(log2f(1.0f + fabsf(r2.h)) * 64.0f) + 1u);
-        }
-        if (x.bad) atomicOr(H->status, ST_BAD_INPUT);
-        const float qi = tq[x.ins].x, qd = tq[x.del].x, qg = tq[x.gcp].x;
-        const float drop = -log2f(fminf(qi, qg));
-        const float grow = log2f(fmaxf(fabsf(1.0f - qi - qd) + (1.0f - qg) + qd, qi + qg));
-        dmax = max(dmax, (uint32_t)ceilf(fmaxf(drop, 0.0f) * 64.0f) + 1u);
-        gmax = max(gmax, (uint32_t)ceilf(fmaxf(grow, 0.0f) * 64.0f) + 1u);
     }
     block_max2(dmax, gmax, H->dropgrow);
     __syncthreads();
@@ -174,7 +233,7 @@ void launch_wait_test(const void* bnd, uint32_t* status, cudaStream_t s) {
 void launch_reset(const BatchHeader* H, int grid, cudaStream_t s) { k_reset<<<grid, 256, 0, s>>>(H); }
 
 void launch_prep32(const BatchHeader* H, const PhredTables* T, int grid, cudaStream_t s) {
-    k_prep32<<<grid, 256, 0, s>>>(H, T);
+    k_prep32<<<grid, kPrepThreads, 0, s>>>(H, T);
 }
 
 void launch_prep32_first(const BatchHeader* H, const PhredTables* T, int grid, cudaStream_t s) {
