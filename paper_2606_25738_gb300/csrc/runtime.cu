@@ -1309,13 +1309,14 @@ int phmm_submit_batch(phmm_ctx* ctx, const phmm_batch* b, uint64_t* ticket) {
             for (auto& cd : tune_cand) runs.push_back({cd.first, cd.second, bl});
         const size_t n_short = runs.size();
         if (tune_long) {
-            // the serial kind needs several multi-warp pairs per resident warp: with fewer
-            // it leaves most of the GPU idle, so it is not worth a (long) trial run
+            // the serial kind needs about one multi-warp pair per resident warp or more:
+            // with far fewer it leaves most of the GPU idle, so it is not worth a (long)
+            // trial run (at half as many pairs as warps it can still win: measured)
             const uint64_t swarps = (uint64_t)ctx->sms * ctx->occ_longk[3] * (kSerialThreads / 32);
             // the 4-warp-CTA kind pays off only for a few very wide pairs (it spreads them over
             // more SMs); with many wide pairs it is not worth a trial run either
             for (int lk : long_kinds_of(ctx->cfg)) {
-                if (kLongSerial[lk] && (uint64_t)P.n_long < 2 * swarps) continue;
+                if (kLongSerial[lk] && 2 * (uint64_t)P.n_long < swarps) continue;
                 if ((lk == 4 || lk == 5) && (uint64_t)P.n_long >= swarps) continue;
                 runs.push_back({-1, -1, lk});
             }
