@@ -1102,16 +1102,38 @@ __device__ __forceinline__ float2 fmul2_sel(float2 a, float2 b) {
 // boundary and record as broadcasts (no record is held in registers across a row).
 // The lane's carry power g^(N lt - 1) stays in registers (reloaded when gcp changes):
 // reading it from L1 every row measured 2% slower on the 1M-pair uneven batch.
-template <int N, bool PACKED, bool LINK = false, bool FUSE = LINK, bool L1P = false>
+// Progress of a strip of the wave kind (the rows whose boundary it has stored): released
+// by its writer after those stores, acquired by the right neighbour before it copies them.
+__device__ __forceinline__ unsigned long long ld_acquire_gpu(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_gpu(unsigned long long* p, unsigned long long v) {
+    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+// Waits (bounded, with backoff) until the left strip has stored rows 1..need.
+__device__ __forceinline__ bool wave_wait(const unsigned long long* p, unsigned long long need) {
+    long long spins = 0;
+    while (ld_acquire_gpu(p) < need) {
+        if (++spins > kSpinLimit) return false;
+        if (spins > kSpinFast) __nanosleep(64);
+    }
+    return true;
+}
+
+template <int N, bool PACKED, bool LINK = false, bool FUSE = LINK, bool L1P = false, bool WAVE = false>
 __device__ SegOut team_run_pipe2(const Rec32J* __restrict__ rec, int l, int lmax,
                                  const uint8_t* __restrict__ hap, int k, int col0, int lt,
                                  int tlast, int nsteps, const PowRow<float>* __restrict__ pow_tab,
                                  const PipeRange& rng, const float4* sin = nullptr, float4* sout = nullptr,
                                  bool has_left = false, bool has_right = false, float4* stg = nullptr,
-                                 float4* rstg = nullptr) {
+                                 float4* rstg = nullptr, const unsigned long long* prog_left = nullptr,
+                                 unsigned long long* prog_me = nullptr, uint32_t* status = nullptr) {
     using NT = Num<float>;
     static_assert(N <= 32 && N % 2 == 0, "match masks hold 32 columns; two halves");
     static_assert(FUSE || !(LINK || L1P), "the serial strips and the L1 tables need the fused row");
+    static_assert(LINK || !WAVE, "the wave kind runs strips in link mode");
     constexpr int H = N / 2;
     uint32_t bmA = 0, bmC = 0, bmG = 0, bmT = 0, flags = rng.ok ? 0u : PF_DEGEN, mflags = 0;
     const int nvalid = max(0, min(k - col0, N));
@@ -1145,6 +1167,12 @@ __device__ SegOut team_run_pipe2(const Rec32J* __restrict__ rec, int l, int lmax
         const float4* src = reinterpret_cast<const float4*>(rec + min(lt, l1));
         cp_async16_cg(rstg + 2 * lt, src);
         cp_async16_cg(rstg + 2 * lt + 1, src + 1);
+        if constexpr (WAVE) {  // the left strip runs concurrently: its rows 1..32 first
+            if (has_left && !wave_wait(prog_left, (unsigned long long)min(l, 32))) {
+                flags |= PF_TIMEOUT;
+                atomicOr(status, ST_TIMEOUT);
+            }
+        }
         if (has_left && lt + 1 <= l) cp_async16_cg(stg + lt, sin + lt);
         cp_async_commit();
         cp_async_wait_0();
@@ -1174,6 +1202,12 @@ __device__ SegOut team_run_pipe2(const Rec32J* __restrict__ rec, int l, int lmax
                 const float4* src = reinterpret_cast<const float4*>(rec + min(r - 1, l1));
                 cp_async16_cg(rstg + 2 * ns, src);
                 cp_async16_cg(rstg + 2 * ns + 1, src + 1);
+                if constexpr (WAVE) {  // the next block's rows of the concurrent left strip
+                    if (has_left && i + 32 <= l && !wave_wait(prog_left, (unsigned long long)min(l, i + 63))) {
+                        flags |= PF_TIMEOUT;
+                        atomicOr(status, ST_TIMEOUT);
+                    }
+                }
                 if (has_left && r <= l) cp_async16_cg(stg + ns, sin + (r - 1));
                 cp_async_commit();
             }
@@ -1423,6 +1457,9 @@ __device__ SegOut team_run_pipe2(const Rec32J* __restrict__ rec, int l, int lmax
                 // column before it, carry included) over its N columns, g^N ndA + ypl
                 const float dl = fmaf((ndA * rg) * P_last1(), P_last2(), ypl);
                 __stcg(sout + (i - 1), make_float4(M2[H - 1].y, jl, dl, __int_as_float(E)));
+                if constexpr (WAVE) {  // rows 1..i stored: publish at block ends and the last row
+                    if ((i & 31) == 0 || i == l) st_release_gpu(prog_me, (unsigned long long)i);
+                }
             }
             const float wl = fmaf(rg, ndA, nm);         // D-hat at the lane's first column
             const float ndB = fmaf(wl * P_hm1(), P_hm2(), yA);  // D-hat at the first half's last column

@@ -692,6 +692,50 @@ k_forward_serial(const BatchHeader* __restrict__ H, const PowRow<float>* __restr
     }
 }
 
+// Wave multi-warp kind (long kind 6): every 1024-column strip of a wide pair is its own
+// item, on its own warp, and the strips of a pair run at the same time.  Strip s stores its
+// right boundary row by row (float4: M, J, D-hat, E of its last column) at wbnd + bnd_out
+// and releases its progress (rows stored) in boundary word `pad` at every 32nd row and the
+// last; strip s + 1 acquires that word before it copies the next 32 rows of the boundary
+// (team_run_pipe2<..., WAVE>), so the strips hand over once per 32 rows.  Items are taken
+// in order and a pair's strips are consecutive: a strip only waits for a strip that some
+// warp already runs, so every wait ends (and each one is bounded).
+template <int N, int MINB>
+__global__ void __launch_bounds__(128, MINB)
+k_forward_wave(const BatchHeader* __restrict__ H, const PowRow<float>* __restrict__ pow) {
+    __shared__ float4 stage[4][64];    // per warp: two blocks of 32 left-boundary rows
+    __shared__ float4 rstage[4][128];  // per warp: two blocks of 32 records (32 B each)
+    const PipeRange rng = pipe_range(H->dropgrow);
+    const uint32_t n_c = H->n_citems;
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+        uint32_t wi = 0;
+        if (lane == 0) wi = atomicAdd(&H->counters[0], 1u);
+        wi = __shfl_sync(kFull, wi, 0);
+        if (wi >= n_c) break;
+        const CtaPair cp = H->cpairs[H->citems[wi].first];
+        const PairDesc d = H->desc[cp.pair];
+        const uint32_t s = cp.strip, S = cp.nstrip;
+        const bool has_left = s > 0, has_right = s + 1 < S;
+        const float4* in = has_left ? H->wbnd + cp.bnd_in : nullptr;
+        float4* outb = has_right ? H->wbnd + cp.bnd_out : nullptr;
+        const unsigned long long* pl = has_left ? H->bnd + (cp.pad - 1) : nullptr;
+        unsigned long long* pm = has_right ? H->bnd + cp.pad : nullptr;
+        const int c0 = (int)cp.col0 + lane * N;
+        const SegOut o = team_run_pipe2<N, true, true, true, false, true>(
+            H->rec32j + d.roff, (int)d.l, (int)d.l, H->hap_bases + d.hoff, (int)d.k, c0, lane, 31, 5, pow, rng,
+            in, outb, has_left, has_right, stage[threadIdx.x >> 5], rstage[threadIdx.x >> 5], pl, pm, H->status);
+        __syncwarp();
+        if (lane == 0) {
+            Partial p;
+            p.S = o.S;
+            p.E = o.E;
+            p.flags = o.flags | PF_DONE;
+            write_strip_part(H, cp.pair, s, S, cp.extra_base, p);
+        }
+    }
+}
+
 // Team lookup of a warp item: this lane's team (first lane, size, pairs) and the scan
 // steps of the widest team.
 struct TeamOf {

@@ -173,6 +173,7 @@ template __global__ void k_forward<float, kNLong32, false>(const BatchHeader*, c
 template __global__ void k_forward_pipe<32, kCtaWarpsPipe>(const BatchHeader*, const PowRow<float>*);
 template __global__ void k_forward_pipe<24, kCtaWarps>(const BatchHeader*, const PowRow<float>*);
 template __global__ void k_forward_serial<32, 3>(const BatchHeader*, const PowRow<float>*);
+template __global__ void k_forward_wave<32, 3>(const BatchHeader*, const PowRow<float>*);
 template __global__ void k_forward_pipe<32, 4>(const BatchHeader*, const PowRow<float>*);
 template __global__ void k_forward_cluster<32, kClusterWarps, kClusterCtas>(const BatchHeader*, const PowRow<float>*);
 template __global__ void k_short_scalar<32, 4>(const BatchHeader*, const PowRow<float>*);
@@ -248,6 +249,7 @@ void launch_forward32_long_pipe(int kind, const BatchHeader* H, const void* pow,
     const PowRow<float>* p = static_cast<const PowRow<float>*>(pow);
     if (kind == 5) k_forward_cluster<32, kClusterWarps, kClusterCtas><<<grid, kClusterWarps * 32, 0, s>>>(H, p);
     else if (kind == 3) k_forward_serial<32, 3><<<grid, kSerialThreads, 0, s>>>(H, p);
+    else if (kind == 6) k_forward_wave<32, 3><<<grid, kSerialThreads, 0, s>>>(H, p);
     else if (kind == 4) k_forward_pipe<32, 4><<<grid, 4 * 32, 0, s>>>(H, p);
     else if (kind == 2) k_forward_pipe<24, kCtaWarps><<<grid, kCtaWarps * 32, 0, s>>>(H, p);
     else k_forward_pipe<32, kCtaWarpsPipe><<<grid, kCtaWarpsPipe * 32, 0, s>>>(H, p);
@@ -334,6 +336,8 @@ int occupancy_forward32_long_pipe(int kind) {
     }
     if (kind == 3)
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_forward_serial<32, 3>, kSerialThreads, 0);
+    else if (kind == 6)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_forward_wave<32, 3>, kSerialThreads, 0);
     else if (kind == 4)
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_forward_pipe<32, 4>, 4 * 32, 0);
     else if (kind == 2)

@@ -205,6 +205,7 @@ struct BatchHeader {
     uint64_t n_bnd_words;
     unsigned long long *rbnd;   // rescue / single-launch scratch: 2 boundaries per CTA
     uint64_t rbnd_words_per_cta;
+    float4 *wbnd;            // strips of the wave kind: each strip's right boundary (l rows)
     float4 *sbnd;            // serial multi-warp pairs: 2 strip boundaries of sbnd_rows rows
     uint32_t sbnd_rows;      // per resident warp of k_forward_serial (not cleared)
     uint32_t sbnd_warps;     // warps the scratch holds (the kernel's grid x warps per CTA)

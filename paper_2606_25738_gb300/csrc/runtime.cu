@@ -97,6 +97,7 @@ struct Plan {
     uint32_t n_extra = 0;     // extra partial slots (strips 1.. of wide pairs)
     int long_kind = 0;        // FP32 multi-warp kernel (launch.h: kLongN / kLongCW)
     uint32_t serial_rows = 0; // long kind 3: longest read among the serial pairs
+    uint64_t wave_rows = 0;   // long kind 6: boundary rows of all strips (float4 each)
     uint64_t cells_br[3] = {0, 0, 0};  // cells of the scalar, packed and multi-warp branches
     bool fp64 = false;        // an FP64 plan (scal_id = the FP64 variant)
 };
@@ -186,7 +187,7 @@ static void pack_teams(std::vector<Team>& run_teams, std::vector<uint32_t>& run_
 // CTA, packed best-fit into CTAs of CW warps (wider pairs: strips of CW warps).  Items
 // are ordered longest first.
 void make_plan(const uint32_t* l, const uint32_t* k, const uint32_t* pr, uint32_t n, int Ns, int NP,
-               int Nl, Plan& P, int kw = 4, int CW = kCtaWarps, bool serial = false) {
+               int Nl, Plan& P, int kw = 4, int CW = kCtaWarps, bool serial = false, bool wave = false) {
     P = Plan();
     P.N = Ns;
     P.NP = NP;
@@ -262,6 +263,37 @@ void make_plan(const uint32_t* l, const uint32_t* k, const uint32_t* pr, uint32_
         cp.bnd_out = kNoBnd;
         return cp;
     };
+    if (wave) {
+        // one item per strip of 32 Nl columns, the pairs largest first and each pair's
+        // strips in order, so a strip is always dequeued after the strip it waits for.
+        // Strip s writes its right boundary (l float4 rows) at wave row bnd_out and
+        // publishes its progress in boundary word `pad`; strip s + 1 reads both.
+        for (uint32_t p : lo) {
+            const uint32_t Wt = W_of(p);
+            const uint32_t extra = n + P.n_extra;
+            const uint64_t r0 = P.wave_rows, w0 = P.bnd_words;
+            for (uint32_t stp = 0; stp < Wt; ++stp) {
+                CtaPair cp = cpair(p, 0, 1);
+                cp.strip = (uint16_t)stp;
+                cp.nstrip = Wt;
+                cp.col0 = stp * seg;
+                cp.extra_base = extra;
+                cp.bnd_in = stp > 0 ? r0 + (uint64_t)(stp - 1) * l[p] : kNoBnd;
+                cp.bnd_out = stp + 1 < Wt ? r0 + (uint64_t)stp * l[p] : kNoBnd;
+                cp.pad = (uint32_t)(w0 + stp);
+                CtaItem it;
+                it.first = (uint32_t)P.cpairs.size();
+                it.n = 1;
+                P.cpairs.push_back(cp);
+                P.citems.push_back(it);
+            }
+            P.wave_rows += (uint64_t)(Wt - 1) * l[p];
+            P.bnd_words += Wt;
+            P.n_extra += Wt - 1;
+            P.cost += (double)l[p] * Wt * 32.0 * (Nl * kCellCost + kRowCost);
+        }
+        return;
+    }
     if (serial) {
         // one item per pair, largest first: a warp runs its W strips of 32 Nl columns in
         // order (strip s >= 1 leaves its partial at extra_base + s - 1)
@@ -448,6 +480,7 @@ struct Slot {
     DevBuf bnd;    // strip boundaries of the batch
     DevBuf rbnd;   // rescue / launch-per-pair boundary scratch
     DevBuf sbnd;   // serial multi-warp pairs: two boundaries per resident warp
+    DevBuf wbnd;   // wave multi-warp pairs: each strip's right boundary
     uint32_t sbnd_warps = 0, sbnd_rows = 0;  // what sbnd holds for the current plan
     DevBuf hdr;
     HostBuf h_out, h_oflags, h_small, h_roff, h_hoff, h_pr, h_ph;
@@ -501,7 +534,7 @@ struct phmm_ctx {
     int occ64v[kNumF64] = {1, 1, 1, 1};     // resident CTAs per SM of the FP64 forward variants
     int occ64s[kNumF64] = {1, 1, 1, 1};     // ... and of the pipelined FP64 short-team kernels
     // resident CTAs per SM of each kernel (long kind 5: resident clusters of the GPU)
-    int occ_packed[kNumPacked] = {}, occ_scalar[kNumScalar] = {}, occ_longk[kNumLong] = {1, 1, 1, 1, 1, 1}, occ64 = 1;
+    int occ_packed[kNumPacked] = {}, occ_scalar[kNumScalar] = {}, occ_longk[kNumLong] = {1, 1, 1, 1, 1, 1, 1}, occ64 = 1;
     std::map<uint64_t, std::array<int, 3>> tuned;  // batch signature -> (scalar id, packed id, long kind)
     uint64_t inflight_foot = 0;             // sum of pending slots' footprints
     bool dead = false;
@@ -529,7 +562,8 @@ int pow_index(int N) { return N == 12 ? 0 : N == 16 ? 1 : N == 20 ? 2 : N == 24 
 DevBuf* arena_bufs(Slot& S, int i) {
     DevBuf* d[] = {&S.in_bases, &S.in_bq, &S.in_iq, &S.in_dq, &S.in_gq, &S.in_hap, &S.in_roff, &S.in_hoff,
                    &S.in_pr, &S.in_ph, &S.desc, &S.rec32, &S.rec32j, &S.rec64, &S.rec64j, &S.teams, &S.witems, &S.witems2,
-                   &S.cpairs, &S.citems, &S.parts, &S.out, &S.oflags, &S.rescue, &S.bnd, &S.rbnd, &S.sbnd};
+                   &S.cpairs, &S.citems, &S.parts, &S.out, &S.oflags, &S.rescue, &S.bnd, &S.rbnd, &S.sbnd,
+                   &S.wbnd};
     return i < (int)(sizeof(d) / sizeof(d[0])) ? d[i] : nullptr;
 }
 
@@ -548,11 +582,16 @@ void release_arenas(Slot& S) {
 // Serial multi-warp pairs (long kind 3): two strip boundaries of serial_rows float4 rows
 // for every warp of k_forward_serial's grid.
 uint64_t serial_bytes(const phmm_ctx* ctx, const Plan& P) {
+    if (kLongWave[P.long_kind]) return P.wave_rows * sizeof(float4);
     if (!kLongSerial[P.long_kind] || P.citems.empty()) return 0;
     const uint64_t warps = (uint64_t)ctx->sms * ctx->occ_longk[P.long_kind] * (kSerialThreads / 32);
     return warps * 2 * P.serial_rows * sizeof(float4);
 }
 cudaError_t ensure_serial(const phmm_ctx* ctx, Slot& S, const Plan& P) {
+    if (kLongWave[P.long_kind]) {  // the wave kind's strip boundaries
+        S.sbnd_warps = S.sbnd_rows = 0;
+        return ensure(S.wbnd, std::max<uint64_t>(P.wave_rows, 1) * sizeof(float4));
+    }
     const uint64_t b = serial_bytes(ctx, P);
     if (b == 0) {
         S.sbnd_warps = S.sbnd_rows = 0;
@@ -696,6 +735,7 @@ void plan_header(const Slot& S, const Plan& P, BatchHeader& hh) {
     hh.sbnd = (float4*)S.sbnd.p;
     hh.sbnd_rows = S.sbnd_rows;
     hh.sbnd_warps = S.sbnd_warps;
+    hh.wbnd = (float4*)S.wbnd.p;
     // the Rec32 layout is read by the lean and packed short kernels and the lean
     // multi-warp kernel only; without them prep skips it
     const bool need32 = P.pack_id >= 0 || !kShortScalarPipe[P.scal_id] || (P.long_kind == 0 && !P.citems.empty());
@@ -767,7 +807,7 @@ void cluster_links(Plan& P) {
 void make_plan_id(const uint32_t* l, const uint32_t* k, const uint32_t* pr, uint32_t n, int scal_id,
                   int pack_id, int long_kind, Plan& P) {
     make_plan(l, k, pr, n, kShortScalarN[scal_id], pack_id >= 0 ? kShortPackedN[pack_id] : 0,
-              kLongN[long_kind], P, 4, kLongCW[long_kind], kLongSerial[long_kind]);
+              kLongN[long_kind], P, 4, kLongCW[long_kind], kLongSerial[long_kind], kLongWave[long_kind]);
     if (long_kind == 5) cluster_links(P);
     P.scal_id = scal_id;
     P.pack_id = pack_id;
@@ -786,8 +826,9 @@ std::vector<int> long_kinds_of(const phmm_config& cfg) {
     if (cfg.flags & PHMM_F_LONG_SERIAL) return {3};
     if (cfg.flags & PHMM_F_LONG_PIPE4) return {4};
     if (cfg.flags & PHMM_F_LONG_CLUSTER) return {5};
+    if (cfg.flags & PHMM_F_LONG_WAVE) return {6};
     if (cfg.kernel_variant == 3) return {0};
-    return {0, 1, 3, 4, 5};  // kind 2 only when forced: measured slower than kind 1 everywhere
+    return {0, 1, 3, 4, 5, 6};  // kind 2 only when forced: measured slower than kind 1 everywhere
 }
 // Without measurement: the serial kind when multi-warp pairs outnumber the resident
 // warps of k_forward_serial four times over (each warp then has several pairs to run),
@@ -849,7 +890,7 @@ int phmm_create(const phmm_config* cfg, phmm_ctx** out) {
     {
         const unsigned lk =
             cfg->flags & (PHMM_F_LONG_LEAN | PHMM_F_LONG_PIPE32 | PHMM_F_LONG_PIPE24 | PHMM_F_LONG_SERIAL |
-                          PHMM_F_LONG_PIPE4 | PHMM_F_LONG_CLUSTER);
+                          PHMM_F_LONG_PIPE4 | PHMM_F_LONG_CLUSTER | PHMM_F_LONG_WAVE);
         if (lk & (lk - 1)) return PHMM_EINVAL;  // more than one forced multi-warp kernel
     }
     {
@@ -910,6 +951,7 @@ int phmm_create(const phmm_config* cfg, phmm_ctx** out) {
     ctx->occ_longk[3] = occupancy_forward32_long_pipe(3);
     ctx->occ_longk[4] = occupancy_forward32_long_pipe(4);
     ctx->occ_longk[5] = occupancy_forward32_long_pipe(5);
+    ctx->occ_longk[6] = occupancy_forward32_long_pipe(6);
     if (getenv("PHMM_DEBUG")) {
         fprintf(stderr, "phmm: sms %d occupancy packed %d %d long %d %d %d %d %d fp64 %d scalar", ctx->sms,
                 ctx->occ_packed[0], ctx->occ_packed[1], ctx->occ_longk[0], ctx->occ_longk[1],
@@ -967,7 +1009,7 @@ void phmm_destroy(phmm_ctx* ctx) {
         DevBuf* d[] = {&S.in_bases, &S.in_bq, &S.in_iq, &S.in_dq, &S.in_gq, &S.in_hap, &S.in_roff,
                        &S.in_hoff, &S.in_pr, &S.in_ph, &S.desc, &S.rec32, &S.rec32j, &S.rec64, &S.rec64j, &S.teams,
                        &S.witems, &S.witems2, &S.cpairs, &S.citems, &S.parts, &S.out, &S.oflags, &S.rescue,
-                       &S.small, &S.hdr, &S.bnd, &S.rbnd, &S.sbnd};
+                       &S.small, &S.hdr, &S.bnd, &S.rbnd, &S.sbnd, &S.wbnd};
         for (auto* b : d) release(*b);
         HostBuf* h[] = {&S.h_out, &S.h_oflags, &S.h_small, &S.h_roff, &S.h_hoff, &S.h_pr, &S.h_ph};
         for (auto* b : h) release(*b);
@@ -1317,7 +1359,7 @@ int phmm_submit_batch(phmm_ctx* ctx, const phmm_batch* b, uint64_t* ticket) {
             // more SMs); with many wide pairs it is not worth a trial run either
             for (int lk : long_kinds_of(ctx->cfg)) {
                 if (kLongSerial[lk] && 2 * (uint64_t)P.n_long < swarps) continue;
-                if ((lk == 4 || lk == 5) && (uint64_t)P.n_long >= swarps) continue;
+                if ((lk == 4 || lk == 5 || lk == 6) && (uint64_t)P.n_long >= swarps) continue;
                 runs.push_back({-1, -1, lk});
             }
         }
@@ -1649,11 +1691,15 @@ int phmm_plan_check(const uint32_t* l, const uint32_t* k, const uint32_t* pair_r
     struct StripSeen {
         uint32_t nstrip = 0, count = 0, extra_base = 0;
         std::vector<int64_t> col0, width, item, w0;
-        std::vector<uint64_t> bin, bout;
+        std::vector<uint64_t> bin, bout, pad;
     };
     std::map<uint32_t, StripSeen> strips;
     std::vector<std::pair<uint64_t, uint64_t>> bnd_ranges, extra_ranges;
     const bool serial = precision != PHMM_PREC_FP64 && kLongSerial[long_kind];
+    // wave kind: one strip per item on one warp; boundaries are float4 rows of wbnd and
+    // each strip's progress is boundary word `pad` (consecutive within a pair)
+    const bool wave = precision != PHMM_PREC_FP64 && kLongWave[long_kind];
+    std::vector<std::pair<uint64_t, uint64_t>> prog_ranges;
     for (size_t it = 0; it < P.citems.size(); ++it) {
         const CtaItem& ci = P.citems[it];
         uint32_t used = 0;
@@ -1697,7 +1743,9 @@ int phmm_plan_check(const uint32_t* l, const uint32_t* k, const uint32_t* pair_r
                 sv.w0.assign(cp.nstrip, -1);
                 sv.bin.assign(cp.nstrip, 0);
                 sv.bout.assign(cp.nstrip, 0);
+                sv.pad.assign(cp.nstrip, 0);
             }
+            if (wave && (ci.n != 1 || cp.W != 1 || cp.w0 != 0)) return fail(31);
             if (cp.nstrip != sv.nstrip || cp.extra_base != sv.extra_base || cp.strip >= sv.nstrip ||
                 sv.item[cp.strip] >= 0)
                 return fail(15);
@@ -1707,6 +1755,7 @@ int phmm_plan_check(const uint32_t* l, const uint32_t* k, const uint32_t* pair_r
             sv.w0[cp.strip] = cp.w0;
             sv.bin[cp.strip] = cp.bnd_in;
             sv.bout[cp.strip] = cp.bnd_out;
+            sv.pad[cp.strip] = cp.pad;
             sv.count++;
         }
     }
@@ -1735,6 +1784,15 @@ int phmm_plan_check(const uint32_t* l, const uint32_t* k, const uint32_t* pair_r
                     return fail(24);
                 }
             }
+            if (wave) {
+                if (sv.pad[st] != sv.pad[0] + st) return fail(32);
+                if (st + 1 < sv.nstrip) {
+                    const uint64_t a = sv.bout[st], b = a + (uint64_t)l[p];
+                    if (b > P.wave_rows) return fail(25);
+                    bnd_ranges.push_back({a, b});
+                }
+                continue;
+            }
             if (st + 1 < sv.nstrip && !is_dsmem_bnd(sv.bout[st])) {
                 const uint64_t a = sv.bout[st], b = a + (uint64_t)l[p] * kw;
                 if (b > P.bnd_words) return fail(25);
@@ -1742,6 +1800,10 @@ int phmm_plan_check(const uint32_t* l, const uint32_t* k, const uint32_t* pair_r
             }
         }
         if ((uint64_t)warps != (k[p] + seg - 1) / seg) return fail(26);
+        if (wave) {
+            if (sv.pad[0] + sv.nstrip > P.bnd_words) return fail(32);
+            prog_ranges.push_back({sv.pad[0], sv.pad[0] + sv.nstrip});
+        }
         if (sv.extra_base < n || sv.extra_base + sv.nstrip - 1 > n + P.n_extra) return fail(27);
         extra_ranges.push_back({sv.extra_base, sv.extra_base + sv.nstrip - 1});
         seen[p]++;
@@ -1754,6 +1816,7 @@ int phmm_plan_check(const uint32_t* l, const uint32_t* k, const uint32_t* pair_r
         return true;
     };
     if (!disjoint(bnd_ranges)) return fail(28);
+    if (!disjoint(prog_ranges)) return fail(32);
     if (!disjoint(extra_ranges)) return fail(29);
     for (uint32_t p = 0; p < n; ++p)
         if (seen[p] != 1) return fail(30);

@@ -123,12 +123,13 @@ def test_columns_per_lane(phmm, variant, N):
     _check(out, flags, oracle.batch(b))
 
 
-LONG_KINDS = ["lean", "pipe32", "pipe24", "serial", "pipe4", "cluster"]
+LONG_KINDS = ["lean", "pipe32", "pipe24", "serial", "pipe4", "cluster", "wave"]
 
 
 def _long_flag(phmm, kind):
     return {"lean": phmm.F_LONG_LEAN, "pipe32": phmm.F_LONG_PIPE32, "pipe24": phmm.F_LONG_PIPE24,
-            "serial": phmm.F_LONG_SERIAL, "pipe4": phmm.F_LONG_PIPE4, "cluster": phmm.F_LONG_CLUSTER}[kind]
+            "serial": phmm.F_LONG_SERIAL, "pipe4": phmm.F_LONG_PIPE4, "cluster": phmm.F_LONG_CLUSTER,
+            "wave": phmm.F_LONG_WAVE}[kind]
 
 
 @pytest.mark.parametrize("variant,N", VARIANTS)
@@ -305,6 +306,22 @@ def test_cluster_kind_single_very_wide_pair(phmm):
     with phmm.Context(precision="fp32", flags=phmm.F_LONG_CLUSTER) as ctx:
         out, flags, rc, st = ctx.run(b)
     assert st["long_kernel"] == 5 and st["n_long"] == 2
+    _check(out, flags, oracle.batch(b))
+
+
+def test_wave_kind_very_wide_pairs(phmm):
+    """The wave kind: 128 strips of one 131072-column pair run at the same time, each
+    waiting for its left neighbour's progress once per 32 rows (a 700-row read: 22
+    blocks), next to a pair of 20 strips; both against the oracle."""
+    rng = np.random.default_rng(45)
+    k = 131072
+    hap = "".join(rng.choice(list("ACGT"), size=k))
+    read = hap[90000:90400] + hap[90410:90710]
+    b = W.from_strings([(read, hap, 30, 45, 45, 10), (read[:333], hap[:20000], 25, 45, 45, 10)])
+    with phmm.Context(precision="fp32", flags=phmm.F_LONG_WAVE) as ctx:
+        out, flags, rc, st = ctx.run(b)
+    assert st["long_kernel"] == 6 and st["n_long"] == 2
+    assert not np.any(flags & phmm.PAIR_ERROR)
     _check(out, flags, oracle.batch(b))
 
 
