@@ -87,7 +87,8 @@ typedef enum {
 #define PHMM_F_LONG_CLUSTER 0x400u
 /* ... or every 1024-column strip of a pair on its own warp at the same time, strips
  * linked through global memory in blocks of 32 rows (a strip waits for its left
- * neighbour once per block: for a few very wide pairs). */
+ * neighbour once per block: for a few very wide pairs); the tuner picks its grid (the
+ * resident maximum or two CTAs per SM). */
 #define PHMM_F_LONG_WAVE 0x800u
 /* No measured tuning: the built-in cost model and defaults choose the kernels.  For
  * serving, where nearly every batch (epoch) has a new shape and tuning would re-run it. */
@@ -193,9 +194,9 @@ typedef struct {
      * <16,6>, k_short_pipe<32,3>, <24,4>, <16,4>, k_short_pipe2<32,3>, <24,4>, and the
      * lean k_short_pipe2<32,4>);
      * packed_kernel = packed-team variant 0..1 (k_short_packed<12,4>, <16,3>);
-     * long_kernel = multi-warp kind 0..6 (lean k_forward<32>, k_forward_pipe<32,12>,
+     * long_kernel = multi-warp kind 0..7 (lean k_forward<32>, k_forward_pipe<32,12>,
      * k_forward_pipe<24,16>, k_forward_serial<32,3>, k_forward_pipe<32,4>,
-     * k_forward_cluster<32,4,8>, k_forward_wave<32,3>). */
+     * k_forward_cluster<32,4,8>, k_forward_wave<32,3>, the same on two CTAs per SM). */
     int32_t short_kernel;
     int32_t packed_kernel;
     int32_t long_kernel;

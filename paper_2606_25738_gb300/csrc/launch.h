@@ -23,12 +23,13 @@ void launch_forward32_long(const BatchHeader* H, const void* pow, int grid, cuda
 // through distributed shared memory (k_forward_cluster), 6 = every 1024-column strip of a
 // pair on its own warp at the same time, the strips linked through global memory in blocks
 // of 32 rows (a strip waits for its left neighbour's progress counter once per block,
-// k_forward_wave).
-constexpr int kNumLong = 7;
-constexpr int kLongN[kNumLong] = {32, 32, 24, 32, 32, 32, 32};
-constexpr int kLongCW[kNumLong] = {16, 12, 16, 1, 4, kClusterWarps, 1};
-constexpr bool kLongSerial[kNumLong] = {false, false, false, true, false, false, false};
-constexpr bool kLongWave[kNumLong] = {false, false, false, false, false, false, true};
+// k_forward_wave), 7 = kind 6 on a grid of two CTAs per SM (fewer warps share each
+// scheduler, so a long strip chain's row step is shorter).
+constexpr int kNumLong = 8;
+constexpr int kLongN[kNumLong] = {32, 32, 24, 32, 32, 32, 32, 32};
+constexpr int kLongCW[kNumLong] = {16, 12, 16, 1, 4, kClusterWarps, 1, 1};
+constexpr bool kLongSerial[kNumLong] = {false, false, false, true, false, false, false, false};
+constexpr bool kLongWave[kNumLong] = {false, false, false, false, false, false, true, true};
 constexpr int kSerialThreads = 128;
 void launch_forward32_long_pipe(int kind, const BatchHeader* H, const void* pow, int grid, cudaStream_t s);
 // Short-pair kernels by variant id (see kShortScalar / kShortPacked).

@@ -534,7 +534,7 @@ struct phmm_ctx {
     int occ64v[kNumF64] = {1, 1, 1, 1};     // resident CTAs per SM of the FP64 forward variants
     int occ64s[kNumF64] = {1, 1, 1, 1};     // ... and of the pipelined FP64 short-team kernels
     // resident CTAs per SM of each kernel (long kind 5: resident clusters of the GPU)
-    int occ_packed[kNumPacked] = {}, occ_scalar[kNumScalar] = {}, occ_longk[kNumLong] = {1, 1, 1, 1, 1, 1, 1}, occ64 = 1;
+    int occ_packed[kNumPacked] = {}, occ_scalar[kNumScalar] = {}, occ_longk[kNumLong] = {1, 1, 1, 1, 1, 1, 1, 1}, occ64 = 1;
     std::map<uint64_t, std::array<int, 3>> tuned;  // batch signature -> (scalar id, packed id, long kind)
     uint64_t inflight_foot = 0;             // sum of pending slots' footprints
     bool dead = false;
@@ -826,9 +826,9 @@ std::vector<int> long_kinds_of(const phmm_config& cfg) {
     if (cfg.flags & PHMM_F_LONG_SERIAL) return {3};
     if (cfg.flags & PHMM_F_LONG_PIPE4) return {4};
     if (cfg.flags & PHMM_F_LONG_CLUSTER) return {5};
-    if (cfg.flags & PHMM_F_LONG_WAVE) return {6};
+    if (cfg.flags & PHMM_F_LONG_WAVE) return {6, 7};  // the wave kernel on either grid
     if (cfg.kernel_variant == 3) return {0};
-    return {0, 1, 3, 4, 5, 6};  // kind 2 only when forced: measured slower than kind 1 everywhere
+    return {0, 1, 3, 4, 5, 6, 7};  // kind 2 only when forced: measured slower than kind 1 everywhere
 }
 // Without measurement: the serial kind when multi-warp pairs outnumber the resident
 // warps of k_forward_serial four times over (each warp then has several pairs to run),
@@ -837,7 +837,8 @@ int default_long_kind(const phmm_config& cfg, uint64_t n_long = 0, uint64_t seri
     const std::vector<int> k = long_kinds_of(cfg);
     if (k.size() == 1) return k[0];
     const bool serial_ok = std::find(k.begin(), k.end(), 3) != k.end();
-    return serial_ok && serial_warps > 0 && n_long >= 4 * serial_warps ? 3 : 1;
+    if (serial_ok && serial_warps > 0 && n_long >= 4 * serial_warps) return 3;
+    return std::find(k.begin(), k.end(), 1) != k.end() ? 1 : k[0];
 }
 
 // Coarse shape of a batch for the tuner cache: pair count, mean read and haplotype
@@ -952,6 +953,7 @@ int phmm_create(const phmm_config* cfg, phmm_ctx** out) {
     ctx->occ_longk[4] = occupancy_forward32_long_pipe(4);
     ctx->occ_longk[5] = occupancy_forward32_long_pipe(5);
     ctx->occ_longk[6] = occupancy_forward32_long_pipe(6);
+    ctx->occ_longk[7] = occupancy_forward32_long_pipe(7);
     if (getenv("PHMM_DEBUG")) {
         fprintf(stderr, "phmm: sms %d occupancy packed %d %d long %d %d %d %d %d fp64 %d scalar", ctx->sms,
                 ctx->occ_packed[0], ctx->occ_packed[1], ctx->occ_longk[0], ctx->occ_longk[1],
@@ -1359,7 +1361,7 @@ int phmm_submit_batch(phmm_ctx* ctx, const phmm_batch* b, uint64_t* ticket) {
             // more SMs); with many wide pairs it is not worth a trial run either
             for (int lk : long_kinds_of(ctx->cfg)) {
                 if (kLongSerial[lk] && 2 * (uint64_t)P.n_long < swarps) continue;
-                if ((lk == 4 || lk == 5 || lk == 6) && (uint64_t)P.n_long >= swarps) continue;
+                if ((lk == 4 || lk == 5 || kLongWave[lk]) && (uint64_t)P.n_long >= swarps) continue;
                 runs.push_back({-1, -1, lk});
             }
         }

@@ -70,7 +70,7 @@ SHORT_KERNELS = ["k_short_scalar<32, 4>", "k_short_scalar<24, 4>", "k_short_scal
 PACKED_KERNELS = ["k_short_packed<12, 4>", "k_short_packed<16, 3>"]
 LONG_KERNELS = ["k_forward<float, 32, 0>", "k_forward_pipe<32, 12>", "k_forward_pipe<24, 16>",
                 "k_forward_serial<32, 3, 0>", "k_forward_pipe<32, 4>", "k_forward_cluster<32, 4, 8>",
-                "k_forward_wave<32, 3>"]
+                "k_forward_wave<32, 3>", "k_forward_wave<32, 3> (2 CTAs/SM)"]
 # FP64 forward variant behind phmm_stats.short_kernel when the precision is FP64.
 FP64_KERNELS = ["k_forward<double, 8, 1, 16>", "k_forward<double, 16, 1, 8>",
                 "k_short_pipe64<16, 2, 0> + k_forward<double, 16, 0, 8>",

@@ -320,7 +320,7 @@ def test_wave_kind_very_wide_pairs(phmm):
     b = W.from_strings([(read, hap, 30, 45, 45, 10), (read[:333], hap[:20000], 25, 45, 45, 10)])
     with phmm.Context(precision="fp32", flags=phmm.F_LONG_WAVE) as ctx:
         out, flags, rc, st = ctx.run(b)
-    assert st["long_kernel"] == 6 and st["n_long"] == 2
+    assert st["long_kernel"] in (6, 7) and st["n_long"] == 2
     assert not np.any(flags & phmm.PAIR_ERROR)
     _check(out, flags, oracle.batch(b))
 
