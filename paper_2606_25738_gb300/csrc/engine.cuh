@@ -1236,7 +1236,9 @@ __device__ SegOut team_run_pipe2(const Rec32J* __restrict__ rec, int l, int lmax
                     gcp = gq;
                 }
             }
-        } else if (gq != gcp) {
+        } else if (LINK ? __any_sync(kFull, gq != gcp) : gq != gcp) {
+            // (link mode: every lane holds the same row, so the vote is exact and the
+            // branch is warp-uniform)
 #pragma unroll
             for (int s = 0; s < 5; ++s) {
                 sp1[s] = lt >= (1 << s) ? __ldg(&pr->sp1[s]) : 0.f;
@@ -1297,17 +1299,25 @@ __device__ SegOut team_run_pipe2(const Rec32J* __restrict__ rec, int l, int lmax
         } else {
             // Row i's partials U = a M' + J' and insertions J = M' + h J' (primes: row
             // i - 1, from the column before for U, the same column for J) are formed
-            // column by column as phase B reaches them, from the old M (ml2) and J.
+            // column by column as phase B reaches them, from the old M and J.  Row i - 1's
+            // D-hat chain runs one column ahead (dA: the D-hat of the column before q; dB:
+            // that of column q, formed from column q - 1's old M), so column q's old M and
+            // J have their last uses (dB, column q + 1's partial, column q's J) before
+            // column q's new M is formed, and the new values take the old ones' registers.
             const float2 rb2 = make_float2(cur.b, cur.b), gp2 = make_float2(gprev, gprev);
             const float2 na2 = make_float2(cur.a, cur.a), nh2 = make_float2(cur.h, cur.h);
-            const float2 jp0 = make_float2(nj, J2[H - 1].x);
+            float2 uq = ffma2_sel<PACKED>(na2, ml2, make_float2(nj, J2[H - 1].x));
+            float2 dA = dt2, dB = ffma2_sel<PACKED>(gp2, dt2, ml2);
 #pragma unroll
             for (int q = 0; q < H; ++q) {
-                const float2 uq = ffma2_sel<PACKED>(na2, ml2, q == 0 ? jp0 : J2[q - 1]);
-                if (q > 0) J2[q - 1] = ffma2_sel<PACKED>(nh2, J2[q - 1], ml2);
-                const float2 u2 = ffma2_sel<PACKED>(rb2, dt2, uq);
-                dt2 = ffma2_sel<PACKED>(gp2, dt2, ml2);
-                ml2 = M2[q];
+                const float2 u2 = ffma2_sel<PACKED>(rb2, dA, uq);
+                const float2 mo = M2[q];
+                if (q + 1 < H) {
+                    dA = dB;
+                    dB = ffma2_sel<PACKED>(gp2, dB, mo);
+                    uq = ffma2_sel<PACKED>(na2, mo, J2[q]);
+                }
+                J2[q] = ffma2_sel<PACKED>(nh2, J2[q], mo);
                 const float2 p2 = make_float2(((mask >> (2 * q)) & 1u) ? pim : pix,
                                               ((mask >> (2 * q + 1)) & 1u) ? pim : pix);
                 const float2 mn = fmul2_sel<PACKED>(p2, u2);
@@ -1315,7 +1325,6 @@ __device__ SegOut team_run_pipe2(const Rec32J* __restrict__ rec, int l, int lmax
                 if (q == H - 1) yp2 = y2;
                 y2 = ffma2_sel<PACKED>(rg2, y2, mn);
             }
-            J2[H - 1] = ffma2_sel<PACKED>(nh2, J2[H - 1], ml2);
         }
         // Eq. 4 when a pair of this warp finishes (I = T_MI J on the last row); a strip
         // of the serial kind is one pair on the whole warp
@@ -1376,15 +1385,11 @@ __device__ SegOut team_run_pipe2(const Rec32J* __restrict__ rec, int l, int lmax
         float zz = __shfl_up_sync(kFull, Z, 2);
         if (lt < 2) zz = 0.f;
         if constexpr (LINK) {
-            float lM = 0.f, lJ = 0.f, lD = 0.f;
-            int Eleft = INT_MIN;
-            if (has_left) {
-                const float4 v = stg[(i - 1) & 63];  // one broadcast read
-                lM = v.x;
-                lJ = v.y;
-                lD = v.z;
-                Eleft = __float_as_int(v.w);
-            }
+            // one broadcast read, taken with or without a left strip (without one the slot is
+            // stale and only selected away: no branch in the row)
+            const float4 v = stg[(i - 1) & 63];
+            float lM = has_left ? v.x : 0.f, lJ = has_left ? v.y : 0.f, lD = has_left ? v.z : 0.f;
+            const int Eleft = has_left ? __float_as_int(v.w) : INT_MIN;
             // checkpoint (same rows in every strip of the pair): E >= E_left, so that left
             // values only ever scale down
             int Enew = E;
