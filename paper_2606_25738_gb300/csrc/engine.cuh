@@ -1244,7 +1244,7 @@ __device__ SegOut team_run_pipe2(const Rec32J* __restrict__ rec, int l, int lmax
                 sp1[s] = lt >= (1 << s) ? __ldg(&pr->sp1[s]) : 0.f;
                 sp2[s] = __ldg(&pr->sp2[s]);
             }
-            last1 = __ldg(&pr->last1);
+            last1 = (!LINK || lt >= 2) ? __ldg(&pr->last1) : 0.f;  // link: zz of lanes 0, 1 drops out
             last2 = __ldg(&pr->last2);
             hh1 = __ldg(&pr->hh1);
             hh2 = __ldg(&pr->hh2);
@@ -1360,7 +1360,7 @@ __device__ SegOut team_run_pipe2(const Rec32J* __restrict__ rec, int l, int lmax
         float nm = __shfl_up_sync(kFull, M2[H - 1].y, 1);
         nj = __shfl_up_sync(kFull, J2[H - 1].y, 1);
         float yp = __shfl_up_sync(kFull, ypl, 1);
-        if (lt == 0) {
+        if (!LINK && lt == 0) {  // link mode replaces lane 0's three after the checkpoint
             nm = 0.f;
             nj = 0.f;
             yp = 0.f;
@@ -1383,7 +1383,7 @@ __device__ SegOut team_run_pipe2(const Rec32J* __restrict__ rec, int l, int lmax
             J2[0] = ffma2_sel<PACKED>(nh2, J2[0], M2[0]);
         }
         float zz = __shfl_up_sync(kFull, Z, 2);
-        if (lt < 2) zz = 0.f;
+        if ((!LINK || L1P) && lt < 2) zz = 0.f;
         if constexpr (LINK) {
             // one broadcast read, taken with or without a left strip (without one the slot is
             // stale and only selected away: no branch in the row)
