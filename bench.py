@@ -305,7 +305,8 @@ def run_reference(args):
 def _flag_bits(args, phmm):
     return {"auto": 0, "lean": phmm.F_LONG_LEAN, "pipe32": phmm.F_LONG_PIPE32, "pipe24": phmm.F_LONG_PIPE24,
             "serial": phmm.F_LONG_SERIAL, "pipe4": phmm.F_LONG_PIPE4,
-            "cluster": phmm.F_LONG_CLUSTER, "wave": phmm.F_LONG_WAVE}[args.long_kind]
+            "cluster": phmm.F_LONG_CLUSTER, "wave": phmm.F_LONG_WAVE,
+            "wave16": phmm.F_LONG_WAVE16}[args.long_kind]
 
 
 def kernel_names(st: dict, phmm) -> list:
@@ -728,7 +729,7 @@ def main():
                     help="short-pair kernel family (default: the built-in tuner decides)")
     ap.add_argument("--cols", type=int, default=0, help="columns per lane (0: tuner)")
     ap.add_argument("--long-kind", default="auto",
-                    choices=["auto", "lean", "pipe32", "pipe24", "serial", "pipe4", "cluster", "wave"],
+                    choices=["auto", "lean", "pipe32", "pipe24", "serial", "pipe4", "cluster", "wave", "wave16"],
                     help="force one multi-warp kernel (default: the tuner decides)")
     ap.add_argument("--extras", default="all", choices=["all", "core", "none"],
                     help="all: cpu_baseline, parity, comparators, extra legs, serving; core: without the "

@@ -85,11 +85,13 @@ typedef enum {
 /* ... or the same 4-warp strips run by thread-block clusters of eight CTAs, neighbouring
  * strips exchanging their boundary rows through distributed shared memory. */
 #define PHMM_F_LONG_CLUSTER 0x400u
-/* ... or every 1024-column strip of a pair on its own warp at the same time, strips
- * linked through global memory in blocks of 32 rows (a strip waits for its left
- * neighbour once per block: for a few very wide pairs); the tuner picks its grid (the
- * resident maximum or two CTAs per SM). */
+/* ... or every strip of a pair on its own warp at the same time, strips linked through
+ * global memory in blocks of 32 rows (a strip waits for its left neighbour once per
+ * block: for a few very wide pairs); the tuner picks the strip width and grid (1024
+ * columns on the resident maximum or on two CTAs per SM, or 512 columns). */
 #define PHMM_F_LONG_WAVE 0x800u
+/* ... or only the 512-column wave strips (multi-warp kind 8). */
+#define PHMM_F_LONG_WAVE16 0x1000u
 /* No measured tuning: the built-in cost model and defaults choose the kernels.  For
  * serving, where nearly every batch (epoch) has a new shape and tuning would re-run it. */
 #define PHMM_F_NO_TUNE 0x80u
@@ -194,9 +196,10 @@ typedef struct {
      * <16,6>, k_short_pipe<32,3>, <24,4>, <16,4>, k_short_pipe2<32,3>, <24,4>, and the
      * lean k_short_pipe2<32,4>);
      * packed_kernel = packed-team variant 0..1 (k_short_packed<12,4>, <16,3>);
-     * long_kernel = multi-warp kind 0..7 (lean k_forward<32>, k_forward_pipe<32,12>,
+     * long_kernel = multi-warp kind 0..8 (lean k_forward<32>, k_forward_pipe<32,12>,
      * k_forward_pipe<24,16>, k_forward_serial<32,3>, k_forward_pipe<32,4>,
-     * k_forward_cluster<32,4,8>, k_forward_wave<32,3>, the same on two CTAs per SM). */
+     * k_forward_cluster<32,4,8>, k_forward_wave<32,3>, the same on two CTAs per SM,
+     * k_forward_wave<16,3>). */
     int32_t short_kernel;
     int32_t packed_kernel;
     int32_t long_kernel;
@@ -277,7 +280,7 @@ int phmm_wait_test(phmm_ctx *ctx);
  * Test entry (host only, no device needed): builds the work plan the runtime would use
  * for a batch with read lengths l[p], haplotype lengths k[p] and read index pair_read[p]
  * (n pairs), for precision (PHMM_PREC_*) and, in FP32, the short-pair kernel ids (scalar
- * 0..8, packed -1..1) and the multi-warp kernel kind (0..4, as phmm_stats.long_kernel),
+ * 0..9, packed -1..1) and the multi-warp kernel kind (0..8, as phmm_stats.long_kernel),
  * and checks it: every pair scheduled exactly once; teams inside their warp, disjoint and
  * wide enough, packed pairs sharing a read; CTA warp ranges inside the CTA and disjoint; a
  * wide pair's strips tiling its columns in order, never placed in an earlier work item

@@ -174,6 +174,7 @@ template __global__ void k_forward_pipe<32, kCtaWarpsPipe>(const BatchHeader*, c
 template __global__ void k_forward_pipe<24, kCtaWarps>(const BatchHeader*, const PowRow<float>*);
 template __global__ void k_forward_serial<32, 3>(const BatchHeader*, const PowRow<float>*);
 template __global__ void k_forward_wave<32, 3>(const BatchHeader*, const PowRow<float>*);
+template __global__ void k_forward_wave<16, 3>(const BatchHeader*, const PowRow<float>*);
 template __global__ void k_forward_pipe<32, 4>(const BatchHeader*, const PowRow<float>*);
 template __global__ void k_forward_cluster<32, kClusterWarps, kClusterCtas>(const BatchHeader*, const PowRow<float>*);
 template __global__ void k_short_scalar<32, 4>(const BatchHeader*, const PowRow<float>*);
@@ -250,6 +251,7 @@ void launch_forward32_long_pipe(int kind, const BatchHeader* H, const void* pow,
     if (kind == 5) k_forward_cluster<32, kClusterWarps, kClusterCtas><<<grid, kClusterWarps * 32, 0, s>>>(H, p);
     else if (kind == 3) k_forward_serial<32, 3><<<grid, kSerialThreads, 0, s>>>(H, p);
     else if (kind == 6 || kind == 7) k_forward_wave<32, 3><<<grid, kSerialThreads, 0, s>>>(H, p);
+    else if (kind == 8) k_forward_wave<16, 3><<<grid, kSerialThreads, 0, s>>>(H, p);
     else if (kind == 4) k_forward_pipe<32, 4><<<grid, 4 * 32, 0, s>>>(H, p);
     else if (kind == 2) k_forward_pipe<24, kCtaWarps><<<grid, kCtaWarps * 32, 0, s>>>(H, p);
     else k_forward_pipe<32, kCtaWarpsPipe><<<grid, kCtaWarpsPipe * 32, 0, s>>>(H, p);
@@ -340,6 +342,8 @@ int occupancy_forward32_long_pipe(int kind) {
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_forward_wave<32, 3>, kSerialThreads, 0);
         if (kind == 7) b = b < 2 ? b : 2;  // the two-CTA grid
     }
+    else if (kind == 8)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_forward_wave<16, 3>, kSerialThreads, 0);
     else if (kind == 4)
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_forward_pipe<32, 4>, 4 * 32, 0);
     else if (kind == 2)

@@ -24,12 +24,13 @@ void launch_forward32_long(const BatchHeader* H, const void* pow, int grid, cuda
 // pair on its own warp at the same time, the strips linked through global memory in blocks
 // of 32 rows (a strip waits for its left neighbour's progress counter once per block,
 // k_forward_wave), 7 = kind 6 on a grid of two CTAs per SM (fewer warps share each
-// scheduler, so a long strip chain's row step is shorter).
-constexpr int kNumLong = 8;
-constexpr int kLongN[kNumLong] = {32, 32, 24, 32, 32, 32, 32, 32};
-constexpr int kLongCW[kNumLong] = {16, 12, 16, 1, 4, kClusterWarps, 1, 1};
-constexpr bool kLongSerial[kNumLong] = {false, false, false, true, false, false, false, false};
-constexpr bool kLongWave[kNumLong] = {false, false, false, false, false, false, true, true};
+// scheduler, so a long strip chain's row step is shorter), 8 = kind 6 with 16 columns per
+// lane (512-column strips: twice the strips, each row step with half the in-lane chain).
+constexpr int kNumLong = 9;
+constexpr int kLongN[kNumLong] = {32, 32, 24, 32, 32, 32, 32, 32, 16};
+constexpr int kLongCW[kNumLong] = {16, 12, 16, 1, 4, kClusterWarps, 1, 1, 1};
+constexpr bool kLongSerial[kNumLong] = {false, false, false, true, false, false, false, false, false};
+constexpr bool kLongWave[kNumLong] = {false, false, false, false, false, false, true, true, true};
 constexpr int kSerialThreads = 128;
 void launch_forward32_long_pipe(int kind, const BatchHeader* H, const void* pow, int grid, cudaStream_t s);
 // Short-pair kernels by variant id (see kShortScalar / kShortPacked).

@@ -534,7 +534,7 @@ struct phmm_ctx {
     int occ64v[kNumF64] = {1, 1, 1, 1};     // resident CTAs per SM of the FP64 forward variants
     int occ64s[kNumF64] = {1, 1, 1, 1};     // ... and of the pipelined FP64 short-team kernels
     // resident CTAs per SM of each kernel (long kind 5: resident clusters of the GPU)
-    int occ_packed[kNumPacked] = {}, occ_scalar[kNumScalar] = {}, occ_longk[kNumLong] = {1, 1, 1, 1, 1, 1, 1, 1}, occ64 = 1;
+    int occ_packed[kNumPacked] = {}, occ_scalar[kNumScalar] = {}, occ_longk[kNumLong] = {1, 1, 1, 1, 1, 1, 1, 1, 1}, occ64 = 1;
     std::map<uint64_t, std::array<int, 3>> tuned;  // batch signature -> (scalar id, packed id, long kind)
     uint64_t inflight_foot = 0;             // sum of pending slots' footprints
     bool dead = false;
@@ -826,9 +826,10 @@ std::vector<int> long_kinds_of(const phmm_config& cfg) {
     if (cfg.flags & PHMM_F_LONG_SERIAL) return {3};
     if (cfg.flags & PHMM_F_LONG_PIPE4) return {4};
     if (cfg.flags & PHMM_F_LONG_CLUSTER) return {5};
-    if (cfg.flags & PHMM_F_LONG_WAVE) return {6, 7};  // the wave kernel on either grid
+    if (cfg.flags & PHMM_F_LONG_WAVE) return {6, 7, 8};  // the wave kernels
+    if (cfg.flags & PHMM_F_LONG_WAVE16) return {8};
     if (cfg.kernel_variant == 3) return {0};
-    return {0, 1, 3, 4, 5, 6, 7};  // kind 2 only when forced: measured slower than kind 1 everywhere
+    return {0, 1, 3, 4, 5, 6, 7, 8};  // kind 2 only when forced: measured slower than kind 1 everywhere
 }
 // Without measurement: the serial kind when multi-warp pairs outnumber the resident
 // warps of k_forward_serial four times over (each warp then has several pairs to run),
@@ -891,7 +892,7 @@ int phmm_create(const phmm_config* cfg, phmm_ctx** out) {
     {
         const unsigned lk =
             cfg->flags & (PHMM_F_LONG_LEAN | PHMM_F_LONG_PIPE32 | PHMM_F_LONG_PIPE24 | PHMM_F_LONG_SERIAL |
-                          PHMM_F_LONG_PIPE4 | PHMM_F_LONG_CLUSTER | PHMM_F_LONG_WAVE);
+                          PHMM_F_LONG_PIPE4 | PHMM_F_LONG_CLUSTER | PHMM_F_LONG_WAVE | PHMM_F_LONG_WAVE16);
         if (lk & (lk - 1)) return PHMM_EINVAL;  // more than one forced multi-warp kernel
     }
     {
@@ -954,6 +955,7 @@ int phmm_create(const phmm_config* cfg, phmm_ctx** out) {
     ctx->occ_longk[5] = occupancy_forward32_long_pipe(5);
     ctx->occ_longk[6] = occupancy_forward32_long_pipe(6);
     ctx->occ_longk[7] = occupancy_forward32_long_pipe(7);
+    ctx->occ_longk[8] = occupancy_forward32_long_pipe(8);
     if (getenv("PHMM_DEBUG")) {
         fprintf(stderr, "phmm: sms %d occupancy packed %d %d long %d %d %d %d %d fp64 %d scalar", ctx->sms,
                 ctx->occ_packed[0], ctx->occ_packed[1], ctx->occ_longk[0], ctx->occ_longk[1],

@@ -22,7 +22,7 @@ PREC = {"fp32": 0, "fp64": 1, "fp32_only": 2}
 VARIANTS = {"auto": 0, "packed": 1, "scalar": 2, "lean": 3, "pipe": 4, "pipe2": 5, "pipe2lean": 6}
 F_NO_GRAPH, F_LAUNCH_PER_PAIR, F_FORCE_RESCUE = 0x1, 0x2, 0x4
 F_LONG_LEAN, F_LONG_PIPE32, F_LONG_PIPE24, F_NO_TUNE, F_LONG_SERIAL = 0x10, 0x20, 0x40, 0x80, 0x100
-F_LONG_PIPE4, F_LONG_CLUSTER, F_LONG_WAVE = 0x200, 0x400, 0x800
+F_LONG_PIPE4, F_LONG_CLUSTER, F_LONG_WAVE, F_LONG_WAVE16 = 0x200, 0x400, 0x800, 0x1000
 PAIR_RESCUED, PAIR_RESCALED, PAIR_FP64, PAIR_ERROR = 0x1, 0x2, 0x4, 0x80
 PAIR_DANGER, PAIR_NONFINITE, PAIR_SMALL_SUM, PAIR_DEGENERATE = 0x8, 0x10, 0x20, 0x40
 
@@ -70,7 +70,7 @@ SHORT_KERNELS = ["k_short_scalar<32, 4>", "k_short_scalar<24, 4>", "k_short_scal
 PACKED_KERNELS = ["k_short_packed<12, 4>", "k_short_packed<16, 3>"]
 LONG_KERNELS = ["k_forward<float, 32, 0>", "k_forward_pipe<32, 12>", "k_forward_pipe<24, 16>",
                 "k_forward_serial<32, 3, 0>", "k_forward_pipe<32, 4>", "k_forward_cluster<32, 4, 8>",
-                "k_forward_wave<32, 3>", "k_forward_wave<32, 3> (2 CTAs/SM)"]
+                "k_forward_wave<32, 3>", "k_forward_wave<32, 3> (2 CTAs/SM)", "k_forward_wave<16, 3>"]
 # FP64 forward variant behind phmm_stats.short_kernel when the precision is FP64.
 FP64_KERNELS = ["k_forward<double, 8, 1, 16>", "k_forward<double, 16, 1, 8>",
                 "k_short_pipe64<16, 2, 0> + k_forward<double, 16, 0, 8>",

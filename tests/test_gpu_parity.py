@@ -123,13 +123,13 @@ def test_columns_per_lane(phmm, variant, N):
     _check(out, flags, oracle.batch(b))
 
 
-LONG_KINDS = ["lean", "pipe32", "pipe24", "serial", "pipe4", "cluster", "wave"]
+LONG_KINDS = ["lean", "pipe32", "pipe24", "serial", "pipe4", "cluster", "wave", "wave16"]
 
 
 def _long_flag(phmm, kind):
     return {"lean": phmm.F_LONG_LEAN, "pipe32": phmm.F_LONG_PIPE32, "pipe24": phmm.F_LONG_PIPE24,
             "serial": phmm.F_LONG_SERIAL, "pipe4": phmm.F_LONG_PIPE4, "cluster": phmm.F_LONG_CLUSTER,
-            "wave": phmm.F_LONG_WAVE}[kind]
+            "wave": phmm.F_LONG_WAVE, "wave16": phmm.F_LONG_WAVE16}[kind]
 
 
 @pytest.mark.parametrize("variant,N", VARIANTS)
@@ -309,18 +309,19 @@ def test_cluster_kind_single_very_wide_pair(phmm):
     _check(out, flags, oracle.batch(b))
 
 
-def test_wave_kind_very_wide_pairs(phmm):
-    """The wave kind: 128 strips of one 131072-column pair run at the same time, each
-    waiting for its left neighbour's progress once per 32 rows (a 700-row read: 22
-    blocks), next to a pair of 20 strips; both against the oracle."""
+@pytest.mark.parametrize("kind", ["wave", "wave16"])
+def test_wave_kind_very_wide_pairs(phmm, kind):
+    """The wave kinds: 128 strips (256 at 512 columns) of one 131072-column pair run at
+    the same time, each waiting for its left neighbour's progress once per 32 rows (a
+    700-row read: 22 blocks), next to a pair of 20 (40) strips; both against the oracle."""
     rng = np.random.default_rng(45)
     k = 131072
     hap = "".join(rng.choice(list("ACGT"), size=k))
     read = hap[90000:90400] + hap[90410:90710]
     b = W.from_strings([(read, hap, 30, 45, 45, 10), (read[:333], hap[:20000], 25, 45, 45, 10)])
-    with phmm.Context(precision="fp32", flags=phmm.F_LONG_WAVE) as ctx:
+    with phmm.Context(precision="fp32", flags=_long_flag(phmm, kind)) as ctx:
         out, flags, rc, st = ctx.run(b)
-    assert st["long_kernel"] in (6, 7) and st["n_long"] == 2
+    assert st["long_kernel"] in ((6, 7, 8) if kind == "wave" else (8,)) and st["n_long"] == 2
     assert not np.any(flags & phmm.PAIR_ERROR)
     _check(out, flags, oracle.batch(b))
 

@@ -42,7 +42,8 @@ SHAPES = _shapes()
 @pytest.mark.parametrize("shape", sorted(SHAPES))
 @pytest.mark.parametrize("scal,pack,kind", [(0, -1, 0), (4, -1, 1), (5, 1, 1), (7, 0, 0), (3, -1, 2), (8, 1, 2),
                                             (7, -1, 3), (5, 1, 3), (7, -1, 4), (4, 0, 4), (7, -1, 5),
-                                            (5, 1, 5), (9, -1, 3), (9, 0, 1), (7, -1, 6), (5, 1, 6), (7, -1, 7)])
+                                            (5, 1, 5), (9, -1, 3), (9, 0, 1), (7, -1, 6), (5, 1, 6), (7, -1, 7),
+                                            (7, -1, 8), (5, 1, 8)])
 def test_fp32_plans_valid(P, shape, scal, pack, kind):
     l, k, pr = SHAPES[shape]
     rc, st = P.plan_check(l, k, pr, "fp32", scal, pack, kind)
@@ -75,7 +76,7 @@ def test_plan_check_rejects_bad_ids(P):
     l, k, pr = SHAPES["edges"]
     assert P.plan_check(l, k, pr, "fp32", 99, -1, 1)[0] == P.PHMM_EINVAL
     assert P.plan_check(l, k, pr, "fp32", 4, 7, 1)[0] == P.PHMM_EINVAL
-    assert P.plan_check(l, k, pr, "fp32", 4, -1, 8)[0] == P.PHMM_EINVAL
+    assert P.plan_check(l, k, pr, "fp32", 4, -1, 9)[0] == P.PHMM_EINVAL
 
 
 def test_serial_plan_one_item_per_long_pair(P):
