@@ -73,6 +73,8 @@ def test_create_rejects_bad_config(lib):
     assert so.phmm_create(ctypes.byref(cfg), ctypes.byref(h)) == lib.PHMM_EINVAL
     cfg = lib.Config(0, 0, 0, 0, lib.F_LONG_SERIAL | lib.F_LONG_PIPE32, None, 0, 0)
     assert so.phmm_create(ctypes.byref(cfg), ctypes.byref(h)) == lib.PHMM_EINVAL
+    cfg = lib.Config(0, 0, 0, 0, lib.F_LONG_WAVE | lib.F_LONG_WAVE16, None, 0, 0)
+    assert so.phmm_create(ctypes.byref(cfg), ctypes.byref(h)) == lib.PHMM_EINVAL
     assert so.phmm_create(None, ctypes.byref(h)) == lib.PHMM_EINVAL
 
 
