@@ -720,6 +720,12 @@ cudaError_t upload_plan(Slot& S, const Plan& P, cudaStream_t cs) {
 }
 
 // Plan fields of the batch header.
+// The Rec32 layout is read by the lean and packed short kernels and the lean multi-warp
+// kernel only; without them prep skips it and the batch needs no arena for it.
+bool plan_needs_rec32(const Plan& P) {
+    return P.pack_id >= 0 || !kShortScalarPipe[P.scal_id] || (P.long_kind == 0 && !P.citems.empty());
+}
+
 void plan_header(const Slot& S, const Plan& P, BatchHeader& hh) {
     hh.witems = (const WarpItem*)S.witems.p;
     hh.witems2 = (const WarpItem*)S.witems2.p;
@@ -736,10 +742,7 @@ void plan_header(const Slot& S, const Plan& P, BatchHeader& hh) {
     hh.sbnd_rows = S.sbnd_rows;
     hh.sbnd_warps = S.sbnd_warps;
     hh.wbnd = (float4*)S.wbnd.p;
-    // the Rec32 layout is read by the lean and packed short kernels and the lean
-    // multi-warp kernel only; without them prep skips it
-    const bool need32 = P.pack_id >= 0 || !kShortScalarPipe[P.scal_id] || (P.long_kind == 0 && !P.citems.empty());
-    if (hh.rec32 || hh.rec32j) hh.rec32 = need32 ? (Rec32*)S.rec32.p : nullptr;
+    if (hh.rec32 || hh.rec32j) hh.rec32 = plan_needs_rec32(P) ? (Rec32*)S.rec32.p : nullptr;
     // FP64 J-form records: only the pipelined FP64 variant reads them
     hh.rec64j = P.fp64 && f64_pipelined(P.scal_id) ? (Rec64J*)S.rec64j.p : nullptr;
 }
@@ -1188,8 +1191,12 @@ int phmm_submit_batch(phmm_ctx* ctx, const phmm_batch* b, uint64_t* ticket) {
         }
     }
     N = P.N;
-    // footprint and admission
+    const auto th_plan = std::chrono::steady_clock::now();
+    // footprint and admission (lean records only for a plan that reads them, or for the
+    // tuner's trials, which may)
     const bool need64 = ctx->cfg.precision != PHMM_PREC_FP32_ONLY;
+    const bool need32 = ctx->cfg.precision != PHMM_PREC_FP64 &&
+                        (tune_short || tune_long || plan_needs_rec32(P));
     uint32_t lmax_b = 0;
     for (uint32_t p = 0; p < np; ++p) lmax_b = std::max(lmax_b, L[p]);
     const uint64_t rb_words = (uint64_t)lmax_b * 8;  // FP64 boundary: 8 words per row
@@ -1198,7 +1205,8 @@ int phmm_submit_batch(phmm_ctx* ctx, const phmm_batch* b, uint64_t* ticket) {
     const uint64_t foot = (dev_in ? 0 : nbases * 5 + nhb + (nr + 1) * 8ull + (nh + 1) * 8ull + np * 8ull) +
                           (ctx->cfg.precision != PHMM_PREC_FP32_ONLY ? rb_bytes : 0) +
                           np * (sizeof(PairDesc) + sizeof(Partial) + 8 + 1 + 4) +
-                          (ctx->cfg.precision == PHMM_PREC_FP64 ? 0 : nbases * (sizeof(Rec32) + sizeof(Rec32J))) +
+                          (ctx->cfg.precision == PHMM_PREC_FP64 ? 0 : nbases * sizeof(Rec32J)) +
+                          (need32 ? nbases * sizeof(Rec32) : 0) +
                           (need64 ? nbases * sizeof(Rec64) : 0) +
                           (ctx->cfg.precision == PHMM_PREC_FP64 ? nbases * sizeof(Rec64J) : 0) +
                           P.teams.size() * sizeof(Team) + (P.witems.size() + P.witems2.size()) * sizeof(WarpItem) +
@@ -1239,6 +1247,9 @@ int phmm_submit_batch(phmm_ctx* ctx, const phmm_batch* b, uint64_t* ticket) {
         CK(cudaMemcpyAsync(S->in_hoff.p, b->hap_off, (nh + 1) * 8ull, cudaMemcpyHostToDevice, cs));
         CK(cudaMemcpyAsync(S->in_pr.p, b->pair_read, np * 4ull, cudaMemcpyHostToDevice, cs));
         CK(cudaMemcpyAsync(S->in_ph.p, b->pair_hap, np * 4ull, cudaMemcpyHostToDevice, cs));
+        if (getenv("PHMM_DEBUG"))
+            fprintf(stderr, "phmm submit: input copies issued %.1f ms after the plan\n",
+                    std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - th_plan).count());
         hh.read_bases = (const uint8_t*)S->in_bases.p; hh.base_q = (const uint8_t*)S->in_bq.p;
         hh.ins_q = (const uint8_t*)S->in_iq.p; hh.del_q = (const uint8_t*)S->in_dq.p;
         hh.gcp_q = (const uint8_t*)S->in_gq.p; hh.hap_bases = (const uint8_t*)S->in_hap.p;
@@ -1247,7 +1258,8 @@ int phmm_submit_batch(phmm_ctx* ctx, const phmm_batch* b, uint64_t* ticket) {
     }
     CK(ensure(S->desc, np * sizeof(PairDesc)));
     if (ctx->cfg.precision != PHMM_PREC_FP64) {
-        CK(ensure(S->rec32, nbases * sizeof(Rec32)));
+        if (need32) CK(ensure(S->rec32, nbases * sizeof(Rec32)));
+        else release(S->rec32);  // e.g. left from the tuner's trials: give the memory back
         CK(ensure(S->rec32j, nbases * sizeof(Rec32J)));
     }
     if (need64) CK(ensure(S->rec64, nbases * sizeof(Rec64)));
@@ -1517,6 +1529,9 @@ int phmm_submit_batch(phmm_ctx* ctx, const phmm_batch* b, uint64_t* ticket) {
     S->plan_hash = hsh;
     S->plan_np = np;
     S->st.ms_host = (float)std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - th0).count();
+    if (getenv("PHMM_DEBUG"))
+        fprintf(stderr, "phmm submit: plan %s %.1f ms, host total %.1f ms\n", reuse ? "reused" : "built",
+                std::chrono::duration<double, std::milli>(th_plan - th0).count(), S->st.ms_host);
     *ticket = S->ticket;
     return PHMM_OK;
 }
