@@ -619,7 +619,7 @@ def run_ours(args):
     d2h = n * 9
     hout = [(torch.empty(n, dtype=torch.float64).pin_memory().numpy(),
              torch.zeros(n, dtype=torch.uint8).pin_memory().numpy()) for _ in range(2)]
-    n_e2e = max(2, min(args.e2e_steps, args.steps))
+    n_e2e = max(2, min(args.e2e_steps, args.steps) if args.e2e_steps > 0 else args.steps)
 
     overlap = [True]
 
@@ -739,7 +739,8 @@ def main():
                          "profiling captures)")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "fp32_only"],
                     help="precision of the timed run (fp32 = FP32 with FP64 rescue, the benchmark)")
-    ap.add_argument("--e2e-steps", type=int, default=3, help="end-to-end steps (host buffers)")
+    ap.add_argument("--e2e-steps", type=int, default=0,
+                    help="end-to-end steps (host buffers); 0: as many as the timed steps")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="cpu_baseline sample size in seconds")
     ap.add_argument("--lpp-pairs", type=int, default=4000,
                     help="pairs sampled for the FP64 launch-per-pair comparator")
