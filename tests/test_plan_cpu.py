@@ -87,3 +87,16 @@ def test_serial_plan_one_item_per_long_pair(P):
     n_long = int(np.sum(k > 1024))
     assert st["cta_items"] == n_long and st["cta_pairs"] == n_long
     assert st["striped_pairs"] == int(np.sum(k > 1024))  # all of them span two or more strips
+
+
+def test_wave_strip_widths(P):
+    """The wave kinds make one work item per strip: 1024 columns per strip for kinds 6 and
+    7, 512 for kind 8, so a pair of k columns has ceil(k / 1024) or ceil(k / 512) items."""
+    k = np.array([1025, 4096, 20000, 131072])
+    l = np.array([300, 50, 700, 150])
+    pr = np.arange(len(k))
+    for kind, width in ((6, 1024), (7, 1024), (8, 512)):
+        rc, st = P.plan_check(l, k, pr, "fp32", 7, -1, kind)
+        assert rc == P.PHMM_OK, st
+        assert st["cta_items"] == int(np.sum((k + width - 1) // width)), (kind, st)
+        assert st["cta_pairs"] == st["cta_items"]
