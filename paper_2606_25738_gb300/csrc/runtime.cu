@@ -721,7 +721,9 @@ cudaError_t upload_plan(Slot& S, const Plan& P, cudaStream_t cs) {
 
 // Plan fields of the batch header.
 // The Rec32 layout is read by the lean and packed short kernels and the lean multi-warp
-// kernel only; without them prep skips it and the batch needs no arena for it.
+// kernel only; without them prep skips it and the batch needs no arena for it (an idle
+// arena up to kKeepRec32Bytes is kept).
+constexpr uint64_t kKeepRec32Bytes = 1ull << 30;
 bool plan_needs_rec32(const Plan& P) {
     return P.pack_id >= 0 || !kShortScalarPipe[P.scal_id] || (P.long_kind == 0 && !P.citems.empty());
 }
@@ -1258,8 +1260,11 @@ int phmm_submit_batch(phmm_ctx* ctx, const phmm_batch* b, uint64_t* ticket) {
     }
     CK(ensure(S->desc, np * sizeof(PairDesc)));
     if (ctx->cfg.precision != PHMM_PREC_FP64) {
+        // a large arena this plan does not read (e.g. left from the tuner's trials) goes
+        // back; a small one stays, so that batches alternating between plans that read it
+        // and plans that do not pay no cudaFree (a device-wide synchronisation) each time
         if (need32) CK(ensure(S->rec32, nbases * sizeof(Rec32)));
-        else release(S->rec32);  // e.g. left from the tuner's trials: give the memory back
+        else if (S->rec32.cap > kKeepRec32Bytes) release(S->rec32);
         CK(ensure(S->rec32j, nbases * sizeof(Rec32J)));
     }
     if (need64) CK(ensure(S->rec64, nbases * sizeof(Rec64)));
